@@ -1,0 +1,233 @@
+/*
+ * bgl.h -- C ABI of the GB300 (sm_103a) layout library for large graphs.
+ *
+ * The library lays out the bipartite address/transaction graph of "Graph
+ * Visualization for Blockchain Data" (Dietl et al., 2024): it builds the
+ * graph from per-transaction input/output address lists (Section 2), labels
+ * its connected components ignoring edge directions (Section 4), splits them
+ * by node count (Section 4), lays out small components with Kamada-Kawai
+ * (Section 3.1) and large ones with ForceAtlas2 whose all-pairs repulsion is
+ * summed exactly or by a 2-D Fast Multipole Method (Sections 3.2, 3.2.1),
+ * and returns coordinates in each component's own frame.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a bgl_status; nothing is thrown or aborted across the
+ *    ABI.  On failure the call leaves its outputs untouched where it can and
+ *    bgl_last_error() describes the failure.
+ *  - Pointers without a `d_` prefix are HOST memory owned by the caller;
+ *    inputs are copied in, outputs must be preallocated by the caller at the
+ *    sizes given by bgl_graph_sizes() / bgl_components().
+ *  - Pointers with a `d_` prefix are DEVICE memory on the context's device,
+ *    owned by the caller, read or written in stream order on the context's
+ *    stream (bgl_ctx_set_stream).  These calls do not synchronise the
+ *    stream except where stated.
+ *  - Handles are opaque and owned by the library; release them with the
+ *    matching destroy call.  A context is used by one host thread at a time.
+ *  - Node ids: transaction t has id t (0 <= t < n_tx); an address has id
+ *    n_tx + (rank of its first appearance when scanning tx 0 inputs, tx 0
+ *    outputs, tx 1 inputs, tx 1 outputs, ...).
+ *  - Edges (Section 2): address -> tx for every input, tx -> address for
+ *    every output; exact duplicate directed edges are kept once.  The
+ *    undirected graph has one edge per unordered pair {u, v} with u != v; the
+ *    degree of a node is its number of distinct undirected neighbours.
+ *  - Components are indexed c = 0 .. n_comp-1 by node count descending, then
+ *    by label (the smallest node id in the component) ascending; the nodes
+ *    of a component are listed in ascending id.  "Local" arrays of a
+ *    component follow that node order.
+ */
+#ifndef BGL_H
+#define BGL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BGL_OK = 0,
+    BGL_EINVAL = -1,   /* an argument is out of range or inconsistent */
+    BGL_ENOMEM = -2,   /* a device or host allocation failed */
+    BGL_ECUDA = -3,    /* a CUDA runtime call failed */
+    BGL_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    BGL_ENUMERIC = -5, /* a non-finite position or force appeared */
+    BGL_ESTATE = -6    /* the call needs a step that has not been run */
+} bgl_status;
+
+typedef struct bgl_ctx bgl_ctx;
+typedef struct bgl_graph bgl_graph;
+
+enum { BGL_REP_EXACT = 0, BGL_REP_FMM = 1, BGL_REP_AUTO = 2 };
+
+/*
+ * Parameters of the layout (defaults from bgl_params_default()).
+ *  ForceAtlas2 (Section 3.2): per iteration each node feels
+ *    repulsion  kr * m_i * sum_j m_j (p_i - p_j) / |p_i - p_j|^2, m = degree + 1,
+ *    attraction -sum_{j adjacent} (p_i - p_j),
+ *    gravity    -kg * m_i * p_i;
+ *  swing and traction (Section 3.2) set the global speed
+ *    s_G = min(tau * trc / swg, 1.5 * s_G) (s_G = 1 and F_{-1} = 0 at the start),
+ *  and node n moves by s_n F_t(n) with
+ *    s_n = ks * s_G / (1 + s_G * sqrt(|F_t(n) - F_{t-1}(n)|)), capped at ksmax / |F_t(n)|.
+ *  swing_variant 0 uses the unweighted sums printed in Section 3.2;
+ *  1 uses ForceAtlas2's (degree+1)-weighted sums with traction halved.
+ *  Kamada-Kawai (Section 3.1): energy sum_{i<j} d_ij^-2 (|p_i - p_j| - kk_l d_ij)^2,
+ *  kk_sweeps Gauss-Seidel sweeps of per-node 2x2 Newton-Raphson steps in
+ *  ascending local order; kk_tol > 0 stops after a sweep whose largest
+ *  gradient norm is below kk_tol.
+ */
+typedef struct bgl_params {
+    uint64_t seed;          /* initial positions (SplitMix64 per node id)      default 0 */
+    int32_t kk_max_nodes;   /* components with <= this many nodes use KK        default 50 */
+    int32_t fa2_iters;      /* ForceAtlas2 iterations                           default 50 */
+    double kr;              /* repulsion constant                               default 1 */
+    double kg;              /* gravity constant                                 default 1 */
+    double ks;              /* node speed constant                              default 0.1 */
+    double ksmax;           /* largest displacement of a node per iteration     default 10 */
+    double tau;             /* traction/swing tolerance                         default 1 */
+    int32_t repulsion;      /* BGL_REP_EXACT, BGL_REP_FMM or BGL_REP_AUTO        default AUTO */
+    int32_t fmm_p;          /* multipole expansion order, 1..24                 default 8 */
+    int32_t leaf_size;      /* quadtree leaf capacity, 1..256                   default 64 */
+    int32_t fmm_min_nodes;  /* AUTO uses the FMM for components at least this big  default 8192 */
+    int32_t swing_variant;  /* 0 as printed (Section 3.2), 1 ForceAtlas2 weights default 0 */
+    int32_t kk_sweeps;      /* KK sweeps                                         default 200 */
+    double kk_l;            /* KK edge length l                                  default 1 */
+    double kk_tol;          /* KK early-stop gradient norm, 0 = fixed sweeps     default 0 */
+} bgl_params;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, with its own non-blocking
+ * stream and device memory pool.  *out receives the handle. */
+bgl_status bgl_ctx_create(int device, bgl_ctx **out);
+
+/* Destroy a context (after its graphs).  NULL is ignored. */
+void bgl_ctx_destroy(bgl_ctx *ctx);
+
+/* Run all later work on `cuda_stream` (a cudaStream_t of the context's
+ * device); NULL restores the context's own stream. */
+bgl_status bgl_ctx_set_stream(bgl_ctx *ctx, void *cuda_stream);
+
+/* Block until all work queued by the context has finished. */
+bgl_status bgl_ctx_sync(bgl_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until
+ * the next call on the context. */
+const char *bgl_last_error(const bgl_ctx *ctx);
+
+/* Fill *p with the defaults listed above. */
+void bgl_params_default(bgl_params *p);
+
+/* --------------------------------------------------------- graph (Section 2) */
+
+/*
+ * Build the bipartite transaction graph of Section 2 from host arrays:
+ * in_off[n_tx+1] / in_addr[in_off[n_tx]] list the input addresses of each
+ * transaction, out_off / out_addr the outputs (CSR form; addresses are
+ * opaque 64-bit keys).  Offsets must start at 0 and never decrease
+ * (BGL_EINVAL otherwise).  The graph stays on the device; *out receives it.
+ */
+bgl_status bgl_graph_build(bgl_ctx *ctx, int64_t n_tx, const int64_t *in_off, const uint64_t *in_addr,
+                           const int64_t *out_off, const uint64_t *out_addr, bgl_graph **out);
+
+/* As bgl_graph_build, from device arrays; n_in = in_off[n_tx] and
+ * n_out = out_off[n_tx] are passed by the caller.  Offsets are validated on
+ * the device (BGL_EINVAL if inconsistent).  Synchronises the stream once. */
+bgl_status bgl_graph_build_dev(bgl_ctx *ctx, int64_t n_tx, int64_t n_in, int64_t n_out,
+                               const int64_t *d_in_off, const uint64_t *d_in_addr,
+                               const int64_t *d_out_off, const uint64_t *d_out_addr, bgl_graph **out);
+
+/* Graph on nodes 0..n-1 from m directed edges u[k] -> v[k] (host arrays),
+ * for graphs of other domains (Section 5).  Duplicates are kept once;
+ * self-loops are kept as directed edges but add no undirected neighbour.
+ * There are no addresses (n_addr = 0, n_tx = 0). */
+bgl_status bgl_graph_from_edges(bgl_ctx *ctx, int64_t n, int64_t m, const int32_t *u, const int32_t *v,
+                                bgl_graph **out);
+
+/* Sizes of a built graph (any pointer may be NULL). */
+bgl_status bgl_graph_sizes(const bgl_graph *g, int64_t *n_nodes, int64_t *n_addr, int64_t *n_dir_edges,
+                           int64_t *n_undir_edges);
+
+/* Address keys in id order: key_out[k] is the key of node n_tx + k (n_addr entries). */
+bgl_status bgl_graph_addresses(const bgl_graph *g, uint64_t *key_out);
+
+/* Directed edges sorted by (src, dst): n_dir_edges entries each. */
+bgl_status bgl_graph_edges(const bgl_graph *g, int32_t *src, int32_t *dst);
+
+/* Undirected adjacency in CSR form: off[n_nodes+1], adj[2 n_undir_edges],
+ * neighbours of each node in ascending id. */
+bgl_status bgl_graph_csr(const bgl_graph *g, int64_t *off, int32_t *adj);
+
+/* deg_out[n_nodes]: number of distinct undirected neighbours. */
+bgl_status bgl_degrees(const bgl_graph *g, int32_t *deg_out);
+
+/* Release a graph and its device memory.  NULL is ignored. */
+bgl_status bgl_graph_destroy(bgl_graph *g);
+
+/* ------------------------------------------------- components (Section 4) */
+
+/* Label connected components ignoring directions (Section 4).
+ * label_out[n_nodes] (may be NULL) receives the smallest node id of each
+ * node's component; *n_comp the number of components. */
+bgl_status bgl_components(bgl_graph *g, int32_t *label_out, int64_t *n_comp);
+
+/* Component order (needs bgl_components): comp_off[n_comp+1] node offsets,
+ * comp_label[n_comp], nodes[n_nodes] node ids grouped by component.  Any
+ * pointer may be NULL. */
+bgl_status bgl_component_nodes(const bgl_graph *g, int64_t *comp_off, int32_t *comp_label, int32_t *nodes);
+
+/* Size split (Section 4): components with at most kk_max_nodes nodes are
+ * laid out by Kamada-Kawai, the others by ForceAtlas2.  Because components
+ * are ordered by size, the ForceAtlas2 ones are c = 0 .. n_fa2-1. */
+bgl_status bgl_split(bgl_graph *g, int32_t kk_max_nodes, int64_t *n_kk, int64_t *n_fa2);
+
+/* ------------------------------------------------------ layout (Section 4) */
+
+/*
+ * Lay out every component (needs bgl_components; runs the split with
+ * p->kk_max_nodes).  Initial positions: node id v starts at
+ * (x, y) = ((h1 >> 40) 2^-24 * 2 - 1, (h2 >> 40) 2^-24 * 2 - 1), where h1, h2
+ * are the first two outputs of SplitMix64 seeded with
+ * p->seed XOR (v * 0x9E3779B97F4A7C15); Kamada-Kawai components scale these
+ * by kk_l * diameter / 2.  Components with one node sit at the origin.
+ * xy_out[2 n_nodes] (host) receives x, y of node v at [2v], [2v+1], each in
+ * its component's own frame.  Synchronises the stream.
+ */
+bgl_status bgl_layout(bgl_graph *g, const bgl_params *p, float *xy_out);
+
+/* As bgl_layout, writing the device array d_xy_out[2 n_nodes]; does not
+ * synchronise the stream after the last kernel. */
+bgl_status bgl_layout_dev(bgl_graph *g, const bgl_params *p, float *d_xy_out);
+
+/* ---------------------------------------- per-component parity entry points */
+
+/* Hop distances of component c (Section 3.1): d_out[n_c * n_c], row-major in
+ * local order.  Components of up to 255 nodes. */
+bgl_status bgl_kk_distances(bgl_graph *g, int64_t c, int32_t *d_out);
+
+/* Kamada-Kawai on component c (at most 255 nodes) from the caller's local
+ * positions xy_inout[2 n_c] (x, y interleaved), p->kk_sweeps sweeps. */
+bgl_status bgl_kk_run(bgl_graph *g, int64_t c, const bgl_params *p, float *xy_inout);
+
+/* One ForceAtlas2 force evaluation on component c at local positions
+ * xy_in[2 n_c]: f_out[2 n_c] receives the total force (repulsion + attraction
+ * + gravity).  p->repulsion selects the exact sum or the FMM (AUTO follows
+ * p->fmm_min_nodes). */
+bgl_status bgl_fa2_forces(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, float *f_out);
+
+/* As bgl_fa2_forces, repulsion only. */
+bgl_status bgl_fa2_repulsion(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, float *f_out);
+
+/* `iters` ForceAtlas2 iterations on component c from local positions
+ * xy_inout[2 n_c], starting from F_{-1} = 0 and s_G = 1.  stats_out
+ * (3 * iters doubles, may be NULL) receives swing, traction and s_G of every
+ * iteration. */
+bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t iters, float *xy_inout,
+                        double *stats_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BGL_H */

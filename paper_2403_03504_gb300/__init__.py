@@ -1,0 +1,327 @@
+"""Python binding of the GB300 layout library (include/bgl.h).
+
+Argument marshalling only: every step of the layout runs in the CUDA kernels
+of ``libbgl.so``.  The library must have been built (``build()``, or
+``__graft_entry__.build()``); importing this package without it raises.
+
+Host arrays are numpy arrays; device arrays are anything with an integer
+device address (a ``torch.Tensor`` on the context's device, or an int).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["BglError", "Context", "Graph", "Params", "params", "build", "lib_path",
+           "REP_EXACT", "REP_FMM", "REP_AUTO"]
+
+REP_EXACT, REP_FMM, REP_AUTO = 0, 1, 2
+
+_STATUS = {0: "BGL_OK", -1: "BGL_EINVAL", -2: "BGL_ENOMEM", -3: "BGL_ECUDA", -4: "BGL_ETIMEOUT",
+           -5: "BGL_ENUMERIC", -6: "BGL_ESTATE"}
+
+
+class BglError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of bgl_params (field order and types must match the header)."""
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("kk_max_nodes", ctypes.c_int32),
+        ("fa2_iters", ctypes.c_int32),
+        ("kr", ctypes.c_double),
+        ("kg", ctypes.c_double),
+        ("ks", ctypes.c_double),
+        ("ksmax", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("repulsion", ctypes.c_int32),
+        ("fmm_p", ctypes.c_int32),
+        ("leaf_size", ctypes.c_int32),
+        ("fmm_min_nodes", ctypes.c_int32),
+        ("swing_variant", ctypes.c_int32),
+        ("kk_sweeps", ctypes.c_int32),
+        ("kk_l", ctypes.c_double),
+        ("kk_tol", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libbgl.so is not built ({_build.LIB}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    VP, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    sigs = {
+        "bgl_ctx_create": ([ctypes.c_int, PP], I32),
+        "bgl_ctx_destroy": ([VP], None),
+        "bgl_ctx_set_stream": ([VP, VP], I32),
+        "bgl_ctx_sync": ([VP], I32),
+        "bgl_last_error": ([VP], ctypes.c_char_p),
+        "bgl_params_default": ([ctypes.POINTER(Params)], None),
+        "bgl_graph_build": ([VP, I64, VP, VP, VP, VP, PP], I32),
+        "bgl_graph_build_dev": ([VP, I64, I64, I64, VP, VP, VP, VP, PP], I32),
+        "bgl_graph_from_edges": ([VP, I64, I64, VP, VP, PP], I32),
+        "bgl_graph_sizes": ([VP, P64, P64, P64, P64], I32),
+        "bgl_graph_addresses": ([VP, VP], I32),
+        "bgl_graph_edges": ([VP, VP, VP], I32),
+        "bgl_graph_csr": ([VP, VP, VP], I32),
+        "bgl_degrees": ([VP, VP], I32),
+        "bgl_graph_destroy": ([VP], I32),
+        "bgl_components": ([VP, VP, P64], I32),
+        "bgl_component_nodes": ([VP, VP, VP, VP], I32),
+        "bgl_split": ([VP, I32, P64, P64], I32),
+        "bgl_layout": ([VP, ctypes.POINTER(Params), VP], I32),
+        "bgl_layout_dev": ([VP, ctypes.POINTER(Params), VP], I32),
+        "bgl_kk_distances": ([VP, I64, VP], I32),
+        "bgl_kk_run": ([VP, I64, ctypes.POINTER(Params), VP], I32),
+        "bgl_fa2_forces": ([VP, I64, ctypes.POINTER(Params), VP, VP], I32),
+        "bgl_fa2_repulsion": ([VP, I64, ctypes.POINTER(Params), VP, VP], I32),
+        "bgl_fa2_step": ([VP, I64, ctypes.POINTER(Params), I32, VP, VP], I32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def params(**kw) -> Params:
+    """bgl_params with the library defaults, overridden by keyword."""
+    p = Params()
+    _load().bgl_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _hp(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dp(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _arr(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Context:
+    """A bgl_ctx: one CUDA device, a stream and a device memory pool."""
+
+    def __init__(self, device: int = 0):
+        self._lib = _load()
+        h = ctypes.c_void_p()
+        st = self._lib.bgl_ctx_create(device, ctypes.byref(h))
+        if st != 0:
+            raise BglError(st, f"bgl_ctx_create({device}) failed")
+        self.h = h
+        self.device = device
+
+    def check(self, st: int):
+        if st != 0:
+            raise BglError(st, self._lib.bgl_last_error(self.h).decode())
+
+    def set_stream(self, stream=None):
+        """Use a CUDA stream (torch.cuda.Stream, raw handle int, or None for the context's own)."""
+        if stream is None:
+            ptr = None
+        elif isinstance(stream, int):
+            ptr = ctypes.c_void_p(stream)
+        else:
+            ptr = ctypes.c_void_p(stream.cuda_stream)
+        self.check(self._lib.bgl_ctx_set_stream(self.h, ptr))
+
+    def sync(self):
+        self.check(self._lib.bgl_ctx_sync(self.h))
+
+    def close(self):
+        if self.h:
+            self._lib.bgl_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Graph:
+    """A device-resident graph (bgl_graph)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+        self._lib = ctx._lib
+
+    # ---------------------------------------------------------- construction
+    @classmethod
+    def build(cls, ctx: Context, in_off, in_addr, out_off, out_addr) -> "Graph":
+        in_off = _arr(in_off, np.int64)
+        out_off = _arr(out_off, np.int64)
+        in_addr = _arr(in_addr, np.uint64)
+        out_addr = _arr(out_addr, np.uint64)
+        h = ctypes.c_void_p()
+        ctx.check(ctx._lib.bgl_graph_build(ctx.h, len(in_off) - 1, _hp(in_off), _hp(in_addr), _hp(out_off),
+                                           _hp(out_addr), ctypes.byref(h)))
+        return cls(ctx, h)
+
+    @classmethod
+    def build_dev(cls, ctx: Context, n_tx, n_in, n_out, d_in_off, d_in_addr, d_out_off, d_out_addr) -> "Graph":
+        h = ctypes.c_void_p()
+        ctx.check(ctx._lib.bgl_graph_build_dev(ctx.h, n_tx, n_in, n_out, _dp(d_in_off), _dp(d_in_addr),
+                                               _dp(d_out_off), _dp(d_out_addr), ctypes.byref(h)))
+        return cls(ctx, h)
+
+    @classmethod
+    def from_edges(cls, ctx: Context, n, u, v) -> "Graph":
+        u = _arr(u, np.int32)
+        v = _arr(v, np.int32)
+        h = ctypes.c_void_p()
+        ctx.check(ctx._lib.bgl_graph_from_edges(ctx.h, n, len(u), _hp(u), _hp(v), ctypes.byref(h)))
+        return cls(ctx, h)
+
+    def destroy(self):
+        if self.h:
+            st = self._lib.bgl_graph_destroy(self.h)
+            self.h = None
+            self.ctx.check(st)
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                self._lib.bgl_graph_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------- queries
+    def sizes(self):
+        n, a, d, u = (ctypes.c_int64() for _ in range(4))
+        self.ctx.check(self._lib.bgl_graph_sizes(self.h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(d),
+                                                 ctypes.byref(u)))
+        return dict(n_nodes=n.value, n_addr=a.value, n_dir_edges=d.value, n_undir_edges=u.value)
+
+    def addresses(self):
+        s = self.sizes()
+        out = np.zeros(s["n_addr"], np.uint64)
+        self.ctx.check(self._lib.bgl_graph_addresses(self.h, _hp(out)))
+        return out
+
+    def edges(self):
+        s = self.sizes()
+        src = np.zeros(s["n_dir_edges"], np.int32)
+        dst = np.zeros(s["n_dir_edges"], np.int32)
+        self.ctx.check(self._lib.bgl_graph_edges(self.h, _hp(src), _hp(dst)))
+        return src, dst
+
+    def csr(self):
+        s = self.sizes()
+        off = np.zeros(s["n_nodes"] + 1, np.int64)
+        adj = np.zeros(2 * s["n_undir_edges"], np.int32)
+        self.ctx.check(self._lib.bgl_graph_csr(self.h, _hp(off), _hp(adj)))
+        return off, adj
+
+    def degrees(self):
+        out = np.zeros(self.sizes()["n_nodes"], np.int32)
+        self.ctx.check(self._lib.bgl_degrees(self.h, _hp(out)))
+        return out
+
+    # ---------------------------------------------------------- Section 4
+    def components(self, labels: bool = True):
+        nc = ctypes.c_int64()
+        lab = np.zeros(self.sizes()["n_nodes"], np.int32) if labels else None
+        self.ctx.check(self._lib.bgl_components(self.h, _hp(lab) if labels else None, ctypes.byref(nc)))
+        self.n_comp = nc.value
+        return (lab, nc.value) if labels else nc.value
+
+    def component_nodes(self):
+        nc = self.n_comp
+        off = np.zeros(nc + 1, np.int64)
+        lab = np.zeros(nc, np.int32)
+        nodes = np.zeros(self.sizes()["n_nodes"], np.int32)
+        self.ctx.check(self._lib.bgl_component_nodes(self.h, _hp(off), _hp(lab), _hp(nodes)))
+        return off, lab, nodes
+
+    def split(self, kk_max_nodes: int):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx.check(self._lib.bgl_split(self.h, kk_max_nodes, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def layout(self, p: Params | None = None):
+        p = p or params()
+        out = np.zeros((self.sizes()["n_nodes"], 2), np.float32)
+        self.ctx.check(self._lib.bgl_layout(self.h, ctypes.byref(p), _hp(out)))
+        return out
+
+    def layout_dev(self, p: Params, d_xy_out):
+        self.ctx.check(self._lib.bgl_layout_dev(self.h, ctypes.byref(p), _dp(d_xy_out)))
+
+    # ---------------------------------------------------------- per component
+    def kk_distances(self, c: int, n_c: int):
+        d = np.zeros((n_c, n_c), np.int32)
+        self.ctx.check(self._lib.bgl_kk_distances(self.h, c, _hp(d)))
+        return d
+
+    def kk_run(self, c: int, p: Params, xy):
+        xy = np.array(xy, np.float32, order="C")
+        self.ctx.check(self._lib.bgl_kk_run(self.h, c, ctypes.byref(p), _hp(xy)))
+        return xy
+
+    def fa2_forces(self, c: int, p: Params, xy):
+        xy = _arr(xy, np.float32)
+        f = np.zeros_like(xy)
+        self.ctx.check(self._lib.bgl_fa2_forces(self.h, c, ctypes.byref(p), _hp(xy), _hp(f)))
+        return f
+
+    def fa2_repulsion(self, c: int, p: Params, xy):
+        xy = _arr(xy, np.float32)
+        f = np.zeros_like(xy)
+        self.ctx.check(self._lib.bgl_fa2_repulsion(self.h, c, ctypes.byref(p), _hp(xy), _hp(f)))
+        return f
+
+    def fa2_step(self, c: int, p: Params, iters: int, xy):
+        xy = np.array(xy, np.float32, order="C")
+        stats = np.zeros((max(iters, 1), 3))
+        self.ctx.check(self._lib.bgl_fa2_step(self.h, c, ctypes.byref(p), iters, _hp(xy), _hp(stats)))
+        return xy, stats[:iters]

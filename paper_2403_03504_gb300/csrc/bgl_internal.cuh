@@ -1,0 +1,180 @@
+// Internal declarations of the GB300 layout library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/bgl.h"
+
+namespace bgl {
+
+// ------------------------------------------------------------------ errors
+
+struct Error : std::runtime_error {
+    bgl_status status;
+    Error(bgl_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+[[noreturn]] void fail(bgl_status s, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+#define BGL_CUDA(call) ::bgl::check_cuda((call), #call, __FILE__, __LINE__)
+#define BGL_LAUNCH_CHECK() ::bgl::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define BGL_REQUIRE(cond, msg) \
+    do {                       \
+        if (!(cond)) ::bgl::fail(BGL_EINVAL, msg); \
+    } while (0)
+
+// ------------------------------------------------------------- allocator
+
+// Caching device allocator: freed blocks are kept per context and reused
+// for later requests of the same or a slightly smaller size, so repeated
+// layouts of similar graphs do not call cudaMalloc/cudaFree.
+class Allocator {
+  public:
+    explicit Allocator(int device) : device_(device) {}
+    ~Allocator();
+    void *alloc(size_t bytes);
+    void free(void *p);
+    size_t cached_bytes() const { return cached_; }
+    void release_cache();
+
+  private:
+    int device_;
+    std::mutex mu_;
+    std::multimap<size_t, void *> free_;      // size -> block
+    std::map<void *, size_t> live_;           // block -> size
+    size_t cached_ = 0;
+};
+
+// Device array owned through the context allocator.
+template <typename T>
+struct DevBuf {
+    Allocator *a = nullptr;
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(Allocator *al, size_t count) { reset(al, count); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : a(o.a), p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); a = o.a; p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void reset(Allocator *al, size_t count) {
+        release();
+        a = al;
+        n = count;
+        p = static_cast<T *>(al->alloc(sizeof(T) * (count > 0 ? count : 1)));
+    }
+    // grow-only: keeps the block when it is already big enough
+    void ensure(Allocator *al, size_t count) {
+        if (p && count <= n) return;
+        reset(al, count);
+    }
+    void release() {
+        if (p && a) a->free(p);
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return sizeof(T) * n; }
+};
+
+}  // namespace bgl
+
+// ------------------------------------------------------------- handles
+
+struct bgl_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    bgl::Allocator *alloc = nullptr;
+    std::string last_error;
+    int *d_flag = nullptr;        // device error/flag words (4 ints)
+    int *h_flag = nullptr;        // pinned mirror
+};
+
+struct bgl_graph {
+    bgl_ctx *ctx = nullptr;
+    int64_t n_tx = 0, n_addr = 0, n = 0;
+    int64_t n_dir = 0, n_undir = 0;
+    bgl::DevBuf<uint64_t> addr;         // [n_addr] address keys in id order
+    bgl::DevBuf<int32_t> src, dst;      // [n_dir] directed edges sorted by (src, dst)
+    bgl::DevBuf<int64_t> off;           // [n+1] undirected CSR
+    bgl::DevBuf<int32_t> adj;           // [2 n_undir]
+    // components (Section 4)
+    bool has_comp = false;
+    int64_t n_comp = 0;
+    bgl::DevBuf<int32_t> label;         // [n]
+    bgl::DevBuf<int64_t> comp_off;      // [n_comp+1] in component order
+    bgl::DevBuf<int32_t> comp_label;    // [n_comp]
+    bgl::DevBuf<int32_t> nodes;         // [n] node ids in component order
+    bgl::DevBuf<int32_t> pos;           // [n] component-order position of each node id
+    bgl::DevBuf<int32_t> node_comp;     // [n] component index of each component-order position
+    bgl::DevBuf<int64_t> coff;          // [n+1] CSR in component order (local = position)
+    bgl::DevBuf<int32_t> cadj;          // [2 n_undir]
+    bgl::DevBuf<float> mass;            // [n] degree + 1, component order
+    std::vector<int64_t> h_comp_off;    // host copy of comp_off
+    // split
+    int32_t kk_max = -1;
+    int64_t n_kk = 0, n_fa2 = 0;
+};
+
+namespace bgl {
+
+// ------------------------------------------------------------- primitives (sort.cu)
+
+// Exclusive prefix sum of n values (in may equal out).  Returns nothing;
+// total (if not null) receives the sum on the device.
+void scan_exclusive_i64(bgl_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total);
+void scan_exclusive_i32(bgl_ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *d_total);
+
+// Stable LSD radix sort of (key, value) pairs on bits [0, bits) of the key.
+// keys/vals are sorted in place (with internal double buffers).  vals may be null.
+void radix_sort_u64(bgl_ctx *c, uint64_t *keys, uint32_t *vals, int64_t n, int bits);
+void radix_sort_u32(bgl_ctx *c, uint32_t *keys, uint32_t *vals, int64_t n, int bits);
+
+int bits_for(uint64_t max_value);   // number of bits needed to hold max_value
+
+// ------------------------------------------------------------- graph.cu
+
+void graph_build_device(bgl_graph *g, int64_t n_tx, int64_t n_in, int64_t n_out, const int64_t *d_in_off,
+                        const uint64_t *d_in_addr, const int64_t *d_out_off, const uint64_t *d_out_addr);
+void graph_from_edges_device(bgl_graph *g, int64_t n, int64_t m, const int32_t *d_u, const int32_t *d_v);
+void components_device(bgl_graph *g);
+void split_device(bgl_graph *g, int32_t kk_max);
+
+// ------------------------------------------------------------- layout kernels
+
+// initial positions (SplitMix64 per node id) for component-order range
+// [q0, q1), written to xy[q - q0]
+void init_positions(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t q0, int64_t q1);
+
+// KK on components [c0, c1) (each at most 255 nodes); xy[q - qbase] holds the
+// position of component-order position q.  If init is true the kernel first
+// sets SplitMix64 initial positions scaled by l * diam / 2; otherwise it
+// starts from xy.
+void kk_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init);
+void kk_distances(bgl_graph *g, int64_t c, int32_t *d_out_dev);
+
+// ForceAtlas2 on components [c0, c1) (exact or FMM per component);
+// xy[q - qbase] holds the position of component-order position q;
+// `iters` iterations from F_{-1} = 0, s_G = 1.  d_stats (device, may be
+// null): swing, traction, s_G per iteration of component c0.
+void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
+                double *d_stats);
+// one force evaluation on component c, xy and f indexed by q - comp_off[c];
+// what: 0 total force, 1 repulsion only
+void fa2_forces(bgl_graph *g, const bgl_params *p, const float2 *xy, float2 *f, int64_t c, int what);
+// true if component c of n nodes uses the FMM under p
+bool use_fmm(const bgl_params *p, int64_t n);
+
+}  // namespace bgl

@@ -1,0 +1,450 @@
+// ForceAtlas2 iteration (Section 3.2) on the device.
+//
+// One iteration over the ForceAtlas2 components [c0, c1):
+//   K1 repulsion      exact: tiles of 512 targets per block, sources of the
+//                     same component staged 1024 at a time in shared memory;
+//                     FMM components run the pipeline in fmm.cu instead.
+//                     f <- F_rep = kr m_i sum_j m_j (p_i - p_j) / |p_i - p_j|^2
+//   K2 attraction     f += -sum_{j adjacent} (p_i - p_j) - kg m_i p_i; one
+//      + gravity      thread per node, one block per node of degree > 128
+//   K3 swing/traction per-node |F_t - F_{t-1}|, |F_t + F_{t-1}| summed in FP64
+//                     per tile (warp shuffles), tiles summed in fixed order by
+//                     the last block to finish, which also updates s_G of every
+//                     component: s_G = min(tau trc / swg, 1.5 s_G)
+//   K4 update         s_n = ks s_G / (1 + s_G sqrt|F_t - F_{t-1}|), capped at
+//                     ksmax / |F_t|; p_n += s_n F_t; F_{t-1} <- F_t
+// The sequence has fixed launch shapes, so it is captured once into a CUDA
+// graph and replayed for every iteration.  Every sum has a fixed order, so
+// runs are bitwise reproducible.
+#include "bgl_internal.cuh"
+#include "fmm.cuh"
+
+namespace bgl {
+
+namespace {
+
+constexpr int EX_THREADS = 256;
+constexpr int EX_R = 2;                        // targets per thread
+constexpr int EX_TILE = EX_THREADS * EX_R;     // targets per block
+constexpr int EX_STILE = 1024;                 // sources per shared-memory stage
+constexpr int HEAVY_DEG = 128;
+constexpr int RED_TILE = 2048;                 // nodes per swing/traction tile
+
+struct Tile {
+    int32_t comp;      // component index relative to c0
+    int32_t pad;
+    int64_t t0, t1;    // target positions [t0, t1)
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// K1 (exact): repulsion of every target in the tile from every node of its component
+__global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
+    const Tile *__restrict__ tiles, const int64_t *__restrict__ comp_off, int64_t c0, const float2 *__restrict__ xy,
+    const float *__restrict__ mass, int64_t qbase, float kr, float2 *__restrict__ f) {
+    __shared__ float4 src[EX_STILE];
+    const Tile t = tiles[blockIdx.x];
+    const int64_t s_begin = comp_off[c0 + t.comp], s_end = comp_off[c0 + t.comp + 1];
+    float xi[EX_R], yi[EX_R], sx[EX_R], sy[EX_R], cx[EX_R], cy[EX_R];
+#pragma unroll
+    for (int r = 0; r < EX_R; ++r) {
+        int64_t q = t.t0 + threadIdx.x + r * EX_THREADS;
+        float2 p = q < t.t1 ? xy[q - qbase] : make_float2(0.f, 0.f);
+        xi[r] = p.x;
+        yi[r] = p.y;
+        sx[r] = sy[r] = cx[r] = cy[r] = 0.f;
+    }
+    for (int64_t s0 = s_begin; s0 < s_end; s0 += EX_STILE) {
+        const int cnt = (int)(s_end - s0 < EX_STILE ? s_end - s0 : EX_STILE);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += EX_THREADS) {
+            float2 p = xy[s0 + k - qbase];
+            src[k] = make_float4(p.x, p.y, mass[s0 + k], 0.f);
+        }
+        __syncthreads();
+        float ax[EX_R], ay[EX_R];
+#pragma unroll
+        for (int r = 0; r < EX_R; ++r) ax[r] = ay[r] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) {
+            const float4 s = src[j];
+#pragma unroll
+            for (int r = 0; r < EX_R; ++r) {
+                float dx = xi[r] - s.x, dy = yi[r] - s.y;
+                float r2 = fmaf(dx, dx, dy * dy);
+                // a coincident pair (the node itself) has dx = dy = 0 and adds 0
+                float w = s.z * rcp_approx(fmaxf(r2, 1e-30f));
+                ax[r] = fmaf(w, dx, ax[r]);
+                ay[r] = fmaf(w, dy, ay[r]);
+            }
+        }
+        // blocked accumulation: each stage's partial sum enters a
+        // compensated (Kahan) running total
+#pragma unroll
+        for (int r = 0; r < EX_R; ++r) {
+            float y = ax[r] - cx[r];
+            float s = sx[r] + y;
+            cx[r] = (s - sx[r]) - y;
+            sx[r] = s;
+            y = ay[r] - cy[r];
+            s = sy[r] + y;
+            cy[r] = (s - sy[r]) - y;
+            sy[r] = s;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < EX_R; ++r) {
+        int64_t q = t.t0 + threadIdx.x + r * EX_THREADS;
+        if (q >= t.t1) continue;
+        float km = kr * mass[q];
+        f[q - qbase] = make_float2(km * sx[r], km * sy[r]);
+    }
+}
+
+// K2: attraction and gravity added to f (Section 3.2)
+__global__ void attraction_gravity_kernel(const float2 *__restrict__ xy, const float *__restrict__ mass,
+                                          const int64_t *__restrict__ coff, const int32_t *__restrict__ cadj,
+                                          int64_t q0, int64_t q1, int64_t qbase, float kg,
+                                          const int32_t *__restrict__ heavy, int64_t n_light_blocks,
+                                          float2 *__restrict__ f) {
+    if (blockIdx.x < n_light_blocks) {
+        int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (q >= q1) return;
+        int64_t e0 = coff[q], e1 = coff[q + 1];
+        if (e1 - e0 > HEAVY_DEG) return;
+        float2 p = xy[q - qbase];
+        float ax = 0.f, ay = 0.f;
+        for (int64_t e = e0; e < e1; ++e) {
+            float2 o = xy[cadj[e] - qbase];
+            ax -= p.x - o.x;
+            ay -= p.y - o.y;
+        }
+        float km = kg * mass[q];
+        float2 fr = f[q - qbase];
+        f[q - qbase] = make_float2((fr.x + ax) - km * p.x, (fr.y + ay) - km * p.y);
+        return;
+    }
+    // one block per node of high degree: strided partial sums, fixed-order reduction
+    __shared__ float rx[32], ry[32];
+    const int64_t q = heavy[blockIdx.x - n_light_blocks];
+    const int64_t e0 = coff[q], e1 = coff[q + 1];
+    const float2 p = xy[q - qbase];
+    float ax = 0.f, ay = 0.f;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        float2 o = xy[cadj[e] - qbase];
+        ax -= p.x - o.x;
+        ay -= p.y - o.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { rx[warp] = ax; ry[warp] = ay; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sx = 0.f, sy = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sx += rx[w]; sy += ry[w]; }
+        float km = kg * mass[q];
+        float2 fr = f[q - qbase];
+        f[q - qbase] = make_float2((fr.x + sx) - km * p.x, (fr.y + sy) - km * p.y);
+    }
+}
+
+__global__ void heavy_flag_kernel(const int64_t *__restrict__ coff, int64_t q0, int64_t n, int32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = (coff[q0 + i + 1] - coff[q0 + i]) > HEAVY_DEG;
+}
+
+__global__ void heavy_list_kernel(const int32_t *__restrict__ flag, const int32_t *__restrict__ fscan, int64_t q0,
+                                  int64_t n, int32_t *__restrict__ heavy) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) heavy[fscan[i]] = (int32_t)(q0 + i);
+}
+
+struct RedArgs {
+    const Tile *tiles;        // node tiles, each inside one component
+    const int64_t *tile_off;  // per component: first tile, [ncomp+1]
+    int ncomp;
+    int ntiles;
+    const float2 *f, *fprev;
+    const float *mass;
+    int64_t qbase;
+    int variant;
+    double tau;
+    double2 *partial;         // [ntiles]
+    double *sg;               // [ncomp]
+    unsigned *counter;        // zero between launches
+    double *stats;            // optional, component 0
+    int *iter;                // iteration counter for stats
+};
+
+// K3: swing / traction sums (Section 3.2) and the global speed of each component
+__global__ void swing_traction_kernel(RedArgs a) {
+    __shared__ double ws[32], wt[32];
+    __shared__ bool last;
+    const Tile t = a.tiles[blockIdx.x];
+    double sw = 0.0, tr = 0.0;
+    for (int64_t q = t.t0 + threadIdx.x; q < t.t1; q += blockDim.x) {
+        float2 F = a.f[q - a.qbase], P = a.fprev[q - a.qbase];
+        float s = sqrtf((F.x - P.x) * (F.x - P.x) + (F.y - P.y) * (F.y - P.y));
+        float u = sqrtf((F.x + P.x) * (F.x + P.x) + (F.y + P.y) * (F.y + P.y));
+        if (a.variant == 1) {
+            float m = a.mass[q];
+            sw += (double)m * s;
+            tr += 0.5 * (double)m * u;
+        } else {
+            sw += s;
+            tr += u;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { ws[warp] = sw; wt[warp] = tr; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, u = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s += ws[w]; u += wt[w]; }
+        a.partial[blockIdx.x] = make_double2(s, u);
+        __threadfence();
+        unsigned done = atomicAdd(a.counter, 1u);
+        last = done == (unsigned)(a.ntiles - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the last block: per component, tiles in order
+    for (int c = threadIdx.x; c < a.ncomp; c += blockDim.x) {
+        double swg = 0.0, trc = 0.0;
+        for (int64_t k = a.tile_off[c]; k < a.tile_off[c + 1]; ++k) {
+            double2 v = __ldcg(&a.partial[k]);   // written by other blocks: bypass L1
+            swg += v.x;
+            trc += v.y;
+        }
+        double g = a.sg[c];
+        double s_new = swg > 0.0 ? a.tau * trc / swg : 1.5 * g;
+        if (s_new > 1.5 * g) s_new = 1.5 * g;
+        a.sg[c] = s_new;
+        if (c == 0 && a.stats) {
+            int it = *a.iter;
+            a.stats[3 * it] = swg;
+            a.stats[3 * it + 1] = trc;
+            a.stats[3 * it + 2] = s_new;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *a.counter = 0u;
+        *a.iter += 1;
+    }
+}
+
+// K4: node speeds and the position update
+__global__ void update_kernel(const float2 *__restrict__ f, float2 *__restrict__ fprev, float2 *__restrict__ xy,
+                              const int32_t *__restrict__ node_comp, const double *__restrict__ sg, int64_t q0,
+                              int64_t q1, int64_t qbase, int64_t c0, float ks, float ksmax, int *bad) {
+    int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    float2 F = f[q - qbase], P = fprev[q - qbase];
+    float g = (float)sg[node_comp[q] - c0];
+    float sw = sqrtf((F.x - P.x) * (F.x - P.x) + (F.y - P.y) * (F.y - P.y));
+    float s = ks * g / (1.f + g * sqrtf(sw));
+    float fn = sqrtf(F.x * F.x + F.y * F.y);
+    if (fn > 0.f && s > ksmax / fn) s = ksmax / fn;
+    float2 p = xy[q - qbase];
+    p.x += s * F.x;
+    p.y += s * F.y;
+    if (!isfinite(p.x) || !isfinite(p.y)) *bad = 1;
+    xy[q - qbase] = p;
+    fprev[q - qbase] = F;
+}
+
+inline unsigned nblocks(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+bool use_fmm(const bgl_params *p, int64_t n) {
+    if (p->repulsion == BGL_REP_FMM) return true;
+    if (p->repulsion == BGL_REP_EXACT) return false;
+    return n >= p->fmm_min_nodes;
+}
+
+// Everything one set of ForceAtlas2 components needs across iterations.
+struct Fa2Run {
+    bgl_graph *g;
+    const bgl_params *p;
+    float2 *xy;
+    int64_t qbase, c0, c1, q0, q1;
+    DevBuf<Tile> ex_tiles, red_tiles;
+    DevBuf<int64_t> red_tile_off;
+    int n_ex_tiles = 0, n_red_tiles = 0;
+    DevBuf<float2> f, fprev;
+    DevBuf<double2> partial;
+    DevBuf<double> sg;
+    DevBuf<unsigned> counter;
+    DevBuf<int> iter;
+    DevBuf<int32_t> heavy;
+    int64_t n_heavy = 0;
+    std::vector<FmmPlan *> fmm;   // one per FMM component
+    std::vector<int64_t> fmm_comp;
+
+    Fa2Run(bgl_graph *g_, const bgl_params *p_, float2 *xy_, int64_t qbase_, int64_t c0_, int64_t c1_)
+        : g(g_), p(p_), xy(xy_), qbase(qbase_), c0(c0_), c1(c1_) {
+        Allocator *A = g->ctx->alloc;
+        cudaStream_t s = g->ctx->stream;
+        q0 = g->h_comp_off[c0];
+        q1 = g->h_comp_off[c1];
+        const int64_t n = q1 - q0;
+        std::vector<Tile> ex, red;
+        std::vector<int64_t> roff(1, 0);
+        for (int64_t c = c0; c < c1; ++c) {
+            int64_t a = g->h_comp_off[c], b = g->h_comp_off[c + 1];
+            if (use_fmm(p, b - a)) {
+                fmm.push_back(fmm_create(g, p, c));
+                fmm_comp.push_back(c);
+            } else {
+                for (int64_t t = a; t < b; t += EX_TILE) ex.push_back(Tile{(int32_t)(c - c0), 0, t, std::min(b, t + EX_TILE)});
+            }
+            for (int64_t t = a; t < b; t += RED_TILE) red.push_back(Tile{(int32_t)(c - c0), 0, t, std::min(b, t + RED_TILE)});
+            roff.push_back((int64_t)red.size());
+        }
+        n_ex_tiles = (int)ex.size();
+        n_red_tiles = (int)red.size();
+        ex_tiles.reset(A, ex.size());
+        red_tiles.reset(A, red.size());
+        red_tile_off.reset(A, roff.size());
+        if (!ex.empty())
+            BGL_CUDA(cudaMemcpyAsync(ex_tiles.p, ex.data(), sizeof(Tile) * ex.size(), cudaMemcpyHostToDevice, s));
+        BGL_CUDA(cudaMemcpyAsync(red_tiles.p, red.data(), sizeof(Tile) * red.size(), cudaMemcpyHostToDevice, s));
+        BGL_CUDA(cudaMemcpyAsync(red_tile_off.p, roff.data(), sizeof(int64_t) * roff.size(), cudaMemcpyHostToDevice, s));
+        f.reset(A, n);
+        fprev.reset(A, n);
+        BGL_CUDA(cudaMemsetAsync(fprev.p, 0, sizeof(float2) * n, s));
+        partial.reset(A, red.size());
+        std::vector<double> ones(c1 - c0, 1.0);
+        sg.reset(A, c1 - c0);
+        BGL_CUDA(cudaMemcpyAsync(sg.p, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, s));
+        counter.reset(A, 1);
+        BGL_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned), s));
+        iter.reset(A, 1);
+        BGL_CUDA(cudaMemsetAsync(iter.p, 0, sizeof(int), s));
+        // nodes of high degree get a block each in the attraction kernel
+        DevBuf<int32_t> flag(A, n), fscan(A, n), tot(A, 1);
+        heavy_flag_kernel<<<nblocks(n, 256), 256, 0, s>>>(g->coff.p, q0, n, flag.p);
+        BGL_LAUNCH_CHECK();
+        scan_exclusive_i32(g->ctx, flag.p, fscan.p, n, tot.p);
+        int32_t nh = 0;
+        BGL_CUDA(cudaMemcpyAsync(&nh, tot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        BGL_CUDA(cudaStreamSynchronize(s));
+        n_heavy = nh;
+        heavy.reset(A, nh);
+        heavy_list_kernel<<<nblocks(n, 256), 256, 0, s>>>(flag.p, fscan.p, q0, n, heavy.p);
+        BGL_LAUNCH_CHECK();
+        BGL_CUDA(cudaStreamSynchronize(s));
+    }
+    ~Fa2Run() {
+        for (auto *pl : fmm) fmm_destroy(pl);
+    }
+
+    // K1 + K2: f <- F (what 0) or F_rep (what 1)
+    void forces(int what) {
+        cudaStream_t s = g->ctx->stream;
+        if (n_ex_tiles > 0) {
+            exact_repulsion_kernel<<<n_ex_tiles, EX_THREADS, 0, s>>>(ex_tiles.p, g->comp_off.p, c0, xy, g->mass.p,
+                                                                     qbase, (float)p->kr, f.p - (q0 - qbase));
+            BGL_LAUNCH_CHECK();
+        }
+        for (size_t k = 0; k < fmm.size(); ++k) fmm_repulsion(fmm[k], xy, qbase, f.p, q0);
+        if (what == 0) {
+            int64_t n = q1 - q0;
+            int64_t nl = nblocks(n, 256);
+            attraction_gravity_kernel<<<(unsigned)(nl + n_heavy), 256, 0, s>>>(
+                xy, g->mass.p, g->coff.p, g->cadj.p, q0, q1, qbase, (float)p->kg, heavy.p, nl, f.p - (q0 - qbase));
+            BGL_LAUNCH_CHECK();
+        }
+    }
+
+    // one full iteration (K1..K4)
+    void iteration(double *d_stats) {
+        cudaStream_t s = g->ctx->stream;
+        forces(0);
+        RedArgs a;
+        a.tiles = red_tiles.p;
+        a.tile_off = red_tile_off.p;
+        a.ncomp = (int)(c1 - c0);
+        a.ntiles = n_red_tiles;
+        a.f = f.p - (q0 - qbase);
+        a.fprev = fprev.p - (q0 - qbase);
+        a.mass = g->mass.p;
+        a.qbase = qbase;
+        a.variant = p->swing_variant;
+        a.tau = p->tau;
+        a.partial = partial.p;
+        a.sg = sg.p;
+        a.counter = counter.p;
+        a.stats = d_stats;
+        a.iter = iter.p;
+        swing_traction_kernel<<<n_red_tiles, 256, 0, s>>>(a);
+        BGL_LAUNCH_CHECK();
+        update_kernel<<<nblocks(q1 - q0, 256), 256, 0, s>>>(f.p - (q0 - qbase), fprev.p - (q0 - qbase), xy,
+                                                            g->node_comp.p, sg.p, q0, q1, qbase, c0, (float)p->ks,
+                                                            (float)p->ksmax, g->ctx->d_flag + 1);
+        BGL_LAUNCH_CHECK();
+    }
+};
+
+void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
+                double *d_stats) {
+    if (c1 <= c0 || iters <= 0) return;
+    bgl_ctx *ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    Fa2Run run(g, p, xy, qbase, c0, c1);
+    BGL_CUDA(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
+    // capture one iteration, replay it
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    BGL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+        run.iteration(d_stats);
+    } catch (...) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(s, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        throw;
+    }
+    BGL_CUDA(cudaStreamEndCapture(s, &graph));
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    BGL_CUDA(e);
+    try {
+        for (int it = 0; it < iters; ++it) BGL_CUDA(cudaGraphLaunch(exec, s));
+    } catch (...) {
+        cudaGraphExecDestroy(exec);
+        throw;
+    }
+    BGL_CUDA(cudaMemcpyAsync(ctx->h_flag + 1, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaStreamSynchronize(s));
+    cudaGraphExecDestroy(exec);
+    if (ctx->h_flag[1]) fail(BGL_ENUMERIC, "fa2: a position became non-finite");
+}
+
+void fa2_forces(bgl_graph *g, const bgl_params *p, const float2 *xy, float2 *f, int64_t c, int what) {
+    int64_t q0 = g->h_comp_off[c];
+    Fa2Run run(g, p, const_cast<float2 *>(xy), q0, c, c + 1);
+    run.forces(what);
+    BGL_CUDA(cudaMemcpyAsync(f, run.f.p, sizeof(float2) * (run.q1 - run.q0), cudaMemcpyDeviceToDevice,
+                             g->ctx->stream));
+    BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
+}
+
+}  // namespace bgl

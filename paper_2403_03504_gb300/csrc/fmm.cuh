@@ -1,0 +1,19 @@
+// Fast Multipole Method for the ForceAtlas2 repulsion (Section 3.2.1).
+#pragma once
+#include "bgl_internal.cuh"
+
+namespace bgl {
+
+struct FmmPlan;
+
+// Buffers for the FMM of component c (sized for its node count); reused
+// across iterations.
+FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c);
+void fmm_destroy(FmmPlan *pl);
+
+// f[q - fbase] <- kr m_q sum_j m_j (p_q - p_j) / |p_q - p_j|^2 for every
+// position q of the component, with xy[q - qbase] the positions.  Launches
+// only (no host synchronisation), so it can be captured in a CUDA graph.
+void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase);
+
+}  // namespace bgl

@@ -1,0 +1,237 @@
+// Kamada-Kawai layout of small components (Section 3.1) and the initial
+// positions shared by every component.
+//
+// One warp lays out one component of at most 255 nodes:
+//  1. all-pairs hop distances by a BFS from every node (lane s runs the BFS
+//     of sources s, s+32, ...) into a uint8 matrix in shared memory; with
+//     unit edge weights this equals the Floyd-Warshall result the paper
+//     names, at O(n (n + E)) instead of O(n^3) work;
+//  2. optional initial positions (SplitMix64 per node id) scaled by
+//     l * diameter / 2;
+//  3. Gauss-Seidel sweeps: for m = 0..n-1 the warp sums the gradient and
+//     Hessian of the KK energy over all i != m (lane-strided FP32 terms,
+//     xor-butterfly reduction so every lane holds identical sums), solves the
+//     2x2 Newton system in FP64 and moves p_m in shared memory.
+#include "bgl_internal.cuh"
+
+namespace bgl {
+
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// x, y uniform on [-1, 1), exactly representable in FP32
+__device__ __forceinline__ float2 initial_position(uint64_t seed, int32_t id) {
+    uint64_t s = seed ^ ((uint64_t)(int64_t)id * 0x9E3779B97F4A7C15ull);
+    uint64_t hx = splitmix64(s), hy = splitmix64(s);
+    float x = (float)(hx >> 40) * 0x1.0p-24f * 2.0f - 1.0f;
+    float y = (float)(hy >> 40) * 0x1.0p-24f * 2.0f - 1.0f;
+    return make_float2(x, y);
+}
+
+__global__ void init_positions_kernel(const int32_t *__restrict__ nodes, int64_t q0, int64_t q1, int64_t qbase,
+                                      uint64_t seed, float2 *__restrict__ xy) {
+    int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    xy[q - qbase] = initial_position(seed, nodes[q]);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct KKArgs {
+    const int64_t *comp_off;
+    const int64_t *coff;
+    const int32_t *cadj;
+    const int32_t *nodes;
+    float2 *xy;            // indexed by q - qbase
+    int64_t qbase;
+    int64_t c0, nc;        // components [c0, c0 + nc)
+    int maxn;              // largest component in the launch
+    int wpc;               // warps per block
+    uint64_t seed;
+    float l;
+    int sweeps;
+    float tol;
+    int init;
+    int32_t *d_out;        // optional int32 distance matrix of component c0
+};
+
+__global__ void kk_kernel(KKArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t c = a.c0 + (int64_t)blockIdx.x * a.wpc + warp;
+    if (c >= a.c0 + a.nc) return;
+    const int64_t q0 = a.comp_off[c];
+    const int n = (int)(a.comp_off[c + 1] - q0);
+    const size_t dbytes = ((size_t)a.maxn * a.maxn + 15) & ~size_t(15);
+    unsigned char *base = smem + (size_t)warp * (dbytes + 8 * (size_t)a.maxn);
+    uint8_t *dist = base;
+    float *px = reinterpret_cast<float *>(base + dbytes);
+    float *py = px + a.maxn;
+
+    // 1. BFS from every node (Section 3.1: all-pairs shortest paths, unit weights)
+    for (int s = lane; s < n; s += 32) {
+        uint8_t *row = dist + (size_t)s * n;
+        for (int v = 0; v < n; ++v) row[v] = 255;
+        row[s] = 0;
+        for (int k = 0; k < 254; ++k) {
+            bool grew = false;
+            for (int v = 0; v < n; ++v) {
+                if (row[v] != k) continue;
+                for (int64_t e = a.coff[q0 + v]; e < a.coff[q0 + v + 1]; ++e) {
+                    int w = (int)(a.cadj[e] - q0);
+                    if (row[w] == 255) {
+                        row[w] = (uint8_t)(k + 1);
+                        grew = true;
+                    }
+                }
+            }
+            if (!grew) break;
+        }
+    }
+    __syncwarp();
+    int diam = 0;
+    for (int i = lane; i < n * n; i += 32) {
+        int d = dist[i];
+        if (d != 255 && d > diam) diam = d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) diam = max(diam, __shfl_xor_sync(0xffffffffu, diam, o));
+
+    if (a.d_out && c == a.c0) {
+        for (int i = lane; i < n * n; i += 32) a.d_out[i] = dist[i] == 255 ? -1 : (int32_t)dist[i];
+    }
+
+    // 2. positions
+    const float scale = a.l * (float)diam * 0.5f;
+    for (int v = lane; v < n; v += 32) {
+        float2 p;
+        if (a.init) {
+            p = initial_position(a.seed, a.nodes[q0 + v]);
+            p.x *= scale;
+            p.y *= scale;
+        } else {
+            p = a.xy[q0 + v - a.qbase];
+        }
+        px[v] = p.x;
+        py[v] = p.y;
+    }
+    __syncwarp();
+
+    // 3. Gauss-Seidel Newton-Raphson sweeps
+    for (int sw = 0; sw < a.sweeps; ++sw) {
+        float gmax = 0.f;
+        for (int m = 0; m < n; ++m) {
+            const float xm = px[m], ym = py[m];
+            const uint8_t *drow = dist + (size_t)m * n;
+            float gx = 0.f, gy = 0.f, hxx = 0.f, hxy = 0.f, hyy = 0.f;
+            for (int i = lane; i < n; i += 32) {
+                int d = drow[i];
+                if (i == m || d == 0 || d == 255) continue;
+                float dx = xm - px[i], dy = ym - py[i];
+                float r2 = dx * dx + dy * dy;
+                if (r2 == 0.f) continue;
+                float fd = (float)d;
+                float k = 1.0f / (fd * fd);
+                float lm = a.l * fd;
+                float rinv = rsqrtf(r2);
+                float t = lm * rinv;              // l_mi / r
+                float u = t * rinv * rinv;        // l_mi / r^3
+                gx += k * dx * (1.f - t);
+                gy += k * dy * (1.f - t);
+                hxx += k * (1.f - u * dy * dy);
+                hyy += k * (1.f - u * dx * dx);
+                hxy += k * u * dx * dy;
+            }
+            gx = warp_sum(gx);
+            gy = warp_sum(gy);
+            hxx = warp_sum(hxx);
+            hxy = warp_sum(hxy);
+            hyy = warp_sum(hyy);
+            gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
+            double Hxx = hxx, Hxy = hxy, Hyy = hyy, Gx = gx, Gy = gy;
+            double det = Hxx * Hyy - Hxy * Hxy;
+            if (fabs(det) > 1e-12 * (Hxx * Hxx + 2.0 * Hxy * Hxy + Hyy * Hyy)) {
+                double dxm = -(Hyy * Gx - Hxy * Gy) / det;
+                double dym = -(-Hxy * Gx + Hxx * Gy) / det;
+                if (lane == 0) {
+                    px[m] = (float)((double)xm + dxm);
+                    py[m] = (float)((double)ym + dym);
+                }
+            }
+            __syncwarp();
+        }
+        if (a.tol > 0.f && gmax < a.tol) break;
+    }
+    for (int v = lane; v < n; v += 32) a.xy[q0 + v - a.qbase] = make_float2(px[v], py[v]);
+}
+
+size_t kk_warp_bytes(int maxn) {
+    return (((size_t)maxn * maxn + 15) & ~size_t(15)) + 8 * (size_t)maxn;
+}
+
+}  // namespace
+
+void init_positions(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t q0, int64_t q1) {
+    if (q1 <= q0) return;
+    int64_t n = q1 - q0;
+    init_positions_kernel<<<(unsigned)((n + 255) / 256), 256, 0, g->ctx->stream>>>(g->nodes.p, q0, q1, q0, p->seed,
+                                                                                   xy);
+    BGL_LAUNCH_CHECK();
+}
+
+static void kk_launch(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init,
+                      int sweeps, int32_t *d_out) {
+    if (c1 <= c0) return;
+    int maxn = (int)(g->h_comp_off[c0 + 1] - g->h_comp_off[c0]);
+    for (int64_t c = c0; c < c1; ++c)
+        maxn = std::max<int>(maxn, (int)(g->h_comp_off[c + 1] - g->h_comp_off[c]));
+    BGL_REQUIRE(maxn <= 255, "kk: components must have at most 255 nodes");
+    if (maxn < 1) maxn = 1;
+    size_t wb = kk_warp_bytes(maxn);
+    int wpc = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(200 * 1024) / wb));
+    size_t smem = wb * wpc;
+    BGL_CUDA(cudaFuncSetAttribute(kk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    KKArgs a;
+    a.comp_off = g->comp_off.p;
+    a.coff = g->coff.p;
+    a.cadj = g->cadj.p;
+    a.nodes = g->nodes.p;
+    a.xy = xy;
+    a.qbase = qbase;
+    a.c0 = c0;
+    a.nc = c1 - c0;
+    a.maxn = maxn;
+    a.wpc = wpc;
+    a.seed = p->seed;
+    a.l = (float)p->kk_l;
+    a.sweeps = sweeps;
+    a.tol = (float)p->kk_tol;
+    a.init = init ? 1 : 0;
+    a.d_out = d_out;
+    int64_t blocks = (a.nc + wpc - 1) / wpc;
+    kk_kernel<<<(unsigned)blocks, 32 * wpc, smem, g->ctx->stream>>>(a);
+    BGL_LAUNCH_CHECK();
+}
+
+void kk_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init) {
+    kk_launch(g, p, xy, qbase, c0, c1, init, p->kk_sweeps, nullptr);
+}
+
+void kk_distances(bgl_graph *g, int64_t c, int32_t *d_out_dev) {
+    bgl_params p;
+    bgl_params_default(&p);
+    DevBuf<float2> tmp(g->ctx->alloc, g->h_comp_off[c + 1] - g->h_comp_off[c]);
+    kk_launch(g, &p, tmp.p, g->h_comp_off[c], c, c + 1, false, 0, d_out_dev);
+}
+
+}  // namespace bgl

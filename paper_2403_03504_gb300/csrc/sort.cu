@@ -1,0 +1,264 @@
+// Device primitives: multi-block exclusive scan and stable LSD radix sort.
+//
+// Scan: reduce-then-scan over tiles of 4096 elements (512 threads x 8).
+// Radix sort: 8-bit digits, tiles of 4096 keys (8 warps x 32 lanes x 16
+// rounds).  Per pass: a per-tile digit histogram (shared-memory integer
+// atomics), one exclusive scan of the digit-major histogram, and a scatter
+// in which each warp ranks its keys with __match_any_sync so that equal
+// digits keep their input order (stable).
+#include "bgl_internal.cuh"
+
+namespace bgl {
+
+namespace {
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *warp_tot, T *total) {
+    // exclusive scan of one value per thread across the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nwarps ? warp_tot[lane] : T(0);
+        T s = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nwarps) warp_tot[lane] = s - w;   // exclusive warp offsets
+        if (lane == nwarps - 1) *total = s;
+    }
+    __syncthreads();
+    T r = warp_tot[warp] + x - v;
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__global__ void scan_reduce_kernel(const T *__restrict__ in, T *__restrict__ tile_sum, int64_t n) {
+    __shared__ T red[SCAN_THREADS / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        int64_t k = base + (int64_t)i * SCAN_THREADS + threadIdx.x;
+        if (k < n) s += in[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += red[w];
+        tile_sum[blockIdx.x] = t;
+    }
+}
+
+// single block: exclusive scan of the tile sums, in place; total to *d_total
+template <typename T>
+__global__ void scan_tiles_kernel(T *tile_sum, int64_t ntiles, T *d_total) {
+    __shared__ T wt[32];
+    __shared__ T tot;
+    T carry = 0;
+    for (int64_t b = 0; b < ntiles; b += blockDim.x) {
+        int64_t k = b + threadIdx.x;
+        T v = k < ntiles ? tile_sum[k] : T(0);
+        T e = block_exclusive_scan<T>(v, wt, &tot);
+        if (k < ntiles) tile_sum[k] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
+template <typename T>
+__global__ void scan_apply_kernel(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ tile_off,
+                                  int64_t n) {
+    __shared__ T buf[SCAN_TILE];
+    __shared__ T wt[32];
+    __shared__ T tot;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        int idx = i * SCAN_THREADS + threadIdx.x;
+        int64_t k = base + idx;
+        buf[idx] = k < n ? in[k] : T(0);
+    }
+    __syncthreads();
+    T v[SCAN_ITEMS];
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = buf[threadIdx.x * SCAN_ITEMS + i];
+        s += v[i];
+    }
+    T e = block_exclusive_scan<T>(s, wt, &tot) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        buf[threadIdx.x * SCAN_ITEMS + i] = e;
+        e += v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        int idx = i * SCAN_THREADS + threadIdx.x;
+        int64_t k = base + idx;
+        if (k < n) out[k] = buf[idx];
+    }
+}
+
+template <typename T>
+void scan_exclusive(bgl_ctx *c, const T *in, T *out, int64_t n, T *d_total) {
+    if (n <= 0) {
+        if (d_total) BGL_CUDA(cudaMemsetAsync(d_total, 0, sizeof(T), c->stream));
+        return;
+    }
+    int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    DevBuf<T> ts(c->alloc, ntiles);
+    scan_reduce_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, c->stream>>>(in, ts.p, n);
+    BGL_LAUNCH_CHECK();
+    scan_tiles_kernel<T><<<1, 1024, 0, c->stream>>>(ts.p, ntiles, d_total);
+    BGL_LAUNCH_CHECK();
+    scan_apply_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, c->stream>>>(in, out, ts.p, n);
+    BGL_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ radix sort
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+template <typename K>
+__global__ void radix_hist_kernel(const K *__restrict__ keys, int64_t n, int shift, int32_t *__restrict__ hist,
+                                  int64_t ntiles) {
+    __shared__ int32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        int64_t k = base + (int64_t)i * RS_THREADS + threadIdx.x;
+        if (k < n) atomicAdd(&h[(unsigned)((keys[k] >> shift) & 0xFF)], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                              K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                              int64_t n, int shift,
+                                                              const int32_t *__restrict__ offs, int64_t ntiles) {
+    __shared__ int32_t cnt[RS_WARPS][256];
+    __shared__ int32_t gbase[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
+    gbase[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * 32 * RS_ITEMS;
+    K key[RS_ITEMS];
+    uint32_t val[RS_ITEMS];
+    int32_t rank[RS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t k = wbase + r * 32 + lane;
+        bool ok = k < n;
+        key[r] = ok ? kin[k] : K(0);
+        val[r] = (ok && vin) ? vin[k] : 0u;
+        unsigned d = ok ? (unsigned)((key[r] >> shift) & 0xFF) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = __popc(peers & lt);
+        int cur = ok ? cnt[warp][d] : 0;
+        __syncwarp();
+        if (ok && before == 0) cnt[warp][d] = cur + __popc(peers);
+        __syncwarp();
+        rank[r] = ok ? (cur + before) : -1;
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps for digit threadIdx.x
+        int d = threadIdx.x;
+        int s = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            int c = cnt[w][d];
+            cnt[w][d] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        if (rank[r] < 0) continue;
+        unsigned d = (unsigned)((key[r] >> shift) & 0xFF);
+        int64_t dst = (int64_t)gbase[d] + cnt[warp][d] + rank[r];
+        kout[dst] = key[r];
+        if (vout) vout[dst] = val[r];
+    }
+}
+
+template <typename K>
+void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
+    if (n <= 1 || bits <= 0) return;
+    BGL_REQUIRE(n < (int64_t(1) << 31), "radix sort: more than 2^31 keys");
+    int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    DevBuf<K> kt(c->alloc, n);
+    DevBuf<uint32_t> vt;
+    if (vals) vt.reset(c->alloc, n);
+    DevBuf<int32_t> hist(c->alloc, 256 * ntiles);
+    K *ka = keys, *kb = kt.p;
+    uint32_t *va = vals, *vb = vals ? vt.p : nullptr;
+    int passes = 0;
+    for (int shift = 0; shift < bits; shift += 8, ++passes) {
+        radix_hist_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, c->stream>>>(ka, n, shift, hist.p, ntiles);
+        BGL_LAUNCH_CHECK();
+        scan_exclusive<int32_t>(c, hist.p, hist.p, 256 * ntiles, nullptr);
+        radix_scatter_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, c->stream>>>(ka, va, kb, vb, n, shift, hist.p,
+                                                                                ntiles);
+        BGL_LAUNCH_CHECK();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (passes & 1) {
+        BGL_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, c->stream));
+        if (vals) BGL_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+}
+
+}  // namespace
+
+void scan_exclusive_i64(bgl_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total) {
+    scan_exclusive<int64_t>(c, in, out, n, d_total);
+}
+void scan_exclusive_i32(bgl_ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *d_total) {
+    scan_exclusive<int32_t>(c, in, out, n, d_total);
+}
+void radix_sort_u64(bgl_ctx *c, uint64_t *keys, uint32_t *vals, int64_t n, int bits) {
+    radix_sort<uint64_t>(c, keys, vals, n, bits);
+}
+void radix_sort_u32(bgl_ctx *c, uint32_t *keys, uint32_t *vals, int64_t n, int bits) {
+    radix_sort<uint32_t>(c, keys, vals, n, bits);
+}
+
+int bits_for(uint64_t v) {
+    int b = 0;
+    while (b < 64 && (v >> b) != 0) ++b;
+    return b;
+}
+
+}  // namespace bgl

@@ -1,0 +1,250 @@
+"""GPU parity of the layout kernels against the FP64 oracle.
+
+Kamada-Kawai (Section 3.1): BFS distances bit-exact; Newton sweeps within
+1e-3 of the component diameter after 10 sweeps, and at the same energy
+minimum after 200 sweeps.  ForceAtlas2 (Section 3.2): forces within 1e-5 of
+the sum of contribution magnitudes (FP32 direct sum), positions within 1e-3
+of the bounding-box diagonal after 10 iterations, and long runs compared by
+layout energy and edge-length statistics (the iteration is chaotic)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2403_03504_gb300 as bgl
+    c = bgl.Context(0)
+    yield c
+    c.close()
+
+
+def _bgl():
+    import paper_2403_03504_gb300 as bgl
+    return bgl
+
+
+class Built:
+    """A graph on both sides plus per-component local data."""
+
+    def __init__(self, ctx, og, g):
+        self.og = og
+        self.g = g
+        self.lab, _ = g.components()
+        self.coff, _, self.nodes = g.component_nodes()
+
+    def comp(self, c):
+        vs = self.nodes[self.coff[c]:self.coff[c + 1]]
+        loff, ladj = oracle.subgraph(self.og.off, self.og.adj, vs)
+        return vs, loff, ladj, np.diff(loff) + 1.0
+
+
+@pytest.fixture(scope="module")
+def c1(ctx):
+    bgl = _bgl()
+    tx = synth.tx_lists(**synth.C1)
+    og = oracle.graph_build(tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    return Built(ctx, og, g)
+
+
+@pytest.fixture(scope="module")
+def forest(ctx):
+    bgl = _bgl()
+    sizes, u, v = synth.forest(17, 300, 3.0, 200.0)
+    n = int(sizes.sum())
+    og = oracle.graph_from_edges(n, u, v)
+    g = bgl.Graph.from_edges(ctx, n, u, v)
+    return Built(ctx, og, g)
+
+
+# ------------------------------------------------------------------ KK
+
+def test_kk_distances_bit_exact(c1, forest):
+    for b in (c1, forest):
+        sizes = np.diff(b.coff)
+        for c in range(len(sizes)):
+            if sizes[c] > 255:
+                continue
+            vs, loff, ladj, _ = b.comp(c)
+            d = b.g.kk_distances(c, len(vs))
+            assert np.array_equal(d, oracle.bfs_apsp(loff, ladj)), c
+
+
+def _kk_start(seed, vs, d, l=1.0):
+    x, y = oracle.init_positions(seed, vs)
+    sc = l * d.max() / 2 if len(vs) > 1 else 0.0
+    return x * sc, y * sc
+
+
+def test_kk_ten_sweeps_match_oracle(c1, forest):
+    bgl = _bgl()
+    p = bgl.params(kk_sweeps=10)
+    worst = 0.0
+    for b in (c1, forest):
+        sizes = np.diff(b.coff)
+        for c in np.flatnonzero((sizes >= 2) & (sizes <= 255))[::3]:
+            vs, loff, ladj, _ = b.comp(c)
+            d = oracle.bfs_apsp(loff, ladj)
+            x, y = _kk_start(5, vs, d)
+            xy = np.stack([x, y], 1).astype(np.float32)
+            got = b.g.kk_run(int(c), p, xy)
+            ox, oy, _, _, _ = oracle.kk_run(xy[:, 0].astype(np.float64), xy[:, 1].astype(np.float64), d, 1.0, 10)
+            err = np.max(np.hypot(got[:, 0] - ox, got[:, 1] - oy)) / max(1, d.max())
+            worst = max(worst, err)
+    assert worst <= 1e-3, worst
+
+
+def test_kk_full_run_reaches_the_oracle_minimum(forest):
+    bgl = _bgl()
+    p = bgl.params(kk_sweeps=200)
+    b = forest
+    sizes = np.diff(b.coff)
+    rel = []
+    for c in np.flatnonzero((sizes >= 3) & (sizes <= 120))[::4]:
+        vs, loff, ladj, _ = b.comp(c)
+        d = oracle.bfs_apsp(loff, ladj)
+        x, y = _kk_start(5, vs, d)
+        xy = np.stack([x, y], 1).astype(np.float32)
+        got = b.g.kk_run(int(c), p, xy).astype(np.float64)
+        ox, oy, e, _, _ = oracle.kk_run(xy[:, 0].astype(np.float64), xy[:, 1].astype(np.float64), d, 1.0, 200)
+        eg = oracle.kk_energy(got[:, 0], got[:, 1], d, 1.0)
+        gmax = max(np.hypot(*oracle.kk_grad_hess(got[:, 0], got[:, 1], d, 1.0, m)[:2]) for m in range(len(vs)))
+        assert gmax <= 1e-3 * max(1.0, e[-1]), (c, gmax)      # the GPU run is stationary too
+        rel.append(abs(eg - e[-1]) / max(e[-1], 1e-12))
+    rel = np.array(rel)
+    # both sides stop at a stationary point; from the same start they reach the
+    # same minimum except where the indefinite-Hessian phase diverges
+    assert np.mean(rel <= 1e-4) >= 0.9, np.sort(rel)[-10:]
+
+
+# ------------------------------------------------------------------ FA2 forces
+
+def _rel_force_err(f_gpu, f_ref, scale):
+    return np.max(np.hypot(*(f_gpu - f_ref).T) / scale)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_fa2_exact_forces_c1(c1, seed):
+    bgl = _bgl()
+    vs, loff, ladj, mass = c1.comp(0)
+    x, y = oracle.init_positions(seed, vs)
+    xy = np.stack([x, y], 1).astype(np.float32)
+    for kr, kg in ((1.0, 1.0), (3.0, 0.2)):
+        p = bgl.params(repulsion=bgl.REP_EXACT, kr=kr, kg=kg)
+        f = c1.g.fa2_forces(0, p, xy)
+        o = oracle.fa2_forces(xy[:, 0], xy[:, 1], mass, loff, ladj, kr, kg)
+        ref = o["frep"] + o["fatt"] + o["fgrav"]
+        assert _rel_force_err(f, ref, o["sabs"]) <= 1e-5
+        fr = c1.g.fa2_repulsion(0, p, xy)
+        rep_scale = kr * mass * np.array([np.sum(mass / np.maximum(np.hypot(xy[i, 0] - xy[:, 0], xy[i, 1] - xy[:, 1]), 1e-300)
+                                                 * (np.arange(len(vs)) != i)) for i in range(len(vs))])
+        assert _rel_force_err(fr, o["frep"], rep_scale) <= 1e-5
+
+
+def test_fa2_ten_iterations_match_oracle(c1):
+    bgl = _bgl()
+    vs, loff, ladj, mass = c1.comp(0)
+    x, y = oracle.init_positions(0, vs)
+    xy = np.stack([x, y], 1).astype(np.float32)
+    for variant in (0, 1):
+        p = bgl.params(repulsion=bgl.REP_EXACT, swing_variant=variant)
+        got, stats = c1.g.fa2_step(0, p, 10, xy)
+        st, ostats = oracle.fa2_run(xy[:, 0], xy[:, 1], mass, loff, ladj, 10, variant=variant)
+        diag = math.hypot(np.ptp(st.x), np.ptp(st.y))
+        err = np.max(np.hypot(got[:, 0] - st.x, got[:, 1] - st.y))
+        assert err <= 1e-3 * diag, (variant, err, diag)
+        assert np.allclose(stats, ostats, rtol=1e-3)
+
+
+def test_fa2_two_node_golden(ctx):
+    bgl = _bgl()
+    gold = json.load(open(os.path.join(GOLDEN, "fa2_two_node.json")))
+    s, e = gold["setup"], gold["expected"]
+    g = bgl.Graph.from_edges(ctx, 2, [0], [1])
+    g.components()
+    p = bgl.params(repulsion=bgl.REP_EXACT, kr=s["kr"], kg=s["kg"], ks=s["ks"], ksmax=s["ksmax"], tau=s["tau"])
+    xy = np.array([s["p0"], s["p1"]], np.float32)
+    got, stats = g.fa2_step(0, p, 1, xy)
+    assert got[0, 0] == pytest.approx(e["x0_after_1"], rel=1e-6)
+    assert got[1, 0] == pytest.approx(e["x1_after_1"], rel=1e-6)
+    assert np.allclose(stats[0], e["stats_1"], rtol=1e-6)
+    got, stats = g.fa2_step(0, p, 2, xy)
+    assert got[0, 0] == pytest.approx(e["x0_after_2"], rel=1e-5)
+    assert np.allclose(stats[1], e["stats_2"], rtol=1e-5)
+    g.destroy()
+
+
+def test_fa2_exact_forces_c2_sampled(ctx):
+    """Full-size giant component (~5.5e5 nodes): forces on 2000 sampled nodes."""
+    bgl = _bgl()
+    tx = synth.tx_lists(**synth.C2)
+    g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    g.components(labels=False)
+    coff, _, nodes = g.component_nodes()
+    off, adj = g.csr()
+    vs = nodes[coff[0]:coff[1]]
+    pos = np.full(len(off) - 1, -1, np.int64)
+    pos[vs] = np.arange(len(vs))
+    loff = np.zeros(len(vs) + 1, np.int64)
+    loff[1:] = np.cumsum(np.diff(off)[vs])
+    ladj = pos[np.concatenate([adj[off[v]:off[v + 1]] for v in vs])].astype(np.int32)
+    mass = np.diff(loff) + 1.0
+    x, y = oracle.init_positions(2, vs)
+    xy = np.stack([x, y], 1).astype(np.float32)
+    p = bgl.params(repulsion=bgl.REP_EXACT)
+    f = g.fa2_forces(0, p, xy)
+    tg = np.random.default_rng(2).choice(len(vs), 2000, replace=False)
+    o = oracle.fa2_forces(xy[:, 0], xy[:, 1], mass, loff, ladj, 1.0, 1.0, targets=tg)
+    ref = o["frep"] + o["fatt"] + o["fgrav"]
+    assert _rel_force_err(f[tg], ref, o["sabs"]) <= 1e-5
+    g.destroy()
+
+
+# ------------------------------------------------------------------ whole layout
+
+def _edge_stats(xy, og):
+    e = og.src, og.dst
+    d = np.hypot(xy[e[0], 0] - xy[e[1], 0], xy[e[0], 1] - xy[e[1], 1])
+    return d.mean(), np.percentile(d, 50), np.percentile(d, 90)
+
+
+def test_layout_c1_against_oracle(c1):
+    bgl = _bgl()
+    p = bgl.params(seed=1, repulsion=bgl.REP_EXACT)
+    xy = c1.g.layout(p).astype(np.float64)
+    again = c1.g.layout(p).astype(np.float64)
+    assert np.array_equal(xy, again)                   # bitwise reproducible
+    oxy = oracle.layout(c1.og, seed=1)
+    sizes = np.diff(c1.coff)
+    # singletons at the origin
+    for c in np.flatnonzero(sizes == 1):
+        assert np.all(xy[c1.nodes[c1.coff[c]]] == 0)
+    # ForceAtlas2 component: energy within 1%, edge lengths within 2%
+    vs, loff, ladj, mass = c1.comp(0)
+    eg = oracle.fa2_energy(xy[vs, 0], xy[vs, 1], mass, loff, ladj)
+    eo = oracle.fa2_energy(oxy[vs, 0], oxy[vs, 1], mass, loff, ladj)
+    assert abs(eg - eo) <= 0.01 * abs(eo)
+    sub = np.isin(c1.og.src, vs)
+
+    class E:
+        src, dst = c1.og.src[sub], c1.og.dst[sub]
+    for a, b in zip(_edge_stats(xy, E), _edge_stats(oxy, E)):
+        assert abs(a - b) <= 0.02 * b
+    # KK components: same energy minimum
+    for c in np.flatnonzero((sizes >= 2) & (sizes <= 50)):
+        vs, loff, ladj, _ = c1.comp(c)
+        d = oracle.bfs_apsp(loff, ladj)
+        eg = oracle.kk_energy(xy[vs, 0], xy[vs, 1], d)
+        eo = oracle.kk_energy(oxy[vs, 0], oxy[vs, 1], d)
+        assert abs(eg - eo) <= 1e-4 * max(eo, 1e-9) + 1e-9, c
