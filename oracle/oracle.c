@@ -38,8 +38,10 @@
  *   - coincident points (distance 0) exert no repulsion on each other;
  *   - KK: k_ij = d_ij^-2, l_ij = l d_ij, one sweep = one 2x2 Newton step per
  *     node in ascending id order using positions already updated in the
- *     sweep; the 2x2 Newton system is solved as it stands; a node whose
- *     Hessian is numerically singular is skipped.
+ *     sweep; where H is not positive definite its non-positive eigenvalues
+ *     are replaced by max(|l|, 0.1 max|l|), and steps are no longer than l
+ *     (a safeguarded Newton-Raphson step: the plain step diverges from
+ *     random starts where H is indefinite).
  * "parity unpinned": none (every function has a pin in tests/test_oracle.py).
  */
 #include <math.h>
@@ -395,16 +397,60 @@ void orc_kk_grad_hess(int64_t n, const double *x, const double *y, const int32_t
 }
 
 /*
+ * One safeguarded Newton-Raphson step for node m (the minimisation step of
+ * Section 3.1): with g the half-gradient and H = l1 P1 + l2 P2 the symmetric
+ * 2x2 half-Hessian (eigenvalues l1 >= l2, P1, P2 the orthogonal projectors
+ * onto their eigenvectors), the step is
+ *   delta = -(P1 g / e1 + P2 g / e2),
+ *   e_i = l_i if l_i > 1e-12 max|l|, else max(|l_i|, 0.1 max|l|),
+ * shortened to length l when longer.  Where H is positive definite and the
+ * step is shorter than l this is the plain Newton step; elsewhere the
+ * directions of non-positive curvature are treated as positive (the plain
+ * step there climbs the energy and throws nodes away from random starts).
+ * H = 0 gives no step (returns 0).
+ */
+static int orc_kk_step(const double *o, double l, double *dxm, double *dym)
+{
+    double gx = o[0], gy = o[1], a = o[2], b = o[3], c = o[4];
+    double tr = 0.5 * (a + c);
+    double dd = hypot(0.5 * (a - c), b);
+    double l1 = tr + dd, l2 = tr - dd;
+    double big = fabs(l1) > fabs(l2) ? fabs(l1) : fabs(l2);
+    if (big == 0.0) return 0;
+    double fl = 0.1 * big;
+    double e1 = l1 > 1e-12 * big ? l1 : (fabs(l1) > fl ? fabs(l1) : fl);
+    double e2 = l2 > 1e-12 * big ? l2 : (fabs(l2) > fl ? fabs(l2) : fl);
+    double sx, sy;
+    if (dd == 0.0) {            /* H = tr I */
+        sx = -gx / e1;
+        sy = -gy / e1;
+    } else {
+        /* P1 = (H - l2 I) / (l1 - l2),  P2 = I - P1, with l1 - l2 = 2 dd and
+           a - l2 = (a - c)/2 + dd, c - l2 = (c - a)/2 + dd */
+        double h = 0.5 * (a - c);
+        double p1x = ((h + dd) * gx + b * gy) / (2.0 * dd);
+        double p1y = (b * gx + (dd - h) * gy) / (2.0 * dd);
+        double p2x = gx - p1x, p2y = gy - p1y;
+        sx = -(p1x / e1 + p2x / e2);
+        sy = -(p1y / e1 + p2y / e2);
+    }
+    double len = hypot(sx, sy);
+    if (len > l) {
+        sx *= l / len;
+        sy *= l / len;
+    }
+    *dxm = sx;
+    *dym = sy;
+    return 1;
+}
+
+/*
  * Newton-Raphson minimisation of the KK energy (Section 3.1), Gauss-Seidel
- * order: one sweep visits m = 0..n-1 and moves p_m by the solution of
- * H delta = -g, using positions already moved in this sweep (the 2x2 system
- * is solved as it stands, as Kamada and Kawai do, also where H is
- * indefinite).  A node whose Hessian is numerically singular
- * (|det| <= 1e-12 (Hxx^2 + 2 Hxy^2 + Hyy^2)) is left where it is for this
- * sweep.  `sweeps` sweeps are run; if tol > 0
- * the run stops after a sweep in which every node had |g| < tol.
+ * order: one sweep visits m = 0..n-1 and moves p_m by orc_kk_step, using
+ * positions already moved in this sweep.  `sweeps` sweeps are run; if
+ * tol > 0 the run stops after a sweep in which every node had |g| < tol.
  * energy (may be NULL) receives the energy after each sweep.
- * Returns the number of skipped node steps; *sweeps_done the sweeps run.
+ * Returns the number of node steps skipped (H = 0); *sweeps_done the sweeps run.
  */
 int64_t orc_kk_run(int64_t n, double *x, double *y, const int32_t *d, double l, int64_t sweeps,
                    double tol, double *energy, int64_t *sweeps_done)
@@ -413,16 +459,11 @@ int64_t orc_kk_run(int64_t n, double *x, double *y, const int32_t *d, double l, 
     for (s = 0; s < sweeps; ++s) {
         double gmax = 0.0;
         for (int64_t m = 0; m < n; ++m) {
-            double o[5];
+            double o[5], dxm, dym;
             orc_kk_grad_hess(n, x, y, d, l, m, o);
             double gn = hypot(o[0], o[1]);
             if (gn > gmax) gmax = gn;
-            double hxx = o[2], hxy = o[3], hyy = o[4];
-            double det = hxx * hyy - hxy * hxy;
-            if (fabs(det) <= 1e-12 * (hxx * hxx + 2.0 * hxy * hxy + hyy * hyy)) { ++skipped; continue; }
-            /* delta = -H^{-1} g */
-            double dxm = -(hyy * o[0] - hxy * o[1]) / det;
-            double dym = -(-hxy * o[0] + hxx * o[1]) / det;
+            if (!orc_kk_step(o, l, &dxm, &dym)) { ++skipped; continue; }
             x[m] += dxm;
             y[m] += dym;
         }

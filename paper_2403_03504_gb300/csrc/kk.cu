@@ -10,8 +10,9 @@
 //     l * diameter / 2;
 //  3. Gauss-Seidel sweeps: for m = 0..n-1 the warp sums the gradient and
 //     Hessian of the KK energy over all i != m (lane-strided FP32 terms,
-//     xor-butterfly reduction so every lane holds identical sums), solves the
-//     2x2 Newton system in FP64 and moves p_m in shared memory.
+//     xor-butterfly reduction so every lane holds identical sums), takes a
+//     safeguarded 2x2 Newton-Raphson step in FP64 (kk_step) and moves p_m
+//     in shared memory.
 #include "bgl_internal.cuh"
 
 namespace bgl {
@@ -45,6 +46,42 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Safeguarded Newton-Raphson step (Section 3.1) in FP64 from the FP32 sums:
+// with H = l1 P1 + l2 P2 (l1 >= l2, P1 + P2 = I), delta = -(P1 g / e1 + P2 g / e2)
+// where e_i = l_i for positive curvature and max(|l_i|, 0.1 max|l|) otherwise;
+// steps longer than l are shortened to l.  Returns false for H = 0.
+__device__ __forceinline__ bool kk_step(float fgx, float fgy, float fa, float fb, float fc, double l, double *dx,
+                                        double *dy) {
+    const double gx = fgx, gy = fgy, a = fa, b = fb, c = fc;
+    const double h = 0.5 * (a - c);
+    const double dd = hypot(h, b);
+    const double tr = 0.5 * (a + c);
+    const double l1 = tr + dd, l2 = tr - dd;
+    const double big = fmax(fabs(l1), fabs(l2));
+    if (big == 0.0) return false;
+    const double fl = 0.1 * big;
+    const double e1 = l1 > 1e-12 * big ? l1 : fmax(fabs(l1), fl);
+    const double e2 = l2 > 1e-12 * big ? l2 : fmax(fabs(l2), fl);
+    double sx, sy;
+    if (dd == 0.0) {
+        sx = -gx / e1;
+        sy = -gy / e1;
+    } else {
+        const double p1x = ((h + dd) * gx + b * gy) / (2.0 * dd);
+        const double p1y = (b * gx + (dd - h) * gy) / (2.0 * dd);
+        sx = -(p1x / e1 + (gx - p1x) / e2);
+        sy = -(p1y / e1 + (gy - p1y) / e2);
+    }
+    const double len = hypot(sx, sy);
+    if (len > l) {
+        sx *= l / len;
+        sy *= l / len;
+    }
+    *dx = sx;
+    *dy = sy;
+    return true;
 }
 
 struct KKArgs {
@@ -158,15 +195,10 @@ __global__ void kk_kernel(KKArgs a) {
             hxy = warp_sum(hxy);
             hyy = warp_sum(hyy);
             gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
-            double Hxx = hxx, Hxy = hxy, Hyy = hyy, Gx = gx, Gy = gy;
-            double det = Hxx * Hyy - Hxy * Hxy;
-            if (fabs(det) > 1e-12 * (Hxx * Hxx + 2.0 * Hxy * Hxy + Hyy * Hyy)) {
-                double dxm = -(Hyy * Gx - Hxy * Gy) / det;
-                double dym = -(-Hxy * Gx + Hxx * Gy) / det;
-                if (lane == 0) {
-                    px[m] = (float)((double)xm + dxm);
-                    py[m] = (float)((double)ym + dym);
-                }
+            double dxm, dym;
+            if (kk_step(gx, gy, hxx, hxy, hyy, (double)a.l, &dxm, &dym) && lane == 0) {
+                px[m] = (float)((double)xm + dxm);
+                py[m] = (float)((double)ym + dym);
             }
             __syncwarp();
         }

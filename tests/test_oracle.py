@@ -368,6 +368,7 @@ def test_kk_path_becomes_straight(n):
     x, y = oracle.init_positions(4, np.arange(n))
     x, y = x * (n - 1) / 2, y * (n - 1) / 2
     x, y, e, _, _ = oracle.kk_run(x, y, d, 1.0, 300)
+    # the straight path is the exact minimum (E = 0)
     assert e[-1] < 1e-16
     for i in range(n):
         for j in range(n):
