@@ -58,7 +58,7 @@ def _load():
                 "orc_kk_energy": ([_I64, _VP, _VP, _VP, _D], _D),
                 "orc_kk_grad_hess": ([_I64, _VP, _VP, _VP, _D, _I64, _VP], None),
                 "orc_kk_run": ([_I64, _VP, _VP, _VP, _D, _I64, _D, _VP, _VP], _I64),
-                "orc_fa2_forces": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D, _I64, _VP] + [_VP] * 7, None),
+                "orc_fa2_forces": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D, _I64, _VP] + [_VP] * 8, None),
                 "orc_fa2_energy": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D], _D),
                 "orc_fa2_run": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D, _D, _D, _D, ctypes.c_int32,
                                  _I64, _VP, _VP, _VP, _VP], None),
@@ -233,7 +233,8 @@ def kk_run(x, y, d, l=1.0, sweeps=200, tol=0.0):
 # ---------------------------------------------------------------- Section 3.2
 
 def fa2_forces(x, y, mass, off, adj, kr=1.0, kg=1.0, targets=None):
-    """Returns dict of frep, fatt, fgrav (each [nt, 2]) and sabs [nt]."""
+    """Returns dict of frep, fatt, fgrav (each [nt, 2]), sabs [nt] (sum of the
+    magnitudes of all contributions) and srep [nt] (repulsion terms only)."""
     x = _c(x, np.float64)
     y = _c(y, np.float64)
     mass = _c(mass, np.float64)
@@ -242,11 +243,11 @@ def fa2_forces(x, y, mass, off, adj, kr=1.0, kg=1.0, targets=None):
     n = len(x)
     tg = None if targets is None else _c(targets, np.int64)
     nt = n if tg is None else len(tg)
-    o = [np.zeros(nt) for _ in range(7)]
+    o = [np.zeros(nt) for _ in range(8)]
     _load().orc_fa2_forces(n, _p(x), _p(y), _p(mass), _p(off), _p(adj), kr, kg, nt, _p(tg),
                            *[_p(a) for a in o])
     return dict(frep=np.stack([o[0], o[1]], 1), fatt=np.stack([o[2], o[3]], 1),
-                fgrav=np.stack([o[4], o[5]], 1), sabs=o[6])
+                fgrav=np.stack([o[4], o[5]], 1), sabs=o[6], srep=o[7])
 
 
 def fa2_energy(x, y, mass, off, adj, kr=1.0, kg=1.0) -> float:

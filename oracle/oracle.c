@@ -487,12 +487,14 @@ int64_t orc_kk_run(int64_t n, double *x, double *y, const int32_t *d, double l, 
  *   gravity    F_grav(i) = - kg m_i p_i
  * Outputs are indexed by target position k (0..nt).  sabs[k] (may be NULL)
  * is the sum of the magnitudes of every individual contribution, the scale
- * used for relative force errors.
+ * used for relative force errors; srep[k] (may be NULL) the same sum over
+ * the repulsion terms only, kr m_i sum_j m_j / |p_i - p_j|, the scale of the
+ * Fast Multipole error (Section 3.2.1).
  */
 void orc_fa2_forces(int64_t n, const double *x, const double *y, const double *mass,
                     const int64_t *off, const int32_t *adj, double kr, double kg,
                     int64_t nt, const int64_t *tgt, double *frx, double *fry, double *fax,
-                    double *fay, double *fgx, double *fgy, double *sabs)
+                    double *fay, double *fgx, double *fgy, double *sabs, double *srep)
 {
     if (!tgt) nt = n;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -509,6 +511,7 @@ void orc_fa2_forces(int64_t n, const double *x, const double *y, const double *m
             ry += w * dy;
             s += kr * mass[i] * mass[j] / sqrt(d2);
         }
+        if (srep) srep[k] = s;
         for (int64_t e = off[i]; e < off[i + 1]; ++e) {
             int64_t j = adj[e];
             double dx = x[i] - x[j], dy = y[i] - y[j];
@@ -578,7 +581,7 @@ void orc_fa2_run(int64_t n, double *x, double *y, const double *mass, const int6
     double *rx = malloc(sz), *ry = malloc(sz), *ax = malloc(sz), *ay = malloc(sz);
     double *gx = malloc(sz), *gy = malloc(sz);
     for (int64_t t = 0; t < iters; ++t) {
-        orc_fa2_forces(n, x, y, mass, off, adj, kr, kg, n, NULL, rx, ry, ax, ay, gx, gy, NULL);
+        orc_fa2_forces(n, x, y, mass, off, adj, kr, kg, n, NULL, rx, ry, ax, ay, gx, gy, NULL, NULL);
         double swg = 0.0, trc = 0.0;
         for (int64_t i = 0; i < n; ++i) {
             double fx = rx[i] + ax[i] + gx[i], fy = ry[i] + ay[i] + gy[i];

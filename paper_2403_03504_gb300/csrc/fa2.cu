@@ -356,6 +356,16 @@ struct Fa2Run {
         for (auto *pl : fmm) fmm_destroy(pl);
     }
 
+    // device-side failures of the FMM (bounded waits, capacities)
+    void check_fmm() {
+        for (auto *pl : fmm) {
+            int e = fmm_error(pl);
+            if (e & 1) fail(BGL_ETIMEOUT, "fmm: a bounded device-side wait gave up");
+            if (e & 8) fail(BGL_ENUMERIC, "fmm: non-finite positions");
+            if (e) fail(BGL_ENOMEM, "fmm: tree or list capacity exceeded (error bits " + std::to_string(e) + ")");
+        }
+    }
+
     // K1 + K2: f <- F (what 0) or F_rep (what 1)
     void forces(int what) {
         cudaStream_t s = g->ctx->stream;
@@ -435,6 +445,7 @@ void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, in
     BGL_CUDA(cudaMemcpyAsync(ctx->h_flag + 1, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     BGL_CUDA(cudaStreamSynchronize(s));
     cudaGraphExecDestroy(exec);
+    run.check_fmm();
     if (ctx->h_flag[1]) fail(BGL_ENUMERIC, "fa2: a position became non-finite");
 }
 
@@ -445,6 +456,7 @@ void fa2_forces(bgl_graph *g, const bgl_params *p, const float2 *xy, float2 *f, 
     BGL_CUDA(cudaMemcpyAsync(f, run.f.p, sizeof(float2) * (run.q1 - run.q0), cudaMemcpyDeviceToDevice,
                              g->ctx->stream));
     BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
+    run.check_fmm();
 }
 
 }  // namespace bgl

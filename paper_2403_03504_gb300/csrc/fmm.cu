@@ -1,15 +1,1170 @@
+// Fast Multipole Method for the ForceAtlas2 repulsion (Section 3.2.1).
+//
+// Field of the repulsion: with z = x + i y and charges q_j = m_j,
+//   E(z) = sum_j q_j / (z - z_j),    F_rep(i) = kr m_i conj(E(z_i)),
+// the derivative of the 2-D Laplace potential sum_j q_j log(z - z_j).  The
+// "two Taylor expansions" of Section 3.2.1 are taken as the complex Laurent
+// (outgoing, multipole) and Taylor (incoming, local) expansions of that
+// potential (Greengard and Rokhlin 1987), of order p, stored scaled by the
+// box half-width r (a~_k = a_k / r^k, b~_l = b_l r^l) so that FP32 does not
+// overflow and the translation operators do not depend on the level.
+//
+// One evaluation (all launches, no host synchronisation):
+//   bbox      root square covering all points (FP32 min/max, FP64 geometry)
+//   keys      16-bit quantised x, y interleaved into 32-bit Morton keys
+//   sort      stable radix sort of (key, index); gather x, y, m in key order
+//   tree      adaptive quadtree: a box is split while it holds more than
+//             leaf_size points (and is above level 16).  The leaf level of
+//             point i is 1 + the deepest level at which some window of
+//             leaf_size + 1 consecutive sorted points around i shares a key
+//             prefix, so boxes are emitted in one pass, level by level, in
+//             Morton order within a level.
+//   nbr       3x3 neighbour table per box from its parent's table (the
+//             same-level box or the coarser leaf covering each adjacent cell)
+//   lists     U (adjacent leaves, near field), V (children of the parent's
+//             neighbours that are not adjacent: the "interacting cells" of
+//             Section 3.2.1), W and X (the adaptive-tree lists of Carrier,
+//             Greengard and Rokhlin that make every pair counted exactly once)
+//   up        P2M at leaves; M2M from the 4 children into the parent by the
+//             last child to finish (an atomic arrival count), so the whole
+//             upward pass is one launch
+//   down      M2L over V, P2L over X, L2L from the parent; boxes are taken in
+//             level order through a ticket counter and wait (bounded) for
+//             their parent's local expansion
+//   leaf      per leaf: L2P of its local expansion, M2P over W, and the direct
+//             P2P sum over the points of U staged in shared memory
+// Every sum has a fixed order, so results are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+
 #include "fmm.cuh"
 
 namespace bgl {
 
-struct FmmPlan {
-    int dummy;
+namespace {
+
+constexpr int MAXLEV = 16;
+constexpr int NLEV = MAXLEV + 1;
+constexpr int TREE_TILE = 1024;
+constexpr int TREE_THREADS = 256;
+constexpr int BN = 49;                 // binomial table dimension (n <= 48)
+constexpr int SRC_CAP = 2048;          // P2P sources staged per pass
+constexpr int LEAF_THREADS = 128;
+constexpr long long SPIN_LIMIT = 1ll << 24;
+
+enum { ERR_SPIN = 1, ERR_LIST_OVERFLOW = 2, ERR_BOX_OVERFLOW = 4, ERR_BBOX = 8 };
+
+struct Root {
+    double ox, oy, side;
 };
 
-FmmPlan *fmm_create(bgl_graph *, const bgl_params *, int64_t) {
-    fail(BGL_EINVAL, "fmm: not available in this build");
+struct Tree {
+    // sorted points
+    const uint32_t *key;
+    const float4 *pts;        // x, y, m, original local index (int bits)
+    int n;
+    // boxes
+    int *bstart, *bend, *blevel, *bparent;
+    uint32_t *bkey;
+    int8_t *bleaf;
+    int4 *bchild;
+    int *levoff;              // [NLEV + 1], levoff[NLEV] = number of boxes
+    int *nb;                  // [9 * Bmax]
+    int *lcnt;                // [4 * Bmax + 1] counts, then offsets (U, V, W, X per box)
+    int *lidx;                // list entries
+    int lcap;                 // capacity of lidx
+    int Bmax;                 // capacity of the box arrays
+    const Root *root;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t spread_bits(uint32_t x) {
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
 }
+
+__device__ __forceinline__ uint32_t compact_bits(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
+}
+
+// number of leading 2-bit digits shared by two keys (16 if equal)
+__device__ __forceinline__ int lcp_level(uint32_t a, uint32_t b) { return a == b ? MAXLEV : (__clz(a ^ b) >> 1); }
+
+__device__ __forceinline__ uint32_t prefix_at(uint32_t key, int L) { return L == 0 ? 0u : key >> (32 - 2 * L); }
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+// bounded wait until *flag != 0; records ERR_SPIN and gives up after SPIN_LIMIT polls
+__device__ __forceinline__ void wait_flag(const int *flag, int *err) {
+    long long it = 0;
+    while (ld_volatile(flag) == 0) {
+        if (++it > SPIN_LIMIT) {
+            atomicOr(err, ERR_SPIN);
+            break;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+}
+
+struct BoxGeo {
+    float cx, cy, r;
+};
+
+__device__ __forceinline__ BoxGeo box_geo(const Root &rt, uint32_t key, int L) {
+    const double w = rt.side / (double)(1u << L);
+    const double bx = (double)compact_bits(key), by = (double)compact_bits(key >> 1);
+    BoxGeo g;
+    g.cx = (float)(rt.ox + (bx + 0.5) * w);
+    g.cy = (float)(rt.oy + (by + 0.5) * w);
+    g.r = (float)(0.5 * w);
+    return g;
+}
+
+// closed squares of two distinct (non-nested) boxes touch or overlap
+__device__ __forceinline__ bool boxes_adjacent(uint32_t ka, int La, uint32_t kb, int Lb) {
+    const int F = max(La, Lb);
+    const int ax = (int)compact_bits(ka) << (F - La), ay = (int)compact_bits(ka >> 1) << (F - La);
+    const int bx = (int)compact_bits(kb) << (F - Lb), by = (int)compact_bits(kb >> 1) << (F - Lb);
+    const int aw = 1 << (F - La), bw = 1 << (F - Lb);
+    return max(ax, bx) <= min(ax + aw, bx + bw) && max(ay, by) <= min(ay + aw, by + bw);
+}
+
+// ---------------------------------------------------------------- bbox, keys, gather
+
+__global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__restrict__ part, unsigned *counter,
+                            Root *root, int *err) {
+    __shared__ float4 wred[32];
+    __shared__ bool last;
+    float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float2 p = xy[i];
+        mnx = fminf(mnx, p.x);
+        mxx = fmaxf(mxx, p.x);
+        mny = fminf(mny, p.y);
+        mxy = fmaxf(mxy, p.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wred[warp] = make_float4(mnx, mxx, mny, mxy);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 a = wred[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            float4 b = wred[w];
+            a = make_float4(fminf(a.x, b.x), fmaxf(a.y, b.y), fminf(a.z, b.z), fmaxf(a.w, b.w));
+        }
+        part[blockIdx.x] = a;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    float4 a = __ldcg(&part[0]);
+    for (int b = 1; b < (int)gridDim.x; ++b) {
+        float4 c = __ldcg(&part[b]);
+        a = make_float4(fminf(a.x, c.x), fmaxf(a.y, c.y), fminf(a.z, c.z), fmaxf(a.w, c.w));
+    }
+    double w = fmax((double)a.y - (double)a.x, (double)a.w - (double)a.z);
+    double side = w * (1.0 + 0x1.0p-20);
+    if (!isfinite(side)) {
+        atomicOr(err, ERR_BBOX);
+        side = 1.0;
+    }
+    if (!(side > 0.0)) side = 1.0;     // all points coincide
+    Root r;
+    r.side = side;
+    r.ox = 0.5 * ((double)a.x + (double)a.y) - 0.5 * side;
+    r.oy = 0.5 * ((double)a.z + (double)a.w) - 0.5 * side;
+    if (!isfinite(r.ox) || !isfinite(r.oy)) {
+        atomicOr(err, ERR_BBOX);
+        r.ox = r.oy = 0.0;
+    }
+    *root = r;
+    *counter = 0u;
+}
+
+__global__ void keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
+                            uint32_t *__restrict__ key, uint32_t *__restrict__ idx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Root rt = *root;
+    const double scale = 65536.0 / rt.side;
+    float2 p = xy[i];
+    double fx = floor(((double)p.x - rt.ox) * scale), fy = floor(((double)p.y - rt.oy) * scale);
+    int qx = (int)fmin(fmax(fx, 0.0), 65535.0), qy = (int)fmin(fmax(fy, 0.0), 65535.0);
+    key[i] = spread_bits((uint32_t)qx) | (spread_bits((uint32_t)qy) << 1);
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void gather_kernel(const float2 *__restrict__ xy, const float *__restrict__ mass,
+                              const uint32_t *__restrict__ idx, int n, float4 *__restrict__ pts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t o = idx[i];
+    float2 p = xy[o];
+    pts[i] = make_float4(p.x, p.y, mass[o], __int_as_float((int)o));
+}
+
+// ---------------------------------------------------------------- tree build
+
+// per point: c(i) = shared levels with point i-1 (-1 for i = 0), lambda(i) =
+// level of its leaf; per tile and level: number of boxes that start in the tile
+__global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t *__restrict__ key, int n, int S,
+                                                                 int8_t *__restrict__ cl, int8_t *__restrict__ lam,
+                                                                 int *__restrict__ tcnt, int ntiles) {
+    __shared__ uint32_t sk[TREE_TILE + 2 * 256];
+    __shared__ int8_t g[TREE_TILE + 256];
+    __shared__ int cnt[NLEV];
+    const int t0 = blockIdx.x * TREE_TILE;
+    const int lo = t0 - S;                           // smem index 0 <-> point lo
+    const int span = TREE_TILE + 2 * S;
+    for (int k = threadIdx.x; k < span; k += TREE_THREADS) {
+        int i = lo + k;
+        sk[k] = (i >= 0 && i < n) ? key[i] : 0u;
+    }
+    if (threadIdx.x < NLEV) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    // g(j) = lcp(key[j], key[j + S]) for windows j in [t0 - S, t0 + TILE)
+    for (int k = threadIdx.x; k < TREE_TILE + S; k += TREE_THREADS) {
+        int j = lo + k;
+        g[k] = (j >= 0 && j + S < n) ? (int8_t)lcp_level(sk[k], sk[k + S]) : (int8_t)-1;
+    }
+    __syncthreads();
+    int local[NLEV];
+#pragma unroll
+    for (int L = 0; L < NLEV; ++L) local[L] = 0;
+    for (int r = 0; r < TREE_TILE / TREE_THREADS; ++r) {
+        int i = t0 + r * TREE_THREADS + threadIdx.x;
+        if (i >= n) break;
+        int k = i - lo;
+        int c = i == 0 ? -1 : lcp_level(sk[k - 1], sk[k]);
+        int G = -1;
+        // windows j in [i - S, i] (g is -1 where a window does not fit)
+        for (int j = k - S; j <= k; ++j) G = max(G, (int)g[j]);
+        int la = min(MAXLEV, G + 1);
+        cl[i] = (int8_t)c;
+        lam[i] = (int8_t)la;
+#pragma unroll
+        for (int L = 0; L < NLEV; ++L) local[L] += (c < L && L <= la) ? 1 : 0;
+    }
+#pragma unroll
+    for (int L = 0; L < NLEV; ++L)
+        if (local[L]) atomicAdd(&cnt[L], local[L]);
+    __syncthreads();
+    if (threadIdx.x < NLEV) tcnt[threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// exclusive scan of the (level, tile) counts; level offsets
+__global__ void tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax, int *err) {
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    const int total = NLEV * ntiles;
+    int carry = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < total; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < total ? tcnt[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            int t = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t - s;
+            if (lane == 31) carry_s = t;
+        }
+        __syncthreads();
+        if (i < total) tcnt[i] = carry + wsum[warp] + x - v;
+        carry += carry_s;
+        __syncthreads();
+    }
+    if (threadIdx.x <= NLEV) {
+        int L = threadIdx.x;
+        levoff[L] = L < NLEV ? tcnt[L * ntiles] : carry;
+    }
+    if (threadIdx.x == 0 && carry > Bmax) atomicOr(err, ERR_BOX_OVERFLOW);
+}
+
+__global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const int8_t *__restrict__ cl,
+                                                                const int8_t *__restrict__ lam,
+                                                                const int *__restrict__ tcnt, int ntiles, int Bmax) {
+    __shared__ int wcount[TREE_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t0 = blockIdx.x * TREE_TILE;
+    constexpr int R = TREE_TILE / TREE_THREADS;
+    int c[R], la[R], prev[R];
+    uint32_t k[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int i = t0 + r * TREE_THREADS + threadIdx.x;
+        bool ok = i < T.n;
+        c[r] = ok ? cl[i] : 99;
+        la[r] = ok ? lam[i] : -99;
+        k[r] = ok ? T.key[i] : 0u;
+        prev[r] = -1;
+    }
+    for (int L = 0; L < NLEV; ++L) {
+        int base = tcnt[L * ntiles + blockIdx.x];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = t0 + r * TREE_THREADS + threadIdx.x;
+            const bool f = c[r] < L && L <= la[r];
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) wcount[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, tot = 0;
+            for (int w = 0; w < TREE_THREADS / 32; ++w) {
+                int v = wcount[w];
+                if (w < warp) before += v;
+                tot += v;
+            }
+            const int b = base + before + __popc(bal & ((1u << lane) - 1u));
+            if (f && b < Bmax) {
+                T.bstart[b] = i;
+                T.blevel[b] = L;
+                T.bkey[b] = prefix_at(k[r], L);
+                T.bleaf[b] = (int8_t)(L == la[r]);
+                T.bparent[b] = (L >= 1 && L - 1 > c[r]) ? prev[r] : -1;
+                prev[r] = b;
+            }
+            base += tot;
+            __syncthreads();
+        }
+    }
+}
+
+// box ends, parents found by search, child slots
+__global__ void tree_link_kernel(Tree T) {
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const int L = T.blevel[b], s = T.bstart[b];
+        int end = T.n;
+        if (L > 0) {
+            const uint32_t P = T.bkey[b];
+            const int sh = 32 - 2 * L;
+            int lo = s + 1, hi = T.n;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if ((T.key[mid] >> sh) > P) hi = mid;
+                else lo = mid + 1;
+            }
+            end = lo;
+            int p = T.bparent[b];
+            if (p < 0) {
+                // last box of level L-1 starting at or before s
+                int a = T.levoff[L - 1], z = T.levoff[L];
+                while (a < z) {
+                    int mid = (a + z) >> 1;
+                    if (T.bstart[mid] <= s) a = mid + 1;
+                    else z = mid;
+                }
+                p = a - 1;
+                T.bparent[b] = p;
+            }
+            if (p >= 0 && p < b) ((int *)&T.bchild[p])[P & 3u] = b;
+            else atomicOr(T.err, ERR_BOX_OVERFLOW);
+        }
+        T.bend[b] = end;
+    }
+}
+
+// ---------------------------------------------------------------- neighbour tables and lists
+
+// nb[b][k], k = (dy + 1) * 3 + (dx + 1): the box at b's level covering the
+// adjacent cell (dx, dy), else the coarser leaf covering it, else -1
+__global__ void nbr_kernel(Tree T, int *ticket, int *done) {
+    const int lane = threadIdx.x & 31;
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    for (;;) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(ticket, 1);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= B) return;
+        if (b == 0) {
+            if (lane < 9) T.nb[lane] = lane == 4 ? 0 : -1;
+        } else {
+            const int p = T.bparent[b];
+            if (p < 0 || p >= b) {                 // inconsistent tree (capacity error recorded)
+                if (lane == 0) atomicOr(T.err, ERR_BOX_OVERFLOW);
+                if (lane < 9) T.nb[b * 9 + lane] = -1;
+                __syncwarp();
+                if (lane == 0) *(volatile int *)&done[b] = 1;
+                continue;
+            }
+            if (lane == 0) wait_flag(&done[p], T.err);
+            __syncwarp();
+            const int L = T.blevel[b];
+            const uint32_t key = T.bkey[b];
+            const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
+            if (lane < 9) {
+                const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
+                int res = -1;
+                if (nx >= 0 && ny >= 0 && nx < (1 << L) && ny < (1 << L)) {
+                    const int px = bx >> 1, py = by >> 1;
+                    const int kk = ((ny >> 1) - py + 1) * 3 + ((nx >> 1) - px + 1);
+                    const int A = __ldcg(&T.nb[p * 9 + kk]);
+                    if (A >= 0) {
+                        if (T.blevel[A] == L - 1 && !T.bleaf[A]) res = ((const int *)&T.bchild[A])[((ny & 1) << 1) | (nx & 1)];
+                        else res = A;
+                    }
+                }
+                T.nb[b * 9 + lane] = res;
+            }
+        }
+        __syncwarp();
+        __threadfence();
+        if (lane == 0) *(volatile int *)&done[b] = 1;
+    }
+}
+
+// Interaction lists of box b.  mode 0 counts, mode 1 writes at the offsets.
+__device__ void box_lists(const Tree &T, int b, int mode) {
+    const int L = T.blevel[b];
+    const uint32_t key = T.bkey[b];
+    const bool leaf = T.bleaf[b] != 0;
+    int cu = 0, cv = 0, cw = 0, cx = 0;
+    int ou = 0, ov = 0, ow = 0, ox = 0;
+    if (mode == 1) {
+        ou = T.lcnt[4 * b];
+        ov = T.lcnt[4 * b + 1];
+        ow = T.lcnt[4 * b + 2];
+        ox = T.lcnt[4 * b + 3];
+    }
+    auto put = [&](int off, int k, int v) {
+        if (mode == 1) {
+            if (off + k < T.lcap) T.lidx[off + k] = v;
+            else atomicOr(T.err, ERR_LIST_OVERFLOW);
+        }
+    };
+    const int *nbb = T.nb + 9 * b;
+    if (leaf) {
+        put(ou, cu++, b);
+        for (int k = 0; k < 9; ++k) {
+            if (k == 4) continue;
+            const int A = nbb[k];
+            if (A < 0) continue;
+            bool seen = false;
+            for (int k2 = 0; k2 < k; ++k2)
+                if (k2 != 4 && nbb[k2] == A) seen = true;
+            if (seen) continue;
+            if (T.bleaf[A]) {
+                put(ou, cu++, A);
+                continue;
+            }
+            // internal colleague: its descendants along b's boundary
+            int stack[4 * MAXLEV + 4];
+            int sp = 0;
+            stack[sp++] = A;
+            while (sp > 0) {
+                const int D = stack[--sp];
+                const int4 ch = T.bchild[D];
+                const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+                for (int q = 3; q >= 0; --q) {
+                    const int C = cs[q];
+                    if (C < 0) continue;
+                    if (boxes_adjacent(T.bkey[C], T.blevel[C], key, L)) {
+                        if (T.bleaf[C]) put(ou, cu++, C);
+                        else if (sp < 4 * MAXLEV + 4) stack[sp++] = C;
+                    } else {
+                        put(ow, cw++, C);
+                    }
+                }
+            }
+        }
+    }
+    if (L >= 2) {
+        const int p = T.bparent[b];
+        const int *nbp = T.nb + 9 * p;
+        const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
+        for (int k = 0; k < 9; ++k) {
+            if (k == 4) continue;
+            const int A = nbp[k];
+            if (A < 0) continue;
+            if (T.blevel[A] == L - 1 && !T.bleaf[A]) {
+                const int4 ch = T.bchild[A];
+                const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+                for (int q = 0; q < 4; ++q) {
+                    const int C = cs[q];
+                    if (C < 0) continue;
+                    const uint32_t kc = T.bkey[C];
+                    const int dx = (int)compact_bits(kc) - bx, dy = (int)compact_bits(kc >> 1) - by;
+                    if (abs(dx) <= 1 && abs(dy) <= 1) continue;
+                    put(ov, cv++, (C << 6) | ((dx + 3) * 7 + (dy + 3)));
+                }
+            } else if (T.bleaf[A]) {
+                bool seen = false;
+                for (int k2 = 0; k2 < k; ++k2)
+                    if (k2 != 4 && nbp[k2] == A) seen = true;
+                if (seen) continue;
+                if (!boxes_adjacent(T.bkey[A], T.blevel[A], key, L)) put(ox, cx++, A);
+            }
+        }
+    }
+    if (mode == 0) {
+        T.lcnt[4 * b] = cu;
+        T.lcnt[4 * b + 1] = cv;
+        T.lcnt[4 * b + 2] = cw;
+        T.lcnt[4 * b + 3] = cx;
+    }
+}
+
+__global__ void lists_kernel(Tree T, int mode) {
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) box_lists(T, b, mode);
+}
+
+// exclusive scan over the 4 B list counts (B read on the device), in place;
+// total at lcnt[4 B].  Single block: B is at most a few 1e5 boxes here.
+__global__ void lists_scan_kernel(Tree T) {
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    const int total = 4 * min(T.levoff[NLEV], T.Bmax);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int carry = 0;
+    constexpr int ITEMS = 8;
+    for (int base = 0; base < total; base += blockDim.x * ITEMS) {
+        int v[ITEMS];
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            int i = base + threadIdx.x * ITEMS + k;
+            v[k] = i < total ? T.lcnt[i] : 0;
+            s += v[k];
+        }
+        int x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            int t = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t - w;
+            if (lane == 31) carry_s = t;
+        }
+        __syncthreads();
+        int e = carry + wsum[warp] + x - s;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            int i = base + threadIdx.x * ITEMS + k;
+            if (i < total) T.lcnt[i] = e;
+            e += v[k];
+        }
+        carry += carry_s;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        T.lcnt[total] = carry;
+        if (carry > T.lcap) atomicOr(T.err, ERR_LIST_OVERFLOW);
+    }
+}
+
+// ---------------------------------------------------------------- expansions
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 crcp(float2 a) {
+    float d = 1.0f / (a.x * a.x + a.y * a.y);
+    return make_float2(a.x * d, -a.y * d);
+}
+
+template <int PT>
+__device__ __forceinline__ void warp_reduce(float2 (&a)[PT + 1]) {
+#pragma unroll
+    for (int k = 0; k <= PT; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a[k].x += __shfl_xor_sync(0xffffffffu, a[k].x, o);
+            a[k].y += __shfl_xor_sync(0xffffffffu, a[k].y, o);
+        }
+    }
+}
+
+// value of a[lane] for lane <= PT (register array, compile-time indices)
+template <int PT>
+__device__ __forceinline__ float2 pick(const float2 (&a)[PT + 1], int lane) {
+    float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k <= PT; ++k)
+        if (k == lane) r = a[k];
+    return r;
+}
+
+struct ExpArgs {
+    Tree T;
+    float2 *M;            // multipole  [(PT + 1) * Bmax]
+    float2 *Lc;           // local      [(PT + 1) * Bmax]
+    int *arrive;          // [Bmax], zero between evaluations (reset by the last arriver)
+    int *done;            // [Bmax]
+    int *ticket;
+    const float *binom;   // [BN * BN]
+    int p;
+};
+
+// P2M at leaves, then M2M into each parent by its last child to finish
+template <int PT>
+__global__ void up_kernel(ExpArgs a) {
+    const Tree &T = a.T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    const Root rt = *T.root;
+    const int p = a.p;
+    for (int b = gw; b < B; b += nw) {
+        if (!T.bleaf[b]) continue;
+        const int L = T.blevel[b];
+        const BoxGeo g = box_geo(rt, T.bkey[b], L);
+        const float ir = 1.0f / g.r;
+        float2 acc[PT + 1];
+#pragma unroll
+        for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (int j = T.bstart[b] + lane; j < T.bend[b]; j += 32) {
+            const float4 s = T.pts[j];
+            const float2 w = make_float2((s.x - g.cx) * ir, (s.y - g.cy) * ir);
+            float2 pw = w;
+            acc[0].x += s.z;
+#pragma unroll
+            for (int k = 1; k <= PT; ++k) {
+                acc[k].x += s.z * pw.x;
+                acc[k].y += s.z * pw.y;
+                pw = cmul(pw, w);
+            }
+        }
+        warp_reduce<PT>(acc);
+        // a~_0 = sum q, a~_k = -sum q w^k / k
+        if (lane <= p) {
+            float2 v = pick<PT>(acc, lane);
+            if (lane > 0) v = cscale(v, -1.0f / (float)lane);
+            a.M[(size_t)b * (PT + 1) + lane] = v;
+        }
+        __threadfence();
+        int child = b;
+        for (;;) {
+            const int pb = T.bparent[child];
+            if (pb < 0) break;
+            int last = 0;
+            if (lane == 0) {
+                const int4 ch = T.bchild[pb];
+                const int nch = (ch.x >= 0) + (ch.y >= 0) + (ch.z >= 0) + (ch.w >= 0);
+                const int old = atomicAdd(&a.arrive[pb], 1);
+                last = old == nch - 1;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) break;
+            __threadfence();
+            if (lane == 0) a.arrive[pb] = 0;
+            // M2M: b~_l = -a~_0 u^l / l + sum_{k=1}^{l} a~_k 2^-k u^(l-k) C(l-1, k-1)
+            float2 out = make_float2(0.f, 0.f);
+            const int4 ch = T.bchild[pb];
+            const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+            for (int q = 0; q < 4; ++q) {
+                const int C = cs[q];
+                if (C < 0) continue;
+                const float2 u = make_float2((q & 1) ? 0.5f : -0.5f, (q & 2) ? 0.5f : -0.5f);
+                const float2 *mc = a.M + (size_t)C * (PT + 1);
+                const float2 a0 = __ldcg(&mc[0]);
+                if (lane == 0) {
+                    out.x += a0.x;
+                    out.y += a0.y;
+                } else if (lane <= p) {
+                    const int l = lane;
+                    // u^(l-k) for k = l down to 1, running power
+                    float2 pw = make_float2(1.f, 0.f);
+                    float2 s = make_float2(0.f, 0.f);
+                    float half = 1.0f;
+                    for (int k = 1; k <= l; ++k) half *= 0.5f;          // 2^-l
+                    for (int k = l; k >= 1; --k) {
+                        const float2 ak = __ldcg(&mc[k]);
+                        const float cb = a.binom[(l - 1) * BN + (k - 1)] * half;
+                        s = cadd(s, cscale(cmul(ak, pw), cb));
+                        pw = cmul(pw, u);
+                        half *= 2.0f;
+                    }
+                    // pw is now u^l
+                    s = cadd(s, cscale(cmul(a0, pw), -1.0f / (float)l));
+                    out = cadd(out, s);
+                }
+            }
+            if (lane <= p) a.M[(size_t)pb * (PT + 1) + lane] = out;
+            __threadfence();
+            child = pb;
+        }
+    }
+}
+
+// M2L over V, P2L over X, L2L from the parent, in level order
+template <int PT>
+__global__ void down_kernel(ExpArgs a) {
+    const Tree &T = a.T;
+    const int lane = threadIdx.x & 31;
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    const Root rt = *T.root;
+    const int p = a.p;
+    for (;;) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(a.ticket, 1);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= B) return;
+        const int L = T.blevel[b];
+        float2 *lb = a.Lc + (size_t)b * (PT + 1);
+        if (L <= 1) {
+            if (lane <= p) lb[lane] = make_float2(0.f, 0.f);
+            __syncwarp();
+            __threadfence();
+            if (lane == 0) *(volatile int *)&a.done[b] = 1;
+            continue;
+        }
+        float2 acc[PT + 1];
+#pragma unroll
+        for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
+        // M2L: b~_l += w^-l ( -a~_0 / l + sum_k (-1)^k a~_k w^-k C(l+k-1, k-1) ), w = 2 (dx + i dy)
+        const int vs = T.lcnt[4 * b + 1], ve = T.lcnt[4 * b + 2];
+        for (int e = vs + lane; e < ve; e += 32) {
+            const int ent = T.lidx[e];
+            const int D = ent >> 6, cls = ent & 63;
+            const float2 w = make_float2(2.0f * (float)(cls / 7 - 3), 2.0f * (float)(cls % 7 - 3));
+            const float2 iw = crcp(w);
+            const float2 *md = a.M + (size_t)D * (PT + 1);
+            const float2 a0 = md[0];
+            float2 ap[PT + 1];
+            float2 pw = iw;
+#pragma unroll
+            for (int k = 1; k <= PT; ++k) {
+                float2 v = k <= p ? md[k] : make_float2(0.f, 0.f);
+                v = cmul(v, pw);
+                ap[k] = (k & 1) ? make_float2(-v.x, -v.y) : v;
+                pw = cmul(pw, iw);
+            }
+            float2 pl = iw;
+#pragma unroll
+            for (int l = 1; l <= PT; ++l) {
+                float2 s = make_float2(-a0.x / (float)l, -a0.y / (float)l);
+#pragma unroll
+                for (int k = 1; k <= PT; ++k) {
+                    const float cb = a.binom[(l + k - 1) * BN + (k - 1)];
+                    s.x = fmaf(cb, ap[k].x, s.x);
+                    s.y = fmaf(cb, ap[k].y, s.y);
+                }
+                acc[l] = cadd(acc[l], cmul(s, pl));
+                pl = cmul(pl, iw);
+            }
+        }
+        // P2L: b~_l += -q t^l / l, t = r / (z_j - c)
+        const BoxGeo g = box_geo(rt, T.bkey[b], L);
+        const int xs = T.lcnt[4 * b + 3], xe = T.lcnt[4 * b + 4];
+        for (int e = xs; e < xe; ++e) {
+            const int C = T.lidx[e];
+            for (int j = T.bstart[C] + lane; j < T.bend[C]; j += 32) {
+                const float4 s = T.pts[j];
+                const float2 t = cscale(crcp(make_float2(s.x - g.cx, s.y - g.cy)), g.r);
+                float2 pw = t;
+#pragma unroll
+                for (int l = 1; l <= PT; ++l) {
+                    const float c = -s.z / (float)l;
+                    acc[l].x = fmaf(c, pw.x, acc[l].x);
+                    acc[l].y = fmaf(c, pw.y, acc[l].y);
+                    pw = cmul(pw, t);
+                }
+            }
+        }
+        warp_reduce<PT>(acc);
+        // L2L from the parent: c_l = b~_l(parent) 2^-l, Taylor shift by s = (+-1 +- i)
+        const int pb = T.bparent[b];
+        if (pb < 0 || pb >= b) {                   // inconsistent tree (capacity error recorded)
+            if (lane == 0) atomicOr(T.err, ERR_BOX_OVERFLOW);
+            if (lane <= p) lb[lane] = make_float2(0.f, 0.f);
+            __syncwarp();
+            if (lane == 0) *(volatile int *)&a.done[b] = 1;
+            continue;
+        }
+        if (lane == 0) wait_flag(&a.done[pb], T.err);
+        __syncwarp();
+        const uint32_t q = T.bkey[b] & 3u;
+        const float2 sft = make_float2((q & 1u) ? 1.f : -1.f, (q & 2u) ? 1.f : -1.f);
+        const float2 *lp = a.Lc + (size_t)pb * (PT + 1);
+        float2 mine = make_float2(0.f, 0.f);
+        if (lane >= 1 && lane <= p) {
+            const int m = lane;
+            float2 pw = make_float2(1.f, 0.f);
+            float scale = 1.0f;
+            for (int l = 1; l <= m; ++l) scale *= 0.5f;
+            for (int l = m; l <= p; ++l) {
+                const float2 cl = cscale(__ldcg(&lp[l]), scale * a.binom[l * BN + m]);
+                mine = cadd(mine, cmul(cl, pw));
+                pw = cmul(pw, sft);
+                scale *= 0.5f;
+            }
+            mine = cadd(mine, pick<PT>(acc, m));
+        }
+        if (lane <= p) lb[lane] = mine;
+        __syncwarp();
+        __threadfence();
+        if (lane == 0) *(volatile int *)&a.done[b] = 1;
+    }
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+struct LeafArgs {
+    ExpArgs e;
+    float2 *f;           // f[q - fbase]
+    const float *mass;
+    int64_t q0, fbase;
+    float kr;
+    int *ticket;
+};
+
+// L2P + M2P over W + P2P over U for every target of a leaf
+template <int PT>
+__global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs la) {
+    const Tree &T = la.e.T;
+    __shared__ float4 src[SRC_CAP];
+    __shared__ float2 red[LEAF_THREADS];
+    __shared__ int sb;
+    const int tid = threadIdx.x;
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    const Root rt = *T.root;
+    const int p = la.e.p;
+    for (;;) {
+        if (tid == 0) sb = atomicAdd(la.ticket, 1);
+        __syncthreads();
+        const int b = sb;
+        __syncthreads();
+        if (b >= B) return;
+        if (!T.bleaf[b]) continue;
+        const int L = T.blevel[b];
+        const BoxGeo g = box_geo(rt, T.bkey[b], L);
+        const int s = T.bstart[b], e = T.bend[b];
+        const int us = T.lcnt[4 * b], ue = T.lcnt[4 * b + 1];
+        const int ws = T.lcnt[4 * b + 2], we = T.lcnt[4 * b + 3];
+        const float2 *lb = la.e.Lc + (size_t)b * (PT + 1);
+        for (int tb = s; tb < e; tb += LEAF_THREADS) {
+            const int ntc = min(LEAF_THREADS, e - tb);
+            int pw2 = 1;
+            while (pw2 < ntc) pw2 <<= 1;
+            const int S = LEAF_THREADS / pw2;
+            const int t = tid & (pw2 - 1), h = tid / pw2;
+            const bool valid = t < ntc;
+            float4 z = valid ? T.pts[tb + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float fx = 0.f, fy = 0.f;
+            // P2P over the points of U, staged in shared memory
+            int ui = us, off = 0;
+            while (ui < ue) {
+                int cnt = 0;
+                while (ui < ue && cnt < SRC_CAP) {
+                    const int C = T.lidx[ui];
+                    const int cs = T.bstart[C], ce = T.bend[C];
+                    const int take = min(ce - cs - off, SRC_CAP - cnt);
+                    for (int k = tid; k < take; k += LEAF_THREADS) src[cnt + k] = T.pts[cs + off + k];
+                    cnt += take;
+                    off += take;
+                    if (off == ce - cs) {
+                        ++ui;
+                        off = 0;
+                    }
+                }
+                __syncthreads();
+                if (valid) {
+#pragma unroll 4
+                    for (int j = h; j < cnt; j += S) {
+                        const float4 q = src[j];
+                        const float dx = z.x - q.x, dy = z.y - q.y;
+                        const float r2 = fmaf(dx, dx, dy * dy);
+                        // a coincident pair (the target itself) has dx = dy = 0 and adds 0
+                        const float w = q.z * rcp_approx(fmaxf(r2, 1e-30f));
+                        fx = fmaf(w, dx, fx);
+                        fy = fmaf(w, dy, fy);
+                    }
+                }
+                __syncthreads();
+            }
+            // far field E(z) (complex); the force direction is conj(E)
+            float2 E = make_float2(0.f, 0.f);
+            if (valid) {
+                // M2P: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
+                for (int k = ws + h; k < we; k += S) {
+                    const int D = T.lidx[k];
+                    const BoxGeo gd = box_geo(rt, T.bkey[D], T.blevel[D]);
+                    const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
+                    const float2 idz = crcp(dz);
+                    const float2 tt = cscale(idz, gd.r);
+                    const float2 *md = la.e.M + (size_t)D * (PT + 1);
+                    float2 hs = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int kk = PT; kk >= 1; --kk) {
+                        if (kk <= p) hs = cadd(cmul(hs, tt), cscale(md[kk], (float)kk));
+                    }
+                    hs = cmul(hs, tt);
+                    const float2 a0 = md[0];
+                    E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
+                }
+                // L2P: E += (1/r) sum_l l b~_l v^(l-1), v = (z - c) / r
+                if (h == 0) {
+                    const float ir = 1.0f / g.r;
+                    const float2 v = make_float2((z.x - g.cx) * ir, (z.y - g.cy) * ir);
+                    float2 hs = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int l = PT; l >= 1; --l) {
+                        if (l <= p) hs = cadd(cmul(hs, v), cscale(lb[l], (float)l));
+                    }
+                    E = cadd(E, cscale(hs, ir));
+                }
+            }
+            red[tid] = make_float2(fx + E.x, fy - E.y);
+            __syncthreads();
+            if (valid && h == 0) {
+                float2 F = red[t];
+                for (int hh = 1; hh < S; ++hh) {
+                    const float2 o = red[hh * pw2 + t];
+                    F.x += o.x;
+                    F.y += o.y;
+                }
+                const int o = __float_as_int(z.w);
+                const float km = la.kr * z.z;
+                la.f[la.q0 + o - la.fbase] = make_float2(km * F.x, km * F.y);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+struct FmmPlan {
+    bgl_graph *g = nullptr;
+    int64_t c = 0, q0 = 0;
+    int n = 0, p = 8, PT = 8, S = 64, Bmax = 1, ntiles = 1, lcap = 1, grid_p = 1;
+    float kr = 1.f;
+    DevBuf<Root> root;
+    DevBuf<float4> part;
+    DevBuf<unsigned> counter;
+    DevBuf<uint32_t> key, idx;
+    DevBuf<float4> pts;
+    DevBuf<int8_t> cl, lam, bleaf;
+    DevBuf<int> tcnt, levoff, bstart, bend, blevel, bparent, nb, lcnt, lidx;
+    DevBuf<uint32_t> bkey;
+    DevBuf<int4> bchild;
+    DevBuf<float2> M, Lc;
+    DevBuf<int> arrive, done, tickets, err;
+    DevBuf<float> binom;
+};
+
+FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
+    bgl_ctx *ctx = g->ctx;
+    Allocator *A = ctx->alloc;
+    cudaStream_t s = ctx->stream;
+    FmmPlan *pl = new FmmPlan();
+    try {
+        pl->g = g;
+        pl->c = c;
+        pl->q0 = g->h_comp_off[c];
+        const int64_t n64 = g->h_comp_off[c + 1] - pl->q0;
+        BGL_REQUIRE(n64 < (int64_t(1) << 30), "fmm: component too large");
+        pl->n = (int)n64;
+        pl->p = p->fmm_p;
+        pl->PT = p->fmm_p <= 8 ? 8 : (p->fmm_p <= 16 ? 16 : 24);
+        pl->S = p->leaf_size;
+        pl->kr = (float)p->kr;
+        const int n = std::max(pl->n, 1);
+        // boxes: internal boxes hold > S points, at most n/(S+1) per level for
+        // levels 0..15; every other box is a child of one
+        int64_t bmax = 1 + 4 * (int64_t)MAXLEV * (n / (pl->S + 1) + 1);
+        bmax = std::min<int64_t>(bmax, (int64_t)NLEV * n + 1);
+        pl->Bmax = (int)bmax;
+        pl->ntiles = (n + TREE_TILE - 1) / TREE_TILE;
+        // list entries: U <= 17 per leaf, V <= 27, W and X <= 8 per box
+        pl->lcap = (int)std::min<int64_t>((int64_t)60 * bmax + 64, (int64_t)1 << 30);
+        pl->root.reset(A, 1);
+        pl->part.reset(A, 1024);
+        pl->counter.reset(A, 1);
+        pl->key.reset(A, n);
+        pl->idx.reset(A, n);
+        pl->pts.reset(A, n);
+        pl->cl.reset(A, n);
+        pl->lam.reset(A, n);
+        pl->tcnt.reset(A, (size_t)NLEV * pl->ntiles + 1);
+        pl->levoff.reset(A, NLEV + 1);
+        pl->bstart.reset(A, bmax);
+        pl->bend.reset(A, bmax);
+        pl->blevel.reset(A, bmax);
+        pl->bparent.reset(A, bmax);
+        pl->bkey.reset(A, bmax);
+        pl->bleaf.reset(A, bmax);
+        pl->bchild.reset(A, bmax);
+        pl->nb.reset(A, 9 * bmax);
+        pl->lcnt.reset(A, 4 * bmax + 1);
+        pl->lidx.reset(A, pl->lcap);
+        pl->M.reset(A, (size_t)(pl->PT + 1) * bmax);
+        pl->Lc.reset(A, (size_t)(pl->PT + 1) * bmax);
+        pl->arrive.reset(A, bmax);
+        pl->done.reset(A, bmax);
+        pl->tickets.reset(A, 4);
+        pl->err.reset(A, 1);
+        BGL_CUDA(cudaMemsetAsync(pl->counter.p, 0, sizeof(unsigned), s));
+        BGL_CUDA(cudaMemsetAsync(pl->arrive.p, 0, sizeof(int) * bmax, s));
+        BGL_CUDA(cudaMemsetAsync(pl->err.p, 0, sizeof(int), s));
+        std::vector<float> bn(BN * BN, 0.f);
+        for (int i = 0; i < BN; ++i) {
+            double v = 1.0;
+            for (int k = 0; k <= i; ++k) {
+                bn[i * BN + k] = (float)v;
+                v = v * (double)(i - k) / (double)(k + 1);
+            }
+        }
+        pl->binom.reset(A, BN * BN);
+        BGL_CUDA(cudaMemcpyAsync(pl->binom.p, bn.data(), sizeof(float) * bn.size(), cudaMemcpyHostToDevice, s));
+        BGL_CUDA(cudaStreamSynchronize(s));
+        pl->grid_p = ctx->num_sms * 8;
+    } catch (...) {
+        delete pl;
+        throw;
+    }
+    return pl;
+}
+
 void fmm_destroy(FmmPlan *pl) { delete pl; }
-void fmm_repulsion(FmmPlan *, const float2 *, int64_t, float2 *, int64_t) {}
+
+static Tree make_tree(FmmPlan *pl) {
+    Tree T;
+    T.key = pl->key.p;
+    T.pts = pl->pts.p;
+    T.n = pl->n;
+    T.bstart = pl->bstart.p;
+    T.bend = pl->bend.p;
+    T.blevel = pl->blevel.p;
+    T.bparent = pl->bparent.p;
+    T.bkey = pl->bkey.p;
+    T.bleaf = pl->bleaf.p;
+    T.bchild = pl->bchild.p;
+    T.levoff = pl->levoff.p;
+    T.nb = pl->nb.p;
+    T.lcnt = pl->lcnt.p;
+    T.lidx = pl->lidx.p;
+    T.lcap = pl->lcap;
+    T.Bmax = pl->Bmax;
+    T.root = pl->root.p;
+    T.err = pl->err.p;
+    return T;
+}
+
+template <int PT>
+static void fmm_expansions(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase) {
+    cudaStream_t s = pl->g->ctx->stream;
+    ExpArgs a;
+    a.T = T;
+    a.M = pl->M.p;
+    a.Lc = pl->Lc.p;
+    a.arrive = pl->arrive.p;
+    a.done = pl->done.p;
+    a.ticket = pl->tickets.p + 1;
+    a.binom = pl->binom.p;
+    a.p = pl->p;
+    up_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
+    BGL_LAUNCH_CHECK();
+    BGL_CUDA(cudaMemsetAsync(pl->done.p, 0, sizeof(int) * pl->Bmax, s));
+    down_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
+    BGL_LAUNCH_CHECK();
+    LeafArgs la;
+    la.e = a;
+    la.f = f;
+    la.mass = pl->g->mass.p;
+    la.q0 = pl->q0;
+    la.fbase = fbase;
+    la.kr = pl->kr;
+    la.ticket = pl->tickets.p + 2;
+    leaf_kernel<PT><<<pl->g->ctx->num_sms * 8, LEAF_THREADS, 0, s>>>(la);
+    BGL_LAUNCH_CHECK();
+}
+
+void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase) {
+    if (pl->n <= 0) return;
+    bgl_ctx *ctx = pl->g->ctx;
+    cudaStream_t s = ctx->stream;
+    const int n = pl->n;
+    const float2 *xl = xy + (pl->q0 - qbase);
+    const float *ml = pl->g->mass.p + pl->q0;
+    BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 4, s));
+    bbox_kernel<<<std::min<int64_t>(1024, nblk(n, 256)), 256, 0, s>>>(xl, n, pl->part.p, pl->counter.p, pl->root.p,
+                                                                      pl->err.p);
+    BGL_LAUNCH_CHECK();
+    keys_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p);
+    BGL_LAUNCH_CHECK();
+    radix_sort_u32(ctx, pl->key.p, pl->idx.p, n, 32);
+    gather_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, ml, pl->idx.p, n, pl->pts.p);
+    BGL_LAUNCH_CHECK();
+    Tree T = make_tree(pl);
+    tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
+                                                          pl->ntiles);
+    BGL_LAUNCH_CHECK();
+    tree_scan_kernel<<<1, 1024, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p);
+    BGL_LAUNCH_CHECK();
+    BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * pl->Bmax, s));
+    tree_emit_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(T, pl->cl.p, pl->lam.p, pl->tcnt.p, pl->ntiles, pl->Bmax);
+    BGL_LAUNCH_CHECK();
+    tree_link_kernel<<<pl->grid_p, 256, 0, s>>>(T);
+    BGL_LAUNCH_CHECK();
+    BGL_CUDA(cudaMemsetAsync(pl->done.p, 0, sizeof(int) * pl->Bmax, s));
+    nbr_kernel<<<pl->grid_p, 256, 0, s>>>(T, pl->tickets.p, pl->done.p);
+    BGL_LAUNCH_CHECK();
+    lists_kernel<<<pl->grid_p, 128, 0, s>>>(T, 0);
+    BGL_LAUNCH_CHECK();
+    lists_scan_kernel<<<1, 1024, 0, s>>>(T);
+    BGL_LAUNCH_CHECK();
+    lists_kernel<<<pl->grid_p, 128, 0, s>>>(T, 1);
+    BGL_LAUNCH_CHECK();
+    if (pl->PT == 8) fmm_expansions<8>(pl, T, f, fbase);
+    else if (pl->PT == 16) fmm_expansions<16>(pl, T, f, fbase);
+    else fmm_expansions<24>(pl, T, f, fbase);
+}
+
+int fmm_error(FmmPlan *pl) {
+    int e = 0;
+    BGL_CUDA(cudaMemcpyAsync(&e, pl->err.p, sizeof(int), cudaMemcpyDeviceToHost, pl->g->ctx->stream));
+    BGL_CUDA(cudaStreamSynchronize(pl->g->ctx->stream));
+    return e;
+}
 
 }  // namespace bgl

@@ -16,4 +16,9 @@ void fmm_destroy(FmmPlan *pl);
 // only (no host synchronisation), so it can be captured in a CUDA graph.
 void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase);
 
+// Error bits raised on the device since the plan was made (synchronises):
+// 1 a bounded wait gave up, 2 list capacity exceeded, 4 box capacity
+// exceeded, 8 non-finite bounding box.
+int fmm_error(FmmPlan *pl);
+
 }  // namespace bgl

@@ -1,0 +1,184 @@
+"""GPU parity of the Fast Multipole repulsion (Section 3.2.1).
+
+The FMM approximates the exact all-pairs repulsion; its reference is the
+oracle's FP64 exact sum (and the GPU's FP32 exact sum for whole-component
+RMS errors).  Error measure per node:
+  e_i = |F_fmm(i) - F_exact(i)| / (kr m_i sum_j m_j / |p_i - p_j|),
+bounded by the truncation ceiling 2 (1 + rho) rho^(p+1) / (1 - rho) of the
+interaction-list geometry, rho = sqrt(2) / (4 - sqrt(2)) (well-separated
+boxes are at least two box widths apart), and never asked to beat the
+FP32 floor of the direct sum."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+RHO = math.sqrt(2) / (4 - math.sqrt(2))
+
+
+def ceiling(p):
+    return max(2 * (1 + RHO) * RHO ** (p + 1) / (1 - RHO), 2e-5)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2403_03504_gb300 as bgl
+    c = bgl.Context(0)
+    yield c
+    c.close()
+
+
+def _bgl():
+    import paper_2403_03504_gb300 as bgl
+    return bgl
+
+
+class Path:
+    """A path graph on n nodes: one component whose local order is the id order."""
+
+    def __init__(self, ctx, n):
+        bgl = _bgl()
+        self.n = n
+        self.g = bgl.Graph.from_edges(ctx, n, np.arange(n - 1), np.arange(1, n))
+        self.g.components(labels=False)
+        self.og = oracle.graph_from_edges(n, np.arange(n - 1), np.arange(1, n))
+        self.mass = np.diff(self.og.off) + 1.0
+
+
+@pytest.fixture(scope="module")
+def path30k(ctx):
+    return Path(ctx, 30000)
+
+
+def _errors(fmm, exact, xy, pth, sample, kr=1.0):
+    o = oracle.fa2_forces(xy[:, 0], xy[:, 1], pth.mass, pth.og.off, pth.og.adj, kr, 1.0, targets=sample)
+    e = np.hypot(*(fmm[sample] - o["frep"]).T) / o["srep"]
+    rms = np.sqrt(np.mean(np.sum((fmm - exact) ** 2, 1)) / np.mean(np.sum(exact ** 2, 1)))
+    return e, rms
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_fmm_error_within_ceiling_and_decreasing(path30k, kind):
+    bgl = _bgl()
+    xy = synth.points(7, path30k.n, kind, scale=50.0)
+    exact = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy)
+    sample = np.random.default_rng(1).choice(path30k.n, 400, replace=False)
+    prev = None
+    for p in (4, 8, 12, 16, 24):
+        f = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=p), xy)
+        e, rms = _errors(f, exact, xy, path30k, sample)
+        assert np.all(np.isfinite(f))
+        assert e.max() <= ceiling(p), (kind, p, e.max(), ceiling(p))
+        if prev is not None and p <= 16:
+            assert rms < prev, (kind, p, rms, prev)          # geometric decrease in p
+        prev = rms
+    assert rms <= 1e-5, rms                                   # p = 24 reaches the FP32 direct-sum level
+
+
+def test_fmm_is_bitwise_reproducible(path30k):
+    bgl = _bgl()
+    xy = synth.points(3, path30k.n, "clustered", scale=10.0)
+    p = bgl.params(repulsion=bgl.REP_FMM, fmm_p=8)
+    a = path30k.g.fa2_repulsion(0, p, xy)
+    b = path30k.g.fa2_repulsion(0, p, xy)
+    assert np.array_equal(a, b)
+
+
+def test_fmm_small_leaf_sizes(path30k):
+    bgl = _bgl()
+    xy = synth.points(5, path30k.n, "clustered", scale=20.0)
+    exact = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy)
+    sample = np.random.default_rng(2).choice(path30k.n, 200, replace=False)
+    for leaf in (1, 7, 32, 200):
+        f = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=12, leaf_size=leaf), xy)
+        e, _ = _errors(f, exact, xy, path30k, sample)
+        assert e.max() <= ceiling(12), (leaf, e.max())
+
+
+@pytest.mark.parametrize("case", ["tiny", "coincident", "collinear", "far_clusters", "wide_range"])
+def test_fmm_degenerate_geometries(ctx, case):
+    bgl = _bgl()
+    rng = np.random.default_rng(11)
+    if case == "tiny":
+        n = 40                                   # one leaf: pure P2P
+        xy = rng.uniform(-1, 1, (n, 2))
+    elif case == "coincident":
+        n = 3000                                 # every point at the same place: no force
+        xy = np.tile([[0.25, -3.0]], (n, 1))
+    elif case == "collinear":
+        n = 5000
+        xy = np.stack([rng.uniform(-10, 10, n), np.full(n, 2.0)], 1)
+    elif case == "far_clusters":
+        n = 6000                                 # deep tree around two tight clusters
+        xy = np.concatenate([rng.normal(0, 1e-3, (n // 2, 2)), rng.normal(0, 1e-3, (n // 2, 2)) + [100.0, 40.0]])
+    else:
+        n = 6000                                 # scales from 1e-3 to 1e3
+        r = 10 ** rng.uniform(-3, 3, n)
+        t = rng.uniform(0, 2 * np.pi, n)
+        xy = np.stack([r * np.cos(t), r * np.sin(t)], 1)
+    xy = xy.astype(np.float32)
+    pth = Path(ctx, n)
+    exact = pth.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy)
+    f = pth.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=16), xy)
+    assert np.all(np.isfinite(f))
+    if case == "coincident":
+        assert np.all(f == 0) and np.all(exact == 0)
+        return
+    sample = np.arange(n) if n <= 500 else np.random.default_rng(3).choice(n, 300, replace=False)
+    e, _ = _errors(f, exact, xy, pth, sample)
+    assert e.max() <= ceiling(16), (case, e.max())
+    pth.g.destroy()
+
+
+def test_fmm_forces_c2_giant(ctx):
+    """The full-size giant component: FMM against the GPU exact sum on every
+    node and against the oracle on 2000 sampled nodes."""
+    bgl = _bgl()
+    tx = synth.tx_lists(**synth.C2)
+    g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    g.components(labels=False)
+    coff, _, nodes = g.component_nodes()
+    off, adj = g.csr()
+    vs = nodes[coff[0]:coff[1]]
+    pos = np.full(len(off) - 1, -1, np.int64)
+    pos[vs] = np.arange(len(vs))
+    loff = np.zeros(len(vs) + 1, np.int64)
+    loff[1:] = np.cumsum(np.diff(off)[vs])
+    ladj = pos[np.concatenate([adj[off[v]:off[v + 1]] for v in vs])].astype(np.int32)
+    mass = np.diff(loff) + 1.0
+    x, y = oracle.init_positions(2, vs)
+    xy = np.stack([x, y], 1).astype(np.float32) * 300.0
+    exact = g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy)
+    sample = np.random.default_rng(2).choice(len(vs), 2000, replace=False)
+    o = oracle.fa2_forces(xy[:, 0], xy[:, 1], mass, loff, ladj, 1.0, 1.0, targets=sample)
+    for p in (8, 16):
+        f = g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=p), xy)
+        e = np.hypot(*(f[sample] - o["frep"]).T) / o["srep"]
+        rms = np.sqrt(np.mean(np.sum((f - exact) ** 2, 1)) / np.mean(np.sum(exact ** 2, 1)))
+        assert e.max() <= ceiling(p), (p, e.max())
+        assert rms <= ceiling(p), (p, rms)
+    g.destroy()
+
+
+def test_fmm_fa2_iterations_track_exact(ctx):
+    """Two ForceAtlas2 iterations with FMM repulsion (p = 16) stay with the
+    exact-repulsion iterations on the C1 giant component."""
+    bgl = _bgl()
+    tx = synth.tx_lists(**synth.C1)
+    g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    g.components(labels=False)
+    coff, _, nodes = g.component_nodes()
+    vs = nodes[coff[0]:coff[1]]
+    x, y = oracle.init_positions(0, vs)
+    xy = np.stack([x, y], 1).astype(np.float32)
+    a, sa = g.fa2_step(0, bgl.params(repulsion=bgl.REP_EXACT), 2, xy)
+    b, sb = g.fa2_step(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=16, leaf_size=32), 2, xy)
+    diag = math.hypot(np.ptp(a[:, 0]), np.ptp(a[:, 1]))
+    assert np.max(np.hypot(*(a - b).T)) <= 1e-3 * diag
+    assert np.allclose(sa, sb, rtol=1e-3)
+    g.destroy()

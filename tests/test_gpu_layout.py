@@ -168,16 +168,32 @@ def test_fa2_exact_forces_c1(c1, seed):
         ref = o["frep"] + o["fatt"] + o["fgrav"]
         assert _rel_force_err(f, ref, o["sabs"]) <= 1e-5
         fr = c1.g.fa2_repulsion(0, p, xy)
-        rep_scale = kr * mass * np.array([np.sum(mass / np.maximum(np.hypot(xy[i, 0] - xy[:, 0], xy[i, 1] - xy[:, 1]), 1e-300)
-                                                 * (np.arange(len(vs)) != i)) for i in range(len(vs))])
-        assert _rel_force_err(fr, o["frep"], rep_scale) <= 1e-5
+        assert _rel_force_err(fr, o["frep"], o["srep"]) <= 1e-5
 
 
-def test_fa2_ten_iterations_match_oracle(c1):
+def test_fa2_three_iterations_from_random_start(c1):
+    # from random positions the iteration amplifies differences about tenfold
+    # per iteration (the oracle against itself: 1e-7 -> 3e-5 of the diagonal
+    # in 3 iterations, 4e-2 in 10), so positions are compared after 3
     bgl = _bgl()
     vs, loff, ladj, mass = c1.comp(0)
     x, y = oracle.init_positions(0, vs)
     xy = np.stack([x, y], 1).astype(np.float32)
+    got, stats = c1.g.fa2_step(0, bgl.params(repulsion=bgl.REP_EXACT), 3, xy)
+    st, ostats = oracle.fa2_run(xy[:, 0], xy[:, 1], mass, loff, ladj, 3)
+    diag = math.hypot(np.ptp(st.x), np.ptp(st.y))
+    assert np.max(np.hypot(got[:, 0] - st.x, got[:, 1] - st.y)) <= 1e-3 * diag
+    assert np.allclose(stats, ostats, rtol=1e-4)
+
+
+def test_fa2_ten_iterations_match_oracle(c1):
+    # ten fresh iterations (F_-1 = 0, s_G = 1) from a relaxed layout: the
+    # oracle's 50-iteration result, rounded to FP32
+    bgl = _bgl()
+    vs, loff, ladj, mass = c1.comp(0)
+    x, y = oracle.init_positions(0, vs)
+    st0, _ = oracle.fa2_run(x, y, mass, loff, ladj, 50)
+    xy = np.stack([st0.x, st0.y], 1).astype(np.float32)
     for variant in (0, 1):
         p = bgl.params(repulsion=bgl.REP_EXACT, swing_variant=variant)
         got, stats = c1.g.fa2_step(0, p, 10, xy)
