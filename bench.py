@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the layout pipeline on the 200k-transaction workload.
+
+One step = the whole hot path on one synthetic transaction graph (200,000
+transactions, ~4.8e5 addresses, seed 2): graph build, components, size
+split, Kamada-Kawai on the components of at most 50 nodes, and 500
+ForceAtlas2 iterations (FMM repulsion, p = 8, leaf 64) on the rest.
+Metric: ForceAtlas2 node-updates per second = nodes in ForceAtlas2
+components x iterations / step time.
+
+  value  inputs resident in HBM before the timed region (bgl_graph_build_dev,
+         bgl_layout_dev); L2 flushed between steps (256 MiB write)
+  e2e    the same through the host-memory C ABI (bgl_graph_build,
+         bgl_layout): host->device copy of the transaction lists and
+         device->host copy of the coordinates inside every step
+
+Multi-GPU: every rank lays out its own replica of the workload (the
+components of one graph are independent, nothing is exchanged); value is the
+sum of node-updates over ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 oracle (exact repulsion) on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FA2 node-updates/s (FMM vs exact) at stated force error; layout p50/p99 latency"
+UNIT = "node-updates/s"
+CONFIG_NAME = "fmm-fa2-200k-tx"
+
+# P2P pair throughput peak: 152 SMs x 2070 MHz x 16 pairs/clk/SM (one MUFU
+# reciprocal per pair; 16 MUFU results per clock per SM; 7 FP32-pipe ops per
+# pair need 7/128 clk, so the MUFU is the binding unit)
+SMS, SM_MAX_MHZ, MUFU_PER_CLK = 152, 2070.0, 16.0
+PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * MUFU_PER_CLK
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(tx, budget_s: float, giant_only=True):
+    """Exact FP64 ForceAtlas2 force evaluations per second on the giant
+    component, timed on a bounded sample of target nodes (each node update
+    is one full force evaluation plus an O(1) step)."""
+    import oracle
+    og = oracle.graph_build(tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    label, _ = oracle.components(og.off, og.adj)
+    comp_off, _, nodes = oracle.component_order(label)
+    vs = nodes[comp_off[0]:comp_off[1]]
+    pos = np.full(og.n_nodes, -1, np.int64)
+    pos[vs] = np.arange(len(vs))
+    loff = np.zeros(len(vs) + 1, np.int64)
+    loff[1:] = np.cumsum(np.diff(og.off)[vs])
+    ladj = pos[np.concatenate([og.adj[og.off[v]:og.off[v + 1]] for v in vs])].astype(np.int32)
+    mass = np.diff(loff) + 1.0
+    x, y = oracle.init_positions(0, vs)
+    rng = np.random.default_rng(0)
+    k = 64
+    t0 = time.perf_counter()
+    oracle.fa2_forces(x, y, mass, loff, ladj, targets=rng.choice(len(vs), k, replace=False))
+    dt = time.perf_counter() - t0
+    k2 = int(max(64, min(len(vs), k * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.fa2_forces(x, y, mass, loff, ladj, targets=rng.choice(len(vs), k2, replace=False))
+    dt2 = time.perf_counter() - t0
+    return dict(value=k2 / dt2, unit=UNIT, cores=oracle.threads(), kind="oracle",
+                sample=f"exact FP64 forces (repulsion, attraction, gravity) of {k2} random nodes of the "
+                       f"{len(vs)}-node giant component at its initial positions, {dt2:.1f} s; "
+                       f"node-updates/s = nodes evaluated / time"), len(vs)
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores: node-updates/s on bounded samples."""
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    tx = synth.tx_lists(**synth.C2)
+    og = oracle.graph_build(tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    label, _ = oracle.components(og.off, og.adj)
+    comp_off, _, nodes = oracle.component_order(label)
+    vs = nodes[comp_off[0]:comp_off[1]]
+    pos = np.full(og.n_nodes, -1, np.int64)
+    pos[vs] = np.arange(len(vs))
+    loff = np.zeros(len(vs) + 1, np.int64)
+    loff[1:] = np.cumsum(np.diff(og.off)[vs])
+    ladj = pos[np.concatenate([og.adj[og.off[v]:og.off[v + 1]] for v in vs])].astype(np.int32)
+    mass = np.diff(loff) + 1.0
+    x, y = oracle.init_positions(0, vs)
+    rng = np.random.default_rng(0)
+    per_step = 512
+    for _ in range(args.warmup):
+        oracle.fa2_forces(x, y, mass, loff, ladj, targets=rng.choice(len(vs), 32, replace=False))
+    times = []
+    for _ in range(args.steps):
+        tg = rng.choice(len(vs), per_step, replace=False)
+        t0 = time.perf_counter()
+        oracle.fa2_forces(x, y, mass, loff, ladj, targets=tg)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    sample = (f"per step: exact FP64 forces of {per_step} random nodes of the {len(vs)}-node giant component "
+              f"(one node update each)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIG_NAME, "n_tx": 200000, "seed": 2, "giant_nodes": int(len(vs))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bgl", choices=["bgl", "reference"])
+    ap.add_argument("--iters", type=int, default=500)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--exact-iters", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="profiling case: FMM and exact repulsion on the giant component only")
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import synth
+    import paper_2403_03504_gb300 as bgl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tx = synth.tx_lists(**synth.C2)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = bgl.Context(local)
+    ctx.set_stream(stream)
+    p = bgl.params(seed=0, fa2_iters=args.iters, repulsion=bgl.REP_AUTO, fmm_p=args.p, leaf_size=64,
+                   kk_max_nodes=50, fmm_min_nodes=8192)
+
+    # device-resident inputs
+    d_in = [torch.from_numpy(a).to(dev) for a in (tx.in_off, tx.in_addr.view(np.int64), tx.out_off,
+                                                  tx.out_addr.view(np.int64))]
+    # pinned host inputs / output for the end-to-end leg
+    h_in = [torch.from_numpy(a).pin_memory() for a in (tx.in_off, tx.in_addr.view(np.int64), tx.out_off,
+                                                       tx.out_addr.view(np.int64))]
+    torch.cuda.synchronize()
+
+    g0 = bgl.Graph.build_dev(ctx, tx.n_tx, len(tx.in_addr), len(tx.out_addr), *d_in)
+    g0.components(labels=False)
+    if args.kernels_only:
+        # a few launches of each repulsion kernel on the 5.5e5-node giant component
+        coff, _, nodes = g0.component_nodes()
+        xy0 = np.random.default_rng(0).normal(0, 300, (int(coff[1] - coff[0]), 2)).astype(np.float32)
+        for _ in range(3):
+            g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=args.p), xy0)
+        g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy0)
+        ctx.sync()
+        print(json.dumps({"kernels_only": True, "giant": int(coff[1] - coff[0])}))
+        return
+    n_nodes = g0.sizes()["n_nodes"]
+    n_kk, n_fa2 = g0.split(p.kk_max_nodes)
+    coff, _, nodes = g0.component_nodes()
+    fa2_nodes = int(coff[n_fa2])
+    giant = int(coff[1] - coff[0])
+    d_xy = torch.empty((n_nodes, 2), dtype=torch.float32, device=dev)
+    h_xy = torch.empty((n_nodes, 2), dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step_dev():
+        g = bgl.Graph.build_dev(ctx, tx.n_tx, len(tx.in_addr), len(tx.out_addr), *d_in)
+        g.components(labels=False)
+        g.layout_dev(p, d_xy)
+        g.destroy()
+
+    def step_e2e():
+        g = bgl.Graph.build(ctx, *(t.numpy() for t in h_in[:1]), h_in[1].numpy().view(np.uint64),
+                            h_in[2].numpy(), h_in[3].numpy().view(np.uint64))
+        g.components(labels=False)
+        g.layout(p, out=h_xy.numpy())
+        g.destroy()
+
+    for _ in range(max(args.warmup, 3)):
+        step_dev()
+    ctx.sync()
+
+    # ---------------------------------------------------------------- timed: device-resident
+    launches0 = bgl.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))                     # L2 flush, outside the event pair
+                ev[k][0].record(stream)
+            step_dev()
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = (bgl.launch_count() - launches0) // max(args.steps, 1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    upd = float(fa2_nodes) * args.iters * args.steps
+    if dist:
+        t = torch.tensor([upd, total_s], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        upd, total_s = float(t[0]), float(tmax[1])
+    value = upd / total_s
+
+    # ---------------------------------------------------------------- timed: end to end (host buffers)
+    step_e2e()
+    e2e_times = []
+    for k in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_e2e()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times)
+    e2e_value = float(fa2_nodes) * args.iters * args.steps / e2e_s
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = h_xy.numel() * 4 + 8 * (len(coff))          # coordinates + component offsets
+
+    # ---------------------------------------------------------------- diagnostics (not timed)
+    xy_final = d_xy.cpu().numpy()
+    giant_xy = np.ascontiguousarray(xy_final[nodes[coff[0]:coff[1]]])
+    stats = g0.fmm_stats(0, p, giant_xy, reps=5)
+    leaf_s = stats["ms_leaf"] / 1e3
+    achieved = stats["p2p_pairs"] / leaf_s
+    exact = bgl.params(seed=0, repulsion=bgl.REP_EXACT)
+    g0.fa2_step(0, exact, 1, giant_xy)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g0.fa2_step(0, exact, args.exact_iters, giant_xy)
+    exact_s = time.perf_counter() - t0
+    exact_rate = giant * args.exact_iters / exact_s
+    f_ex = g0.fa2_repulsion(0, exact, giant_xy)
+    errs = {}
+    for pp in (8, 16):
+        f_f = g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=pp), giant_xy)
+        rms = float(np.sqrt(np.mean(np.sum((f_f - f_ex) ** 2, 1)) / np.mean(np.sum(f_ex ** 2, 1))))
+        errs[f"p{pp}_rms_rel"] = rms
+    p16 = bgl.params(seed=0, fa2_iters=args.iters, repulsion=bgl.REP_AUTO, fmm_p=16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = bgl.Graph.build_dev(ctx, tx.n_tx, len(tx.in_addr), len(tx.out_addr), *d_in)
+    g.components(labels=False)
+    g.layout_dev(p16, d_xy)
+    g.destroy()
+    torch.cuda.synchronize()
+    p16_s = time.perf_counter() - t0
+
+    clocks = clk.summary()
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu, _ = cpu_oracle_rate(tx, args.cpu_budget)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONFIG_NAME, "n_tx": tx.n_tx, "seed": 2, "n_nodes": n_nodes,
+                   "fa2_nodes": fa2_nodes, "giant_nodes": giant, "kk_components": n_kk, "fa2_iters": args.iters,
+                   "repulsion": "fmm", "fmm_p": args.p, "leaf_size": 64, "kk_max_nodes": 50, "kk_sweeps": 200,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "fmm leaf pass (L2P + M2P + P2P)", "achieved": achieved / 1e9,
+                     "peak": PAIR_PEAK / 1e9, "unit": "Gpairs/s", "frac": achieved / PAIR_PEAK, "traffic": None,
+                     "peak_source": "152 SMs x 2070 MHz x 16 MUFU rcp/clk/SM (one rcp per pair)"},
+        "force_error": {"reference": "GPU FP32 exact sum at the final layout", **errs},
+        "exact_fa2": {"value": exact_rate, "unit": UNIT, "iters": args.exact_iters, "nodes": giant},
+        "fmm_p16_step_ms": 1e3 * p16_s,
+        "fmm_profile": stats,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "step_ms": step_ms,
+        "e2e_step_ms": [1e3 * t for t in e2e_times],
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -226,6 +226,30 @@ bgl_status bgl_fa2_repulsion(bgl_graph *g, int64_t c, const bgl_params *p, const
 bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t iters, float *xy_inout,
                         double *stats_out);
 
+/* ---------------------------------------------------------------- profiling */
+
+#define BGL_FMM_NSTATS 13
+
+/*
+ * Profiling aid for the Fast Multipole repulsion (Section 3.2.1) on
+ * component c at local positions xy_in[2 n_c]: runs `reps` evaluations with
+ * p->fmm_p and p->leaf_size and fills out[BGL_FMM_NSTATS] with
+ *   0 boxes, 1 leaves, 2 depth (deepest level),
+ *   3 near-field pairs (targets x sources over the U lists, self pairs included),
+ *   4 M2L translations (V entries), 5 M2P terms (W entries x targets),
+ *   6 P2L terms (sources of the X entries),
+ *   7..12 mean device milliseconds of the phases: points (bounding box, Morton
+ *   keys, radix sort, gather), tree, interaction lists, upward pass (P2M,
+ *   M2M), downward pass (M2L, P2L, L2L), leaf pass (L2P, M2P, P2P).
+ * Synchronises the stream.
+ */
+bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, int32_t reps,
+                         double *out);
+
+/* Number of kernels this process has launched through the library so far
+ * (direct launches plus the kernel nodes of every CUDA graph replay). */
+int64_t bgl_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["BglError", "Context", "Graph", "Params", "params", "build", "lib_path",
+__all__ = ["BglError", "Context", "Graph", "Params", "params", "build", "lib_path", "launch_count", "FMM_STATS",
            "REP_EXACT", "REP_FMM", "REP_AUTO"]
 
 REP_EXACT, REP_FMM, REP_AUTO = 0, 1, 2
@@ -103,6 +103,8 @@ def _load():
         "bgl_fa2_forces": ([VP, I64, ctypes.POINTER(Params), VP, VP], I32),
         "bgl_fa2_repulsion": ([VP, I64, ctypes.POINTER(Params), VP, VP], I32),
         "bgl_fa2_step": ([VP, I64, ctypes.POINTER(Params), I32, VP, VP], I32),
+        "bgl_fmm_stats": ([VP, I64, ctypes.POINTER(Params), VP, I32, VP], I32),
+        "bgl_launch_count": ([], I64),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -110,6 +112,15 @@ def _load():
         fn.restype = res
     _lib = lib
     return lib
+
+
+FMM_STATS = ("boxes", "leaves", "depth", "p2p_pairs", "m2l", "m2p", "p2l", "ms_points", "ms_tree", "ms_lists",
+             "ms_up", "ms_down", "ms_leaf")
+
+
+def launch_count() -> int:
+    """Kernels launched through the library by this process so far."""
+    return int(_load().bgl_launch_count())
 
 
 def params(**kw) -> Params:
@@ -288,9 +299,13 @@ class Graph:
         self.ctx.check(self._lib.bgl_split(self.h, kk_max_nodes, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    def layout(self, p: Params | None = None):
+    def layout(self, p: Params | None = None, out: np.ndarray | None = None):
+        """Coordinates [n_nodes, 2] (float32) in node-id order; `out` may be a
+        preallocated (e.g. pinned) float32 array of that shape."""
         p = p or params()
-        out = np.zeros((self.sizes()["n_nodes"], 2), np.float32)
+        if out is None:
+            out = np.zeros((self.sizes()["n_nodes"], 2), np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == 2 * self.sizes()["n_nodes"]
         self.ctx.check(self._lib.bgl_layout(self.h, ctypes.byref(p), _hp(out)))
         return out
 
@@ -319,6 +334,12 @@ class Graph:
         f = np.zeros_like(xy)
         self.ctx.check(self._lib.bgl_fa2_repulsion(self.h, c, ctypes.byref(p), _hp(xy), _hp(f)))
         return f
+
+    def fmm_stats(self, c: int, p: Params, xy, reps: int = 3) -> dict:
+        xy = _arr(xy, np.float32)
+        out = np.zeros(len(FMM_STATS))
+        self.ctx.check(self._lib.bgl_fmm_stats(self.h, c, ctypes.byref(p), _hp(xy), reps, _hp(out)))
+        return dict(zip(FMM_STATS, out.tolist()))
 
     def fa2_step(self, c: int, p: Params, iters: int, xy):
         xy = np.array(xy, np.float32, order="C")

@@ -3,14 +3,20 @@
 // device pipeline.  No exception crosses the ABI: every entry point maps
 // failures to a bgl_status and keeps the message for bgl_last_error().
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
 #include "bgl_internal.cuh"
+#include "fmm.cuh"
 
 namespace bgl {
 
 void fail(bgl_status s, const std::string &msg) { throw Error(s, msg); }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
     if (e == cudaSuccess) return;
@@ -490,5 +496,30 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
         sync(g->ctx);
     });
 }
+
+bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, int32_t reps,
+                         double *out) {
+    if (!g || !xy_in || !out) return BGL_EINVAL;
+    return guarded(g->ctx, [&] {
+        check_params(p);
+        require_c(g, c);
+        BGL_REQUIRE(reps >= 1, "reps must be >= 1");
+        int64_t q0 = g->h_comp_off[c], n = g->h_comp_off[c + 1] - q0;
+        DevBuf<float2> xy(g->ctx->alloc, n);
+        h2d(g->ctx, xy.p, reinterpret_cast<const float2 *>(xy_in), n);
+        FmmPlan *pl = fmm_create(g, p, c);
+        try {
+            fmm_profile(pl, xy.p, q0, reps, out);
+            int e = fmm_error(pl);
+            if (e) fail(e & 1 ? BGL_ETIMEOUT : BGL_ENOMEM, "fmm_stats: device error bits " + std::to_string(e));
+        } catch (...) {
+            fmm_destroy(pl);
+            throw;
+        }
+        fmm_destroy(pl);
+    });
+}
+
+int64_t bgl_launch_count(void) { return bgl::launch_count(); }
 
 }  // extern "C"

@@ -24,7 +24,13 @@ struct Error : std::runtime_error {
 [[noreturn]] void fail(bgl_status s, const std::string &msg);
 void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 #define BGL_CUDA(call) ::bgl::check_cuda((call), #call, __FILE__, __LINE__)
-#define BGL_LAUNCH_CHECK() ::bgl::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+void count_launches(int64_t k);   // kernels launched through the library
+int64_t launch_count();
+#define BGL_LAUNCH_CHECK()                                                        \
+    do {                                                                          \
+        ::bgl::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); \
+        ::bgl::count_launches(1);                                                 \
+    } while (0)
 #define BGL_REQUIRE(cond, msg) \
     do {                       \
         if (!(cond)) ::bgl::fail(BGL_EINVAL, msg); \

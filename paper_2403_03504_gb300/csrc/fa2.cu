@@ -423,6 +423,7 @@ void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, in
     // capture one iteration, replay it
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    const int64_t before = launch_count();
     BGL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
         run.iteration(d_stats);
@@ -433,9 +434,22 @@ void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, in
         throw;
     }
     BGL_CUDA(cudaStreamEndCapture(s, &graph));
+    // captured launches run only when the graph is replayed
+    count_launches(before - launch_count());
+    size_t nn = 0;
+    int64_t kernels = 0;
+    BGL_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) BGL_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        BGL_CUDA(cudaGraphNodeGetType(nd, &t));
+        if (t == cudaGraphNodeTypeKernel) ++kernels;
+    }
     cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     BGL_CUDA(e);
+    count_launches(kernels * iters);
     try {
         for (int it = 0; it < iters; ++it) BGL_CUDA(cudaGraphLaunch(exec, s));
     } catch (...) {

@@ -1091,8 +1091,23 @@ static Tree make_tree(FmmPlan *pl) {
 }
 
 template <int PT>
-static void fmm_expansions(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase) {
-    cudaStream_t s = pl->g->ctx->stream;
+static void fmm_up(FmmPlan *pl, const ExpArgs &a) {
+    up_kernel<PT><<<pl->grid_p, 256, 0, pl->g->ctx->stream>>>(a);
+    BGL_LAUNCH_CHECK();
+}
+template <int PT>
+static void fmm_down(FmmPlan *pl, const ExpArgs &a) {
+    BGL_CUDA(cudaMemsetAsync(pl->done.p, 0, sizeof(int) * pl->Bmax, pl->g->ctx->stream));
+    down_kernel<PT><<<pl->grid_p, 256, 0, pl->g->ctx->stream>>>(a);
+    BGL_LAUNCH_CHECK();
+}
+template <int PT>
+static void fmm_leaf(FmmPlan *pl, const LeafArgs &la) {
+    leaf_kernel<PT><<<pl->g->ctx->num_sms * 8, LEAF_THREADS, 0, pl->g->ctx->stream>>>(la);
+    BGL_LAUNCH_CHECK();
+}
+
+static ExpArgs exp_args(FmmPlan *pl, const Tree &T) {
     ExpArgs a;
     a.T = T;
     a.M = pl->M.p;
@@ -1102,11 +1117,10 @@ static void fmm_expansions(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase)
     a.ticket = pl->tickets.p + 1;
     a.binom = pl->binom.p;
     a.p = pl->p;
-    up_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
-    BGL_LAUNCH_CHECK();
-    BGL_CUDA(cudaMemsetAsync(pl->done.p, 0, sizeof(int) * pl->Bmax, s));
-    down_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
-    BGL_LAUNCH_CHECK();
+    return a;
+}
+
+static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbase) {
     LeafArgs la;
     la.e = a;
     la.f = f;
@@ -1115,16 +1129,14 @@ static void fmm_expansions(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase)
     la.fbase = fbase;
     la.kr = pl->kr;
     la.ticket = pl->tickets.p + 2;
-    leaf_kernel<PT><<<pl->g->ctx->num_sms * 8, LEAF_THREADS, 0, s>>>(la);
-    BGL_LAUNCH_CHECK();
+    return la;
 }
 
-void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase) {
-    if (pl->n <= 0) return;
+// phase 0: bounding box, keys, sort, gather
+static void phase_points(FmmPlan *pl, const float2 *xl) {
     bgl_ctx *ctx = pl->g->ctx;
     cudaStream_t s = ctx->stream;
     const int n = pl->n;
-    const float2 *xl = xy + (pl->q0 - qbase);
     const float *ml = pl->g->mass.p + pl->q0;
     BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 4, s));
     bbox_kernel<<<std::min<int64_t>(1024, nblk(n, 256)), 256, 0, s>>>(xl, n, pl->part.p, pl->counter.p, pl->root.p,
@@ -1135,8 +1147,12 @@ void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int6
     radix_sort_u32(ctx, pl->key.p, pl->idx.p, n, 32);
     gather_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, ml, pl->idx.p, n, pl->pts.p);
     BGL_LAUNCH_CHECK();
-    Tree T = make_tree(pl);
-    tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
+}
+
+// phase 1: boxes in level order, ends, parents, children
+static void phase_tree(FmmPlan *pl, const Tree &T) {
+    cudaStream_t s = pl->g->ctx->stream;
+    tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, pl->n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
                                                           pl->ntiles);
     BGL_LAUNCH_CHECK();
     tree_scan_kernel<<<1, 1024, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p);
@@ -1146,6 +1162,11 @@ void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int6
     BGL_LAUNCH_CHECK();
     tree_link_kernel<<<pl->grid_p, 256, 0, s>>>(T);
     BGL_LAUNCH_CHECK();
+}
+
+// phase 2: neighbour tables and U/V/W/X lists
+static void phase_lists(FmmPlan *pl, const Tree &T) {
+    cudaStream_t s = pl->g->ctx->stream;
     BGL_CUDA(cudaMemsetAsync(pl->done.p, 0, sizeof(int) * pl->Bmax, s));
     nbr_kernel<<<pl->grid_p, 256, 0, s>>>(T, pl->tickets.p, pl->done.p);
     BGL_LAUNCH_CHECK();
@@ -1155,9 +1176,126 @@ void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int6
     BGL_LAUNCH_CHECK();
     lists_kernel<<<pl->grid_p, 128, 0, s>>>(T, 1);
     BGL_LAUNCH_CHECK();
-    if (pl->PT == 8) fmm_expansions<8>(pl, T, f, fbase);
-    else if (pl->PT == 16) fmm_expansions<16>(pl, T, f, fbase);
-    else fmm_expansions<24>(pl, T, f, fbase);
+}
+
+template <int PT>
+static void phases_expand(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase, cudaEvent_t *ev) {
+    cudaStream_t s = pl->g->ctx->stream;
+    const ExpArgs a = exp_args(pl, T);
+    fmm_up<PT>(pl, a);
+    if (ev) BGL_CUDA(cudaEventRecord(ev[0], s));
+    fmm_down<PT>(pl, a);
+    if (ev) BGL_CUDA(cudaEventRecord(ev[1], s));
+    fmm_leaf<PT>(pl, leaf_args(pl, a, f, fbase));
+}
+
+static void expand(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase, cudaEvent_t *ev) {
+    if (pl->PT == 8) phases_expand<8>(pl, T, f, fbase, ev);
+    else if (pl->PT == 16) phases_expand<16>(pl, T, f, fbase, ev);
+    else phases_expand<24>(pl, T, f, fbase, ev);
+}
+
+void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase) {
+    if (pl->n <= 0) return;
+    const float2 *xl = xy + (pl->q0 - qbase);
+    const Tree T = make_tree(pl);
+    phase_points(pl, xl);
+    phase_tree(pl, T);
+    phase_lists(pl, T);
+    expand(pl, T, f, fbase, nullptr);
+}
+
+namespace {
+
+// interaction counts: P2P pairs, M2P and P2L point-box terms
+__global__ void count_kernel(Tree T, unsigned long long *out) {
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    unsigned long long p2p = 0, m2p = 0, p2l = 0, leaves = 0, depth = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        depth = max(depth, (unsigned long long)T.blevel[b]);
+        const int X0 = T.lcnt[4 * b + 3], X1 = T.lcnt[4 * b + 4];
+        for (int e = X0; e < X1; ++e) {
+            const int C = T.lidx[e];
+            p2l += (unsigned long long)(T.bend[C] - T.bstart[C]);
+        }
+        if (!T.bleaf[b]) continue;
+        ++leaves;
+        const unsigned long long nt = (unsigned long long)(T.bend[b] - T.bstart[b]);
+        unsigned long long ns = 0;
+        for (int e = T.lcnt[4 * b]; e < T.lcnt[4 * b + 1]; ++e) {
+            const int C = T.lidx[e];
+            ns += (unsigned long long)(T.bend[C] - T.bstart[C]);
+        }
+        p2p += nt * ns;
+        m2p += nt * (unsigned long long)(T.lcnt[4 * b + 3] - T.lcnt[4 * b + 2]);
+    }
+    atomicAdd(&out[0], p2p);
+    atomicAdd(&out[1], m2p);
+    atomicAdd(&out[2], p2l);
+    atomicAdd(&out[3], leaves);
+    atomicMax(&out[4], depth);
+}
+
+}  // namespace
+
+void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double *out) {
+    bgl_ctx *ctx = pl->g->ctx;
+    cudaStream_t s = ctx->stream;
+    const float2 *xl = xy + (pl->q0 - qbase);
+    const Tree T = make_tree(pl);
+    DevBuf<float2> f(ctx->alloc, std::max(pl->n, 1));
+    cudaEvent_t ev[7];
+    for (auto &e : ev) BGL_CUDA(cudaEventCreate(&e));
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    try {
+        for (int r = 0; r < std::max(reps, 1); ++r) {
+            BGL_CUDA(cudaEventRecord(ev[0], s));
+            phase_points(pl, xl);
+            BGL_CUDA(cudaEventRecord(ev[1], s));
+            phase_tree(pl, T);
+            BGL_CUDA(cudaEventRecord(ev[2], s));
+            phase_lists(pl, T);
+            BGL_CUDA(cudaEventRecord(ev[3], s));
+            expand(pl, T, f.p, pl->q0, ev + 4);
+            BGL_CUDA(cudaEventRecord(ev[6], s));
+            BGL_CUDA(cudaEventSynchronize(ev[6]));
+            float ms;
+            const int order[7] = {0, 1, 2, 3, 4, 5, 6};
+            for (int k = 0; k < 6; ++k) {
+                BGL_CUDA(cudaEventElapsedTime(&ms, ev[order[k]], ev[order[k + 1]]));
+                acc[k] += ms;
+            }
+        }
+    } catch (...) {
+        for (auto &e : ev) cudaEventDestroy(e);
+        throw;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    DevBuf<unsigned long long> cnt(ctx->alloc, 5);
+    BGL_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 5, s));
+    count_kernel<<<pl->grid_p, 256, 0, s>>>(T, cnt.p);
+    BGL_LAUNCH_CHECK();
+    unsigned long long h[5];
+    int lev[NLEV + 1];
+    BGL_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaMemcpyAsync(lev, pl->levoff.p, sizeof(lev), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaStreamSynchronize(s));
+    int nbox = std::min(lev[NLEV], pl->Bmax);
+    // V entries per box from the list offsets
+    std::vector<int> offs(4 * (size_t)nbox + 1);
+    BGL_CUDA(cudaMemcpyAsync(offs.data(), pl->lcnt.p, sizeof(int) * offs.size(), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaStreamSynchronize(s));
+    long long m2l = 0;
+    for (int b = 0; b < nbox; ++b) m2l += offs[4 * b + 2] - offs[4 * b + 1];
+    const double R = std::max(reps, 1);
+    out[0] = nbox;
+    out[1] = (double)h[3];
+    out[2] = (double)h[4];
+    out[3] = (double)h[0];
+    out[4] = (double)m2l;
+    out[5] = (double)h[1];
+    out[6] = (double)h[2];
+    for (int k = 0; k < 6; ++k) out[7 + k] = acc[k] / R;
 }
 
 int fmm_error(FmmPlan *pl) {

@@ -16,6 +16,12 @@ void fmm_destroy(FmmPlan *pl);
 // only (no host synchronisation), so it can be captured in a CUDA graph.
 void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase);
 
+// Counts and per-phase device times of `reps` evaluations (synchronises);
+// out[13]: boxes, leaves, depth, P2P pairs, M2L translations, M2P terms,
+// P2L terms, then milliseconds of: points (bbox, keys, sort, gather), tree,
+// lists, upward pass, downward pass, leaf pass.
+void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double *out);
+
 // Error bits raised on the device since the plan was made (synchronises):
 // 1 a bounded wait gave up, 2 list capacity exceeded, 4 box capacity
 // exceeded, 8 non-finite bounding box.
