@@ -39,6 +39,7 @@ void Allocator::release_cache() {
 }
 
 void *Allocator::alloc(size_t bytes) {
+    if (forbid) throw Error(BGL_ESTATE, "internal: device allocation inside a captured CUDA graph");
     bytes = (bytes + 255) & ~size_t(255);
     {
         std::lock_guard<std::mutex> lk(mu_);

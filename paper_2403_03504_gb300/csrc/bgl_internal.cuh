@@ -49,6 +49,9 @@ class Allocator {
     void free(void *p);
     size_t cached_bytes() const { return cached_; }
     void release_cache();
+    // set while a stream capture is open: allocating then would bake a
+    // block that is freed after the capture into the replayed graph
+    bool forbid = false;
 
   private:
     int device_;
@@ -147,6 +150,16 @@ void scan_exclusive_i32(bgl_ctx *c, const int32_t *in, int32_t *out, int64_t n, 
 // keys/vals are sorted in place (with internal double buffers).  vals may be null.
 void radix_sort_u64(bgl_ctx *c, uint64_t *keys, uint32_t *vals, int64_t n, int bits);
 void radix_sort_u32(bgl_ctx *c, uint32_t *keys, uint32_t *vals, int64_t n, int bits);
+
+// Preallocated temporaries for sorting up to `cap` 32-bit keys with values,
+// so that a sort can run inside a captured CUDA graph.
+struct SortWorkspace {
+    DevBuf<uint32_t> keys, vals;
+    DevBuf<int32_t> hist, tiles;
+    int64_t cap = 0;
+    void reserve(Allocator *a, int64_t n);
+};
+void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits);
 
 int bits_for(uint64_t max_value);   // number of bits needed to hold max_value
 

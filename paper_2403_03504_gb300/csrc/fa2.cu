@@ -425,14 +425,17 @@ void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, in
     cudaGraphExec_t exec = nullptr;
     const int64_t before = launch_count();
     BGL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ctx->alloc->forbid = true;
     try {
         run.iteration(d_stats);
     } catch (...) {
+        ctx->alloc->forbid = false;
         cudaGraph_t tmp = nullptr;
         cudaStreamEndCapture(s, &tmp);
         if (tmp) cudaGraphDestroy(tmp);
         throw;
     }
+    ctx->alloc->forbid = false;
     BGL_CUDA(cudaStreamEndCapture(s, &graph));
     // captured launches run only when the graph is replayed
     count_launches(before - launch_count());

@@ -990,6 +990,7 @@ struct FmmPlan {
     DevBuf<float2> M, Lc;
     DevBuf<int> arrive, done, tickets, err;
     DevBuf<float> binom;
+    SortWorkspace sortws;
 };
 
 FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
@@ -1042,6 +1043,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->arrive.reset(A, bmax);
         pl->done.reset(A, bmax);
         pl->tickets.reset(A, 4);
+        pl->sortws.reserve(A, n);
         pl->err.reset(A, 1);
         BGL_CUDA(cudaMemsetAsync(pl->counter.p, 0, sizeof(unsigned), s));
         BGL_CUDA(cudaMemsetAsync(pl->arrive.p, 0, sizeof(int) * bmax, s));
@@ -1144,7 +1146,7 @@ static void phase_points(FmmPlan *pl, const float2 *xl) {
     BGL_LAUNCH_CHECK();
     keys_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p);
     BGL_LAUNCH_CHECK();
-    radix_sort_u32(ctx, pl->key.p, pl->idx.p, n, 32);
+    radix_sort_u32_ws(ctx, pl->sortws, pl->key.p, pl->idx.p, n, 32);
     gather_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, ml, pl->idx.p, n, pl->pts.p);
     BGL_LAUNCH_CHECK();
 }

@@ -121,18 +121,22 @@ __global__ void scan_apply_kernel(const T *__restrict__ in, T *__restrict__ out,
 }
 
 template <typename T>
-void scan_exclusive(bgl_ctx *c, const T *in, T *out, int64_t n, T *d_total) {
+void scan_exclusive(bgl_ctx *c, const T *in, T *out, int64_t n, T *d_total, T *tiles = nullptr) {
     if (n <= 0) {
         if (d_total) BGL_CUDA(cudaMemsetAsync(d_total, 0, sizeof(T), c->stream));
         return;
     }
     int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    DevBuf<T> ts(c->alloc, ntiles);
-    scan_reduce_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, c->stream>>>(in, ts.p, n);
+    DevBuf<T> own;
+    if (!tiles) {
+        own.reset(c->alloc, ntiles);
+        tiles = own.p;
+    }
+    scan_reduce_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, c->stream>>>(in, tiles, n);
     BGL_LAUNCH_CHECK();
-    scan_tiles_kernel<T><<<1, 1024, 0, c->stream>>>(ts.p, ntiles, d_total);
+    scan_tiles_kernel<T><<<1, 1024, 0, c->stream>>>(tiles, ntiles, d_total);
     BGL_LAUNCH_CHECK();
-    scan_apply_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, c->stream>>>(in, out, ts.p, n);
+    scan_apply_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, c->stream>>>(in, out, tiles, n);
     BGL_LAUNCH_CHECK();
 }
 
@@ -213,22 +217,17 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(const K *__re
 }
 
 template <typename K>
-void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
-    if (n <= 1 || bits <= 0) return;
-    BGL_REQUIRE(n < (int64_t(1) << 31), "radix sort: more than 2^31 keys");
+void radix_sort_buffers(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits, K *ktmp, uint32_t *vtmp,
+                        int32_t *hist, int32_t *tiles) {
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    DevBuf<K> kt(c->alloc, n);
-    DevBuf<uint32_t> vt;
-    if (vals) vt.reset(c->alloc, n);
-    DevBuf<int32_t> hist(c->alloc, 256 * ntiles);
-    K *ka = keys, *kb = kt.p;
-    uint32_t *va = vals, *vb = vals ? vt.p : nullptr;
+    K *ka = keys, *kb = ktmp;
+    uint32_t *va = vals, *vb = vals ? vtmp : nullptr;
     int passes = 0;
     for (int shift = 0; shift < bits; shift += 8, ++passes) {
-        radix_hist_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, c->stream>>>(ka, n, shift, hist.p, ntiles);
+        radix_hist_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, c->stream>>>(ka, n, shift, hist, ntiles);
         BGL_LAUNCH_CHECK();
-        scan_exclusive<int32_t>(c, hist.p, hist.p, 256 * ntiles, nullptr);
-        radix_scatter_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, c->stream>>>(ka, va, kb, vb, n, shift, hist.p,
+        scan_exclusive<int32_t>(c, hist, hist, 256 * ntiles, nullptr, tiles);
+        radix_scatter_kernel<K><<<(unsigned)ntiles, RS_THREADS, 0, c->stream>>>(ka, va, kb, vb, n, shift, hist,
                                                                                 ntiles);
         BGL_LAUNCH_CHECK();
         std::swap(ka, kb);
@@ -238,6 +237,21 @@ void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
         BGL_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, c->stream));
         if (vals) BGL_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
     }
+}
+
+inline int64_t rs_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+inline int64_t scan_tiles_for(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+template <typename K>
+void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
+    if (n <= 1 || bits <= 0) return;
+    BGL_REQUIRE(n < (int64_t(1) << 31), "radix sort: more than 2^31 keys");
+    const int64_t ntiles = rs_tiles(n);
+    DevBuf<K> kt(c->alloc, n);
+    DevBuf<uint32_t> vt;
+    if (vals) vt.reset(c->alloc, n);
+    DevBuf<int32_t> hist(c->alloc, 256 * ntiles), tiles(c->alloc, scan_tiles_for(256 * ntiles));
+    radix_sort_buffers<K>(c, keys, vals, n, bits, kt.p, vals ? vt.p : nullptr, hist.p, tiles.p);
 }
 
 }  // namespace
@@ -253,6 +267,21 @@ void radix_sort_u64(bgl_ctx *c, uint64_t *keys, uint32_t *vals, int64_t n, int b
 }
 void radix_sort_u32(bgl_ctx *c, uint32_t *keys, uint32_t *vals, int64_t n, int bits) {
     radix_sort<uint32_t>(c, keys, vals, n, bits);
+}
+
+void SortWorkspace::reserve(Allocator *a, int64_t n) {
+    if (n <= cap) return;
+    keys.reset(a, n);
+    vals.reset(a, n);
+    hist.reset(a, 256 * rs_tiles(n));
+    tiles.reset(a, scan_tiles_for(256 * rs_tiles(n)));
+    cap = n;
+}
+
+void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits) {
+    if (n <= 1 || bits <= 0) return;
+    BGL_REQUIRE(n <= ws.cap, "radix sort: workspace too small");
+    radix_sort_buffers<uint32_t>(c, keys, vals, n, bits, ws.keys.p, ws.vals.p, ws.hist.p, ws.tiles.p);
 }
 
 int bits_for(uint64_t v) {
