@@ -174,11 +174,27 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    float4 a = __ldcg(&part[0]);
-    for (int b = 1; b < (int)gridDim.x; ++b) {
+    float4 a = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
         float4 c = __ldcg(&part[b]);
+        a = make_float4(fminf(a.x, c.x), fmaxf(a.y, c.y), fminf(a.z, c.z), fmaxf(a.w, c.w));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.x = fminf(a.x, __shfl_xor_sync(0xffffffffu, a.x, o));
+        a.y = fmaxf(a.y, __shfl_xor_sync(0xffffffffu, a.y, o));
+        a.z = fminf(a.z, __shfl_xor_sync(0xffffffffu, a.z, o));
+        a.w = fmaxf(a.w, __shfl_xor_sync(0xffffffffu, a.w, o));
+    }
+    __syncthreads();
+    if (lane == 0) wred[warp] = a;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    a = wred[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        float4 c = wred[w];
         a = make_float4(fminf(a.x, c.x), fmaxf(a.y, c.y), fminf(a.z, c.z), fmaxf(a.w, c.w));
     }
     double w = fmax((double)a.y - (double)a.x, (double)a.w - (double)a.z);
@@ -639,9 +655,13 @@ struct ExpArgs {
 
 // P2M at leaves, then M2M into each parent by its last child to finish
 template <int PT>
-__global__ void up_kernel(ExpArgs a) {
+__global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
+    __shared__ float sbin[BN * BN];
+    __shared__ float2 stage[8][4][PT + 1];
+    for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
+    __syncthreads();
     const Tree &T = a.T;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
@@ -655,15 +675,16 @@ __global__ void up_kernel(ExpArgs a) {
         float2 acc[PT + 1];
 #pragma unroll
         for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
-        for (int j = T.bstart[b] + lane; j < T.bend[b]; j += 32) {
+        const int e = T.bend[b];
+        for (int j = T.bstart[b] + lane; j < e; j += 32) {
             const float4 s = T.pts[j];
             const float2 w = make_float2((s.x - g.cx) * ir, (s.y - g.cy) * ir);
             float2 pw = w;
             acc[0].x += s.z;
 #pragma unroll
             for (int k = 1; k <= PT; ++k) {
-                acc[k].x += s.z * pw.x;
-                acc[k].y += s.z * pw.y;
+                acc[k].x = fmaf(s.z, pw.x, acc[k].x);
+                acc[k].y = fmaf(s.z, pw.y, acc[k].y);
                 pw = cmul(pw, w);
             }
         }
@@ -680,8 +701,9 @@ __global__ void up_kernel(ExpArgs a) {
             const int pb = T.bparent[child];
             if (pb < 0) break;
             int last = 0;
+            const int4 ch = T.bchild[pb];
+            const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
             if (lane == 0) {
-                const int4 ch = T.bchild[pb];
                 const int nch = (ch.x >= 0) + (ch.y >= 0) + (ch.z >= 0) + (ch.w >= 0);
                 const int old = atomicAdd(&a.arrive[pb], 1);
                 last = old == nch - 1;
@@ -690,39 +712,39 @@ __global__ void up_kernel(ExpArgs a) {
             if (!last) break;
             __threadfence();
             if (lane == 0) a.arrive[pb] = 0;
+            // stage the children's coefficients (one coalesced load per lane and child)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (cs[q] >= 0 && lane <= p) stage[wib][q][lane] = __ldcg(&a.M[(size_t)cs[q] * (PT + 1) + lane]);
+            __syncwarp();
             // M2M: b~_l = -a~_0 u^l / l + sum_{k=1}^{l} a~_k 2^-k u^(l-k) C(l-1, k-1)
             float2 out = make_float2(0.f, 0.f);
-            const int4 ch = T.bchild[pb];
-            const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
-            for (int q = 0; q < 4; ++q) {
-                const int C = cs[q];
-                if (C < 0) continue;
-                const float2 u = make_float2((q & 1) ? 0.5f : -0.5f, (q & 2) ? 0.5f : -0.5f);
-                const float2 *mc = a.M + (size_t)C * (PT + 1);
-                const float2 a0 = __ldcg(&mc[0]);
-                if (lane == 0) {
-                    out.x += a0.x;
-                    out.y += a0.y;
-                } else if (lane <= p) {
-                    const int l = lane;
-                    // u^(l-k) for k = l down to 1, running power
+            if (lane <= p) {
+                const int l = lane;
+                for (int q = 0; q < 4; ++q) {
+                    if (cs[q] < 0) continue;
+                    const float2 u = make_float2((q & 1) ? 0.5f : -0.5f, (q & 2) ? 0.5f : -0.5f);
+                    const float2 a0 = stage[wib][q][0];
+                    if (l == 0) {
+                        out = cadd(out, a0);
+                        continue;
+                    }
                     float2 pw = make_float2(1.f, 0.f);
                     float2 s = make_float2(0.f, 0.f);
-                    float half = 1.0f;
-                    for (int k = 1; k <= l; ++k) half *= 0.5f;          // 2^-l
-                    for (int k = l; k >= 1; --k) {
-                        const float2 ak = __ldcg(&mc[k]);
-                        const float cb = a.binom[(l - 1) * BN + (k - 1)] * half;
-                        s = cadd(s, cscale(cmul(ak, pw), cb));
-                        pw = cmul(pw, u);
-                        half *= 2.0f;
+#pragma unroll
+                    for (int k = PT; k >= 1; --k) {
+                        if (k <= l) {
+                            const float cb = sbin[(l - 1) * BN + (k - 1)] * ldexpf(1.0f, -k);
+                            s = cadd(s, cscale(cmul(stage[wib][q][k], pw), cb));
+                            pw = cmul(pw, u);
+                        }
                     }
-                    // pw is now u^l
-                    s = cadd(s, cscale(cmul(a0, pw), -1.0f / (float)l));
+                    s = cadd(s, cscale(cmul(a0, pw), -1.0f / (float)l));   // pw = u^l
                     out = cadd(out, s);
                 }
+                a.M[(size_t)pb * (PT + 1) + l] = out;
             }
-            if (lane <= p) a.M[(size_t)pb * (PT + 1) + lane] = out;
+            __syncwarp();
             __threadfence();
             child = pb;
         }
@@ -731,7 +753,10 @@ __global__ void up_kernel(ExpArgs a) {
 
 // M2L over V, P2L over X, L2L from the parent, in level order
 template <int PT>
-__global__ void down_kernel(ExpArgs a) {
+__global__ void __launch_bounds__(256) down_kernel(ExpArgs a) {
+    __shared__ float sbin[BN * BN];
+    for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
+    __syncthreads();
     const Tree &T = a.T;
     const int lane = threadIdx.x & 31;
     const int B = min(T.levoff[NLEV], T.Bmax);
@@ -778,7 +803,7 @@ __global__ void down_kernel(ExpArgs a) {
                 float2 s = make_float2(-a0.x / (float)l, -a0.y / (float)l);
 #pragma unroll
                 for (int k = 1; k <= PT; ++k) {
-                    const float cb = a.binom[(l + k - 1) * BN + (k - 1)];
+                    const float cb = sbin[(l + k - 1) * BN + (k - 1)];
                     s.x = fmaf(cb, ap[k].x, s.x);
                     s.y = fmaf(cb, ap[k].y, s.y);
                 }
@@ -826,7 +851,7 @@ __global__ void down_kernel(ExpArgs a) {
             float scale = 1.0f;
             for (int l = 1; l <= m; ++l) scale *= 0.5f;
             for (int l = m; l <= p; ++l) {
-                const float2 cl = cscale(__ldcg(&lp[l]), scale * a.binom[l * BN + m]);
+                const float2 cl = cscale(__ldcg(&lp[l]), scale * sbin[l * BN + m]);
                 mine = cadd(mine, cmul(cl, pw));
                 pw = cmul(pw, sft);
                 scale *= 0.5f;
