@@ -246,6 +246,43 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
 bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, int32_t reps,
                          double *out);
 
+/* ------------------------------------------------------- allocation-free step */
+
+#define BGL_NOALLOC_MAX_NODES (1 << 20)
+
+/*
+ * One ForceAtlas2 iteration with exact repulsion on one component held in
+ * caller-owned device arrays, allocating no memory.  The paper has no
+ * counterpart: this is a variant of bgl_fa2_step for callers that cannot
+ * allocate device memory when they run it -- a process that reserves all of
+ * its HBM for its own pool up front, or a latency-bound loop that cannot
+ * take the device-wide synchronisation cudaMalloc/cudaFree may cause.
+ *
+ * Arrays (device memory of the context's device, local ids 0..n-1):
+ *   d_off[n+1], d_adj[d_off[n]]  undirected adjacency (CSR)
+ *   d_mass[n]                    degree + 1
+ *   d_xy[2n]      in/out         positions (x, y interleaved)
+ *   d_fprev[2n]   in/out         previous forces; zero before the first iteration
+ *   d_f[2n]       out            this iteration's forces
+ *   d_sg[1]       in/out         global speed s_G; 1.0 before the first iteration
+ * Calling it `iters` times from zero d_fprev and d_sg = 1 performs what
+ * bgl_fa2_step does with p->repulsion = BGL_REP_EXACT (same force, swing,
+ * traction and update rules, p->kr, kg, ks, ksmax, tau, swing_variant).
+ *
+ * Scratch: the per-tile swing/traction sums and a counter live in one
+ * fixed array of about 8 KiB per device (room for BGL_NOALLOC_MAX_NODES
+ * nodes), held by every GPU that loads the library until exit.  n above
+ * BGL_NOALLOC_MAX_NODES returns BGL_EINVAL.  The first call on a device
+ * looks up that array's device address; make that first call before any
+ * stream capture.  Every call shares the array and leaves its last contents
+ * there: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Work is queued
+ * on the context's stream; the call does not synchronise it.
+ */
+bgl_status bgl_fa2_iteration_noalloc(bgl_ctx *ctx, int64_t n, const int64_t *d_off, const int32_t *d_adj,
+                                     const float *d_mass, float *d_xy, float *d_fprev, float *d_f, double *d_sg,
+                                     const bgl_params *p);
+
 /* Number of kernels this process has launched through the library so far
  * (direct launches plus the kernel nodes of every CUDA graph replay). */
 int64_t bgl_launch_count(void);

@@ -105,6 +105,7 @@ def _load():
         "bgl_fa2_step": ([VP, I64, ctypes.POINTER(Params), I32, VP, VP], I32),
         "bgl_fmm_stats": ([VP, I64, ctypes.POINTER(Params), VP, I32, VP], I32),
         "bgl_launch_count": ([], I64),
+        "bgl_fa2_iteration_noalloc": ([VP, I64, VP, VP, VP, VP, VP, VP, VP, ctypes.POINTER(Params)], I32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -178,6 +179,13 @@ class Context:
 
     def sync(self):
         self.check(self._lib.bgl_ctx_sync(self.h))
+
+    def fa2_iteration_noalloc(self, n, d_off, d_adj, d_mass, d_xy, d_fprev, d_f, d_sg, p: Params):
+        """One exact-repulsion ForceAtlas2 iteration on device arrays without
+        allocating (bgl_fa2_iteration_noalloc); arguments are device tensors or
+        addresses, queued on the context's stream."""
+        self.check(self._lib.bgl_fa2_iteration_noalloc(self.h, n, _dp(d_off), _dp(d_adj), _dp(d_mass), _dp(d_xy),
+                                                       _dp(d_fprev), _dp(d_f), _dp(d_sg), ctypes.byref(p)))
 
     def close(self):
         if self.h:

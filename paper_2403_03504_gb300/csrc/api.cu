@@ -521,6 +521,17 @@ bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const flo
     });
 }
 
+bgl_status bgl_fa2_iteration_noalloc(bgl_ctx *ctx, int64_t n, const int64_t *d_off, const int32_t *d_adj,
+                                     const float *d_mass, float *d_xy, float *d_fprev, float *d_f, double *d_sg,
+                                     const bgl_params *p) {
+    if (!ctx) return BGL_EINVAL;
+    return guarded(ctx, [&] {
+        check_params(p);
+        fa2_iteration_noalloc(ctx, n, d_off, d_adj, d_mass, reinterpret_cast<float2 *>(d_xy),
+                              reinterpret_cast<float2 *>(d_fprev), reinterpret_cast<float2 *>(d_f), d_sg, p);
+    });
+}
+
 int64_t bgl_launch_count(void) { return bgl::launch_count(); }
 
 }  // extern "C"

@@ -196,4 +196,9 @@ void fa2_forces(bgl_graph *g, const bgl_params *p, const float2 *xy, float2 *f, 
 // true if component c of n nodes uses the FMM under p
 bool use_fmm(const bgl_params *p, int64_t n);
 
+// one exact-repulsion ForceAtlas2 iteration on caller device arrays, with
+// static scratch (noalloc.cu)
+void fa2_iteration_noalloc(bgl_ctx *c, int64_t n, const int64_t *d_off, const int32_t *d_adj, const float *d_mass,
+                           float2 *d_xy, float2 *d_fprev, float2 *d_f, double *d_sg, const bgl_params *p);
+
 }  // namespace bgl
