@@ -228,7 +228,7 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
 
 /* ---------------------------------------------------------------- profiling */
 
-#define BGL_FMM_NSTATS 13
+#define BGL_FMM_NSTATS 15
 
 /*
  * Profiling aid for the Fast Multipole repulsion (Section 3.2.1) on
@@ -238,9 +238,13 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
  *   3 near-field pairs (targets x sources over the U lists, self pairs included),
  *   4 M2L translations (V entries), 5 M2P terms (W entries x targets),
  *   6 P2L terms (sources of the X entries),
- *   7..12 mean device milliseconds of the phases: points (bounding box, Morton
- *   keys, radix sort, gather), tree, interaction lists, upward pass (P2M,
- *   M2M), downward pass (M2L, P2L, L2L), leaf pass (L2P, M2P, P2P).
+ *   7..13 mean device milliseconds of the phases run one after another:
+ *   points (bounding box, Morton keys, radix sort, gather), tree,
+ *   neighbour tables and interaction lists, upward pass (P2M, M2M),
+ *   downward pass (M2L, P2L, L2L), near field (P2P), far field (L2P, M2P);
+ *   14 mean milliseconds of a whole evaluation in the schedule used inside
+ *   ForceAtlas2 iterations (upward and downward passes overlapping the near
+ *   field on a second stream).
  * Synchronises the stream.
  */
 bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, int32_t reps,

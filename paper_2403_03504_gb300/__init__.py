@@ -116,7 +116,7 @@ def _load():
 
 
 FMM_STATS = ("boxes", "leaves", "depth", "p2p_pairs", "m2l", "m2p", "p2l", "ms_points", "ms_tree", "ms_lists",
-             "ms_up", "ms_down", "ms_leaf")
+             "ms_up", "ms_down", "ms_near", "ms_far", "ms_total")
 
 
 def launch_count() -> int:

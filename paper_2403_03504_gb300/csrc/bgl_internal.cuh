@@ -157,9 +157,11 @@ struct SortWorkspace {
     DevBuf<uint32_t> keys, vals;
     DevBuf<int32_t> hist, tiles;
     int64_t cap = 0;
-    void reserve(Allocator *a, int64_t n);
+    void reserve(Allocator *a, int64_t n, cudaStream_t s);
 };
 void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits);
+// nonzero if a bounded wait of a workspace sort gave up (synchronises)
+int sort_workspace_error(bgl_ctx *c, SortWorkspace &ws);
 
 int bits_for(uint64_t max_value);   // number of bits needed to hold max_value
 

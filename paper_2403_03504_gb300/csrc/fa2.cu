@@ -6,11 +6,12 @@
 //                     FMM components run the pipeline in fmm.cu instead.
 //                     f <- F_rep = kr m_i sum_j m_j (p_i - p_j) / |p_i - p_j|^2
 //   K2 attraction     f += -sum_{j adjacent} (p_i - p_j) - kg m_i p_i; one
-//      + gravity      thread per node, one block per node of degree > 128
+//      + gravity      thread per node; nodes of degree > 128 in chunks of 2048
+//                     entries, one block each, combined in chunk order
 //   K3 swing/traction per-node |F_t - F_{t-1}|, |F_t + F_{t-1}| summed in FP64
-//                     per tile (warp shuffles), tiles summed in fixed order by
-//                     the last block to finish, which also updates s_G of every
-//                     component: s_G = min(tau trc / swg, 1.5 s_G)
+//                     per tile (warp shuffles); the last block to finish sums
+//                     each component's tiles (a warp per component, fixed
+//                     order) and updates s_G = min(tau trc / swg, 1.5 s_G)
 //   K4 update         s_n = ks s_G / (1 + s_G sqrt|F_t - F_{t-1}|), capped at
 //                     ksmax / |F_t|; p_n += s_n F_t; F_{t-1} <- F_t
 // The sequence has fixed launch shapes, so it is captured once into a CUDA
@@ -28,6 +29,7 @@ constexpr int EX_R = 2;                        // targets per thread
 constexpr int EX_TILE = EX_THREADS * EX_R;     // targets per block
 constexpr int EX_STILE = 1024;                 // sources per shared-memory stage
 constexpr int HEAVY_DEG = 128;
+constexpr int HEAVY_CHUNK = 2048;              // adjacency entries per block for high-degree nodes
 constexpr int RED_TILE = 2048;                 // nodes per swing/traction tile
 
 struct Tile {
@@ -105,12 +107,24 @@ __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
     }
 }
 
-// K2: attraction and gravity added to f (Section 3.2)
+// K2: attraction and gravity added to f (Section 3.2).  Blocks below
+// n_light_blocks: one thread per node of degree <= HEAVY_DEG.  The others:
+// one block per chunk of HEAVY_CHUNK adjacency entries of a node of higher
+// degree; the chunk sums go to `part` and the last chunk of the node to
+// finish adds them in chunk order (arrival count per node).
+struct HeavyChunk {
+    int32_t q;        // component-order position of the node
+    int32_t h;        // index of the node among the heavy nodes
+    int32_t first;    // index of the node's first chunk
+    int32_t nchunk;   // chunks of the node
+    int64_t e0, e1;   // adjacency entries of this chunk
+};
+
 __global__ void attraction_gravity_kernel(const float2 *__restrict__ xy, const float *__restrict__ mass,
                                           const int64_t *__restrict__ coff, const int32_t *__restrict__ cadj,
                                           int64_t q0, int64_t q1, int64_t qbase, float kg,
-                                          const int32_t *__restrict__ heavy, int64_t n_light_blocks,
-                                          float2 *__restrict__ f) {
+                                          const HeavyChunk *__restrict__ chunks, int64_t n_light_blocks,
+                                          float2 *part, int *arrive, float2 *__restrict__ f) {
     if (blockIdx.x < n_light_blocks) {
         int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (q >= q1) return;
@@ -128,13 +142,13 @@ __global__ void attraction_gravity_kernel(const float2 *__restrict__ xy, const f
         f[q - qbase] = make_float2((fr.x + ax) - km * p.x, (fr.y + ay) - km * p.y);
         return;
     }
-    // one block per node of high degree: strided partial sums, fixed-order reduction
     __shared__ float rx[32], ry[32];
-    const int64_t q = heavy[blockIdx.x - n_light_blocks];
-    const int64_t e0 = coff[q], e1 = coff[q + 1];
-    const float2 p = xy[q - qbase];
+    __shared__ bool last;
+    const int64_t k = (int64_t)blockIdx.x - n_light_blocks;
+    const HeavyChunk ch = chunks[k];
+    const float2 p = xy[ch.q - qbase];
     float ax = 0.f, ay = 0.f;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += blockDim.x) {
         float2 o = xy[cadj[e] - qbase];
         ax -= p.x - o.x;
         ay -= p.y - o.y;
@@ -147,13 +161,25 @@ __global__ void attraction_gravity_kernel(const float2 *__restrict__ xy, const f
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) { rx[warp] = ax; ry[warp] = ay; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float sx = 0.f, sy = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sx += rx[w]; sy += ry[w]; }
-        float km = kg * mass[q];
-        float2 fr = f[q - qbase];
-        f[q - qbase] = make_float2((fr.x + sx) - km * p.x, (fr.y + sy) - km * p.y);
+    if (threadIdx.x != 0) return;
+    float sx = 0.f, sy = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sx += rx[w]; sy += ry[w]; }
+    part[k] = make_float2(sx, sy);
+    __threadfence();
+    last = atomicAdd(&arrive[ch.h], 1) == ch.nchunk - 1;
+    if (!last) return;
+    __threadfence();
+    sx = 0.f;
+    sy = 0.f;
+    for (int j = 0; j < ch.nchunk; ++j) {
+        const float2 v = __ldcg(&part[ch.first + j]);
+        sx += v.x;
+        sy += v.y;
     }
+    arrive[ch.h] = 0;
+    const float km = kg * mass[ch.q];
+    const float2 fr = f[ch.q - qbase];
+    f[ch.q - qbase] = make_float2((fr.x + sx) - km * p.x, (fr.y + sy) - km * p.y);
 }
 
 __global__ void heavy_flag_kernel(const int64_t *__restrict__ coff, int64_t q0, int64_t n, int32_t *__restrict__ flag) {
@@ -166,6 +192,14 @@ __global__ void heavy_list_kernel(const int32_t *__restrict__ flag, const int32_
                                   int64_t n, int32_t *__restrict__ heavy) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && flag[i]) heavy[fscan[i]] = (int32_t)(q0 + i);
+}
+
+__global__ void heavy_rows_kernel(const int32_t *__restrict__ heavy, const int64_t *__restrict__ coff, int64_t nh,
+                                  int64_t *__restrict__ rows) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nh) return;
+    rows[2 * i] = coff[heavy[i]];
+    rows[2 * i + 1] = coff[heavy[i] + 1];
 }
 
 struct RedArgs {
@@ -223,23 +257,32 @@ __global__ void swing_traction_kernel(RedArgs a) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the last block: per component, tiles in order
-    for (int c = threadIdx.x; c < a.ncomp; c += blockDim.x) {
+    // the last block: one warp per component, lanes over its tiles, fixed
+    // butterfly order
+    const int nwarps = (int)(blockDim.x >> 5);
+    for (int c = warp; c < a.ncomp; c += nwarps) {
         double swg = 0.0, trc = 0.0;
-        for (int64_t k = a.tile_off[c]; k < a.tile_off[c + 1]; ++k) {
-            double2 v = __ldcg(&a.partial[k]);   // written by other blocks: bypass L1
+        for (int64_t k = a.tile_off[c] + lane; k < a.tile_off[c + 1]; k += 32) {
+            const double2 v = __ldcg(&a.partial[k]);   // written by other blocks: bypass L1
             swg += v.x;
             trc += v.y;
         }
-        double g = a.sg[c];
-        double s_new = swg > 0.0 ? a.tau * trc / swg : 1.5 * g;
-        if (s_new > 1.5 * g) s_new = 1.5 * g;
-        a.sg[c] = s_new;
-        if (c == 0 && a.stats) {
-            int it = *a.iter;
-            a.stats[3 * it] = swg;
-            a.stats[3 * it + 1] = trc;
-            a.stats[3 * it + 2] = s_new;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            swg += __shfl_xor_sync(0xffffffffu, swg, o);
+            trc += __shfl_xor_sync(0xffffffffu, trc, o);
+        }
+        if (lane == 0) {
+            double g = a.sg[c];
+            double s_new = swg > 0.0 ? a.tau * trc / swg : 1.5 * g;
+            if (s_new > 1.5 * g) s_new = 1.5 * g;
+            a.sg[c] = s_new;
+            if (c == 0 && a.stats) {
+                int it = *a.iter;
+                a.stats[3 * it] = swg;
+                a.stats[3 * it + 1] = trc;
+                a.stats[3 * it + 2] = s_new;
+            }
         }
     }
     __syncthreads();
@@ -293,8 +336,10 @@ struct Fa2Run {
     DevBuf<double> sg;
     DevBuf<unsigned> counter;
     DevBuf<int> iter;
-    DevBuf<int32_t> heavy;
-    int64_t n_heavy = 0;
+    DevBuf<HeavyChunk> chunks;
+    DevBuf<float2> chunk_part;
+    DevBuf<int> chunk_arrive;
+    int64_t n_chunks = 0;
     std::vector<FmmPlan *> fmm;   // one per FMM component
     std::vector<int64_t> fmm_comp;
 
@@ -338,7 +383,7 @@ struct Fa2Run {
         BGL_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned), s));
         iter.reset(A, 1);
         BGL_CUDA(cudaMemsetAsync(iter.p, 0, sizeof(int), s));
-        // nodes of high degree get a block each in the attraction kernel
+        // nodes of high degree: chunks of HEAVY_CHUNK adjacency entries
         DevBuf<int32_t> flag(A, n), fscan(A, n), tot(A, 1);
         heavy_flag_kernel<<<nblocks(n, 256), 256, 0, s>>>(g->coff.p, q0, n, flag.p);
         BGL_LAUNCH_CHECK();
@@ -346,10 +391,35 @@ struct Fa2Run {
         int32_t nh = 0;
         BGL_CUDA(cudaMemcpyAsync(&nh, tot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         BGL_CUDA(cudaStreamSynchronize(s));
-        n_heavy = nh;
-        heavy.reset(A, nh);
-        heavy_list_kernel<<<nblocks(n, 256), 256, 0, s>>>(flag.p, fscan.p, q0, n, heavy.p);
-        BGL_LAUNCH_CHECK();
+        std::vector<HeavyChunk> hc;
+        if (nh > 0) {
+            DevBuf<int32_t> heavy(A, nh);
+            heavy_list_kernel<<<nblocks(n, 256), 256, 0, s>>>(flag.p, fscan.p, q0, n, heavy.p);
+            BGL_LAUNCH_CHECK();
+            DevBuf<int64_t> hrow(A, 2 * (size_t)nh);
+            heavy_rows_kernel<<<nblocks(nh, 256), 256, 0, s>>>(heavy.p, g->coff.p, nh, hrow.p);
+            BGL_LAUNCH_CHECK();
+            std::vector<int32_t> hq(nh);
+            std::vector<int64_t> ho(2 * (size_t)nh);
+            BGL_CUDA(cudaMemcpyAsync(hq.data(), heavy.p, sizeof(int32_t) * nh, cudaMemcpyDeviceToHost, s));
+            BGL_CUDA(cudaMemcpyAsync(ho.data(), hrow.p, sizeof(int64_t) * 2 * nh, cudaMemcpyDeviceToHost, s));
+            BGL_CUDA(cudaStreamSynchronize(s));
+            for (int32_t h = 0; h < nh; ++h) {
+                const int64_t r0 = ho[2 * h], r1 = ho[2 * h + 1];
+                const int32_t first = (int32_t)hc.size();
+                const int32_t nchunk = (int32_t)((r1 - r0 + HEAVY_CHUNK - 1) / HEAVY_CHUNK);
+                for (int32_t j = 0; j < nchunk; ++j)
+                    hc.push_back(HeavyChunk{hq[h], h, first, nchunk, r0 + (int64_t)j * HEAVY_CHUNK,
+                                            std::min<int64_t>(r1, r0 + (int64_t)(j + 1) * HEAVY_CHUNK)});
+            }
+        }
+        n_chunks = (int64_t)hc.size();
+        chunks.reset(A, hc.size());
+        chunk_part.reset(A, hc.size());
+        chunk_arrive.reset(A, std::max<int32_t>(nh, 1));
+        BGL_CUDA(cudaMemsetAsync(chunk_arrive.p, 0, sizeof(int) * std::max<int32_t>(nh, 1), s));
+        if (!hc.empty())
+            BGL_CUDA(cudaMemcpyAsync(chunks.p, hc.data(), sizeof(HeavyChunk) * hc.size(), cudaMemcpyHostToDevice, s));
         BGL_CUDA(cudaStreamSynchronize(s));
     }
     ~Fa2Run() {
@@ -378,8 +448,9 @@ struct Fa2Run {
         if (what == 0) {
             int64_t n = q1 - q0;
             int64_t nl = nblocks(n, 256);
-            attraction_gravity_kernel<<<(unsigned)(nl + n_heavy), 256, 0, s>>>(
-                xy, g->mass.p, g->coff.p, g->cadj.p, q0, q1, qbase, (float)p->kg, heavy.p, nl, f.p - (q0 - qbase));
+            attraction_gravity_kernel<<<(unsigned)(nl + n_chunks), 256, 0, s>>>(
+                xy, g->mass.p, g->coff.p, g->cadj.p, q0, q1, qbase, (float)p->kg, chunks.p, nl, chunk_part.p,
+                chunk_arrive.p, f.p - (q0 - qbase));
             BGL_LAUNCH_CHECK();
         }
     }

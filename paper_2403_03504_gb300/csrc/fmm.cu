@@ -70,8 +70,9 @@ struct Tree {
     int4 *bchild;
     int *levoff;              // [NLEV + 1], levoff[NLEV] = number of boxes
     int *nb;                  // [9 * Bmax]
-    int *lcnt;                // [4 * Bmax + 1] counts, then offsets (U, V, W, X per box)
-    int *lidx;                // list entries
+    int *lofs;                // [5 * Bmax] per box: starts of U, V, W, X and the end, in lidx
+    int *lidx;                // list entries (each box's lists in one chunk)
+    int *pool;                // entries handed out so far (zero at the start of an evaluation)
     int lcap;                 // capacity of lidx
     int Bmax;                 // capacity of the box arrays
     const Root *root;
@@ -413,9 +414,115 @@ __global__ void tree_link_kernel(Tree T) {
 
 // ---------------------------------------------------------------- neighbour tables and lists
 
-// nb[b][k], k = (dy + 1) * 3 + (dx + 1): the box at b's level covering the
-// adjacent cell (dx, dy), else the coarser leaf covering it, else -1
-__global__ void nbr_kernel(Tree T, int *ticket, int *done) {
+// Interaction lists of box b (B leaf for U and W).  Each builder counts
+// when out is null and writes otherwise, in one fixed order.
+//   U: b itself, adjacent leaves at b's level or coarser (each once), and the
+//      leaves inside adjacent internal boxes that touch b;
+//   W: children met in that descent that do not touch b (their parent does);
+//   V: children of the parent's neighbours at the parent's level that do not
+//      touch b, with their offset class (dx + 3) * 7 + (dy + 3);
+//   X: leaves at the parent's level or coarser that touch the parent but not b.
+__device__ void lists_uw(const Tree &T, int b, int *ou, int *ow, int &cu, int &cw) {
+    cu = cw = 0;
+    if (!T.bleaf[b]) return;
+    const int L = T.blevel[b];
+    const uint32_t key = T.bkey[b];
+    const int *nbb = T.nb + 9 * b;
+    if (ou) ou[cu] = b;
+    ++cu;
+    for (int k = 0; k < 9; ++k) {
+        if (k == 4) continue;
+        const int A = nbb[k];
+        if (A < 0) continue;
+        bool seen = false;
+        for (int k2 = 0; k2 < k; ++k2)
+            if (k2 != 4 && nbb[k2] == A) seen = true;
+        if (seen) continue;
+        if (T.bleaf[A]) {
+            if (ou) ou[cu] = A;
+            ++cu;
+            continue;
+        }
+        int stack[4 * MAXLEV + 4];
+        int sp = 0;
+        stack[sp++] = A;
+        while (sp > 0) {
+            const int D = stack[--sp];
+            const int4 ch = T.bchild[D];
+            const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+            for (int q = 3; q >= 0; --q) {
+                const int C = cs[q];
+                if (C < 0) continue;
+                if (boxes_adjacent(T.bkey[C], T.blevel[C], key, L)) {
+                    if (T.bleaf[C]) {
+                        if (ou) ou[cu] = C;
+                        ++cu;
+                    } else if (sp < 4 * MAXLEV + 4) {
+                        stack[sp++] = C;
+                    } else {
+                        atomicOr(T.err, ERR_LIST_OVERFLOW);
+                    }
+                } else {
+                    if (ow) ow[cw] = C;
+                    ++cw;
+                }
+            }
+        }
+    }
+}
+
+__device__ void lists_v(const Tree &T, int b, int *ov, int &cv) {
+    cv = 0;
+    const int L = T.blevel[b];
+    if (L < 2) return;
+    const uint32_t key = T.bkey[b];
+    const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
+    const int *nbp = T.nb + 9 * T.bparent[b];
+    for (int k = 0; k < 9; ++k) {
+        if (k == 4) continue;
+        const int A = nbp[k];
+        if (A < 0 || T.blevel[A] != L - 1 || T.bleaf[A]) continue;
+        const int4 ch = T.bchild[A];
+        const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+        for (int q = 0; q < 4; ++q) {
+            const int C = cs[q];
+            if (C < 0) continue;
+            const uint32_t kc = T.bkey[C];
+            const int dx = (int)compact_bits(kc) - bx, dy = (int)compact_bits(kc >> 1) - by;
+            if (abs(dx) <= 1 && abs(dy) <= 1) continue;
+            if (ov) ov[cv] = (C << 6) | ((dx + 3) * 7 + (dy + 3));
+            ++cv;
+        }
+    }
+}
+
+__device__ void lists_x(const Tree &T, int b, int *ox, int &cx) {
+    cx = 0;
+    const int L = T.blevel[b];
+    if (L < 2) return;
+    const uint32_t key = T.bkey[b];
+    const int *nbp = T.nb + 9 * T.bparent[b];
+    for (int k = 0; k < 9; ++k) {
+        if (k == 4) continue;
+        const int A = nbp[k];
+        if (A < 0 || !T.bleaf[A]) continue;
+        bool seen = false;
+        for (int k2 = 0; k2 < k; ++k2)
+            if (k2 != 4 && nbp[k2] == A) seen = true;
+        if (seen) continue;
+        if (boxes_adjacent(T.bkey[A], T.blevel[A], key, L)) continue;
+        if (ox) ox[cx] = A;
+        ++cx;
+    }
+}
+
+// Boxes in level order through a ticket counter: the 3x3 neighbour table
+// nb[b][k], k = (dy + 1) * 3 + (dx + 1) (the box at b's level covering the
+// adjacent cell, else the coarser leaf covering it, else -1), built from
+// the parent's table after a bounded wait for it; then the U, V, W and X
+// lists, counted, given one chunk of lidx by an atomic reservation, and
+// written (lanes 0, 1, 2 take U+W, V and X).
+__global__ void nbr_lists_kernel(Tree T, int *ticket, int *done) {
     const int lane = threadIdx.x & 31;
     const int B = min(T.levoff[NLEV], T.Bmax);
     for (;;) {
@@ -423,190 +530,77 @@ __global__ void nbr_kernel(Tree T, int *ticket, int *done) {
         if (lane == 0) b = atomicAdd(ticket, 1);
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= B) return;
+        bool ok = true;
         if (b == 0) {
             if (lane < 9) T.nb[lane] = lane == 4 ? 0 : -1;
         } else {
             const int p = T.bparent[b];
             if (p < 0 || p >= b) {                 // inconsistent tree (capacity error recorded)
+                ok = false;
                 if (lane == 0) atomicOr(T.err, ERR_BOX_OVERFLOW);
                 if (lane < 9) T.nb[b * 9 + lane] = -1;
+            } else {
+                if (lane == 0) wait_flag(&done[p], T.err);
                 __syncwarp();
-                if (lane == 0) *(volatile int *)&done[b] = 1;
-                continue;
-            }
-            if (lane == 0) wait_flag(&done[p], T.err);
-            __syncwarp();
-            const int L = T.blevel[b];
-            const uint32_t key = T.bkey[b];
-            const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
-            if (lane < 9) {
-                const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
-                int res = -1;
-                if (nx >= 0 && ny >= 0 && nx < (1 << L) && ny < (1 << L)) {
-                    const int px = bx >> 1, py = by >> 1;
-                    const int kk = ((ny >> 1) - py + 1) * 3 + ((nx >> 1) - px + 1);
-                    const int A = __ldcg(&T.nb[p * 9 + kk]);
-                    if (A >= 0) {
-                        if (T.blevel[A] == L - 1 && !T.bleaf[A]) res = ((const int *)&T.bchild[A])[((ny & 1) << 1) | (nx & 1)];
-                        else res = A;
+                const int L = T.blevel[b];
+                const uint32_t key = T.bkey[b];
+                const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
+                if (lane < 9) {
+                    const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
+                    int res = -1;
+                    if (nx >= 0 && ny >= 0 && nx < (1 << L) && ny < (1 << L)) {
+                        const int px = bx >> 1, py = by >> 1;
+                        const int kk = ((ny >> 1) - py + 1) * 3 + ((nx >> 1) - px + 1);
+                        const int A = __ldcg(&T.nb[p * 9 + kk]);
+                        if (A >= 0) {
+                            if (T.blevel[A] == L - 1 && !T.bleaf[A])
+                                res = ((const int *)&T.bchild[A])[((ny & 1) << 1) | (nx & 1)];
+                            else res = A;
+                        }
                     }
+                    T.nb[b * 9 + lane] = res;
                 }
-                T.nb[b * 9 + lane] = res;
             }
         }
         __syncwarp();
         __threadfence();
         if (lane == 0) *(volatile int *)&done[b] = 1;
-    }
-}
-
-// Interaction lists of box b.  mode 0 counts, mode 1 writes at the offsets.
-__device__ void box_lists(const Tree &T, int b, int mode) {
-    const int L = T.blevel[b];
-    const uint32_t key = T.bkey[b];
-    const bool leaf = T.bleaf[b] != 0;
-    int cu = 0, cv = 0, cw = 0, cx = 0;
-    int ou = 0, ov = 0, ow = 0, ox = 0;
-    if (mode == 1) {
-        ou = T.lcnt[4 * b];
-        ov = T.lcnt[4 * b + 1];
-        ow = T.lcnt[4 * b + 2];
-        ox = T.lcnt[4 * b + 3];
-    }
-    auto put = [&](int off, int k, int v) {
-        if (mode == 1) {
-            if (off + k < T.lcap) T.lidx[off + k] = v;
-            else atomicOr(T.err, ERR_LIST_OVERFLOW);
+        // interaction lists of b
+        int c0 = 0, c1 = 0;
+        if (ok) {
+            if (lane == 0) lists_uw(T, b, nullptr, nullptr, c0, c1);
+            else if (lane == 1) lists_v(T, b, nullptr, c0);
+            else if (lane == 2) lists_x(T, b, nullptr, c0);
         }
-    };
-    const int *nbb = T.nb + 9 * b;
-    if (leaf) {
-        put(ou, cu++, b);
-        for (int k = 0; k < 9; ++k) {
-            if (k == 4) continue;
-            const int A = nbb[k];
-            if (A < 0) continue;
-            bool seen = false;
-            for (int k2 = 0; k2 < k; ++k2)
-                if (k2 != 4 && nbb[k2] == A) seen = true;
-            if (seen) continue;
-            if (T.bleaf[A]) {
-                put(ou, cu++, A);
-                continue;
-            }
-            // internal colleague: its descendants along b's boundary
-            int stack[4 * MAXLEV + 4];
-            int sp = 0;
-            stack[sp++] = A;
-            while (sp > 0) {
-                const int D = stack[--sp];
-                const int4 ch = T.bchild[D];
-                const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
-                for (int q = 3; q >= 0; --q) {
-                    const int C = cs[q];
-                    if (C < 0) continue;
-                    if (boxes_adjacent(T.bkey[C], T.blevel[C], key, L)) {
-                        if (T.bleaf[C]) put(ou, cu++, C);
-                        else if (sp < 4 * MAXLEV + 4) stack[sp++] = C;
-                    } else {
-                        put(ow, cw++, C);
-                    }
-                }
+        const int cu = __shfl_sync(0xffffffffu, c0, 0), cw = __shfl_sync(0xffffffffu, c1, 0);
+        const int cv = __shfl_sync(0xffffffffu, c0, 1), cx = __shfl_sync(0xffffffffu, c0, 2);
+        const int total = cu + cv + cw + cx;
+        int base = 0;
+        if (lane == 0) {
+            base = atomicAdd(T.pool, total);
+            if (base + total > T.lcap) {
+                atomicOr(T.err, ERR_LIST_OVERFLOW);
+                base = -1;
             }
         }
-    }
-    if (L >= 2) {
-        const int p = T.bparent[b];
-        const int *nbp = T.nb + 9 * p;
-        const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
-        for (int k = 0; k < 9; ++k) {
-            if (k == 4) continue;
-            const int A = nbp[k];
-            if (A < 0) continue;
-            if (T.blevel[A] == L - 1 && !T.bleaf[A]) {
-                const int4 ch = T.bchild[A];
-                const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
-                for (int q = 0; q < 4; ++q) {
-                    const int C = cs[q];
-                    if (C < 0) continue;
-                    const uint32_t kc = T.bkey[C];
-                    const int dx = (int)compact_bits(kc) - bx, dy = (int)compact_bits(kc >> 1) - by;
-                    if (abs(dx) <= 1 && abs(dy) <= 1) continue;
-                    put(ov, cv++, (C << 6) | ((dx + 3) * 7 + (dy + 3)));
-                }
-            } else if (T.bleaf[A]) {
-                bool seen = false;
-                for (int k2 = 0; k2 < k; ++k2)
-                    if (k2 != 4 && nbp[k2] == A) seen = true;
-                if (seen) continue;
-                if (!boxes_adjacent(T.bkey[A], T.blevel[A], key, L)) put(ox, cx++, A);
-            }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base < 0) {
+            if (lane < 5) T.lofs[5 * b + lane] = 0;
+            continue;
         }
-    }
-    if (mode == 0) {
-        T.lcnt[4 * b] = cu;
-        T.lcnt[4 * b + 1] = cv;
-        T.lcnt[4 * b + 2] = cw;
-        T.lcnt[4 * b + 3] = cx;
-    }
-}
-
-__global__ void lists_kernel(Tree T, int mode) {
-    const int B = min(T.levoff[NLEV], T.Bmax);
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) box_lists(T, b, mode);
-}
-
-// exclusive scan over the 4 B list counts (B read on the device), in place;
-// total at lcnt[4 B].  Single block: B is at most a few 1e5 boxes here.
-__global__ void lists_scan_kernel(Tree T) {
-    __shared__ int wsum[32];
-    __shared__ int carry_s;
-    const int total = 4 * min(T.levoff[NLEV], T.Bmax);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int carry = 0;
-    constexpr int ITEMS = 8;
-    for (int base = 0; base < total; base += blockDim.x * ITEMS) {
-        int v[ITEMS];
-        int s = 0;
-#pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            int i = base + threadIdx.x * ITEMS + k;
-            v[k] = i < total ? T.lcnt[i] : 0;
-            s += v[k];
+        if (lane == 0) {
+            T.lofs[5 * b] = base;
+            T.lofs[5 * b + 1] = base + cu;
+            T.lofs[5 * b + 2] = base + cu + cv;
+            T.lofs[5 * b + 3] = base + cu + cv + cw;
+            T.lofs[5 * b + 4] = base + total;
         }
-        int x = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        if (ok && total > 0) {
+            int d0, d1;
+            if (lane == 0) lists_uw(T, b, T.lidx + base, T.lidx + base + cu + cv, d0, d1);
+            else if (lane == 1) lists_v(T, b, T.lidx + base + cu, d0);
+            else if (lane == 2) lists_x(T, b, T.lidx + base + cu + cv + cw, d0);
         }
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
-            int t = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            wsum[lane] = t - w;
-            if (lane == 31) carry_s = t;
-        }
-        __syncthreads();
-        int e = carry + wsum[warp] + x - s;
-#pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            int i = base + threadIdx.x * ITEMS + k;
-            if (i < total) T.lcnt[i] = e;
-            e += v[k];
-        }
-        carry += carry_s;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        T.lcnt[total] = carry;
-        if (carry > T.lcap) atomicOr(T.err, ERR_LIST_OVERFLOW);
     }
 }
 
@@ -780,7 +774,7 @@ __global__ void __launch_bounds__(256) down_kernel(ExpArgs a) {
 #pragma unroll
         for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
         // M2L: b~_l += w^-l ( -a~_0 / l + sum_k (-1)^k a~_k w^-k C(l+k-1, k-1) ), w = 2 (dx + i dy)
-        const int vs = T.lcnt[4 * b + 1], ve = T.lcnt[4 * b + 2];
+        const int vs = T.lofs[5 * b + 1], ve = T.lofs[5 * b + 2];
         for (int e = vs + lane; e < ve; e += 32) {
             const int ent = T.lidx[e];
             const int D = ent >> 6, cls = ent & 63;
@@ -813,7 +807,7 @@ __global__ void __launch_bounds__(256) down_kernel(ExpArgs a) {
         }
         // P2L: b~_l += -q t^l / l, t = r / (z_j - c)
         const BoxGeo g = box_geo(rt, T.bkey[b], L);
-        const int xs = T.lcnt[4 * b + 3], xe = T.lcnt[4 * b + 4];
+        const int xs = T.lofs[5 * b + 3], xe = T.lofs[5 * b + 4];
         for (int e = xs; e < xe; ++e) {
             const int C = T.lidx[e];
             for (int j = T.bstart[C] + lane; j < T.bend[C]; j += 32) {
@@ -874,54 +868,65 @@ __device__ __forceinline__ float rcp_approx(float x) {
 struct LeafArgs {
     ExpArgs e;
     float2 *f;           // f[q - fbase]
-    const float *mass;
     int64_t q0, fbase;
     float kr;
     int *ticket;
 };
 
-// L2P + M2P over W + P2P over U for every target of a leaf
-template <int PT>
-__global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs la) {
+// Near field: the direct sum over the points of U for every target of a
+// leaf.  One warp per leaf (leaves taken through a ticket counter), sources
+// staged NEAR_SRC at a time in the warp's own shared memory (no block-wide
+// barriers).  Targets: leaves of 33..64 targets give each lane two targets;
+// smaller ones give each target 32 / ntp lanes (ntp = targets rounded up to a
+// power of two) that split the sources and combine by a fixed butterfly.
+// Writes the raw sum sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the far
+// kernel completes it).
+constexpr int NEAR_WARPS = 8;
+constexpr int NEAR_SRC = 256;
+
+__device__ __forceinline__ void p2p_pair(const float4 &z, const float4 &q, float &fx, float &fy) {
+    const float dx = z.x - q.x, dy = z.y - q.y;
+    const float r2 = fmaf(dx, dx, dy * dy);
+    // a coincident pair (the target itself) has dx = dy = 0 and adds 0
+    const float w = q.z * rcp_approx(fmaxf(r2, 1e-30f));
+    fx = fmaf(w, dx, fx);
+    fy = fmaf(w, dy, fy);
+}
+
+__global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
     const Tree &T = la.e.T;
-    __shared__ float4 src[SRC_CAP];
-    __shared__ float2 red[LEAF_THREADS];
-    __shared__ int sb;
-    const int tid = threadIdx.x;
+    __shared__ float4 stage[NEAR_WARPS][NEAR_SRC];
+    const int lane = threadIdx.x & 31;
+    float4 *src = stage[threadIdx.x >> 5];
     const int B = min(T.levoff[NLEV], T.Bmax);
-    const Root rt = *T.root;
-    const int p = la.e.p;
     for (;;) {
-        if (tid == 0) sb = atomicAdd(la.ticket, 1);
-        __syncthreads();
-        const int b = sb;
-        __syncthreads();
+        int b = 0;
+        if (lane == 0) b = atomicAdd(la.ticket, 1);
+        b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= B) return;
         if (!T.bleaf[b]) continue;
-        const int L = T.blevel[b];
-        const BoxGeo g = box_geo(rt, T.bkey[b], L);
         const int s = T.bstart[b], e = T.bend[b];
-        const int us = T.lcnt[4 * b], ue = T.lcnt[4 * b + 1];
-        const int ws = T.lcnt[4 * b + 2], we = T.lcnt[4 * b + 3];
-        const float2 *lb = la.e.Lc + (size_t)b * (PT + 1);
-        for (int tb = s; tb < e; tb += LEAF_THREADS) {
-            const int ntc = min(LEAF_THREADS, e - tb);
-            int pw2 = 1;
-            while (pw2 < ntc) pw2 <<= 1;
-            const int S = LEAF_THREADS / pw2;
-            const int t = tid & (pw2 - 1), h = tid / pw2;
-            const bool valid = t < ntc;
-            float4 z = valid ? T.pts[tb + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float fx = 0.f, fy = 0.f;
-            // P2P over the points of U, staged in shared memory
+        const int us = T.lofs[5 * b], ue = T.lofs[5 * b + 1];
+        for (int tb = s; tb < e; tb += 64) {
+            const int ntc = min(64, e - tb);
+            const bool two = ntc > 32;
+            int ntp = 1;
+            while (ntp < ntc && ntp < 32) ntp <<= 1;
+            const int S = two ? 1 : 32 / ntp;
+            const int t = two ? lane : (lane & (ntp - 1));
+            const int h = two ? 0 : lane / ntp;
+            const bool v0 = t < ntc, v1 = two && t + 32 < ntc;
+            const float4 z0 = v0 ? T.pts[tb + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 z1 = v1 ? T.pts[tb + t + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float fx0 = 0.f, fy0 = 0.f, fx1 = 0.f, fy1 = 0.f;
             int ui = us, off = 0;
             while (ui < ue) {
                 int cnt = 0;
-                while (ui < ue && cnt < SRC_CAP) {
+                while (ui < ue && cnt < NEAR_SRC) {
                     const int C = T.lidx[ui];
                     const int cs = T.bstart[C], ce = T.bend[C];
-                    const int take = min(ce - cs - off, SRC_CAP - cnt);
-                    for (int k = tid; k < take; k += LEAF_THREADS) src[cnt + k] = T.pts[cs + off + k];
+                    const int take = min(ce - cs - off, NEAR_SRC - cnt);
+                    for (int k = lane; k < take; k += 32) src[cnt + k] = T.pts[cs + off + k];
                     cnt += take;
                     off += take;
                     if (off == ce - cs) {
@@ -929,67 +934,86 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs la) {
                         off = 0;
                     }
                 }
-                __syncthreads();
-                if (valid) {
+                __syncwarp();
+                if (two) {
 #pragma unroll 4
-                    for (int j = h; j < cnt; j += S) {
+                    for (int j = 0; j < cnt; ++j) {
                         const float4 q = src[j];
-                        const float dx = z.x - q.x, dy = z.y - q.y;
-                        const float r2 = fmaf(dx, dx, dy * dy);
-                        // a coincident pair (the target itself) has dx = dy = 0 and adds 0
-                        const float w = q.z * rcp_approx(fmaxf(r2, 1e-30f));
-                        fx = fmaf(w, dx, fx);
-                        fy = fmaf(w, dy, fy);
+                        p2p_pair(z0, q, fx0, fy0);
+                        p2p_pair(z1, q, fx1, fy1);
                     }
+                } else {
+#pragma unroll 4
+                    for (int j = h; j < cnt; j += S) p2p_pair(z0, src[j], fx0, fy0);
                 }
-                __syncthreads();
+                __syncwarp();
             }
-            // far field E(z) (complex); the force direction is conj(E)
+            if (!two) {
+                for (int o = ntp; o < 32; o <<= 1) {
+                    fx0 += __shfl_xor_sync(0xffffffffu, fx0, o);
+                    fy0 += __shfl_xor_sync(0xffffffffu, fy0, o);
+                }
+            }
+            if (v0 && h == 0) la.f[la.q0 + __float_as_int(z0.w) - la.fbase] = make_float2(fx0, fy0);
+            if (v1) la.f[la.q0 + __float_as_int(z1.w) - la.fbase] = make_float2(fx1, fy1);
+        }
+    }
+}
+
+// Far field of every target of a leaf (one warp per leaf, a lane per
+// target): L2P of the leaf's local expansion and M2P over W, added to the
+// near sum; then F_rep = kr m_i (near + conj(E_far)).
+template <int PT>
+__global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
+    const Tree &T = la.e.T;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    const Root rt = *T.root;
+    const int p = la.e.p;
+    for (int b = gw; b < B; b += nw) {
+        if (!T.bleaf[b]) continue;
+        const BoxGeo g = box_geo(rt, T.bkey[b], T.blevel[b]);
+        const int s = T.bstart[b], e = T.bend[b];
+        const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
+        const float2 *lb = la.e.Lc + (size_t)b * (PT + 1);
+        for (int t = s + lane; t < e; t += 32) {
+            const float4 z = T.pts[t];
             float2 E = make_float2(0.f, 0.f);
-            if (valid) {
-                // M2P: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
-                for (int k = ws + h; k < we; k += S) {
-                    const int D = T.lidx[k];
-                    const BoxGeo gd = box_geo(rt, T.bkey[D], T.blevel[D]);
-                    const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
-                    const float2 idz = crcp(dz);
-                    const float2 tt = cscale(idz, gd.r);
-                    const float2 *md = la.e.M + (size_t)D * (PT + 1);
-                    float2 hs = make_float2(0.f, 0.f);
+            // L2P: E = (1/r) sum_l l b~_l v^(l-1), v = (z - c) / r
+            {
+                const float ir = 1.0f / g.r;
+                const float2 v = make_float2((z.x - g.cx) * ir, (z.y - g.cy) * ir);
+                float2 hs = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int kk = PT; kk >= 1; --kk) {
-                        if (kk <= p) hs = cadd(cmul(hs, tt), cscale(md[kk], (float)kk));
-                    }
-                    hs = cmul(hs, tt);
-                    const float2 a0 = md[0];
-                    E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
+                for (int l = PT; l >= 1; --l) {
+                    if (l <= p) hs = cadd(cmul(hs, v), cscale(lb[l], (float)l));
                 }
-                // L2P: E += (1/r) sum_l l b~_l v^(l-1), v = (z - c) / r
-                if (h == 0) {
-                    const float ir = 1.0f / g.r;
-                    const float2 v = make_float2((z.x - g.cx) * ir, (z.y - g.cy) * ir);
-                    float2 hs = make_float2(0.f, 0.f);
+                E = cscale(hs, ir);
+            }
+            // M2P: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
+            for (int k = ws; k < we; ++k) {
+                const int D = T.lidx[k];
+                const BoxGeo gd = box_geo(rt, T.bkey[D], T.blevel[D]);
+                const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
+                const float2 idz = crcp(dz);
+                const float2 tt = cscale(idz, gd.r);
+                const float2 *md = la.e.M + (size_t)D * (PT + 1);
+                float2 hs = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int l = PT; l >= 1; --l) {
-                        if (l <= p) hs = cadd(cmul(hs, v), cscale(lb[l], (float)l));
-                    }
-                    E = cadd(E, cscale(hs, ir));
+                for (int kk = PT; kk >= 1; --kk) {
+                    if (kk <= p) hs = cadd(cmul(hs, tt), cscale(md[kk], (float)kk));
                 }
+                hs = cmul(hs, tt);
+                const float2 a0 = md[0];
+                E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
             }
-            red[tid] = make_float2(fx + E.x, fy - E.y);
-            __syncthreads();
-            if (valid && h == 0) {
-                float2 F = red[t];
-                for (int hh = 1; hh < S; ++hh) {
-                    const float2 o = red[hh * pw2 + t];
-                    F.x += o.x;
-                    F.y += o.y;
-                }
-                const int o = __float_as_int(z.w);
-                const float km = la.kr * z.z;
-                la.f[la.q0 + o - la.fbase] = make_float2(km * F.x, km * F.y);
-            }
-            __syncthreads();
+            const int o = __float_as_int(z.w);
+            float2 *fo = la.f + (la.q0 + o - la.fbase);
+            const float2 nr = *fo;
+            const float km = la.kr * z.z;
+            *fo = make_float2(km * (nr.x + E.x), km * (nr.y - E.y));
         }
     }
 }
@@ -1009,13 +1033,20 @@ struct FmmPlan {
     DevBuf<uint32_t> key, idx;
     DevBuf<float4> pts;
     DevBuf<int8_t> cl, lam, bleaf;
-    DevBuf<int> tcnt, levoff, bstart, bend, blevel, bparent, nb, lcnt, lidx;
+    DevBuf<int> tcnt, levoff, bstart, bend, blevel, bparent, nb, lofs, lidx;
     DevBuf<uint32_t> bkey;
     DevBuf<int4> bchild;
     DevBuf<float2> M, Lc;
-    DevBuf<int> arrive, done, tickets, err;
+    DevBuf<int> arrive, done_nb, done_dn, tickets, err;
     DevBuf<float> binom;
     SortWorkspace sortws;
+    cudaStream_t side = nullptr;          // second stream for the concurrent branch
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~FmmPlan() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        if (side) cudaStreamDestroy(side);
+    }
 };
 
 FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
@@ -1061,15 +1092,16 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->bleaf.reset(A, bmax);
         pl->bchild.reset(A, bmax);
         pl->nb.reset(A, 9 * bmax);
-        pl->lcnt.reset(A, 4 * bmax + 1);
+        pl->lofs.reset(A, 5 * bmax);
         pl->lidx.reset(A, pl->lcap);
         pl->M.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->Lc.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->arrive.reset(A, bmax);
-        pl->done.reset(A, bmax);
-        pl->tickets.reset(A, 4);
-        pl->sortws.reserve(A, n);
+        pl->done_nb.reset(A, bmax);
+        pl->done_dn.reset(A, bmax);
+        pl->tickets.reset(A, 8);
         pl->err.reset(A, 1);
+        pl->sortws.reserve(A, n, s);
         BGL_CUDA(cudaMemsetAsync(pl->counter.p, 0, sizeof(unsigned), s));
         BGL_CUDA(cudaMemsetAsync(pl->arrive.p, 0, sizeof(int) * bmax, s));
         BGL_CUDA(cudaMemsetAsync(pl->err.p, 0, sizeof(int), s));
@@ -1083,6 +1115,8 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         }
         pl->binom.reset(A, BN * BN);
         BGL_CUDA(cudaMemcpyAsync(pl->binom.p, bn.data(), sizeof(float) * bn.size(), cudaMemcpyHostToDevice, s));
+        BGL_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
+        for (auto &e : pl->ev) BGL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         BGL_CUDA(cudaStreamSynchronize(s));
         pl->grid_p = ctx->num_sms * 8;
     } catch (...) {
@@ -1108,30 +1142,14 @@ static Tree make_tree(FmmPlan *pl) {
     T.bchild = pl->bchild.p;
     T.levoff = pl->levoff.p;
     T.nb = pl->nb.p;
-    T.lcnt = pl->lcnt.p;
+    T.lofs = pl->lofs.p;
     T.lidx = pl->lidx.p;
+    T.pool = pl->tickets.p + 3;
     T.lcap = pl->lcap;
     T.Bmax = pl->Bmax;
     T.root = pl->root.p;
     T.err = pl->err.p;
     return T;
-}
-
-template <int PT>
-static void fmm_up(FmmPlan *pl, const ExpArgs &a) {
-    up_kernel<PT><<<pl->grid_p, 256, 0, pl->g->ctx->stream>>>(a);
-    BGL_LAUNCH_CHECK();
-}
-template <int PT>
-static void fmm_down(FmmPlan *pl, const ExpArgs &a) {
-    BGL_CUDA(cudaMemsetAsync(pl->done.p, 0, sizeof(int) * pl->Bmax, pl->g->ctx->stream));
-    down_kernel<PT><<<pl->grid_p, 256, 0, pl->g->ctx->stream>>>(a);
-    BGL_LAUNCH_CHECK();
-}
-template <int PT>
-static void fmm_leaf(FmmPlan *pl, const LeafArgs &la) {
-    leaf_kernel<PT><<<pl->g->ctx->num_sms * 8, LEAF_THREADS, 0, pl->g->ctx->stream>>>(la);
-    BGL_LAUNCH_CHECK();
 }
 
 static ExpArgs exp_args(FmmPlan *pl, const Tree &T) {
@@ -1140,7 +1158,7 @@ static ExpArgs exp_args(FmmPlan *pl, const Tree &T) {
     a.M = pl->M.p;
     a.Lc = pl->Lc.p;
     a.arrive = pl->arrive.p;
-    a.done = pl->done.p;
+    a.done = pl->done_dn.p;
     a.ticket = pl->tickets.p + 1;
     a.binom = pl->binom.p;
     a.p = pl->p;
@@ -1151,7 +1169,6 @@ static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbas
     LeafArgs la;
     la.e = a;
     la.f = f;
-    la.mass = pl->g->mass.p;
     la.q0 = pl->q0;
     la.fbase = fbase;
     la.kr = pl->kr;
@@ -1159,26 +1176,32 @@ static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbas
     return la;
 }
 
-// phase 0: bounding box, keys, sort, gather
-static void phase_points(FmmPlan *pl, const float2 *xl) {
+// points: bounding box, keys, sort, gather (also clears the tickets and the list pool)
+static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
     bgl_ctx *ctx = pl->g->ctx;
-    cudaStream_t s = ctx->stream;
     const int n = pl->n;
     const float *ml = pl->g->mass.p + pl->q0;
-    BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 4, s));
+    BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 8, s));
     bbox_kernel<<<std::min<int64_t>(1024, nblk(n, 256)), 256, 0, s>>>(xl, n, pl->part.p, pl->counter.p, pl->root.p,
                                                                       pl->err.p);
     BGL_LAUNCH_CHECK();
     keys_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p);
     BGL_LAUNCH_CHECK();
-    radix_sort_u32_ws(ctx, pl->sortws, pl->key.p, pl->idx.p, n, 32);
+    cudaStream_t keep = ctx->stream;
+    ctx->stream = s;
+    try {
+        radix_sort_u32_ws(ctx, pl->sortws, pl->key.p, pl->idx.p, n, 32);
+    } catch (...) {
+        ctx->stream = keep;
+        throw;
+    }
+    ctx->stream = keep;
     gather_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, ml, pl->idx.p, n, pl->pts.p);
     BGL_LAUNCH_CHECK();
 }
 
-// phase 1: boxes in level order, ends, parents, children
-static void phase_tree(FmmPlan *pl, const Tree &T) {
-    cudaStream_t s = pl->g->ctx->stream;
+// tree: boxes in level order, ends, parents, children
+static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
     tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, pl->n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
                                                           pl->ntiles);
     BGL_LAUNCH_CHECK();
@@ -1191,45 +1214,86 @@ static void phase_tree(FmmPlan *pl, const Tree &T) {
     BGL_LAUNCH_CHECK();
 }
 
-// phase 2: neighbour tables and U/V/W/X lists
-static void phase_lists(FmmPlan *pl, const Tree &T) {
-    cudaStream_t s = pl->g->ctx->stream;
-    BGL_CUDA(cudaMemsetAsync(pl->done.p, 0, sizeof(int) * pl->Bmax, s));
-    nbr_kernel<<<pl->grid_p, 256, 0, s>>>(T, pl->tickets.p, pl->done.p);
-    BGL_LAUNCH_CHECK();
-    lists_kernel<<<pl->grid_p, 128, 0, s>>>(T, 0);
-    BGL_LAUNCH_CHECK();
-    lists_scan_kernel<<<1, 1024, 0, s>>>(T);
-    BGL_LAUNCH_CHECK();
-    lists_kernel<<<pl->grid_p, 128, 0, s>>>(T, 1);
+// neighbour tables and interaction lists
+static void phase_lists(FmmPlan *pl, const Tree &T, cudaStream_t s) {
+    BGL_CUDA(cudaMemsetAsync(pl->done_nb.p, 0, sizeof(int) * pl->Bmax, s));
+    nbr_lists_kernel<<<pl->grid_p, 256, 0, s>>>(T, pl->tickets.p, pl->done_nb.p);
     BGL_LAUNCH_CHECK();
 }
 
 template <int PT>
-static void phases_expand(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase, cudaEvent_t *ev) {
-    cudaStream_t s = pl->g->ctx->stream;
-    const ExpArgs a = exp_args(pl, T);
-    fmm_up<PT>(pl, a);
-    if (ev) BGL_CUDA(cudaEventRecord(ev[0], s));
-    fmm_down<PT>(pl, a);
-    if (ev) BGL_CUDA(cudaEventRecord(ev[1], s));
-    fmm_leaf<PT>(pl, leaf_args(pl, a, f, fbase));
+static void launch_up(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
+    up_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
+    BGL_LAUNCH_CHECK();
+}
+template <int PT>
+static void launch_down(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
+    BGL_CUDA(cudaMemsetAsync(pl->done_dn.p, 0, sizeof(int) * pl->Bmax, s));
+    down_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
+    BGL_LAUNCH_CHECK();
+}
+static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
+    near_kernel<<<pl->g->ctx->num_sms * 6, NEAR_WARPS * 32, 0, s>>>(la);
+    BGL_LAUNCH_CHECK();
+}
+template <int PT>
+static void launch_far(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
+    far_kernel<PT><<<pl->grid_p, 256, 0, s>>>(la);
+    BGL_LAUNCH_CHECK();
 }
 
-static void expand(FmmPlan *pl, const Tree &T, float2 *f, int64_t fbase, cudaEvent_t *ev) {
-    if (pl->PT == 8) phases_expand<8>(pl, T, f, fbase, ev);
-    else if (pl->PT == 16) phases_expand<16>(pl, T, f, fbase, ev);
-    else phases_expand<24>(pl, T, f, fbase, ev);
+// Whole evaluation.  With `concurrent`, the upward and downward passes run
+// on the plan's side stream while the near field runs on the main stream:
+//   main: points, tree --+-- lists ----+-- near ------------+-- far --
+//   side:                +-- up -------+-- (lists) down ----+
+// ev (timing events, 7, may be null) forces one stream and marks the phases.
+template <int PT>
+static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev) {
+    cudaStream_t s = pl->g->ctx->stream;
+    const Tree T = make_tree(pl);
+    const ExpArgs a = exp_args(pl, T);
+    const LeafArgs la = leaf_args(pl, a, f, fbase);
+    if (ev) BGL_CUDA(cudaEventRecord(ev[0], s));
+    phase_points(pl, xl, s);
+    if (ev) BGL_CUDA(cudaEventRecord(ev[1], s));
+    phase_tree(pl, T, s);
+    if (ev) BGL_CUDA(cudaEventRecord(ev[2], s));
+    if (!concurrent) {
+        phase_lists(pl, T, s);
+        if (ev) BGL_CUDA(cudaEventRecord(ev[3], s));
+        launch_up<PT>(pl, a, s);
+        if (ev) BGL_CUDA(cudaEventRecord(ev[4], s));
+        launch_down<PT>(pl, a, s);
+        if (ev) BGL_CUDA(cudaEventRecord(ev[5], s));
+        launch_near(pl, la, s);
+        if (ev) BGL_CUDA(cudaEventRecord(ev[6], s));
+        launch_far<PT>(pl, la, s);
+        if (ev) BGL_CUDA(cudaEventRecord(ev[7], s));
+        return;
+    }
+    cudaStream_t t = pl->side;
+    BGL_CUDA(cudaEventRecord(pl->ev[0], s));           // tree built
+    BGL_CUDA(cudaStreamWaitEvent(t, pl->ev[0], 0));
+    launch_up<PT>(pl, a, t);
+    phase_lists(pl, T, s);
+    BGL_CUDA(cudaEventRecord(pl->ev[1], s));           // lists built
+    launch_near(pl, la, s);
+    BGL_CUDA(cudaStreamWaitEvent(t, pl->ev[1], 0));
+    launch_down<PT>(pl, a, t);
+    BGL_CUDA(cudaEventRecord(pl->ev[2], t));           // local expansions ready
+    BGL_CUDA(cudaStreamWaitEvent(s, pl->ev[2], 0));
+    launch_far<PT>(pl, la, s);
+}
+
+static void evaluate_any(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev) {
+    if (pl->PT == 8) evaluate<8>(pl, xl, f, fbase, concurrent, ev);
+    else if (pl->PT == 16) evaluate<16>(pl, xl, f, fbase, concurrent, ev);
+    else evaluate<24>(pl, xl, f, fbase, concurrent, ev);
 }
 
 void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase) {
     if (pl->n <= 0) return;
-    const float2 *xl = xy + (pl->q0 - qbase);
-    const Tree T = make_tree(pl);
-    phase_points(pl, xl);
-    phase_tree(pl, T);
-    phase_lists(pl, T);
-    expand(pl, T, f, fbase, nullptr);
+    evaluate_any(pl, xy + (pl->q0 - qbase), f, fbase, true, nullptr);
 }
 
 namespace {
@@ -1237,10 +1301,11 @@ namespace {
 // interaction counts: P2P pairs, M2P and P2L point-box terms
 __global__ void count_kernel(Tree T, unsigned long long *out) {
     const int B = min(T.levoff[NLEV], T.Bmax);
-    unsigned long long p2p = 0, m2p = 0, p2l = 0, leaves = 0, depth = 0;
+    unsigned long long p2p = 0, m2p = 0, p2l = 0, leaves = 0, depth = 0, m2l = 0;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
         depth = max(depth, (unsigned long long)T.blevel[b]);
-        const int X0 = T.lcnt[4 * b + 3], X1 = T.lcnt[4 * b + 4];
+        m2l += (unsigned long long)(T.lofs[5 * b + 2] - T.lofs[5 * b + 1]);
+        const int X0 = T.lofs[5 * b + 3], X1 = T.lofs[5 * b + 4];
         for (int e = X0; e < X1; ++e) {
             const int C = T.lidx[e];
             p2l += (unsigned long long)(T.bend[C] - T.bstart[C]);
@@ -1249,18 +1314,19 @@ __global__ void count_kernel(Tree T, unsigned long long *out) {
         ++leaves;
         const unsigned long long nt = (unsigned long long)(T.bend[b] - T.bstart[b]);
         unsigned long long ns = 0;
-        for (int e = T.lcnt[4 * b]; e < T.lcnt[4 * b + 1]; ++e) {
+        for (int e = T.lofs[5 * b]; e < T.lofs[5 * b + 1]; ++e) {
             const int C = T.lidx[e];
             ns += (unsigned long long)(T.bend[C] - T.bstart[C]);
         }
         p2p += nt * ns;
-        m2p += nt * (unsigned long long)(T.lcnt[4 * b + 3] - T.lcnt[4 * b + 2]);
+        m2p += nt * (unsigned long long)(T.lofs[5 * b + 3] - T.lofs[5 * b + 2]);
     }
     atomicAdd(&out[0], p2p);
     atomicAdd(&out[1], m2p);
     atomicAdd(&out[2], p2l);
     atomicAdd(&out[3], leaves);
     atomicMax(&out[4], depth);
+    atomicAdd(&out[5], m2l);
 }
 
 }  // namespace
@@ -1271,64 +1337,66 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
     const float2 *xl = xy + (pl->q0 - qbase);
     const Tree T = make_tree(pl);
     DevBuf<float2> f(ctx->alloc, std::max(pl->n, 1));
-    cudaEvent_t ev[7];
+    cudaEvent_t ev[8], c0, c1;
     for (auto &e : ev) BGL_CUDA(cudaEventCreate(&e));
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    BGL_CUDA(cudaEventCreate(&c0));
+    BGL_CUDA(cudaEventCreate(&c1));
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     try {
-        for (int r = 0; r < std::max(reps, 1); ++r) {
-            BGL_CUDA(cudaEventRecord(ev[0], s));
-            phase_points(pl, xl);
-            BGL_CUDA(cudaEventRecord(ev[1], s));
-            phase_tree(pl, T);
-            BGL_CUDA(cudaEventRecord(ev[2], s));
-            phase_lists(pl, T);
-            BGL_CUDA(cudaEventRecord(ev[3], s));
-            expand(pl, T, f.p, pl->q0, ev + 4);
-            BGL_CUDA(cudaEventRecord(ev[6], s));
-            BGL_CUDA(cudaEventSynchronize(ev[6]));
+        const int R = std::max(reps, 1);
+        for (int r = 0; r < R; ++r) {
+            evaluate_any(pl, xl, f.p, pl->q0, false, ev);
+            BGL_CUDA(cudaEventSynchronize(ev[7]));
             float ms;
-            const int order[7] = {0, 1, 2, 3, 4, 5, 6};
-            for (int k = 0; k < 6; ++k) {
-                BGL_CUDA(cudaEventElapsedTime(&ms, ev[order[k]], ev[order[k + 1]]));
+            for (int k = 0; k < 7; ++k) {
+                BGL_CUDA(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
                 acc[k] += ms;
             }
         }
+        // the concurrent schedule used inside ForceAtlas2 iterations
+        for (int r = 0; r < R; ++r) {
+            BGL_CUDA(cudaEventRecord(c0, s));
+            evaluate_any(pl, xl, f.p, pl->q0, true, nullptr);
+            BGL_CUDA(cudaEventRecord(c1, s));
+            BGL_CUDA(cudaEventSynchronize(c1));
+            float ms;
+            BGL_CUDA(cudaEventElapsedTime(&ms, c0, c1));
+            acc[7] += ms;
+        }
     } catch (...) {
         for (auto &e : ev) cudaEventDestroy(e);
+        cudaEventDestroy(c0);
+        cudaEventDestroy(c1);
         throw;
     }
     for (auto &e : ev) cudaEventDestroy(e);
-    DevBuf<unsigned long long> cnt(ctx->alloc, 5);
-    BGL_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 5, s));
+    cudaEventDestroy(c0);
+    cudaEventDestroy(c1);
+    DevBuf<unsigned long long> cnt(ctx->alloc, 6);
+    BGL_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 6, s));
     count_kernel<<<pl->grid_p, 256, 0, s>>>(T, cnt.p);
     BGL_LAUNCH_CHECK();
-    unsigned long long h[5];
+    unsigned long long h[6];
     int lev[NLEV + 1];
     BGL_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     BGL_CUDA(cudaMemcpyAsync(lev, pl->levoff.p, sizeof(lev), cudaMemcpyDeviceToHost, s));
     BGL_CUDA(cudaStreamSynchronize(s));
-    int nbox = std::min(lev[NLEV], pl->Bmax);
-    // V entries per box from the list offsets
-    std::vector<int> offs(4 * (size_t)nbox + 1);
-    BGL_CUDA(cudaMemcpyAsync(offs.data(), pl->lcnt.p, sizeof(int) * offs.size(), cudaMemcpyDeviceToHost, s));
-    BGL_CUDA(cudaStreamSynchronize(s));
-    long long m2l = 0;
-    for (int b = 0; b < nbox; ++b) m2l += offs[4 * b + 2] - offs[4 * b + 1];
     const double R = std::max(reps, 1);
-    out[0] = nbox;
+    out[0] = std::min(lev[NLEV], pl->Bmax);
     out[1] = (double)h[3];
     out[2] = (double)h[4];
     out[3] = (double)h[0];
-    out[4] = (double)m2l;
+    out[4] = (double)h[5];
     out[5] = (double)h[1];
     out[6] = (double)h[2];
-    for (int k = 0; k < 6; ++k) out[7 + k] = acc[k] / R;
+    for (int k = 0; k < 8; ++k) out[7 + k] = acc[k] / R;
 }
 
 int fmm_error(FmmPlan *pl) {
     int e = 0;
     BGL_CUDA(cudaMemcpyAsync(&e, pl->err.p, sizeof(int), cudaMemcpyDeviceToHost, pl->g->ctx->stream));
     BGL_CUDA(cudaStreamSynchronize(pl->g->ctx->stream));
+    if (sort_workspace_error(pl->g->ctx, pl->sortws)) e |= ERR_SPIN;
     return e;
 }
 

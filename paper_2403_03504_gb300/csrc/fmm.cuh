@@ -17,9 +17,10 @@ void fmm_destroy(FmmPlan *pl);
 void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase);
 
 // Counts and per-phase device times of `reps` evaluations (synchronises);
-// out[13]: boxes, leaves, depth, P2P pairs, M2L translations, M2P terms,
+// out[15]: boxes, leaves, depth, P2P pairs, M2L translations, M2P terms,
 // P2L terms, then milliseconds of: points (bbox, keys, sort, gather), tree,
-// lists, upward pass, downward pass, leaf pass.
+// lists, upward pass, downward pass, near field, far field (one stream),
+// and of a whole evaluation in the concurrent schedule.
 void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double *out);
 
 // Error bits raised on the device since the plan was made (synchronises):

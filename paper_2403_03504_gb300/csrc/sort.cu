@@ -6,6 +6,8 @@
 // atomics), one exclusive scan of the digit-major histogram, and a scatter
 // in which each warp ranks its keys with __match_any_sync so that equal
 // digits keep their input order (stable).
+#include <algorithm>
+
 #include "bgl_internal.cuh"
 
 namespace bgl {
@@ -254,6 +256,147 @@ void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
     radix_sort_buffers<K>(c, keys, vals, n, bits, kt.p, vals ? vt.p : nullptr, hist.p, tiles.p);
 }
 
+// ------------------------------------------------------------------ onesweep (32-bit keys)
+//
+// Four 8-bit digit passes.  One histogram kernel counts all four digit
+// histograms at once and its last block turns them into global digit
+// bases.  Each pass is then a single kernel: tiles take increasing indices
+// from a ticket counter, rank their keys stably (per-warp __match_any_sync
+// counts, warps in order), publish their per-digit counts, and look back
+// over earlier tiles' published counts (decoupled look-back, Merrill and
+// Garland) for their global offsets.  Waits are bounded; a wait that gives
+// up records an error bit and the tile carries on.
+
+constexpr int OS_THREADS = 256;
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr int OS_ITEMS = 8;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
+constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_MASK = (1u << 30) - 1u;
+constexpr long long OS_SPIN = 1ll << 24;
+
+__global__ void os_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, uint32_t *hist, uint32_t *base,
+                               unsigned *counter) {
+    __shared__ uint32_t h[4][256];
+    __shared__ bool last;
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) atomicAdd(&h[d][(k >> (8 * d)) & 0xFF], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
+        if ((&h[0][0])[i]) atomicAdd(&hist[i], (&h[0][0])[i]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // exclusive scan of each digit histogram (thread = bin)
+    __shared__ uint32_t ws[8];
+    for (int d = 0; d < 4; ++d) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t v = __ldcg(&hist[d * 256 + threadIdx.x]);
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += ws[w];
+        base[d * 256 + threadIdx.x] = pre + x - v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+__global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *__restrict__ kin,
+                                                                 const uint32_t *__restrict__ vin,
+                                                                 uint32_t *__restrict__ kout,
+                                                                 uint32_t *__restrict__ vout, int64_t n, int shift,
+                                                                 const uint32_t *__restrict__ base,
+                                                                 uint32_t *status, unsigned *ticket, int *err) {
+    __shared__ int32_t cnt[OS_WARPS][256];
+    __shared__ uint32_t gofs[256];
+    __shared__ int tile_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) tile_s = (int)atomicAdd(ticket, 1u);
+    for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int tile = tile_s;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t wbase = (int64_t)tile * OS_TILE + (int64_t)warp * 32 * OS_ITEMS;
+    uint32_t key[OS_ITEMS], val[OS_ITEMS];
+    int32_t rank[OS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < OS_ITEMS; ++r) {
+        const int64_t k = wbase + r * 32 + lane;
+        const bool ok = k < n;
+        key[r] = ok ? kin[k] : 0u;
+        val[r] = ok ? vin[k] : 0u;
+        const unsigned d = ok ? ((key[r] >> shift) & 0xFF) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int before = __popc(peers & lt);
+        const int cur = ok ? cnt[warp][d] : 0;
+        __syncwarp();
+        if (ok && before == 0) cnt[warp][d] = cur + __popc(peers);
+        __syncwarp();
+        rank[r] = ok ? cur + before : -1;
+    }
+    __syncthreads();
+    {
+        // thread = digit: prefix over warps, publish, look back
+        const int d = threadIdx.x;
+        int s = 0;
+#pragma unroll
+        for (int w = 0; w < OS_WARPS; ++w) {
+            const int c = cnt[w][d];
+            cnt[w][d] = s;
+            s += c;
+        }
+        volatile uint32_t *st = status;
+        const uint32_t own = (uint32_t)s;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            st[d] = OS_INC | own;
+        } else {
+            st[(int64_t)tile * 256 + d] = OS_AGG | own;
+            for (int t = tile - 1; t >= 0; --t) {
+                uint32_t v;
+                long long it = 0;
+                while (((v = st[(int64_t)t * 256 + d]) & ~OS_MASK) == 0) {
+                    if (++it > OS_SPIN) {
+                        atomicOr(err, 1);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                excl += v & OS_MASK;
+                if (v & OS_INC) break;
+            }
+            __threadfence();
+            st[(int64_t)tile * 256 + d] = OS_INC | (excl + own);
+        }
+        gofs[d] = base[d] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < OS_ITEMS; ++r) {
+        if (rank[r] < 0) continue;
+        const unsigned d = (key[r] >> shift) & 0xFF;
+        const uint32_t dst = gofs[d] + (uint32_t)cnt[warp][d] + (uint32_t)rank[r];
+        kout[dst] = key[r];
+        vout[dst] = val[r];
+    }
+}
+
+inline int64_t os_tiles(int64_t n) { return (n + OS_TILE - 1) / OS_TILE; }
+
 }  // namespace
 
 void scan_exclusive_i64(bgl_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total) {
@@ -269,19 +412,52 @@ void radix_sort_u32(bgl_ctx *c, uint32_t *keys, uint32_t *vals, int64_t n, int b
     radix_sort<uint32_t>(c, keys, vals, n, bits);
 }
 
-void SortWorkspace::reserve(Allocator *a, int64_t n) {
+void SortWorkspace::reserve(Allocator *a, int64_t n, cudaStream_t s) {
     if (n <= cap) return;
     keys.reset(a, n);
     vals.reset(a, n);
-    hist.reset(a, 256 * rs_tiles(n));
-    tiles.reset(a, scan_tiles_for(256 * rs_tiles(n)));
+    // hist: 4 x 256 digit counts, 4 x 256 digit bases, 4 tickets, 1 counter, error word
+    hist.reset(a, 8 * 256 + 8);
+    BGL_CUDA(cudaMemsetAsync(hist.p, 0, hist.bytes(), s));
+    tiles.reset(a, 4 * 256 * os_tiles(n));   // look-back status words, one block per pass
     cap = n;
 }
 
 void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits) {
     if (n <= 1 || bits <= 0) return;
-    BGL_REQUIRE(n <= ws.cap, "radix sort: workspace too small");
-    radix_sort_buffers<uint32_t>(c, keys, vals, n, bits, ws.keys.p, ws.vals.p, ws.hist.p, ws.tiles.p);
+    BGL_REQUIRE(n <= ws.cap && n < (int64_t(1) << 30), "radix sort: workspace too small");
+    BGL_REQUIRE(bits == 32 && vals, "radix sort: the workspace sort takes 32-bit keys with values");
+    cudaStream_t s = c->stream;
+    const int64_t nt = os_tiles(n);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws.hist.p);
+    uint32_t *base = hist + 4 * 256;
+    unsigned *tickets = reinterpret_cast<unsigned *>(hist + 8 * 256);
+    unsigned *counter = tickets + 4;
+    int *err = reinterpret_cast<int *>(tickets + 5);
+    uint32_t *status = reinterpret_cast<uint32_t *>(ws.tiles.p);
+    BGL_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * 256, s));
+    BGL_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * 5, s));
+    BGL_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t) * 4 * 256 * nt, s));
+    const int hblocks = (int)std::min<int64_t>(2 * c->num_sms, (n + 255) / 256);
+    os_hist_kernel<<<hblocks, 256, 0, s>>>(keys, n, hist, base, counter);
+    BGL_LAUNCH_CHECK();
+    uint32_t *ka = keys, *kb = ws.keys.p, *va = vals, *vb = ws.vals.p;
+    for (int d = 0; d < 4; ++d) {
+        os_scatter_kernel<<<(unsigned)nt, OS_THREADS, 0, s>>>(ka, va, kb, vb, n, 8 * d, base + 256 * d,
+                                                              status + (int64_t)d * 256 * nt, tickets + d, err);
+        BGL_LAUNCH_CHECK();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    // four passes: the sorted data is back in keys / vals
+}
+
+int sort_workspace_error(bgl_ctx *c, SortWorkspace &ws) {
+    int e = 0;
+    int *err = reinterpret_cast<int *>(reinterpret_cast<unsigned *>(ws.hist.p + 8 * 256) + 5);
+    BGL_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BGL_CUDA(cudaStreamSynchronize(c->stream));
+    return e;
 }
 
 int bits_for(uint64_t v) {
