@@ -54,8 +54,13 @@ constexpr long long SPIN_LIMIT = 1ll << 24;
 
 enum { ERR_SPIN = 1, ERR_LIST_OVERFLOW = 2, ERR_BOX_OVERFLOW = 4, ERR_BBOX = 8 };
 
+// Root square and the per-level box geometry in FP32 (GB300's FP64 rate is
+// a small fraction of its FP32 rate, so nothing per point or per box uses it)
 struct Root {
-    double ox, oy, side;
+    double ox, oy, side;        // the square, as computed (FP64, once)
+    float oxf, oyf, scale;      // origin and 65536 / side, for the keys
+    float w[MAXLEV + 1];        // box side at each level
+    float r[MAXLEV + 1];        // box half-width at each level
 };
 
 struct Tree {
@@ -68,6 +73,7 @@ struct Tree {
     uint32_t *bkey;
     int8_t *bleaf;
     int4 *bchild;
+    int2 *bmeta;              // per box {key prefix, level | leaf << 8}: one load in the list builders
     int *levoff;              // [NLEV + 1], levoff[NLEV] = number of boxes
     int *nb;                  // [9 * Bmax]
     int *lofs;                // [5 * Bmax] per box: starts of U, V, W, X and the end, in lidx
@@ -121,13 +127,12 @@ struct BoxGeo {
     float cx, cy, r;
 };
 
-__device__ __forceinline__ BoxGeo box_geo(const Root &rt, uint32_t key, int L) {
-    const double w = rt.side / (double)(1u << L);
-    const double bx = (double)compact_bits(key), by = (double)compact_bits(key >> 1);
+__device__ __forceinline__ BoxGeo box_geo(const Root *__restrict__ rt, uint32_t key, int L) {
+    const float w = rt->w[L];
     BoxGeo g;
-    g.cx = (float)(rt.ox + (bx + 0.5) * w);
-    g.cy = (float)(rt.oy + (by + 0.5) * w);
-    g.r = (float)(0.5 * w);
+    g.cx = rt->oxf + ((float)compact_bits(key) + 0.5f) * w;
+    g.cy = rt->oyf + ((float)compact_bits(key >> 1) + 0.5f) * w;
+    g.r = rt->r[L];
     return g;
 }
 
@@ -213,6 +218,13 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
         atomicOr(err, ERR_BBOX);
         r.ox = r.oy = 0.0;
     }
+    r.oxf = (float)r.ox;
+    r.oyf = (float)r.oy;
+    r.scale = (float)(65536.0 / side);
+    for (int L = 0; L <= MAXLEV; ++L) {
+        r.w[L] = (float)(side / (double)(1u << L));
+        r.r[L] = (float)(0.5 * side / (double)(1u << L));
+    }
     *root = r;
     *counter = 0u;
 }
@@ -221,11 +233,10 @@ __global__ void keys_kernel(const float2 *__restrict__ xy, int n, const Root *__
                             uint32_t *__restrict__ key, uint32_t *__restrict__ idx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const Root rt = *root;
-    const double scale = 65536.0 / rt.side;
+    const float ox = root->oxf, oy = root->oyf, sc = root->scale;
     float2 p = xy[i];
-    double fx = floor(((double)p.x - rt.ox) * scale), fy = floor(((double)p.y - rt.oy) * scale);
-    int qx = (int)fmin(fmax(fx, 0.0), 65535.0), qy = (int)fmin(fmax(fy, 0.0), 65535.0);
+    const float fx = floorf((p.x - ox) * sc), fy = floorf((p.y - oy) * sc);
+    const int qx = (int)fminf(fmaxf(fx, 0.f), 65535.f), qy = (int)fminf(fmaxf(fy, 0.f), 65535.f);
     key[i] = spread_bits((uint32_t)qx) | (spread_bits((uint32_t)qy) << 1);
     idx[i] = (uint32_t)i;
 }
@@ -368,6 +379,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
                 T.blevel[b] = L;
                 T.bkey[b] = prefix_at(k[r], L);
                 T.bleaf[b] = (int8_t)(L == la[r]);
+                T.bmeta[b] = make_int2((int)prefix_at(k[r], L), L | ((L == la[r]) ? 256 : 0));
                 T.bparent[b] = (L >= 1 && L - 1 > c[r]) ? prev[r] : -1;
                 prev[r] = b;
             }
@@ -414,116 +426,129 @@ __global__ void tree_link_kernel(Tree T) {
 
 // ---------------------------------------------------------------- neighbour tables and lists
 
-// Interaction lists of box b (B leaf for U and W).  Each builder counts
-// when out is null and writes otherwise, in one fixed order.
-//   U: b itself, adjacent leaves at b's level or coarser (each once), and the
-//      leaves inside adjacent internal boxes that touch b;
-//   W: children met in that descent that do not touch b (their parent does);
-//   V: children of the parent's neighbours at the parent's level that do not
-//      touch b, with their offset class (dx + 3) * 7 + (dy + 3);
-//   X: leaves at the parent's level or coarser that touch the parent but not b.
-__device__ void lists_uw(const Tree &T, int b, int *ou, int *ow, int &cu, int &cw) {
+__device__ __forceinline__ int meta_level(int2 m) { return m.y & 255; }
+__device__ __forceinline__ bool meta_leaf(int2 m) { return (m.y & 256) != 0; }
+
+// Contribution of neighbour cell k (0..8, k = 4 is the box itself) to the
+// interaction lists of box b.  Each builder counts when out is null and
+// writes otherwise, in a fixed order.
+//   U (b a leaf): b itself (k = 4); the leaf at b's level or coarser covering
+//      cell k (once, if no earlier cell had it); or, for an internal box at
+//      cell k, the leaves inside it that touch b;
+//   W (b a leaf): the children met in that descent that do not touch b;
+//   V (level >= 2): children of the parent's neighbour box at cell k (at the
+//      parent's level) that do not touch b, with their offset class
+//      (dx + 3) * 7 + (dy + 3);
+//   X (level >= 2): the leaf at the parent's level or coarser covering the
+//      parent's cell k, if it does not touch b (once).
+__device__ void lists_uw(const Tree &T, int b, int2 mb, const int *nbb, int k, int *ou, int *ow, int &cu, int &cw) {
     cu = cw = 0;
-    if (!T.bleaf[b]) return;
-    const int L = T.blevel[b];
-    const uint32_t key = T.bkey[b];
-    const int *nbb = T.nb + 9 * b;
-    if (ou) ou[cu] = b;
-    ++cu;
-    for (int k = 0; k < 9; ++k) {
-        if (k == 4) continue;
-        const int A = nbb[k];
-        if (A < 0) continue;
-        bool seen = false;
-        for (int k2 = 0; k2 < k; ++k2)
-            if (k2 != 4 && nbb[k2] == A) seen = true;
-        if (seen) continue;
-        if (T.bleaf[A]) {
-            if (ou) ou[cu] = A;
-            ++cu;
-            continue;
-        }
-        int stack[4 * MAXLEV + 4];
-        int sp = 0;
-        stack[sp++] = A;
-        while (sp > 0) {
-            const int D = stack[--sp];
-            const int4 ch = T.bchild[D];
-            const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
-            for (int q = 3; q >= 0; --q) {
-                const int C = cs[q];
-                if (C < 0) continue;
-                if (boxes_adjacent(T.bkey[C], T.blevel[C], key, L)) {
-                    if (T.bleaf[C]) {
-                        if (ou) ou[cu] = C;
-                        ++cu;
-                    } else if (sp < 4 * MAXLEV + 4) {
-                        stack[sp++] = C;
-                    } else {
-                        atomicOr(T.err, ERR_LIST_OVERFLOW);
-                    }
+    if (!meta_leaf(mb)) return;
+    if (k == 4) {
+        if (ou) ou[0] = b;
+        cu = 1;
+        return;
+    }
+    const int A = nbb[k];
+    if (A < 0) return;
+    for (int k2 = 0; k2 < k; ++k2)
+        if (k2 != 4 && nbb[k2] == A) return;
+    const int2 ma = T.bmeta[A];
+    if (meta_leaf(ma)) {
+        if (ou) ou[0] = A;
+        cu = 1;
+        return;
+    }
+    const uint32_t key = (uint32_t)mb.x;
+    const int L = meta_level(mb);
+    int stack[4 * MAXLEV + 4];
+    int sp = 0;
+    stack[sp++] = A;
+    while (sp > 0) {
+        const int D = stack[--sp];
+        const int4 ch = T.bchild[D];
+        const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+        int2 mc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mc[q] = cs[q] >= 0 ? T.bmeta[cs[q]] : make_int2(0, 0);
+        for (int q = 3; q >= 0; --q) {
+            const int C = cs[q];
+            if (C < 0) continue;
+            if (boxes_adjacent((uint32_t)mc[q].x, meta_level(mc[q]), key, L)) {
+                if (meta_leaf(mc[q])) {
+                    if (ou) ou[cu] = C;
+                    ++cu;
+                } else if (sp < 4 * MAXLEV + 4) {
+                    stack[sp++] = C;
                 } else {
-                    if (ow) ow[cw] = C;
-                    ++cw;
+                    atomicOr(T.err, ERR_LIST_OVERFLOW);
                 }
+            } else {
+                if (ow) ow[cw] = C;
+                ++cw;
             }
         }
     }
 }
 
-__device__ void lists_v(const Tree &T, int b, int *ov, int &cv) {
+__device__ void lists_v(const Tree &T, int2 mb, const int *nbp, int k, int *ov, int &cv) {
     cv = 0;
-    const int L = T.blevel[b];
-    if (L < 2) return;
-    const uint32_t key = T.bkey[b];
+    const int L = meta_level(mb);
+    if (L < 2 || k == 4) return;
+    const int A = nbp[k];
+    if (A < 0) return;
+    const int2 ma = T.bmeta[A];
+    if (meta_level(ma) != L - 1 || meta_leaf(ma)) return;
+    const uint32_t key = (uint32_t)mb.x;
     const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
-    const int *nbp = T.nb + 9 * T.bparent[b];
-    for (int k = 0; k < 9; ++k) {
-        if (k == 4) continue;
-        const int A = nbp[k];
-        if (A < 0 || T.blevel[A] != L - 1 || T.bleaf[A]) continue;
-        const int4 ch = T.bchild[A];
-        const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
-        for (int q = 0; q < 4; ++q) {
-            const int C = cs[q];
-            if (C < 0) continue;
-            const uint32_t kc = T.bkey[C];
-            const int dx = (int)compact_bits(kc) - bx, dy = (int)compact_bits(kc >> 1) - by;
-            if (abs(dx) <= 1 && abs(dy) <= 1) continue;
-            if (ov) ov[cv] = (C << 6) | ((dx + 3) * 7 + (dy + 3));
-            ++cv;
-        }
+    const int4 ch = T.bchild[A];
+    const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+    for (int q = 0; q < 4; ++q) {
+        const int C = cs[q];
+        if (C < 0) continue;
+        const uint32_t kc = (uint32_t)T.bmeta[C].x;
+        const int dx = (int)compact_bits(kc) - bx, dy = (int)compact_bits(kc >> 1) - by;
+        if (abs(dx) <= 1 && abs(dy) <= 1) continue;
+        if (ov) ov[cv] = (C << 6) | ((dx + 3) * 7 + (dy + 3));
+        ++cv;
     }
 }
 
-__device__ void lists_x(const Tree &T, int b, int *ox, int &cx) {
+__device__ void lists_x(const Tree &T, int2 mb, const int *nbp, int k, int *ox, int &cx) {
     cx = 0;
-    const int L = T.blevel[b];
-    if (L < 2) return;
-    const uint32_t key = T.bkey[b];
-    const int *nbp = T.nb + 9 * T.bparent[b];
-    for (int k = 0; k < 9; ++k) {
-        if (k == 4) continue;
-        const int A = nbp[k];
-        if (A < 0 || !T.bleaf[A]) continue;
-        bool seen = false;
-        for (int k2 = 0; k2 < k; ++k2)
-            if (k2 != 4 && nbp[k2] == A) seen = true;
-        if (seen) continue;
-        if (boxes_adjacent(T.bkey[A], T.blevel[A], key, L)) continue;
-        if (ox) ox[cx] = A;
-        ++cx;
+    const int L = meta_level(mb);
+    if (L < 2 || k == 4) return;
+    const int A = nbp[k];
+    if (A < 0) return;
+    for (int k2 = 0; k2 < k; ++k2)
+        if (k2 != 4 && nbp[k2] == A) return;
+    const int2 ma = T.bmeta[A];
+    if (!meta_leaf(ma)) return;
+    if (boxes_adjacent((uint32_t)ma.x, meta_level(ma), (uint32_t)mb.x, L)) return;
+    if (ox) ox[0] = A;
+    cx = 1;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
     }
+    return v;
 }
 
 // Boxes in level order through a ticket counter: the 3x3 neighbour table
 // nb[b][k], k = (dy + 1) * 3 + (dx + 1) (the box at b's level covering the
 // adjacent cell, else the coarser leaf covering it, else -1), built from
 // the parent's table after a bounded wait for it; then the U, V, W and X
-// lists, counted, given one chunk of lidx by an atomic reservation, and
-// written (lanes 0, 1, 2 take U+W, V and X).
+// lists: lanes 0-8 build U and W for cells k = 0..8, lanes 9-17 V and lanes
+// 18-26 X for the parent's cells; warp scans give each lane its offsets in
+// a chunk of lidx reserved by one atomic, so the order is fixed.
 __global__ void nbr_lists_kernel(Tree T, int *ticket, int *done) {
     const int lane = threadIdx.x & 31;
+    const int role = lane / 9, k = lane % 9;
     const int B = min(T.levoff[NLEV], T.Bmax);
     for (;;) {
         int b = 0;
@@ -531,50 +556,57 @@ __global__ void nbr_lists_kernel(Tree T, int *ticket, int *done) {
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= B) return;
         bool ok = true;
+        const int2 mb = T.bmeta[b];
+        const int p = b == 0 ? -1 : T.bparent[b];
         if (b == 0) {
             if (lane < 9) T.nb[lane] = lane == 4 ? 0 : -1;
+        } else if (p < 0 || p >= b) {              // inconsistent tree (capacity error recorded)
+            ok = false;
+            if (lane == 0) atomicOr(T.err, ERR_BOX_OVERFLOW);
+            if (lane < 9) T.nb[b * 9 + lane] = -1;
         } else {
-            const int p = T.bparent[b];
-            if (p < 0 || p >= b) {                 // inconsistent tree (capacity error recorded)
-                ok = false;
-                if (lane == 0) atomicOr(T.err, ERR_BOX_OVERFLOW);
-                if (lane < 9) T.nb[b * 9 + lane] = -1;
-            } else {
-                if (lane == 0) wait_flag(&done[p], T.err);
-                __syncwarp();
-                const int L = T.blevel[b];
-                const uint32_t key = T.bkey[b];
-                const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
-                if (lane < 9) {
-                    const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
-                    int res = -1;
-                    if (nx >= 0 && ny >= 0 && nx < (1 << L) && ny < (1 << L)) {
-                        const int px = bx >> 1, py = by >> 1;
-                        const int kk = ((ny >> 1) - py + 1) * 3 + ((nx >> 1) - px + 1);
-                        const int A = __ldcg(&T.nb[p * 9 + kk]);
-                        if (A >= 0) {
-                            if (T.blevel[A] == L - 1 && !T.bleaf[A])
-                                res = ((const int *)&T.bchild[A])[((ny & 1) << 1) | (nx & 1)];
-                            else res = A;
-                        }
+            if (lane == 0) wait_flag(&done[p], T.err);
+            __syncwarp();
+            const int L = meta_level(mb);
+            const uint32_t key = (uint32_t)mb.x;
+            const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
+            if (lane < 9) {
+                const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
+                int res = -1;
+                if (nx >= 0 && ny >= 0 && nx < (1 << L) && ny < (1 << L)) {
+                    const int px = bx >> 1, py = by >> 1;
+                    const int kk = ((ny >> 1) - py + 1) * 3 + ((nx >> 1) - px + 1);
+                    const int A = __ldcg(&T.nb[p * 9 + kk]);
+                    if (A >= 0) {
+                        const int2 ma = T.bmeta[A];
+                        if (meta_level(ma) == L - 1 && !meta_leaf(ma))
+                            res = ((const int *)&T.bchild[A])[((ny & 1) << 1) | (nx & 1)];
+                        else res = A;
                     }
-                    T.nb[b * 9 + lane] = res;
                 }
+                T.nb[b * 9 + lane] = res;
             }
         }
         __syncwarp();
         __threadfence();
         if (lane == 0) *(volatile int *)&done[b] = 1;
-        // interaction lists of b
-        int c0 = 0, c1 = 0;
-        if (ok) {
-            if (lane == 0) lists_uw(T, b, nullptr, nullptr, c0, c1);
-            else if (lane == 1) lists_v(T, b, nullptr, c0);
-            else if (lane == 2) lists_x(T, b, nullptr, c0);
+        // neighbour rows in registers (own row written by lanes 0-8 just above)
+        int nbb[9], nbp[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            nbb[j] = ok ? T.nb[b * 9 + j] : -1;
+            nbp[j] = (ok && p >= 0) ? __ldcg(&T.nb[p * 9 + j]) : -1;
         }
-        const int cu = __shfl_sync(0xffffffffu, c0, 0), cw = __shfl_sync(0xffffffffu, c1, 0);
-        const int cv = __shfl_sync(0xffffffffu, c0, 1), cx = __shfl_sync(0xffffffffu, c0, 2);
-        const int total = cu + cv + cw + cx;
+        int cu = 0, cw = 0, cv = 0, cx = 0;
+        if (ok) {
+            if (role == 0) lists_uw(T, b, mb, nbb, k, nullptr, nullptr, cu, cw);
+            else if (role == 1) lists_v(T, mb, nbp, k, nullptr, cv);
+            else if (role == 2) lists_x(T, mb, nbp, k, nullptr, cx);
+        }
+        const int iu = warp_incl_scan(cu), iw = warp_incl_scan(cw), iv = warp_incl_scan(cv), ix = warp_incl_scan(cx);
+        const int tu = __shfl_sync(0xffffffffu, iu, 31), tw = __shfl_sync(0xffffffffu, iw, 31);
+        const int tv = __shfl_sync(0xffffffffu, iv, 31), tx = __shfl_sync(0xffffffffu, ix, 31);
+        const int total = tu + tv + tw + tx;
         int base = 0;
         if (lane == 0) {
             base = atomicAdd(T.pool, total);
@@ -590,16 +622,17 @@ __global__ void nbr_lists_kernel(Tree T, int *ticket, int *done) {
         }
         if (lane == 0) {
             T.lofs[5 * b] = base;
-            T.lofs[5 * b + 1] = base + cu;
-            T.lofs[5 * b + 2] = base + cu + cv;
-            T.lofs[5 * b + 3] = base + cu + cv + cw;
+            T.lofs[5 * b + 1] = base + tu;
+            T.lofs[5 * b + 2] = base + tu + tv;
+            T.lofs[5 * b + 3] = base + tu + tv + tw;
             T.lofs[5 * b + 4] = base + total;
         }
         if (ok && total > 0) {
             int d0, d1;
-            if (lane == 0) lists_uw(T, b, T.lidx + base, T.lidx + base + cu + cv, d0, d1);
-            else if (lane == 1) lists_v(T, b, T.lidx + base + cu, d0);
-            else if (lane == 2) lists_x(T, b, T.lidx + base + cu + cv + cw, d0);
+            if (role == 0)
+                lists_uw(T, b, mb, nbb, k, T.lidx + base + (iu - cu), T.lidx + base + tu + tv + (iw - cw), d0, d1);
+            else if (role == 1) lists_v(T, mb, nbp, k, T.lidx + base + tu + (iv - cv), d0);
+            else if (role == 2) lists_x(T, mb, nbp, k, T.lidx + base + tu + tv + tw + (ix - cx), d0);
         }
     }
 }
@@ -659,7 +692,7 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
-    const Root rt = *T.root;
+    const Root *rt = T.root;
     const int p = a.p;
     for (int b = gw; b < B; b += nw) {
         if (!T.bleaf[b]) continue;
@@ -754,7 +787,7 @@ __global__ void __launch_bounds__(256) down_kernel(ExpArgs a) {
     const Tree &T = a.T;
     const int lane = threadIdx.x & 31;
     const int B = min(T.levoff[NLEV], T.Bmax);
-    const Root rt = *T.root;
+    const Root *rt = T.root;
     const int p = a.p;
     for (;;) {
         int b = 0;
@@ -970,7 +1003,7 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
-    const Root rt = *T.root;
+    const Root *rt = T.root;
     const int p = la.e.p;
     for (int b = gw; b < B; b += nw) {
         if (!T.bleaf[b]) continue;
@@ -1036,6 +1069,7 @@ struct FmmPlan {
     DevBuf<int> tcnt, levoff, bstart, bend, blevel, bparent, nb, lofs, lidx;
     DevBuf<uint32_t> bkey;
     DevBuf<int4> bchild;
+    DevBuf<int2> bmeta;
     DevBuf<float2> M, Lc;
     DevBuf<int> arrive, done_nb, done_dn, tickets, err;
     DevBuf<float> binom;
@@ -1091,6 +1125,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->bkey.reset(A, bmax);
         pl->bleaf.reset(A, bmax);
         pl->bchild.reset(A, bmax);
+        pl->bmeta.reset(A, bmax);
         pl->nb.reset(A, 9 * bmax);
         pl->lofs.reset(A, 5 * bmax);
         pl->lidx.reset(A, pl->lcap);
@@ -1140,6 +1175,7 @@ static Tree make_tree(FmmPlan *pl) {
     T.bkey = pl->bkey.p;
     T.bleaf = pl->bleaf.p;
     T.bchild = pl->bchild.p;
+    T.bmeta = pl->bmeta.p;
     T.levoff = pl->levoff.p;
     T.nb = pl->nb.p;
     T.lofs = pl->lofs.p;
