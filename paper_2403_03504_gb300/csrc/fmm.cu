@@ -127,12 +127,15 @@ struct BoxGeo {
     float cx, cy, r;
 };
 
+// Box geometry is defined by the float origin and side: the centre of box
+// (bx, by) at level L is origin + (2 bx + 1) r_L with r_L = side 2^-(L+1)
+// (exact), evaluated with one rounding by a fused multiply-add.
 __device__ __forceinline__ BoxGeo box_geo(const Root *__restrict__ rt, uint32_t key, int L) {
-    const float w = rt->w[L];
+    const float r = rt->r[L];
     BoxGeo g;
-    g.cx = rt->oxf + ((float)compact_bits(key) + 0.5f) * w;
-    g.cy = rt->oyf + ((float)compact_bits(key >> 1) + 0.5f) * w;
-    g.r = rt->r[L];
+    g.cx = fmaf((float)(2 * compact_bits(key) + 1), r, rt->oxf);
+    g.cy = fmaf((float)(2 * compact_bits(key >> 1) + 1), r, rt->oyf);
+    g.r = r;
     return g;
 }
 
@@ -220,10 +223,11 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
     }
     r.oxf = (float)r.ox;
     r.oyf = (float)r.oy;
-    r.scale = (float)(65536.0 / side);
+    const float sidef = (float)(side * (1.0 + 0x1.0p-22));   // rounding up keeps every point inside
+    r.scale = 65536.0f / sidef;
     for (int L = 0; L <= MAXLEV; ++L) {
-        r.w[L] = (float)(side / (double)(1u << L));
-        r.r[L] = (float)(0.5 * side / (double)(1u << L));
+        r.w[L] = ldexpf(sidef, -L);
+        r.r[L] = ldexpf(sidef, -(L + 1));
     }
     *root = r;
     *counter = 0u;
@@ -907,30 +911,61 @@ struct LeafArgs {
 };
 
 // Near field: the direct sum over the points of U for every target of a
-// leaf.  One warp per leaf (leaves taken through a ticket counter), sources
-// staged NEAR_SRC at a time in the warp's own shared memory (no block-wide
-// barriers).  Targets: leaves of 33..64 targets give each lane two targets;
-// smaller ones give each target 32 / ntp lanes (ntp = targets rounded up to a
-// power of two) that split the sources and combine by a fixed butterfly.
-// Writes the raw sum sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the far
-// kernel completes it).
+// leaf.  One warp per leaf (leaves taken through a ticket counter).  The
+// sources are staged NEAR_SRC at a time in the warp's own shared memory
+// with asynchronous 16-byte copies (cp.async), double-buffered: the copies
+// of the next chunk are in flight while the current chunk is summed.
+// Each lane owns two targets: with lps = (targets / 2 rounded up to a power
+// of two) lanes per source split, lane l takes targets l % lps and
+// l % lps + lps of split l / lps, the 32 / lps splits share the sources and
+// combine by a fixed butterfly.  Writes the raw sum
+// sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the far kernel completes it).
 constexpr int NEAR_WARPS = 8;
-constexpr int NEAR_SRC = 256;
+constexpr int NEAR_SRC = 128;
 
 __device__ __forceinline__ void p2p_pair(const float4 &z, const float4 &q, float &fx, float &fy) {
     const float dx = z.x - q.x, dy = z.y - q.y;
-    const float r2 = fmaf(dx, dx, dy * dy);
-    // a coincident pair (the target itself) has dx = dy = 0 and adds 0
-    const float w = q.z * rcp_approx(fmaxf(r2, 1e-30f));
+    // r^2 + 1e-30: a coincident pair (the target itself) has dx = dy = 0 and
+    // adds exactly 0; for any other pair of FP32 points the shift is far below
+    // one rounding of r^2
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
+    const float w = q.z * rcp_approx(r2);
     fx = fmaf(w, dx, fx);
     fy = fmaf(w, dy, fy);
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Issue the copies of the next chunk (up to NEAR_SRC sources of the U list
+// from entry *ui, offset *off) into buf; returns the chunk size.
+__device__ __forceinline__ int stage_chunk(const Tree &T, float4 *buf, int &ui, int &off, int ue, int lane) {
+    int cnt = 0;
+    while (ui < ue && cnt < NEAR_SRC) {
+        const int C = T.lidx[ui];
+        const int cs = T.bstart[C], ce = T.bend[C];
+        const int take = min(ce - cs - off, NEAR_SRC - cnt);
+        for (int k = lane; k < take; k += 32) cp_async16(buf + cnt + k, T.pts + cs + off + k);
+        cnt += take;
+        off += take;
+        if (off == ce - cs) {
+            ++ui;
+            off = 0;
+        }
+    }
+    cp_async_commit();
+    return cnt;
+}
+
 __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
     const Tree &T = la.e.T;
-    __shared__ float4 stage[NEAR_WARPS][NEAR_SRC];
+    __shared__ __align__(16) float4 stage[NEAR_WARPS][2][NEAR_SRC];
     const int lane = threadIdx.x & 31;
-    float4 *src = stage[threadIdx.x >> 5];
+    float4(*buf)[NEAR_SRC] = stage[threadIdx.x >> 5];
     const int B = min(T.levoff[NLEV], T.Bmax);
     for (;;) {
         int b = 0;
@@ -942,53 +977,42 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
         const int us = T.lofs[5 * b], ue = T.lofs[5 * b + 1];
         for (int tb = s; tb < e; tb += 64) {
             const int ntc = min(64, e - tb);
-            const bool two = ntc > 32;
-            int ntp = 1;
-            while (ntp < ntc && ntp < 32) ntp <<= 1;
-            const int S = two ? 1 : 32 / ntp;
-            const int t = two ? lane : (lane & (ntp - 1));
-            const int h = two ? 0 : lane / ntp;
-            const bool v0 = t < ntc, v1 = two && t + 32 < ntc;
+            int lps = 1;
+            while (2 * lps < ntc) lps <<= 1;
+            const int S = 32 / lps;
+            const int t = lane & (lps - 1), h = lane / lps;
+            const bool v0 = t < ntc, v1 = t + lps < ntc;
             const float4 z0 = v0 ? T.pts[tb + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 z1 = v1 ? T.pts[tb + t + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 z1 = v1 ? T.pts[tb + t + lps] : make_float4(0.f, 0.f, 0.f, 0.f);
             float fx0 = 0.f, fy0 = 0.f, fx1 = 0.f, fy1 = 0.f;
-            int ui = us, off = 0;
-            while (ui < ue) {
-                int cnt = 0;
-                while (ui < ue && cnt < NEAR_SRC) {
-                    const int C = T.lidx[ui];
-                    const int cs = T.bstart[C], ce = T.bend[C];
-                    const int take = min(ce - cs - off, NEAR_SRC - cnt);
-                    for (int k = lane; k < take; k += 32) src[cnt + k] = T.pts[cs + off + k];
-                    cnt += take;
-                    off += take;
-                    if (off == ce - cs) {
-                        ++ui;
-                        off = 0;
-                    }
+            int ui = us, off = 0, cur = 0;
+            int cnt = stage_chunk(T, buf[0], ui, off, ue, lane);
+            while (cnt > 0) {
+                // next chunk in flight while this one is summed
+                const int nxt = ui < ue ? stage_chunk(T, buf[cur ^ 1], ui, off, ue, lane) : (cp_async_commit(), 0);
+                cp_async_wait_one();
+                __syncwarp();
+                const float4 *src = buf[cur];
+#pragma unroll 4
+                for (int j = h; j < cnt; j += S) {
+                    const float4 q = src[j];
+                    p2p_pair(z0, q, fx0, fy0);
+                    p2p_pair(z1, q, fx1, fy1);
                 }
                 __syncwarp();
-                if (two) {
-#pragma unroll 4
-                    for (int j = 0; j < cnt; ++j) {
-                        const float4 q = src[j];
-                        p2p_pair(z0, q, fx0, fy0);
-                        p2p_pair(z1, q, fx1, fy1);
-                    }
-                } else {
-#pragma unroll 4
-                    for (int j = h; j < cnt; j += S) p2p_pair(z0, src[j], fx0, fy0);
-                }
-                __syncwarp();
+                cur ^= 1;
+                cnt = nxt;
             }
-            if (!two) {
-                for (int o = ntp; o < 32; o <<= 1) {
-                    fx0 += __shfl_xor_sync(0xffffffffu, fx0, o);
-                    fy0 += __shfl_xor_sync(0xffffffffu, fy0, o);
-                }
+            for (int o = lps; o < 32; o <<= 1) {
+                fx0 += __shfl_xor_sync(0xffffffffu, fx0, o);
+                fy0 += __shfl_xor_sync(0xffffffffu, fy0, o);
+                fx1 += __shfl_xor_sync(0xffffffffu, fx1, o);
+                fy1 += __shfl_xor_sync(0xffffffffu, fy1, o);
             }
-            if (v0 && h == 0) la.f[la.q0 + __float_as_int(z0.w) - la.fbase] = make_float2(fx0, fy0);
-            if (v1) la.f[la.q0 + __float_as_int(z1.w) - la.fbase] = make_float2(fx1, fy1);
+            if (h == 0) {
+                if (v0) la.f[la.q0 + __float_as_int(z0.w) - la.fbase] = make_float2(fx0, fy0);
+                if (v1) la.f[la.q0 + __float_as_int(z1.w) - la.fbase] = make_float2(fx1, fy1);
+            }
         }
     }
 }
