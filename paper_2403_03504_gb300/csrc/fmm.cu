@@ -75,10 +75,13 @@ struct Tree {
     int4 *bchild;
     int2 *bmeta;              // per box {key prefix, level | leaf << 8}: one load in the list builders
     int *levoff;              // [NLEV + 1], levoff[NLEV] = number of boxes
-    int *nb;                  // [9 * Bmax]
     int *lofs;                // [5 * Bmax] per box: starts of U, V, W, X and the end, in lidx
     int *lidx;                // list entries (each box's lists in one chunk)
     int *pool;                // entries handed out so far (zero at the start of an evaluation)
+    unsigned long long *hkey; // box hash table: keys tagged with the evaluation epoch
+    int *hval;                //   and box indices
+    int hmask;                // table size - 1 (a power of two)
+    const unsigned *epoch;    // evaluation counter (1..2^24-1)
     int lcap;                 // capacity of lidx
     int Bmax;                 // capacity of the box arrays
     const Root *root;
@@ -148,10 +151,75 @@ __device__ __forceinline__ bool boxes_adjacent(uint32_t ka, int La, uint32_t kb,
     return max(ax, bx) <= min(ax + aw, bx + bw) && max(ay, by) <= min(ay + aw, by + bw);
 }
 
+// ---------------------------------------------------------------- box hash table
+//
+// Keys: epoch (24 bits) << 40 | level << 35 | Morton prefix (32 bits).  A
+// slot holding another epoch's key counts as empty, so the table is never
+// cleared; linear probing; the value array is written by the inserting
+// thread and read only by later kernels.
+__device__ __forceinline__ unsigned long long hash_key(unsigned epoch, int L, uint32_t prefix) {
+    return ((unsigned long long)epoch << 40) | ((unsigned long long)L << 35) | (unsigned long long)prefix;
+}
+
+__device__ __forceinline__ unsigned hash_slot(unsigned long long k, int mask) {
+    k ^= k >> 31;
+    k *= 0x7fb5d329728ea185ull;
+    k ^= k >> 27;
+    return (unsigned)k & (unsigned)mask;
+}
+
+__device__ void hash_insert(const unsigned long long *hk_, int *hv, int mask, unsigned epoch, int L, uint32_t prefix,
+                            int box, int *err) {
+    unsigned long long *hk = const_cast<unsigned long long *>(hk_);
+    const unsigned long long k = hash_key(epoch, L, prefix);
+    unsigned s = hash_slot(k, mask);
+    for (int probe = 0; probe <= mask; ++probe) {
+        unsigned long long cur = hk[s];
+        while ((cur >> 40) != epoch) {             // empty (stale): try to claim it
+            const unsigned long long prev = atomicCAS(&hk[s], cur, k);
+            if (prev == cur) {
+                hv[s] = box;
+                return;
+            }
+            cur = prev;
+        }
+        s = (s + 1) & (unsigned)mask;
+    }
+    atomicOr(err, 4);                              // table full (cannot happen at twice the box capacity)
+}
+
+// box index of (L, prefix) in this evaluation, or -1
+__device__ __forceinline__ int hash_find(const Tree &T, unsigned epoch, int L, uint32_t prefix) {
+    const unsigned long long k = hash_key(epoch, L, prefix);
+    unsigned s = hash_slot(k, T.hmask);
+    for (int probe = 0; probe <= T.hmask; ++probe) {
+        const unsigned long long cur = __ldcg(&T.hkey[s]);
+        if (cur == k) return __ldcg(&T.hval[s]);
+        if ((cur >> 40) != epoch) return -1;
+        s = (s + 1) & (unsigned)T.hmask;
+    }
+    return -1;
+}
+
+// The box at level L covering cell (cx, cy) of level L, else the coarser
+// leaf covering it, else -1 (empty cell or outside the root square).
+__device__ int cover(const Tree &T, unsigned epoch, int L, int cx, int cy) {
+    if (cx < 0 || cy < 0 || cx >= (1 << L) || cy >= (1 << L)) return -1;
+    for (int l = L; l >= 0; --l) {
+        const int d = L - l;
+        const uint32_t pre = spread_bits((uint32_t)(cx >> d)) | (spread_bits((uint32_t)(cy >> d)) << 1);
+        const int A = hash_find(T, epoch, l, pre);
+        if (A < 0) continue;
+        if (l == L) return A;
+        return (T.bmeta[A].y & 256) ? A : -1;
+    }
+    return -1;
+}
+
 // ---------------------------------------------------------------- bbox, keys, gather
 
 __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__restrict__ part, unsigned *counter,
-                            Root *root, int *err) {
+                            Root *root, int *err, unsigned *epoch) {
     __shared__ float4 wred[32];
     __shared__ bool last;
     float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
@@ -231,6 +299,7 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
     }
     *root = r;
     *counter = 0u;
+    *epoch = (*epoch % 0xFFFFFEu) + 1u;   // 1 .. 2^24 - 2; 0 never tags a live key
 }
 
 __global__ void keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
@@ -425,6 +494,7 @@ __global__ void tree_link_kernel(Tree T) {
             else atomicOr(T.err, ERR_BOX_OVERFLOW);
         }
         T.bend[b] = end;
+        hash_insert(T.hkey, T.hval, T.hmask, *T.epoch, L, T.bkey[b], b, T.err);
     }
 }
 
@@ -543,70 +613,43 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
-// Boxes in level order through a ticket counter: the 3x3 neighbour table
-// nb[b][k], k = (dy + 1) * 3 + (dx + 1) (the box at b's level covering the
-// adjacent cell, else the coarser leaf covering it, else -1), built from
-// the parent's table after a bounded wait for it; then the U, V, W and X
-// lists: lanes 0-8 build U and W for cells k = 0..8, lanes 9-17 V and lanes
-// 18-26 X for the parent's cells; warp scans give each lane its offsets in
-// a chunk of lidx reserved by one atomic, so the order is fixed.
-__global__ void nbr_lists_kernel(Tree T, int *ticket, int *done) {
+// Neighbour cells and interaction lists, one warp per box (no waits).
+// Lanes 0-8 look up the 3x3 cells around the box (k = (dy + 1) * 3 + dx + 1:
+// the box at its level covering the cell, else the coarser leaf covering it,
+// else -1), lanes 9-17 those around its parent; then lanes 0-8 build U and W
+// for cells k = 0..8, lanes 9-17 V and lanes 18-26 X for the parent's cells;
+// warp scans give each lane its offsets in a chunk of lidx reserved by one
+// atomic, so the order inside every list is fixed.
+__global__ void nbr_lists_kernel(Tree T) {
     const int lane = threadIdx.x & 31;
     const int role = lane / 9, k = lane % 9;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
-    for (;;) {
-        int b = 0;
-        if (lane == 0) b = atomicAdd(ticket, 1);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= B) return;
-        bool ok = true;
+    const unsigned epoch = *T.epoch;
+    for (int b = gw; b < B; b += nw) {
         const int2 mb = T.bmeta[b];
+        const int L = meta_level(mb);
+        const uint32_t key = (uint32_t)mb.x;
+        const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
         const int p = b == 0 ? -1 : T.bparent[b];
-        if (b == 0) {
-            if (lane < 9) T.nb[lane] = lane == 4 ? 0 : -1;
-        } else if (p < 0 || p >= b) {              // inconsistent tree (capacity error recorded)
-            ok = false;
-            if (lane == 0) atomicOr(T.err, ERR_BOX_OVERFLOW);
-            if (lane < 9) T.nb[b * 9 + lane] = -1;
-        } else {
-            if (lane == 0) wait_flag(&done[p], T.err);
-            __syncwarp();
-            const int L = meta_level(mb);
-            const uint32_t key = (uint32_t)mb.x;
-            const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
-            if (lane < 9) {
-                const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
-                int res = -1;
-                if (nx >= 0 && ny >= 0 && nx < (1 << L) && ny < (1 << L)) {
-                    const int px = bx >> 1, py = by >> 1;
-                    const int kk = ((ny >> 1) - py + 1) * 3 + ((nx >> 1) - px + 1);
-                    const int A = __ldcg(&T.nb[p * 9 + kk]);
-                    if (A >= 0) {
-                        const int2 ma = T.bmeta[A];
-                        if (meta_level(ma) == L - 1 && !meta_leaf(ma))
-                            res = ((const int *)&T.bchild[A])[((ny & 1) << 1) | (nx & 1)];
-                        else res = A;
-                    }
-                }
-                T.nb[b * 9 + lane] = res;
-            }
+        int mine = -1;
+        if (lane < 9) {
+            mine = lane == 4 ? b : cover(T, epoch, L, bx + lane % 3 - 1, by + lane / 3 - 1);
+        } else if (lane < 18 && p >= 0) {
+            const int j = lane - 9;
+            mine = j == 4 ? p : cover(T, epoch, L - 1, (bx >> 1) + j % 3 - 1, (by >> 1) + j / 3 - 1);
         }
-        __syncwarp();
-        __threadfence();
-        if (lane == 0) *(volatile int *)&done[b] = 1;
-        // neighbour rows in registers (own row written by lanes 0-8 just above)
         int nbb[9], nbp[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            nbb[j] = ok ? T.nb[b * 9 + j] : -1;
-            nbp[j] = (ok && p >= 0) ? __ldcg(&T.nb[p * 9 + j]) : -1;
+            nbb[j] = __shfl_sync(0xffffffffu, mine, j);
+            nbp[j] = __shfl_sync(0xffffffffu, mine, 9 + j);
         }
         int cu = 0, cw = 0, cv = 0, cx = 0;
-        if (ok) {
-            if (role == 0) lists_uw(T, b, mb, nbb, k, nullptr, nullptr, cu, cw);
-            else if (role == 1) lists_v(T, mb, nbp, k, nullptr, cv);
-            else if (role == 2) lists_x(T, mb, nbp, k, nullptr, cx);
-        }
+        if (role == 0) lists_uw(T, b, mb, nbb, k, nullptr, nullptr, cu, cw);
+        else if (role == 1 && p >= 0) lists_v(T, mb, nbp, k, nullptr, cv);
+        else if (role == 2 && p >= 0) lists_x(T, mb, nbp, k, nullptr, cx);
         const int iu = warp_incl_scan(cu), iw = warp_incl_scan(cw), iv = warp_incl_scan(cv), ix = warp_incl_scan(cx);
         const int tu = __shfl_sync(0xffffffffu, iu, 31), tw = __shfl_sync(0xffffffffu, iw, 31);
         const int tv = __shfl_sync(0xffffffffu, iv, 31), tx = __shfl_sync(0xffffffffu, ix, 31);
@@ -631,12 +674,12 @@ __global__ void nbr_lists_kernel(Tree T, int *ticket, int *done) {
             T.lofs[5 * b + 3] = base + tu + tv + tw;
             T.lofs[5 * b + 4] = base + total;
         }
-        if (ok && total > 0) {
+        if (total > 0) {
             int d0, d1;
             if (role == 0)
                 lists_uw(T, b, mb, nbb, k, T.lidx + base + (iu - cu), T.lidx + base + tu + tv + (iw - cw), d0, d1);
-            else if (role == 1) lists_v(T, mb, nbp, k, T.lidx + base + tu + (iv - cv), d0);
-            else if (role == 2) lists_x(T, mb, nbp, k, T.lidx + base + tu + tv + tw + (ix - cx), d0);
+            else if (role == 1 && p >= 0) lists_v(T, mb, nbp, k, T.lidx + base + tu + (iv - cv), d0);
+            else if (role == 2 && p >= 0) lists_x(T, mb, nbp, k, T.lidx + base + tu + tv + tw + (ix - cx), d0);
         }
     }
 }
@@ -684,7 +727,13 @@ struct ExpArgs {
     int p;
 };
 
-// P2M at leaves, then M2M into each parent by its last child to finish
+// Outgoing expansions of the boxes of level >= 2 (the only ones any list
+// uses).  A box of at most P2M_MAX points gets its expansion directly from
+// its points (P2M, one warp, fixed butterfly).  The few larger boxes near
+// the root get theirs by M2M from their four children, computed by the last
+// child to finish (an arrival count per box), so no warp waits.
+constexpr int P2M_MAX = 2048;
+
 template <int PT>
 __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
     __shared__ float sbin[BN * BN];
@@ -696,26 +745,27 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
+    const int b0 = min(T.levoff[2], B);
     const Root *rt = T.root;
     const int p = a.p;
-    for (int b = gw; b < B; b += nw) {
-        if (!T.bleaf[b]) continue;
-        const int L = T.blevel[b];
-        const BoxGeo g = box_geo(rt, T.bkey[b], L);
+    for (int b = b0 + gw; b < B; b += nw) {
+        const int s = T.bstart[b], e = T.bend[b];
+        const int2 mb = T.bmeta[b];
+        if (e - s > P2M_MAX && !meta_leaf(mb)) continue;   // filled by M2M below
+        const BoxGeo g = box_geo(rt, (uint32_t)mb.x, mb.y & 255);
         const float ir = 1.0f / g.r;
         float2 acc[PT + 1];
 #pragma unroll
         for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
-        const int e = T.bend[b];
-        for (int j = T.bstart[b] + lane; j < e; j += 32) {
-            const float4 s = T.pts[j];
-            const float2 w = make_float2((s.x - g.cx) * ir, (s.y - g.cy) * ir);
+        for (int j = s + lane; j < e; j += 32) {
+            const float4 q = T.pts[j];
+            const float2 w = make_float2((q.x - g.cx) * ir, (q.y - g.cy) * ir);
             float2 pw = w;
-            acc[0].x += s.z;
+            acc[0].x += q.z;
 #pragma unroll
             for (int k = 1; k <= PT; ++k) {
-                acc[k].x = fmaf(s.z, pw.x, acc[k].x);
-                acc[k].y = fmaf(s.z, pw.y, acc[k].y);
+                acc[k].x = fmaf(q.z, pw.x, acc[k].x);
+                acc[k].y = fmaf(q.z, pw.y, acc[k].y);
                 pw = cmul(pw, w);
             }
         }
@@ -730,7 +780,7 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
         int child = b;
         for (;;) {
             const int pb = T.bparent[child];
-            if (pb < 0) break;
+            if (pb < 0 || (T.bmeta[pb].y & 255) < 2 || T.bend[pb] - T.bstart[pb] <= P2M_MAX) break;
             int last = 0;
             const int4 ch = T.bchild[pb];
             const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
@@ -761,17 +811,17 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
                         continue;
                     }
                     float2 pw = make_float2(1.f, 0.f);
-                    float2 s = make_float2(0.f, 0.f);
+                    float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int k = PT; k >= 1; --k) {
                         if (k <= l) {
                             const float cb = sbin[(l - 1) * BN + (k - 1)] * ldexpf(1.0f, -k);
-                            s = cadd(s, cscale(cmul(stage[wib][q][k], pw), cb));
+                            sum = cadd(sum, cscale(cmul(stage[wib][q][k], pw), cb));
                             pw = cmul(pw, u);
                         }
                     }
-                    s = cadd(s, cscale(cmul(a0, pw), -1.0f / (float)l));   // pw = u^l
-                    out = cadd(out, s);
+                    sum = cadd(sum, cscale(cmul(a0, pw), -1.0f / (float)l));   // pw = u^l
+                    out = cadd(out, sum);
                 }
                 a.M[(size_t)pb * (PT + 1) + l] = out;
             }
@@ -782,31 +832,25 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
     }
 }
 
-// M2L over V, P2L over X, L2L from the parent, in level order
+// Incoming expansion of every box of level >= 2 from its own interaction
+// lists only (no parent term): M2L over V and P2L over X, one warp per box,
+// lanes over the V entries and over the points of X leaves, a fixed
+// butterfly to combine.  Boxes are independent, so the pass has no waits;
+// the parents' contributions are folded in at the leaves (far_kernel).
 template <int PT>
-__global__ void __launch_bounds__(256) down_kernel(ExpArgs a) {
+__global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
     __shared__ float sbin[BN * BN];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
     __syncthreads();
     const Tree &T = a.T;
     const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
+    const int b0 = min(T.levoff[2], B);            // boxes of levels 0 and 1 have empty lists
     const Root *rt = T.root;
     const int p = a.p;
-    for (;;) {
-        int b = 0;
-        if (lane == 0) b = atomicAdd(a.ticket, 1);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= B) return;
-        const int L = T.blevel[b];
-        float2 *lb = a.Lc + (size_t)b * (PT + 1);
-        if (L <= 1) {
-            if (lane <= p) lb[lane] = make_float2(0.f, 0.f);
-            __syncwarp();
-            __threadfence();
-            if (lane == 0) *(volatile int *)&a.done[b] = 1;
-            continue;
-        }
+    for (int b = b0 + gw; b < B; b += nw) {
         float2 acc[PT + 1];
 #pragma unroll
         for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -843,7 +887,8 @@ __global__ void __launch_bounds__(256) down_kernel(ExpArgs a) {
             }
         }
         // P2L: b~_l += -q t^l / l, t = r / (z_j - c)
-        const BoxGeo g = box_geo(rt, T.bkey[b], L);
+        const int2 mb = T.bmeta[b];
+        const BoxGeo g = box_geo(rt, (uint32_t)mb.x, mb.y & 255);
         const int xs = T.lofs[5 * b + 3], xe = T.lofs[5 * b + 4];
         for (int e = xs; e < xe; ++e) {
             const int C = T.lidx[e];
@@ -861,38 +906,7 @@ __global__ void __launch_bounds__(256) down_kernel(ExpArgs a) {
             }
         }
         warp_reduce<PT>(acc);
-        // L2L from the parent: c_l = b~_l(parent) 2^-l, Taylor shift by s = (+-1 +- i)
-        const int pb = T.bparent[b];
-        if (pb < 0 || pb >= b) {                   // inconsistent tree (capacity error recorded)
-            if (lane == 0) atomicOr(T.err, ERR_BOX_OVERFLOW);
-            if (lane <= p) lb[lane] = make_float2(0.f, 0.f);
-            __syncwarp();
-            if (lane == 0) *(volatile int *)&a.done[b] = 1;
-            continue;
-        }
-        if (lane == 0) wait_flag(&a.done[pb], T.err);
-        __syncwarp();
-        const uint32_t q = T.bkey[b] & 3u;
-        const float2 sft = make_float2((q & 1u) ? 1.f : -1.f, (q & 2u) ? 1.f : -1.f);
-        const float2 *lp = a.Lc + (size_t)pb * (PT + 1);
-        float2 mine = make_float2(0.f, 0.f);
-        if (lane >= 1 && lane <= p) {
-            const int m = lane;
-            float2 pw = make_float2(1.f, 0.f);
-            float scale = 1.0f;
-            for (int l = 1; l <= m; ++l) scale *= 0.5f;
-            for (int l = m; l <= p; ++l) {
-                const float2 cl = cscale(__ldcg(&lp[l]), scale * sbin[l * BN + m]);
-                mine = cadd(mine, cmul(cl, pw));
-                pw = cmul(pw, sft);
-                scale *= 0.5f;
-            }
-            mine = cadd(mine, pick<PT>(acc, m));
-        }
-        if (lane <= p) lb[lane] = mine;
-        __syncwarp();
-        __threadfence();
-        if (lane == 0) *(volatile int *)&a.done[b] = 1;
+        if (lane <= p) a.Lc[(size_t)b * (PT + 1) + lane] = lane == 0 ? make_float2(0.f, 0.f) : pick<PT>(acc, lane);
     }
 }
 
@@ -1017,27 +1031,68 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
     }
 }
 
-// Far field of every target of a leaf (one warp per leaf, a lane per
-// target): L2P of the leaf's local expansion and M2P over W, added to the
-// near sum; then F_rep = kr m_i (near + conj(E_far)).
+// Far field of every target of a leaf (one warp per leaf).  First the
+// leaf's incoming expansion: the sum over its ancestors A of levels >= 2
+// (and itself) of A's M2L + P2L expansion shifted from c_A to the leaf
+// centre -- the chain of L2L shifts of the downward pass composed into one
+// shift per ancestor:
+//   b~_m(leaf) += 2^(-D m) sum_{l >= m} b~_l(A) C(l, m) t^(l-m),
+//   t = (c_leaf - c_A) / r_A, D = level(leaf) - level(A);
+// lane m computes coefficient m.  Then, a lane per target: L2P of that
+// expansion and M2P over W, added to the near sum; F_rep = kr m_i
+// (near + conj(E_far)).
 template <int PT>
 __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
+    __shared__ float sbin[BN * BN];
+    __shared__ float2 loc[8][PT + 1];
+    for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = la.e.binom[i];
+    __syncthreads();
     const Tree &T = la.e.T;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
     const Root *rt = T.root;
     const int p = la.e.p;
     for (int b = gw; b < B; b += nw) {
-        if (!T.bleaf[b]) continue;
-        const BoxGeo g = box_geo(rt, T.bkey[b], T.blevel[b]);
+        const int2 mb = T.bmeta[b];
+        if (!meta_leaf(mb)) continue;
+        const int Lb = mb.y & 255;
+        const uint32_t kb = (uint32_t)mb.x;
+        // incoming expansion of the leaf, lane m = coefficient m
+        float2 mine = make_float2(0.f, 0.f);
+        if (lane >= 1 && lane <= p) {
+            const int m = lane;
+            int A = b;
+            while (A >= 0) {
+                const int2 ma = T.bmeta[A];
+                const int La = ma.y & 255;
+                if (La < 2) break;
+                const int D = Lb - La;
+                const uint32_t ka = (uint32_t)ma.x;
+                // t = (c_leaf - c_A) / r_A: offsets in units of the leaf half-width, scaled by 2^-D
+                const float sx = (float)((int)(2 * compact_bits(kb) + 1) - (int)(2 * compact_bits(ka) + 1) * (1 << D));
+                const float sy = (float)((int)(2 * compact_bits(kb >> 1) + 1) -
+                                         (int)(2 * compact_bits(ka >> 1) + 1) * (1 << D));
+                const float2 t = make_float2(ldexpf(sx, -D), ldexpf(sy, -D));
+                const float2 *la_ = la.e.Lc + (size_t)A * (PT + 1);
+                float2 s = make_float2(0.f, 0.f), pw = make_float2(1.f, 0.f);
+                for (int l = m; l <= p; ++l) {
+                    s = cadd(s, cscale(cmul(la_[l], pw), sbin[l * BN + m]));
+                    pw = cmul(pw, t);
+                }
+                mine = cadd(mine, cscale(s, ldexpf(1.0f, -D * m)));
+                A = T.bparent[A];
+            }
+        }
+        if (lane <= PT) loc[wib][lane] = mine;
+        __syncwarp();
+        const BoxGeo g = box_geo(rt, kb, Lb);
         const int s = T.bstart[b], e = T.bend[b];
         const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
-        const float2 *lb = la.e.Lc + (size_t)b * (PT + 1);
-        for (int t = s + lane; t < e; t += 32) {
-            const float4 z = T.pts[t];
-            float2 E = make_float2(0.f, 0.f);
+        for (int tt = s + lane; tt < e; tt += 32) {
+            const float4 z = T.pts[tt];
+            float2 E;
             // L2P: E = (1/r) sum_l l b~_l v^(l-1), v = (z - c) / r
             {
                 const float ir = 1.0f / g.r;
@@ -1045,24 +1100,25 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
                 float2 hs = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int l = PT; l >= 1; --l) {
-                    if (l <= p) hs = cadd(cmul(hs, v), cscale(lb[l], (float)l));
+                    if (l <= p) hs = cadd(cmul(hs, v), cscale(loc[wib][l], (float)l));
                 }
                 E = cscale(hs, ir);
             }
             // M2P: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
             for (int k = ws; k < we; ++k) {
-                const int D = T.lidx[k];
-                const BoxGeo gd = box_geo(rt, T.bkey[D], T.blevel[D]);
+                const int Dx = T.lidx[k];
+                const int2 md_ = T.bmeta[Dx];
+                const BoxGeo gd = box_geo(rt, (uint32_t)md_.x, md_.y & 255);
                 const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
                 const float2 idz = crcp(dz);
-                const float2 tt = cscale(idz, gd.r);
-                const float2 *md = la.e.M + (size_t)D * (PT + 1);
+                const float2 tt2 = cscale(idz, gd.r);
+                const float2 *md = la.e.M + (size_t)Dx * (PT + 1);
                 float2 hs = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int kk = PT; kk >= 1; --kk) {
-                    if (kk <= p) hs = cadd(cmul(hs, tt), cscale(md[kk], (float)kk));
+                    if (kk <= p) hs = cadd(cmul(hs, tt2), cscale(md[kk], (float)kk));
                 }
-                hs = cmul(hs, tt);
+                hs = cmul(hs, tt2);
                 const float2 a0 = md[0];
                 E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
             }
@@ -1072,6 +1128,7 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
             const float km = la.kr * z.z;
             *fo = make_float2(km * (nr.x + E.x), km * (nr.y - E.y));
         }
+        __syncwarp();
     }
 }
 
@@ -1090,12 +1147,16 @@ struct FmmPlan {
     DevBuf<uint32_t> key, idx;
     DevBuf<float4> pts;
     DevBuf<int8_t> cl, lam, bleaf;
-    DevBuf<int> tcnt, levoff, bstart, bend, blevel, bparent, nb, lofs, lidx;
+    DevBuf<int> tcnt, levoff, bstart, bend, blevel, bparent, lofs, lidx;
     DevBuf<uint32_t> bkey;
     DevBuf<int4> bchild;
     DevBuf<int2> bmeta;
     DevBuf<float2> M, Lc;
-    DevBuf<int> arrive, done_nb, done_dn, tickets, err;
+    DevBuf<int> arrive, tickets, err;
+    DevBuf<unsigned long long> hkey;
+    DevBuf<int> hval;
+    DevBuf<unsigned> epoch;
+    int hmask = 0;
     DevBuf<float> binom;
     SortWorkspace sortws;
     cudaStream_t side = nullptr;          // second stream for the concurrent branch
@@ -1150,14 +1211,19 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->bleaf.reset(A, bmax);
         pl->bchild.reset(A, bmax);
         pl->bmeta.reset(A, bmax);
-        pl->nb.reset(A, 9 * bmax);
         pl->lofs.reset(A, 5 * bmax);
         pl->lidx.reset(A, pl->lcap);
         pl->M.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->Lc.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->arrive.reset(A, bmax);
-        pl->done_nb.reset(A, bmax);
-        pl->done_dn.reset(A, bmax);
+        int64_t hs = 1;
+        while (hs < 2 * bmax) hs <<= 1;
+        pl->hmask = (int)(hs - 1);
+        pl->hkey.reset(A, hs);
+        pl->hval.reset(A, hs);
+        pl->epoch.reset(A, 1);
+        BGL_CUDA(cudaMemsetAsync(pl->hkey.p, 0, sizeof(unsigned long long) * hs, s));
+        BGL_CUDA(cudaMemsetAsync(pl->epoch.p, 0, sizeof(unsigned), s));
         pl->tickets.reset(A, 8);
         pl->err.reset(A, 1);
         pl->sortws.reserve(A, n, s);
@@ -1201,10 +1267,13 @@ static Tree make_tree(FmmPlan *pl) {
     T.bchild = pl->bchild.p;
     T.bmeta = pl->bmeta.p;
     T.levoff = pl->levoff.p;
-    T.nb = pl->nb.p;
     T.lofs = pl->lofs.p;
     T.lidx = pl->lidx.p;
     T.pool = pl->tickets.p + 3;
+    T.hkey = pl->hkey.p;
+    T.hval = pl->hval.p;
+    T.hmask = pl->hmask;
+    T.epoch = pl->epoch.p;
     T.lcap = pl->lcap;
     T.Bmax = pl->Bmax;
     T.root = pl->root.p;
@@ -1218,7 +1287,7 @@ static ExpArgs exp_args(FmmPlan *pl, const Tree &T) {
     a.M = pl->M.p;
     a.Lc = pl->Lc.p;
     a.arrive = pl->arrive.p;
-    a.done = pl->done_dn.p;
+    a.done = nullptr;
     a.ticket = pl->tickets.p + 1;
     a.binom = pl->binom.p;
     a.p = pl->p;
@@ -1243,7 +1312,7 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
     const float *ml = pl->g->mass.p + pl->q0;
     BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 8, s));
     bbox_kernel<<<std::min<int64_t>(1024, nblk(n, 256)), 256, 0, s>>>(xl, n, pl->part.p, pl->counter.p, pl->root.p,
-                                                                      pl->err.p);
+                                                                      pl->err.p, pl->epoch.p);
     BGL_LAUNCH_CHECK();
     keys_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p);
     BGL_LAUNCH_CHECK();
@@ -1276,8 +1345,7 @@ static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
 
 // neighbour tables and interaction lists
 static void phase_lists(FmmPlan *pl, const Tree &T, cudaStream_t s) {
-    BGL_CUDA(cudaMemsetAsync(pl->done_nb.p, 0, sizeof(int) * pl->Bmax, s));
-    nbr_lists_kernel<<<pl->grid_p, 256, 0, s>>>(T, pl->tickets.p, pl->done_nb.p);
+    nbr_lists_kernel<<<pl->grid_p, 256, 0, s>>>(T);
     BGL_LAUNCH_CHECK();
 }
 
@@ -1288,8 +1356,7 @@ static void launch_up(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
 }
 template <int PT>
 static void launch_down(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
-    BGL_CUDA(cudaMemsetAsync(pl->done_dn.p, 0, sizeof(int) * pl->Bmax, s));
-    down_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
+    m2l_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
     BGL_LAUNCH_CHECK();
 }
 static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
