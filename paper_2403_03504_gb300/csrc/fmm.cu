@@ -1035,7 +1035,7 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
 // leaf's incoming expansion: the sum over its ancestors A of levels >= 2
 // (and itself) of A's M2L + P2L expansion shifted from c_A to the leaf
 // centre -- the chain of L2L shifts of the downward pass composed into one
-// shift per ancestor:
+// shift per ancestor (ancestors found by independent hash lookups):
 //   b~_m(leaf) += 2^(-D m) sum_{l >= m} b~_l(A) C(l, m) t^(l-m),
 //   t = (c_leaf - c_A) / r_A, D = level(leaf) - level(A);
 // lane m computes coefficient m.  Then, a lane per target: L2P of that
@@ -1045,6 +1045,7 @@ template <int PT>
 __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
     __shared__ float sbin[BN * BN];
     __shared__ float2 loc[8][PT + 1];
+    __shared__ float2 ancl[8][MAXLEV - 1][PT + 1];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = la.e.binom[i];
     __syncthreads();
     const Tree &T = la.e.T;
@@ -1054,35 +1055,39 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
     const int B = min(T.levoff[NLEV], T.Bmax);
     const Root *rt = T.root;
     const int p = la.e.p;
+    const unsigned epoch = *T.epoch;
     for (int b = gw; b < B; b += nw) {
         const int2 mb = T.bmeta[b];
         if (!meta_leaf(mb)) continue;
         const int Lb = mb.y & 255;
         const uint32_t kb = (uint32_t)mb.x;
+        // ancestors of levels >= 2 (lane j: level Lb - j, key kb >> 2j), found by
+        // independent hash lookups; their partial locals staged in shared memory
+        const int nA = Lb >= 2 ? Lb - 1 : 0;
+        int anc = -1;
+        if (lane < nA) anc = lane == 0 ? b : hash_find(T, epoch, Lb - lane, kb >> (2 * lane));
+        for (int j = 0; j < nA; ++j) {
+            const int A = __shfl_sync(0xffffffffu, anc, j);
+            if (lane <= p) ancl[wib][j][lane] = A >= 0 ? la.e.Lc[(size_t)A * (PT + 1) + lane] : make_float2(0.f, 0.f);
+        }
+        __syncwarp();
         // incoming expansion of the leaf, lane m = coefficient m
         float2 mine = make_float2(0.f, 0.f);
         if (lane >= 1 && lane <= p) {
             const int m = lane;
-            int A = b;
-            while (A >= 0) {
-                const int2 ma = T.bmeta[A];
-                const int La = ma.y & 255;
-                if (La < 2) break;
-                const int D = Lb - La;
-                const uint32_t ka = (uint32_t)ma.x;
-                // t = (c_leaf - c_A) / r_A: offsets in units of the leaf half-width, scaled by 2^-D
-                const float sx = (float)((int)(2 * compact_bits(kb) + 1) - (int)(2 * compact_bits(ka) + 1) * (1 << D));
+            for (int j = 0; j < nA; ++j) {
+                // t = (c_leaf - c_A) / r_A, A the ancestor j levels up
+                const uint32_t ka = kb >> (2 * j);
+                const float sx = (float)((int)(2 * compact_bits(kb) + 1) - (int)(2 * compact_bits(ka) + 1) * (1 << j));
                 const float sy = (float)((int)(2 * compact_bits(kb >> 1) + 1) -
-                                         (int)(2 * compact_bits(ka >> 1) + 1) * (1 << D));
-                const float2 t = make_float2(ldexpf(sx, -D), ldexpf(sy, -D));
-                const float2 *la_ = la.e.Lc + (size_t)A * (PT + 1);
+                                         (int)(2 * compact_bits(ka >> 1) + 1) * (1 << j));
+                const float2 t = make_float2(ldexpf(sx, -j), ldexpf(sy, -j));
                 float2 s = make_float2(0.f, 0.f), pw = make_float2(1.f, 0.f);
                 for (int l = m; l <= p; ++l) {
-                    s = cadd(s, cscale(cmul(la_[l], pw), sbin[l * BN + m]));
+                    s = cadd(s, cscale(cmul(ancl[wib][j][l], pw), sbin[l * BN + m]));
                     pw = cmul(pw, t);
                 }
-                mine = cadd(mine, cscale(s, ldexpf(1.0f, -D * m)));
-                A = T.bparent[A];
+                mine = cadd(mine, cscale(s, ldexpf(1.0f, -j * m)));
             }
         }
         if (lane <= PT) loc[wib][lane] = mine;
