@@ -413,40 +413,51 @@ __global__ void tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax, i
     if (threadIdx.x == 0 && carry > Bmax) atomicOr(err, ERR_BOX_OVERFLOW);
 }
 
+// Boxes of the tile, level by level in point order.  Warp w owns the
+// contiguous points [t0 + w * PW, t0 + (w + 1) * PW) in rounds of 32, so a
+// box's rank in its level is the tile's level offset + the counts of the
+// earlier warps (one barrier) + the earlier rounds and lanes of its warp
+// (ballots).
 __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const int8_t *__restrict__ cl,
                                                                 const int8_t *__restrict__ lam,
                                                                 const int *__restrict__ tcnt, int ntiles, int Bmax) {
-    __shared__ int wcount[TREE_THREADS / 32];
+    constexpr int NW = TREE_THREADS / 32;
+    constexpr int R = TREE_TILE / TREE_THREADS;        // rounds per warp
+    constexpr int PW = TREE_TILE / NW;                 // points per warp
+    __shared__ int wcount[NLEV][NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t0 = blockIdx.x * TREE_TILE;
-    constexpr int R = TREE_TILE / TREE_THREADS;
-    int c[R], la[R], prev[R];
+    const unsigned lt = (1u << lane) - 1u;
+    int c[R], la[R];
     uint32_t k[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        int i = t0 + r * TREE_THREADS + threadIdx.x;
-        bool ok = i < T.n;
+        const int i = t0 + warp * PW + r * 32 + lane;
+        const bool ok = i < T.n;
         c[r] = ok ? cl[i] : 99;
         la[r] = ok ? lam[i] : -99;
         k[r] = ok ? T.key[i] : 0u;
-        prev[r] = -1;
     }
+    // per-warp totals of every level
+    for (int L = 0; L < NLEV; ++L) {
+        int tot = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) tot += __popc(__ballot_sync(0xffffffffu, c[r] < L && L <= la[r]));
+        if (lane == 0) wcount[L][warp] = tot;
+    }
+    __syncthreads();
+    int prev[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) prev[r] = -1;
     for (int L = 0; L < NLEV; ++L) {
         int base = tcnt[L * ntiles + blockIdx.x];
+        for (int w = 0; w < warp; ++w) base += wcount[L][w];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int i = t0 + r * TREE_THREADS + threadIdx.x;
+            const int i = t0 + warp * PW + r * 32 + lane;
             const bool f = c[r] < L && L <= la[r];
-            const unsigned bal = __ballot_sync(0xffffffffu, f);
-            if (lane == 0) wcount[warp] = __popc(bal);
-            __syncthreads();
-            int before = 0, tot = 0;
-            for (int w = 0; w < TREE_THREADS / 32; ++w) {
-                int v = wcount[w];
-                if (w < warp) before += v;
-                tot += v;
-            }
-            const int b = base + before + __popc(bal & ((1u << lane) - 1u));
+            const unsigned bl = __ballot_sync(0xffffffffu, f);
+            const int b = base + __popc(bl & lt);
             if (f && b < Bmax) {
                 T.bstart[b] = i;
                 T.blevel[b] = L;
@@ -454,10 +465,9 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
                 T.bleaf[b] = (int8_t)(L == la[r]);
                 T.bmeta[b] = make_int2((int)prefix_at(k[r], L), L | ((L == la[r]) ? 256 : 0));
                 T.bparent[b] = (L >= 1 && L - 1 > c[r]) ? prev[r] : -1;
-                prev[r] = b;
             }
-            base += tot;
-            __syncthreads();
+            if (f) prev[r] = b;
+            base += __popc(bl);
         }
     }
 }

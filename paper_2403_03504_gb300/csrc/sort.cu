@@ -264,8 +264,9 @@ void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
 // from a ticket counter, rank their keys stably (per-warp __match_any_sync
 // counts, warps in order), publish their per-digit counts, and look back
 // over earlier tiles' published counts (decoupled look-back, Merrill and
-// Garland) for their global offsets.  Waits are bounded; a wait that gives
-// up records an error bit and the tile carries on.
+// Garland) for their global offsets; keys are regrouped by digit in shared
+// memory so each digit run is written with coalesced stores.  Waits are
+// bounded; a wait that gives up records an error bit and the tile carries on.
 
 constexpr int OS_THREADS = 256;
 constexpr int OS_WARPS = OS_THREADS / 32;
@@ -323,14 +324,19 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
                                                                  uint32_t *status, unsigned *ticket, int *err) {
     __shared__ int32_t cnt[OS_WARPS][256];
     __shared__ uint32_t gofs[256];
+    __shared__ int32_t lstart[256];
+    __shared__ int32_t wsum[OS_WARPS];
+    __shared__ uint32_t skey[OS_TILE], sval[OS_TILE];
     __shared__ int tile_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) tile_s = (int)atomicAdd(ticket, 1u);
     for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const int tile = tile_s;
+    const int64_t t0 = (int64_t)tile * OS_TILE;
+    const int tcount = (int)(n - t0 < OS_TILE ? n - t0 : OS_TILE);
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t wbase = (int64_t)tile * OS_TILE + (int64_t)warp * 32 * OS_ITEMS;
+    const int64_t wbase = t0 + (int64_t)warp * 32 * OS_ITEMS;
     uint32_t key[OS_ITEMS], val[OS_ITEMS];
     int32_t rank[OS_ITEMS];
 #pragma unroll
@@ -350,7 +356,9 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
     }
     __syncthreads();
     {
-        // thread = digit: prefix over warps, publish, look back
+        // thread = digit: prefix over warps, then an exclusive scan over digits
+        // (tile-local start of each digit run), then the look-back for the
+        // global offset of each digit run
         const int d = threadIdx.x;
         int s = 0;
 #pragma unroll
@@ -359,6 +367,13 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
             cnt[w][d] = s;
             s += c;
         }
+        int x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         volatile uint32_t *st = status;
         const uint32_t own = (uint32_t)s;
         uint32_t excl = 0;
@@ -383,15 +398,28 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
             st[(int64_t)tile * 256 + d] = OS_INC | (excl + own);
         }
         gofs[d] = base[d] + excl;
+        __syncthreads();
+        int pre = 0;
+        for (int w = 0; w < warp; ++w) pre += wsum[w];
+        lstart[d] = pre + x - s;
     }
     __syncthreads();
+    // keys to their tile-local sorted position, then coalesced runs to global
 #pragma unroll
     for (int r = 0; r < OS_ITEMS; ++r) {
         if (rank[r] < 0) continue;
         const unsigned d = (key[r] >> shift) & 0xFF;
-        const uint32_t dst = gofs[d] + (uint32_t)cnt[warp][d] + (uint32_t)rank[r];
-        kout[dst] = key[r];
-        vout[dst] = val[r];
+        const int lp = lstart[d] + cnt[warp][d] + rank[r];
+        skey[lp] = key[r];
+        sval[lp] = val[r];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tcount; i += OS_THREADS) {
+        const uint32_t k = skey[i];
+        const unsigned d = (k >> shift) & 0xFF;
+        const uint32_t dst = gofs[d] + (uint32_t)(i - lstart[d]);
+        kout[dst] = k;
+        vout[dst] = sval[i];
     }
 }
 
