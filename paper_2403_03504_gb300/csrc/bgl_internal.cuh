@@ -159,7 +159,10 @@ struct SortWorkspace {
     int64_t cap = 0;
     void reserve(Allocator *a, int64_t n, cudaStream_t s);
 };
-void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits);
+// With gpts, the last pass writes gpts[i] = {gxy[v].x, gxy[v].y, gmass[v], v}
+// (v = the value of sorted key i, as int bits) instead of the sorted values.
+void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits,
+                       const float2 *gxy = nullptr, const float *gmass = nullptr, float4 *gpts = nullptr);
 // nonzero if a bounded wait of a workspace sort gave up (synchronises)
 int sort_workspace_error(bgl_ctx *c, SortWorkspace &ws);
 

@@ -12,7 +12,7 @@
 // One evaluation (all launches, no host synchronisation):
 //   bbox      root square covering all points (FP32 min/max, FP64 geometry)
 //   keys      16-bit quantised x, y interleaved into 32-bit Morton keys
-//   sort      stable radix sort of (key, index); gather x, y, m in key order
+//   sort      stable radix sort of (key, index); the last pass writes x, y, m in key order
 //   tree      adaptive quadtree: a box is split while it holds more than
 //             leaf_size points (and is above level 16).  The leaf level of
 //             point i is 1 + the deepest level at which some window of
@@ -73,7 +73,7 @@ struct Tree {
     uint32_t *bkey;
     int8_t *bleaf;
     int4 *bchild;
-    int2 *bmeta;              // per box {key prefix, level | leaf << 8}: one load in the list builders
+    int2 *bmeta;              // per box {x | y << 16 at its level, level | leaf << 8}: one load
     int *levoff;              // [NLEV + 1], levoff[NLEV] = number of boxes
     int *lofs;                // [5 * Bmax] per box: starts of U, V, W, X and the end, in lidx
     int *lidx;                // list entries (each box's lists in one chunk)
@@ -130,26 +130,33 @@ struct BoxGeo {
     float cx, cy, r;
 };
 
+
+// packed integer box coordinates (x | y << 16) at the box's level
+__device__ __forceinline__ int mx_(int c) { return c & 0xFFFF; }
+__device__ __forceinline__ int my_(int c) { return (int)((unsigned)c >> 16); }
+__device__ __forceinline__ int pack_xy(uint32_t key) { return (int)(compact_bits(key) | (compact_bits(key >> 1) << 16)); }
+
 // Box geometry is defined by the float origin and side: the centre of box
 // (bx, by) at level L is origin + (2 bx + 1) r_L with r_L = side 2^-(L+1)
 // (exact), evaluated with one rounding by a fused multiply-add.
-__device__ __forceinline__ BoxGeo box_geo(const Root *__restrict__ rt, uint32_t key, int L) {
+__device__ __forceinline__ BoxGeo box_geo_xy(const Root *__restrict__ rt, int c, int L) {
     const float r = rt->r[L];
     BoxGeo g;
-    g.cx = fmaf((float)(2 * compact_bits(key) + 1), r, rt->oxf);
-    g.cy = fmaf((float)(2 * compact_bits(key >> 1) + 1), r, rt->oyf);
+    g.cx = fmaf((float)(2 * mx_(c) + 1), r, rt->oxf);
+    g.cy = fmaf((float)(2 * my_(c) + 1), r, rt->oyf);
     g.r = r;
     return g;
 }
 
-// closed squares of two distinct (non-nested) boxes touch or overlap
-__device__ __forceinline__ bool boxes_adjacent(uint32_t ka, int La, uint32_t kb, int Lb) {
+// closed squares of two distinct (non-nested) boxes (packed coordinates) touch or overlap
+__device__ __forceinline__ bool adjacent_xy(int ca, int La, int cb, int Lb) {
     const int F = max(La, Lb);
-    const int ax = (int)compact_bits(ka) << (F - La), ay = (int)compact_bits(ka >> 1) << (F - La);
-    const int bx = (int)compact_bits(kb) << (F - Lb), by = (int)compact_bits(kb >> 1) << (F - Lb);
+    const int ax = mx_(ca) << (F - La), ay = my_(ca) << (F - La);
+    const int bx = mx_(cb) << (F - Lb), by = my_(cb) << (F - Lb);
     const int aw = 1 << (F - La), bw = 1 << (F - Lb);
     return max(ax, bx) <= min(ax + aw, bx + bw) && max(ay, by) <= min(ay + aw, by + bw);
 }
+
 
 // ---------------------------------------------------------------- box hash table
 //
@@ -314,14 +321,6 @@ __global__ void keys_kernel(const float2 *__restrict__ xy, int n, const Root *__
     idx[i] = (uint32_t)i;
 }
 
-__global__ void gather_kernel(const float2 *__restrict__ xy, const float *__restrict__ mass,
-                              const uint32_t *__restrict__ idx, int n, float4 *__restrict__ pts) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t o = idx[i];
-    float2 p = xy[o];
-    pts[i] = make_float4(p.x, p.y, mass[o], __int_as_float((int)o));
-}
 
 // ---------------------------------------------------------------- tree build
 
@@ -463,7 +462,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
                 T.blevel[b] = L;
                 T.bkey[b] = prefix_at(k[r], L);
                 T.bleaf[b] = (int8_t)(L == la[r]);
-                T.bmeta[b] = make_int2((int)prefix_at(k[r], L), L | ((L == la[r]) ? 256 : 0));
+                T.bmeta[b] = make_int2(pack_xy(prefix_at(k[r], L)), L | ((L == la[r]) ? 256 : 0));
                 T.bparent[b] = (L >= 1 && L - 1 > c[r]) ? prev[r] : -1;
             }
             if (f) prev[r] = b;
@@ -543,7 +542,7 @@ __device__ void lists_uw(const Tree &T, int b, int2 mb, const int *nbb, int k, i
         cu = 1;
         return;
     }
-    const uint32_t key = (uint32_t)mb.x;
+    const int cb = mb.x;
     const int L = meta_level(mb);
     int stack[4 * MAXLEV + 4];
     int sp = 0;
@@ -558,7 +557,7 @@ __device__ void lists_uw(const Tree &T, int b, int2 mb, const int *nbb, int k, i
         for (int q = 3; q >= 0; --q) {
             const int C = cs[q];
             if (C < 0) continue;
-            if (boxes_adjacent((uint32_t)mc[q].x, meta_level(mc[q]), key, L)) {
+            if (adjacent_xy(mc[q].x, meta_level(mc[q]), cb, L)) {
                 if (meta_leaf(mc[q])) {
                     if (ou) ou[cu] = C;
                     ++cu;
@@ -583,15 +582,14 @@ __device__ void lists_v(const Tree &T, int2 mb, const int *nbp, int k, int *ov, 
     if (A < 0) return;
     const int2 ma = T.bmeta[A];
     if (meta_level(ma) != L - 1 || meta_leaf(ma)) return;
-    const uint32_t key = (uint32_t)mb.x;
-    const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
+    const int bx = mx_(mb.x), by = my_(mb.x);
     const int4 ch = T.bchild[A];
     const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
     for (int q = 0; q < 4; ++q) {
         const int C = cs[q];
         if (C < 0) continue;
-        const uint32_t kc = (uint32_t)T.bmeta[C].x;
-        const int dx = (int)compact_bits(kc) - bx, dy = (int)compact_bits(kc >> 1) - by;
+        const int cc = T.bmeta[C].x;
+        const int dx = mx_(cc) - bx, dy = my_(cc) - by;
         if (abs(dx) <= 1 && abs(dy) <= 1) continue;
         if (ov) ov[cv] = (C << 6) | ((dx + 3) * 7 + (dy + 3));
         ++cv;
@@ -608,7 +606,7 @@ __device__ void lists_x(const Tree &T, int2 mb, const int *nbp, int k, int *ox, 
         if (k2 != 4 && nbp[k2] == A) return;
     const int2 ma = T.bmeta[A];
     if (!meta_leaf(ma)) return;
-    if (boxes_adjacent((uint32_t)ma.x, meta_level(ma), (uint32_t)mb.x, L)) return;
+    if (adjacent_xy(ma.x, meta_level(ma), mb.x, L)) return;
     if (ox) ox[0] = A;
     cx = 1;
 }
@@ -640,8 +638,7 @@ __global__ void nbr_lists_kernel(Tree T) {
     for (int b = gw; b < B; b += nw) {
         const int2 mb = T.bmeta[b];
         const int L = meta_level(mb);
-        const uint32_t key = (uint32_t)mb.x;
-        const int bx = (int)compact_bits(key), by = (int)compact_bits(key >> 1);
+        const int bx = mx_(mb.x), by = my_(mb.x);
         const int p = b == 0 ? -1 : T.bparent[b];
         int mine = -1;
         if (lane < 9) {
@@ -762,7 +759,7 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
         const int s = T.bstart[b], e = T.bend[b];
         const int2 mb = T.bmeta[b];
         if (e - s > P2M_MAX && !meta_leaf(mb)) continue;   // filled by M2M below
-        const BoxGeo g = box_geo(rt, (uint32_t)mb.x, mb.y & 255);
+        const BoxGeo g = box_geo_xy(rt, mb.x, mb.y & 255);
         const float ir = 1.0f / g.r;
         float2 acc[PT + 1];
 #pragma unroll
@@ -898,7 +895,7 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
         }
         // P2L: b~_l += -q t^l / l, t = r / (z_j - c)
         const int2 mb = T.bmeta[b];
-        const BoxGeo g = box_geo(rt, (uint32_t)mb.x, mb.y & 255);
+        const BoxGeo g = box_geo_xy(rt, mb.x, mb.y & 255);
         const int xs = T.lofs[5 * b + 3], xe = T.lofs[5 * b + 4];
         for (int e = xs; e < xe; ++e) {
             const int C = T.lidx[e];
@@ -939,10 +936,10 @@ struct LeafArgs {
 // sources are staged NEAR_SRC at a time in the warp's own shared memory
 // with asynchronous 16-byte copies (cp.async), double-buffered: the copies
 // of the next chunk are in flight while the current chunk is summed.
-// Each lane owns two targets: with lps = (targets / 2 rounded up to a power
-// of two) lanes per source split, lane l takes targets l % lps and
-// l % lps + lps of split l / lps, the 32 / lps splits share the sources and
-// combine by a fixed butterfly.  Writes the raw sum
+// Each lane owns R targets (1..4): with S source splits of lps = 32 / S
+// lanes, lane l takes targets l % lps + r * lps of split l / lps; (R, S) is
+// chosen per leaf for the fewest padded target slots; the splits share the
+// sources and combine by a fixed butterfly.  Writes the raw sum
 // sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the far kernel completes it).
 constexpr int NEAR_WARPS = 8;
 constexpr int NEAR_SRC = 128;
@@ -985,6 +982,63 @@ __device__ __forceinline__ int stage_chunk(const Tree &T, float4 *buf, int &ui, 
     return cnt;
 }
 
+// Pairs of the targets tb + t + r * lps (r < R) with every S-th staged
+// source from h; R targets per lane amortise each shared-memory load.
+template <int R>
+__device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*buf)[NEAR_SRC], int tb, int ntc,
+                                          int lps, int S, int us, int ue, int lane) {
+    const int t = lane % lps, h = lane / lps;
+    float4 z[R];
+    float fx[R], fy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = t + r * lps;
+        z[r] = i < ntc ? T.pts[tb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        fx[r] = fy[r] = 0.f;
+    }
+    int ui = us, off = 0, cur = 0;
+    int cnt = stage_chunk(T, buf[0], ui, off, ue, lane);
+    while (cnt > 0) {
+        // next chunk in flight while this one is summed
+        const int nxt = ui < ue ? stage_chunk(T, buf[cur ^ 1], ui, off, ue, lane) : (cp_async_commit(), 0);
+        cp_async_wait_one();
+        __syncwarp();
+        const float4 *src = buf[cur];
+        if (S == 1) {
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q = src[j];
+#pragma unroll
+                for (int r = 0; r < R; ++r) p2p_pair(z[r], q, fx[r], fy[r]);
+            }
+        } else {
+#pragma unroll 2
+            for (int j = h; j < cnt; j += S) {
+                const float4 q = src[j];
+#pragma unroll
+                for (int r = 0; r < R; ++r) p2p_pair(z[r], q, fx[r], fy[r]);
+            }
+        }
+        __syncwarp();
+        cur ^= 1;
+        cnt = nxt;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        for (int o = lps; o < 32; o <<= 1) {
+            fx[r] += __shfl_xor_sync(0xffffffffu, fx[r], o);
+            fy[r] += __shfl_xor_sync(0xffffffffu, fy[r], o);
+        }
+    }
+    if (h == 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = t + r * lps;
+            if (i < ntc) la.f[la.q0 + __float_as_int(z[r].w) - la.fbase] = make_float2(fx[r], fy[r]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
     const Tree &T = la.e.T;
     __shared__ __align__(16) float4 stage[NEAR_WARPS][2][NEAR_SRC];
@@ -1001,42 +1055,23 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
         const int us = T.lofs[5 * b], ue = T.lofs[5 * b + 1];
         for (int tb = s; tb < e; tb += 64) {
             const int ntc = min(64, e - tb);
-            int lps = 1;
-            while (2 * lps < ntc) lps <<= 1;
-            const int S = 32 / lps;
-            const int t = lane & (lps - 1), h = lane / lps;
-            const bool v0 = t < ntc, v1 = t + lps < ntc;
-            const float4 z0 = v0 ? T.pts[tb + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 z1 = v1 ? T.pts[tb + t + lps] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float fx0 = 0.f, fy0 = 0.f, fx1 = 0.f, fy1 = 0.f;
-            int ui = us, off = 0, cur = 0;
-            int cnt = stage_chunk(T, buf[0], ui, off, ue, lane);
-            while (cnt > 0) {
-                // next chunk in flight while this one is summed
-                const int nxt = ui < ue ? stage_chunk(T, buf[cur ^ 1], ui, off, ue, lane) : (cp_async_commit(), 0);
-                cp_async_wait_one();
-                __syncwarp();
-                const float4 *src = buf[cur];
-#pragma unroll 4
-                for (int j = h; j < cnt; j += S) {
-                    const float4 q = src[j];
-                    p2p_pair(z0, q, fx0, fy0);
-                    p2p_pair(z1, q, fx1, fy1);
+            // fewest padded target slots: R targets on lps = 32 / S lanes
+            int R = 2, S = 1, best = 64;
+            for (int s2 = 1; s2 <= 32; s2 <<= 1) {
+                for (int r2 = 4; r2 >= 1; --r2) {
+                    const int slots = r2 * (32 / s2);
+                    if (slots >= ntc && slots < best) {
+                        best = slots;
+                        R = r2;
+                        S = s2;
+                    }
                 }
-                __syncwarp();
-                cur ^= 1;
-                cnt = nxt;
             }
-            for (int o = lps; o < 32; o <<= 1) {
-                fx0 += __shfl_xor_sync(0xffffffffu, fx0, o);
-                fy0 += __shfl_xor_sync(0xffffffffu, fy0, o);
-                fx1 += __shfl_xor_sync(0xffffffffu, fx1, o);
-                fy1 += __shfl_xor_sync(0xffffffffu, fy1, o);
-            }
-            if (h == 0) {
-                if (v0) la.f[la.q0 + __float_as_int(z0.w) - la.fbase] = make_float2(fx0, fy0);
-                if (v1) la.f[la.q0 + __float_as_int(z1.w) - la.fbase] = make_float2(fx1, fy1);
-            }
+            const int lps = 32 / S;
+            if (R == 4) near_tile<4>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else if (R == 2) near_tile<2>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else near_tile<1>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
         }
     }
 }
@@ -1070,7 +1105,7 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
         const int2 mb = T.bmeta[b];
         if (!meta_leaf(mb)) continue;
         const int Lb = mb.y & 255;
-        const uint32_t kb = (uint32_t)mb.x;
+        const uint32_t kb = T.bkey[b];
         // ancestors of levels >= 2 (lane j: level Lb - j, key kb >> 2j), found by
         // independent hash lookups; their partial locals staged in shared memory
         const int nA = Lb >= 2 ? Lb - 1 : 0;
@@ -1102,7 +1137,7 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
         }
         if (lane <= PT) loc[wib][lane] = mine;
         __syncwarp();
-        const BoxGeo g = box_geo(rt, kb, Lb);
+        const BoxGeo g = box_geo_xy(rt, mb.x, Lb);
         const int s = T.bstart[b], e = T.bend[b];
         const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
         for (int tt = s + lane; tt < e; tt += 32) {
@@ -1123,7 +1158,7 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
             for (int k = ws; k < we; ++k) {
                 const int Dx = T.lidx[k];
                 const int2 md_ = T.bmeta[Dx];
-                const BoxGeo gd = box_geo(rt, (uint32_t)md_.x, md_.y & 255);
+                const BoxGeo gd = box_geo_xy(rt, md_.x, md_.y & 255);
                 const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
                 const float2 idz = crcp(dz);
                 const float2 tt2 = cscale(idz, gd.r);
@@ -1334,14 +1369,12 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
     cudaStream_t keep = ctx->stream;
     ctx->stream = s;
     try {
-        radix_sort_u32_ws(ctx, pl->sortws, pl->key.p, pl->idx.p, n, 32);
+        radix_sort_u32_ws(ctx, pl->sortws, pl->key.p, pl->idx.p, n, 32, xl, ml, pl->pts.p);
     } catch (...) {
         ctx->stream = keep;
         throw;
     }
     ctx->stream = keep;
-    gather_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, ml, pl->idx.p, n, pl->pts.p);
-    BGL_LAUNCH_CHECK();
 }
 
 // tree: boxes in level order, ends, parents, children

@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
                                                                  uint32_t *__restrict__ kout,
                                                                  uint32_t *__restrict__ vout, int64_t n, int shift,
                                                                  const uint32_t *__restrict__ base,
-                                                                 uint32_t *status, unsigned *ticket, int *err) {
+                                                                 uint32_t *status, unsigned *ticket, int *err,
+                                                                 const float2 *__restrict__ gxy,
+                                                                 const float *__restrict__ gmass,
+                                                                 float4 *__restrict__ gpts) {
     __shared__ int32_t cnt[OS_WARPS][256];
     __shared__ uint32_t gofs[256];
     __shared__ int32_t lstart[256];
@@ -419,7 +422,13 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
         const unsigned d = (k >> shift) & 0xFF;
         const uint32_t dst = gofs[d] + (uint32_t)(i - lstart[d]);
         kout[dst] = k;
-        vout[dst] = sval[i];
+        const uint32_t v = sval[i];
+        if (gpts) {   // last pass with a gather: the sorted record {x, y, m, index}
+            const float2 p = gxy[v];
+            gpts[dst] = make_float4(p.x, p.y, gmass[v], __int_as_float((int)v));
+        } else {
+            vout[dst] = v;
+        }
     }
 }
 
@@ -451,7 +460,8 @@ void SortWorkspace::reserve(Allocator *a, int64_t n, cudaStream_t s) {
     cap = n;
 }
 
-void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits) {
+void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits,
+                       const float2 *gxy, const float *gmass, float4 *gpts) {
     if (n <= 1 || bits <= 0) return;
     BGL_REQUIRE(n <= ws.cap && n < (int64_t(1) << 30), "radix sort: workspace too small");
     BGL_REQUIRE(bits == 32 && vals, "radix sort: the workspace sort takes 32-bit keys with values");
@@ -471,13 +481,16 @@ void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *
     BGL_LAUNCH_CHECK();
     uint32_t *ka = keys, *kb = ws.keys.p, *va = vals, *vb = ws.vals.p;
     for (int d = 0; d < 4; ++d) {
+        const bool g = d == 3 && gpts;
         os_scatter_kernel<<<(unsigned)nt, OS_THREADS, 0, s>>>(ka, va, kb, vb, n, 8 * d, base + 256 * d,
-                                                              status + (int64_t)d * 256 * nt, tickets + d, err);
+                                                              status + (int64_t)d * 256 * nt, tickets + d, err,
+                                                              g ? gxy : nullptr, g ? gmass : nullptr,
+                                                              g ? gpts : nullptr);
         BGL_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
     }
-    // four passes: the sorted data is back in keys / vals
+    // four passes: the sorted keys (and values unless gathered) are back in keys / vals
 }
 
 int sort_workspace_error(bgl_ctx *c, SortWorkspace &ws) {
