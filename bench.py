@@ -236,6 +236,8 @@ def main():
         for _ in range(3):
             g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=args.p), xy0)
         g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy0)
+        # three whole ForceAtlas2 iterations (FMM, attraction, gravity, speed, update)
+        g0.fa2_step(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=args.p), 3, xy0)
         ctx.sync()
         print(json.dumps({"kernels_only": True, "giant": int(coff[1] - coff[0])}))
         return

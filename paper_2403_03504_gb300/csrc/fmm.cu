@@ -373,40 +373,53 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
 
 // exclusive scan of the (level, tile) counts; level offsets
 __global__ void tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax, int *err) {
+    constexpr int ITEMS = 8;
     __shared__ int wsum[32];
     __shared__ int carry_s;
     const int total = NLEV * ntiles;
     int carry = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < total; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v = i < total ? tcnt[i] : 0;
-        int x = v;
+    for (int base = 0; base < total; base += blockDim.x * ITEMS) {
+        int v[ITEMS];
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int i = base + threadIdx.x * ITEMS + k;
+            v[k] = i < total ? tcnt[i] : 0;
+            s += v[k];
+        }
+        int x = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) wsum[warp] = x;
         __syncthreads();
         if (warp == 0) {
-            int s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
-            int t = s;
+            const int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            int t = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, t, o);
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
                 if (lane >= o) t += y;
             }
-            wsum[lane] = t - s;
+            wsum[lane] = t - w;
             if (lane == 31) carry_s = t;
         }
         __syncthreads();
-        if (i < total) tcnt[i] = carry + wsum[warp] + x - v;
+        int e = carry + wsum[warp] + x - s;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int i = base + threadIdx.x * ITEMS + k;
+            if (i < total) tcnt[i] = e;
+            e += v[k];
+        }
         carry += carry_s;
         __syncthreads();
     }
     if (threadIdx.x <= NLEV) {
-        int L = threadIdx.x;
+        const int L = threadIdx.x;
         levoff[L] = L < NLEV ? tcnt[L * ntiles] : carry;
     }
     if (threadIdx.x == 0 && carry > Bmax) atomicOr(err, ERR_BOX_OVERFLOW);
@@ -1086,11 +1099,14 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
 // lane m computes coefficient m.  Then, a lane per target: L2P of that
 // expansion and M2P over W, added to the near sum; F_rep = kr m_i
 // (near + conj(E_far)).
+constexpr int FAR_WARPS = 4;
+
 template <int PT>
-__global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
+__global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
     __shared__ float sbin[BN * BN];
-    __shared__ float2 loc[8][PT + 1];
-    __shared__ float2 ancl[8][MAXLEV - 1][PT + 1];
+    __shared__ float2 loc[FAR_WARPS][PT + 1];
+    __shared__ float2 ancl[FAR_WARPS][MAXLEV - 1][PT + 1];
+    __shared__ float2 part_[FAR_WARPS][MAXLEV - 1][PT + 1];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = la.e.binom[i];
     __syncthreads();
     const Tree &T = la.e.T;
@@ -1111,30 +1127,43 @@ __global__ void __launch_bounds__(256) far_kernel(LeafArgs la) {
         const int nA = Lb >= 2 ? Lb - 1 : 0;
         int anc = -1;
         if (lane < nA) anc = lane == 0 ? b : hash_find(T, epoch, Lb - lane, kb >> (2 * lane));
-        for (int j = 0; j < nA; ++j) {
-            const int A = __shfl_sync(0xffffffffu, anc, j);
-            if (lane <= p) ancl[wib][j][lane] = A >= 0 ? la.e.Lc[(size_t)A * (PT + 1) + lane] : make_float2(0.f, 0.f);
-        }
-        __syncwarp();
-        // incoming expansion of the leaf, lane m = coefficient m
-        float2 mine = make_float2(0.f, 0.f);
-        if (lane >= 1 && lane <= p) {
-            const int m = lane;
-            for (int j = 0; j < nA; ++j) {
-                // t = (c_leaf - c_A) / r_A, A the ancestor j levels up
-                const uint32_t ka = kb >> (2 * j);
-                const float sx = (float)((int)(2 * compact_bits(kb) + 1) - (int)(2 * compact_bits(ka) + 1) * (1 << j));
-                const float sy = (float)((int)(2 * compact_bits(kb >> 1) + 1) -
-                                         (int)(2 * compact_bits(ka >> 1) + 1) * (1 << j));
-                const float2 t = make_float2(ldexpf(sx, -j), ldexpf(sy, -j));
-                float2 s = make_float2(0.f, 0.f), pw = make_float2(1.f, 0.f);
-                for (int l = m; l <= p; ++l) {
-                    s = cadd(s, cscale(cmul(ancl[wib][j][l], pw), sbin[l * BN + m]));
-                    pw = cmul(pw, t);
-                }
-                mine = cadd(mine, cscale(s, ldexpf(1.0f, -j * m)));
+        {
+            int ancj[MAXLEV - 1];
+#pragma unroll
+            for (int j = 0; j < MAXLEV - 1; ++j) ancj[j] = __shfl_sync(0xffffffffu, anc, j);
+            for (int it = lane; it < nA * (p + 1); it += 32) {
+                const int j = it / (p + 1), l = it % (p + 1);
+                int A = -1;
+#pragma unroll
+                for (int jj = 0; jj < MAXLEV - 1; ++jj)
+                    if (jj == j) A = ancj[jj];
+                ancl[wib][j][l] = A >= 0 ? la.e.Lc[(size_t)A * (PT + 1) + l] : make_float2(0.f, 0.f);
             }
         }
+        __syncwarp();
+        // incoming expansion of the leaf: items (ancestor j, coefficient m)
+        // spread over all lanes, then each coefficient summed over j in order
+        for (int it = lane; it < nA * p; it += 32) {
+            const int j = it / p, m = it % p + 1;
+            // t = (c_leaf - c_A) / r_A, A the ancestor j levels up
+            const uint32_t ka = kb >> (2 * j);
+            const float sx = (float)((int)(2 * compact_bits(kb) + 1) - (int)(2 * compact_bits(ka) + 1) * (1 << j));
+            const float sy = (float)((int)(2 * compact_bits(kb >> 1) + 1) - (int)(2 * compact_bits(ka >> 1) + 1) * (1 << j));
+            const float sc = 1.0f / (float)(1 << j);
+            const float2 t = make_float2(sx * sc, sy * sc);
+            float2 s = make_float2(0.f, 0.f), pw = make_float2(1.f, 0.f);
+            for (int l = m; l <= p; ++l) {
+                s = cadd(s, cscale(cmul(ancl[wib][j][l], pw), sbin[l * BN + m]));
+                pw = cmul(pw, t);
+            }
+            float scm = 1.0f;
+            for (int q = 0; q < m; ++q) scm *= sc;          // 2^(-j m)
+            part_[wib][j][m] = cscale(s, scm);
+        }
+        __syncwarp();
+        float2 mine = make_float2(0.f, 0.f);
+        if (lane >= 1 && lane <= p)
+            for (int j = 0; j < nA; ++j) mine = cadd(mine, part_[wib][j][lane]);
         if (lane <= PT) loc[wib][lane] = mine;
         __syncwarp();
         const BoxGeo g = box_geo_xy(rt, mb.x, Lb);
@@ -1361,8 +1390,8 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
     const int n = pl->n;
     const float *ml = pl->g->mass.p + pl->q0;
     BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 8, s));
-    bbox_kernel<<<std::min<int64_t>(1024, nblk(n, 256)), 256, 0, s>>>(xl, n, pl->part.p, pl->counter.p, pl->root.p,
-                                                                      pl->err.p, pl->epoch.p);
+    bbox_kernel<<<std::min<int64_t>(2 * ctx->num_sms, nblk(n, 256)), 256, 0, s>>>(
+        xl, n, pl->part.p, pl->counter.p, pl->root.p, pl->err.p, pl->epoch.p);
     BGL_LAUNCH_CHECK();
     keys_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p);
     BGL_LAUNCH_CHECK();
@@ -1413,7 +1442,7 @@ static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
 }
 template <int PT>
 static void launch_far(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
-    far_kernel<PT><<<pl->grid_p, 256, 0, s>>>(la);
+    far_kernel<PT><<<2 * pl->grid_p, FAR_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
 }
 

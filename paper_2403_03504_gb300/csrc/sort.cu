@@ -476,7 +476,7 @@ void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *
     BGL_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * 256, s));
     BGL_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * 5, s));
     BGL_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t) * 4 * 256 * nt, s));
-    const int hblocks = (int)std::min<int64_t>(2 * c->num_sms, (n + 255) / 256);
+    const int hblocks = (int)std::min<int64_t>(64, (n + 255) / 256);   // few blocks: fewer global atomics
     os_hist_kernel<<<hblocks, 256, 0, s>>>(keys, n, hist, base, counter);
     BGL_LAUNCH_CHECK();
     uint32_t *ka = keys, *kb = ws.keys.p, *va = vals, *vb = ws.vals.p;
