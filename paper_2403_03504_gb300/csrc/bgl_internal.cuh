@@ -165,6 +165,19 @@ void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *
                        const float2 *gxy = nullptr, const float *gmass = nullptr, float4 *gpts = nullptr);
 // nonzero if a bounded wait of a workspace sort gave up (synchronises)
 int sort_workspace_error(bgl_ctx *c, SortWorkspace &ws);
+// The same sort in two halves, so that a caller's kernel can count the digit
+// histograms while it makes the keys: radix_sort_u32_ws_begin clears the
+// counts and returns them; every block of the caller's kernel (256 threads)
+// then calls os_block_hist (sort_hist.cuh) on its keys; and
+// radix_sort_u32_ws_scatter runs the four passes.
+struct OsHist {
+    uint32_t *hist;      // 4 x 256 digit counts
+    uint32_t *base;      // 4 x 256 exclusive digit bases (written by the last block)
+    unsigned *counter;   // arrival count of the blocks (reset by the last block)
+};
+OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n);
+void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n,
+                               const float2 *gxy = nullptr, const float *gmass = nullptr, float4 *gpts = nullptr);
 
 int bits_for(uint64_t max_value);   // number of bits needed to hold max_value
 

@@ -5,9 +5,11 @@
 //                     same component staged 1024 at a time in shared memory;
 //                     FMM components run the pipeline in fmm.cu instead.
 //                     f <- F_rep = kr m_i sum_j m_j (p_i - p_j) / |p_i - p_j|^2
-//   K2 attraction     f += -sum_{j adjacent} (p_i - p_j) - kg m_i p_i; one
+//   K2 attraction     fa <- -sum_{j adjacent} (p_i - p_j) - kg m_i p_i; one
 //      + gravity      thread per node; nodes of degree > 128 in chunks of 2048
-//                     entries, one block each, combined in chunk order
+//                     entries, one block each, combined in chunk order.  It
+//                     runs on a second stream beside the repulsion, whose
+//                     final writes add fa: f <- F_rep + fa
 //   K3 swing/traction per-node |F_t - F_{t-1}|, |F_t + F_{t-1}| summed in FP64
 //                     per tile (warp shuffles); the last block to finish sums
 //                     each component's tiles (a warp per component, fixed
@@ -19,6 +21,7 @@
 // runs are bitwise reproducible.
 #include "bgl_internal.cuh"
 #include "fmm.cuh"
+#include "p2p.cuh"
 
 namespace bgl {
 
@@ -38,26 +41,22 @@ struct Tile {
     int64_t t0, t1;    // target positions [t0, t1)
 };
 
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // K1 (exact): repulsion of every target in the tile from every node of its component
 __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
     const Tile *__restrict__ tiles, const int64_t *__restrict__ comp_off, int64_t c0, const float2 *__restrict__ xy,
-    const float *__restrict__ mass, int64_t qbase, float kr, float2 *__restrict__ f) {
+    const float *__restrict__ mass, int64_t qbase, float kr, const float2 *__restrict__ fa, float2 *__restrict__ f) {
     __shared__ float4 src[EX_STILE];
     const Tile t = tiles[blockIdx.x];
     const int64_t s_begin = comp_off[c0 + t.comp], s_end = comp_off[c0 + t.comp + 1];
-    float xi[EX_R], yi[EX_R], sx[EX_R], sy[EX_R], cx[EX_R], cy[EX_R];
+    f2x zx[EX_R], zy[EX_R];
+    float sx[EX_R], sy[EX_R], cx[EX_R], cy[EX_R];
 #pragma unroll
     for (int r = 0; r < EX_R; ++r) {
         int64_t q = t.t0 + threadIdx.x + r * EX_THREADS;
         float2 p = q < t.t1 ? xy[q - qbase] : make_float2(0.f, 0.f);
-        xi[r] = p.x;
-        yi[r] = p.y;
+        zx[r] = pk2(p.x, p.x);
+        zy[r] = pk2(p.y, p.y);
         sx[r] = sy[r] = cx[r] = cy[r] = 0.f;
     }
     for (int64_t s0 = s_begin; s0 < s_end; s0 += EX_STILE) {
@@ -67,32 +66,32 @@ __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
             float2 p = xy[s0 + k - qbase];
             src[k] = make_float4(p.x, p.y, mass[s0 + k], 0.f);
         }
+        // an odd stage is padded with a massless source
+        if ((cnt & 1) && threadIdx.x == 0) src[cnt] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        float ax[EX_R], ay[EX_R];
+        f2x ax[EX_R], ay[EX_R];
 #pragma unroll
-        for (int r = 0; r < EX_R; ++r) ax[r] = ay[r] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < cnt; ++j) {
-            const float4 s = src[j];
+        for (int r = 0; r < EX_R; ++r) ax[r] = ay[r] = 0ull;
+        const int np = (cnt + 1) >> 1;
+#pragma unroll 2
+        for (int j = 0; j < np; ++j) {
+            const float4 q0 = src[2 * j], q1 = src[2 * j + 1];
+            const f2x qx = pk2(q0.x, q1.x), qy = pk2(q0.y, q1.y), qm = pk2(q0.z, q1.z);
 #pragma unroll
-            for (int r = 0; r < EX_R; ++r) {
-                float dx = xi[r] - s.x, dy = yi[r] - s.y;
-                float r2 = fmaf(dx, dx, dy * dy);
-                // a coincident pair (the node itself) has dx = dy = 0 and adds 0
-                float w = s.z * rcp_approx(fmaxf(r2, 1e-30f));
-                ax[r] = fmaf(w, dx, ax[r]);
-                ay[r] = fmaf(w, dy, ay[r]);
-            }
+            for (int r = 0; r < EX_R; ++r) p2p_pair2(zx[r], zy[r], qx, qy, qm, ax[r], ay[r]);
         }
         // blocked accumulation: each stage's partial sum enters a
         // compensated (Kahan) running total
 #pragma unroll
         for (int r = 0; r < EX_R; ++r) {
-            float y = ax[r] - cx[r];
+            float a0, a1, b0, b1;
+            upk2(ax[r], a0, a1);
+            upk2(ay[r], b0, b1);
+            float y = (a0 + a1) - cx[r];
             float s = sx[r] + y;
             cx[r] = (s - sx[r]) - y;
             sx[r] = s;
-            y = ay[r] - cy[r];
+            y = (b0 + b1) - cy[r];
             s = sy[r] + y;
             cy[r] = (s - sy[r]) - y;
             sy[r] = s;
@@ -103,11 +102,12 @@ __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
         int64_t q = t.t0 + threadIdx.x + r * EX_THREADS;
         if (q >= t.t1) continue;
         float km = kr * mass[q];
-        f[q - qbase] = make_float2(km * sx[r], km * sy[r]);
+        const float2 a = fa ? fa[q - qbase] : make_float2(0.f, 0.f);
+        f[q - qbase] = make_float2(fmaf(km, sx[r], a.x), fmaf(km, sy[r], a.y));
     }
 }
 
-// K2: attraction and gravity added to f (Section 3.2).  Blocks below
+// K2: attraction and gravity written to fa (Section 3.2).  Blocks below
 // n_light_blocks: one thread per node of degree <= HEAVY_DEG.  The others:
 // one block per chunk of HEAVY_CHUNK adjacency entries of a node of higher
 // degree; the chunk sums go to `part` and the last chunk of the node to
@@ -124,7 +124,7 @@ __global__ void attraction_gravity_kernel(const float2 *__restrict__ xy, const f
                                           const int64_t *__restrict__ coff, const int32_t *__restrict__ cadj,
                                           int64_t q0, int64_t q1, int64_t qbase, float kg,
                                           const HeavyChunk *__restrict__ chunks, int64_t n_light_blocks,
-                                          float2 *part, int *arrive, float2 *__restrict__ f) {
+                                          float2 *part, int *arrive, float2 *__restrict__ fa) {
     if (blockIdx.x < n_light_blocks) {
         int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (q >= q1) return;
@@ -138,8 +138,7 @@ __global__ void attraction_gravity_kernel(const float2 *__restrict__ xy, const f
             ay -= p.y - o.y;
         }
         float km = kg * mass[q];
-        float2 fr = f[q - qbase];
-        f[q - qbase] = make_float2((fr.x + ax) - km * p.x, (fr.y + ay) - km * p.y);
+        fa[q - qbase] = make_float2(ax - km * p.x, ay - km * p.y);
         return;
     }
     __shared__ float rx[32], ry[32];
@@ -178,8 +177,7 @@ __global__ void attraction_gravity_kernel(const float2 *__restrict__ xy, const f
     }
     arrive[ch.h] = 0;
     const float km = kg * mass[ch.q];
-    const float2 fr = f[ch.q - qbase];
-    f[ch.q - qbase] = make_float2((fr.x + sx) - km * p.x, (fr.y + sy) - km * p.y);
+    fa[ch.q - qbase] = make_float2(sx - km * p.x, sy - km * p.y);
 }
 
 __global__ void heavy_flag_kernel(const int64_t *__restrict__ coff, int64_t q0, int64_t n, int32_t *__restrict__ flag) {
@@ -331,7 +329,7 @@ struct Fa2Run {
     DevBuf<Tile> ex_tiles, red_tiles;
     DevBuf<int64_t> red_tile_off;
     int n_ex_tiles = 0, n_red_tiles = 0;
-    DevBuf<float2> f, fprev;
+    DevBuf<float2> f, fprev, fa;
     DevBuf<double2> partial;
     DevBuf<double> sg;
     DevBuf<unsigned> counter;
@@ -342,6 +340,8 @@ struct Fa2Run {
     int64_t n_chunks = 0;
     std::vector<FmmPlan *> fmm;   // one per FMM component
     std::vector<int64_t> fmm_comp;
+    cudaStream_t side = nullptr;  // attraction + gravity, beside the repulsion
+    cudaEvent_t ev_fork = nullptr, ev_fa = nullptr;
 
     Fa2Run(bgl_graph *g_, const bgl_params *p_, float2 *xy_, int64_t qbase_, int64_t c0_, int64_t c1_)
         : g(g_), p(p_), xy(xy_), qbase(qbase_), c0(c0_), c1(c1_) {
@@ -373,6 +373,7 @@ struct Fa2Run {
         BGL_CUDA(cudaMemcpyAsync(red_tiles.p, red.data(), sizeof(Tile) * red.size(), cudaMemcpyHostToDevice, s));
         BGL_CUDA(cudaMemcpyAsync(red_tile_off.p, roff.data(), sizeof(int64_t) * roff.size(), cudaMemcpyHostToDevice, s));
         f.reset(A, n);
+        fa.reset(A, n);
         fprev.reset(A, n);
         BGL_CUDA(cudaMemsetAsync(fprev.p, 0, sizeof(float2) * n, s));
         partial.reset(A, red.size());
@@ -420,10 +421,16 @@ struct Fa2Run {
         BGL_CUDA(cudaMemsetAsync(chunk_arrive.p, 0, sizeof(int) * std::max<int32_t>(nh, 1), s));
         if (!hc.empty())
             BGL_CUDA(cudaMemcpyAsync(chunks.p, hc.data(), sizeof(HeavyChunk) * hc.size(), cudaMemcpyHostToDevice, s));
+        BGL_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        BGL_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        BGL_CUDA(cudaEventCreateWithFlags(&ev_fa, cudaEventDisableTiming));
         BGL_CUDA(cudaStreamSynchronize(s));
     }
     ~Fa2Run() {
         for (auto *pl : fmm) fmm_destroy(pl);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_fa) cudaEventDestroy(ev_fa);
+        if (side) cudaStreamDestroy(side);
     }
 
     // device-side failures of the FMM (bounded waits, capacities)
@@ -436,21 +443,31 @@ struct Fa2Run {
         }
     }
 
-    // K1 + K2: f <- F (what 0) or F_rep (what 1)
+    // K1 + K2: f <- F (what 0) or F_rep (what 1).  K2 runs on the side
+    // stream from the start; the repulsion kernels that write f last wait
+    // for it (event ev_fa) and add fa.
     void forces(int what) {
         cudaStream_t s = g->ctx->stream;
-        if (n_ex_tiles > 0) {
-            exact_repulsion_kernel<<<n_ex_tiles, EX_THREADS, 0, s>>>(ex_tiles.p, g->comp_off.p, c0, xy, g->mass.p,
-                                                                     qbase, (float)p->kr, f.p - (q0 - qbase));
-            BGL_LAUNCH_CHECK();
-        }
-        for (size_t k = 0; k < fmm.size(); ++k) fmm_repulsion(fmm[k], xy, qbase, f.p, q0);
-        if (what == 0) {
+        const bool att = what == 0;
+        if (att) {
+            BGL_CUDA(cudaEventRecord(ev_fork, s));
+            BGL_CUDA(cudaStreamWaitEvent(side, ev_fork, 0));
             int64_t n = q1 - q0;
             int64_t nl = nblocks(n, 256);
-            attraction_gravity_kernel<<<(unsigned)(nl + n_chunks), 256, 0, s>>>(
+            attraction_gravity_kernel<<<(unsigned)(nl + n_chunks), 256, 0, side>>>(
                 xy, g->mass.p, g->coff.p, g->cadj.p, q0, q1, qbase, (float)p->kg, chunks.p, nl, chunk_part.p,
-                chunk_arrive.p, f.p - (q0 - qbase));
+                chunk_arrive.p, fa.p - (q0 - qbase));
+            BGL_LAUNCH_CHECK();
+            BGL_CUDA(cudaEventRecord(ev_fa, side));
+        }
+        for (size_t k = 0; k < fmm.size(); ++k)
+            fmm_repulsion(fmm[k], xy, qbase, f.p, q0, att ? fa.p : nullptr, att ? ev_fa : nullptr);
+        if (att) BGL_CUDA(cudaStreamWaitEvent(s, ev_fa, 0));
+        if (n_ex_tiles > 0) {
+            exact_repulsion_kernel<<<n_ex_tiles, EX_THREADS, 0, s>>>(ex_tiles.p, g->comp_off.p, c0, xy, g->mass.p,
+                                                                     qbase, (float)p->kr,
+                                                                     att ? fa.p - (q0 - qbase) : nullptr,
+                                                                     f.p - (q0 - qbase));
             BGL_LAUNCH_CHECK();
         }
     }

@@ -38,6 +38,8 @@
 #include <cmath>
 
 #include "fmm.cuh"
+#include "p2p.cuh"
+#include "sort_hist.cuh"
 
 namespace bgl {
 
@@ -230,12 +232,18 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
     __shared__ float4 wred[32];
     __shared__ bool last;
     float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float2 p = xy[i];
-        mnx = fminf(mnx, p.x);
-        mxx = fmaxf(mxx, p.x);
-        mny = fminf(mny, p.y);
-        mxy = fmaxf(mxy, p.y);
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+        float2 p[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) p[r] = i + r * stride < n ? xy[i + r * stride] : xy[i];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            mnx = fminf(mnx, p[r].x);
+            mxx = fmaxf(mxx, p[r].x);
+            mny = fminf(mny, p[r].y);
+            mxy = fmaxf(mxy, p[r].y);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -309,16 +317,35 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
     *epoch = (*epoch % 0xFFFFFEu) + 1u;   // 1 .. 2^24 - 2; 0 never tags a live key
 }
 
-__global__ void keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
-                            uint32_t *__restrict__ key, uint32_t *__restrict__ idx) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// Morton keys (KEY_ITEMS per thread) and, in the same pass, the digit
+// histograms of the radix sort that orders them
+constexpr int KEY_ITEMS = 8;
+
+__global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
+                                                   uint32_t *__restrict__ key, uint32_t *__restrict__ idx, OsHist h) {
     const float ox = root->oxf, oy = root->oyf, sc = root->scale;
-    float2 p = xy[i];
-    const float fx = floorf((p.x - ox) * sc), fy = floorf((p.y - oy) * sc);
-    const int qx = (int)fminf(fmaxf(fx, 0.f), 65535.f), qy = (int)fminf(fmaxf(fy, 0.f), 65535.f);
-    key[i] = spread_bits((uint32_t)qx) | (spread_bits((uint32_t)qy) << 1);
-    idx[i] = (uint32_t)i;
+    const int i0 = blockIdx.x * 256 * KEY_ITEMS + threadIdx.x;
+    uint32_t k[KEY_ITEMS];
+    unsigned valid = 0;
+    float2 p[KEY_ITEMS];
+#pragma unroll
+    for (int r = 0; r < KEY_ITEMS; ++r) {
+        const int i = i0 + r * 256;
+        p[r] = i < n ? xy[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < KEY_ITEMS; ++r) {
+        const int i = i0 + r * 256;
+        const float fx = floorf((p[r].x - ox) * sc), fy = floorf((p[r].y - oy) * sc);
+        const int qx = (int)fminf(fmaxf(fx, 0.f), 65535.f), qy = (int)fminf(fmaxf(fy, 0.f), 65535.f);
+        k[r] = spread_bits((uint32_t)qx) | (spread_bits((uint32_t)qy) << 1);
+        if (i < n) {
+            key[i] = k[r];
+            idx[i] = (uint32_t)i;
+            valid |= 1u << r;
+        }
+    }
+    os_block_hist<KEY_ITEMS>(k, valid, h);
 }
 
 
@@ -587,42 +614,56 @@ __device__ void lists_uw(const Tree &T, int b, int2 mb, const int *nbb, int k, i
     }
 }
 
-__device__ void lists_v(const Tree &T, int2 mb, const int *nbp, int k, int *ov, int &cv) {
+// (ov[q] for child q, -1 where it is absent or adjacent; cv = how many are set)
+__device__ __forceinline__ void lists_v(const Tree &T, int2 mb, int A, int k, int (&ov)[4], int &cv) {
     cv = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ov[q] = -1;
     const int L = meta_level(mb);
     if (L < 2 || k == 4) return;
-    const int A = nbp[k];
     if (A < 0) return;
     const int2 ma = T.bmeta[A];
     if (meta_level(ma) != L - 1 || meta_leaf(ma)) return;
     const int bx = mx_(mb.x), by = my_(mb.x);
     const int4 ch = T.bchild[A];
     const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
+    int cc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cc[q] = cs[q] >= 0 ? T.bmeta[cs[q]].x : 0;
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int C = cs[q];
         if (C < 0) continue;
-        const int cc = T.bmeta[C].x;
-        const int dx = mx_(cc) - bx, dy = my_(cc) - by;
+        const int dx = mx_(cc[q]) - bx, dy = my_(cc[q]) - by;
         if (abs(dx) <= 1 && abs(dy) <= 1) continue;
-        if (ov) ov[cv] = (C << 6) | ((dx + 3) * 7 + (dy + 3));
+        ov[q] = (C << 6) | ((dx + 3) * 7 + (dy + 3));
         ++cv;
     }
 }
 
-__device__ void lists_x(const Tree &T, int2 mb, const int *nbp, int k, int *ox, int &cx) {
+// (dup: an earlier cell of the parent had the same box)
+__device__ void lists_x(const Tree &T, int2 mb, int A, int k, bool dup, int *ox, int &cx) {
     cx = 0;
     const int L = meta_level(mb);
     if (L < 2 || k == 4) return;
-    const int A = nbp[k];
-    if (A < 0) return;
-    for (int k2 = 0; k2 < k; ++k2)
-        if (k2 != 4 && nbp[k2] == A) return;
+    if (A < 0 || dup) return;
     const int2 ma = T.bmeta[A];
     if (!meta_leaf(ma)) return;
     if (adjacent_xy(ma.x, meta_level(ma), mb.x, L)) return;
     if (ox) ox[0] = A;
     cx = 1;
 }
+
+// Warp-wide breadth-first descent from the internal same-level neighbours
+// of leaf (cb, L) (front[0 .. nf)): every child that touches the leaf is a
+// U entry if it is a leaf and joins the next frontier otherwise; every child
+// that does not touch it is a W entry.  The frontier is taken 32 boxes at a
+// time, a lane per box; one warp scan of packed class counts orders the
+// outputs (level by level, frontier order, child order).  Entries go to
+// su[nu ..] and sw[nw ..] while they fit in LST_CAP; returns false if any
+// list or frontier exceeded its staging capacity (the counts stay exact).
+constexpr int LST_CAP = 256;
+constexpr int FRONT_CAP = 128;
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
     const int lane = threadIdx.x & 31;
@@ -634,23 +675,101 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
+__device__ bool descend(const Tree &T, int cb, int L, int *front, int nf, int *su, int &nu, int *sw, int &nw,
+                        int lane) {
+    int *cur = front, *nxt = front + FRONT_CAP;
+    bool ok = true;
+    while (nf > 0) {
+        int nn = 0;
+        for (int base = 0; base < nf; base += 32) {
+            const int i = base + lane;
+            int cs[4] = {-1, -1, -1, -1};
+            unsigned cls = 0;       // 2 bits per child: 0 none, 1 U, 2 W, 3 frontier
+            if (i < nf) {
+                const int4 ch = T.bchild[cur[i]];
+                cs[0] = ch.x;
+                cs[1] = ch.y;
+                cs[2] = ch.z;
+                cs[3] = ch.w;
+                int2 mc[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) mc[q] = cs[q] >= 0 ? T.bmeta[cs[q]] : make_int2(0, 0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (cs[q] < 0) continue;
+                    const unsigned c = adjacent_xy(mc[q].x, mc[q].y & 255, cb, L) ? (mc[q].y & 256 ? 1u : 3u) : 2u;
+                    cls |= c << (2 * q);
+                }
+            }
+            // counts packed 10 bits per class (at most 4 per lane, 128 per warp)
+            int cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned c = (cls >> (2 * q)) & 3u;
+                cnt += c == 1u ? 1 : (c == 2u ? (1 << 10) : (c == 3u ? (1 << 20) : 0));
+            }
+            const int inc = warp_incl_scan(cnt);
+            const int tot = __shfl_sync(0xffffffffu, inc, 31);
+            int pu = nu + ((inc - cnt) & 1023), pw = nw + (((inc - cnt) >> 10) & 1023), pf = nn + ((inc - cnt) >> 20);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned c = (cls >> (2 * q)) & 3u;
+                if (c == 1u) {
+                    if (pu < LST_CAP) su[pu] = cs[q];
+                    ++pu;
+                } else if (c == 2u) {
+                    if (pw < LST_CAP) sw[pw] = cs[q];
+                    ++pw;
+                } else if (c == 3u) {
+                    if (pf < FRONT_CAP) nxt[pf] = cs[q];
+                    ++pf;
+                }
+            }
+            nu += tot & 1023;
+            nw += (tot >> 10) & 1023;
+            nn += tot >> 20;
+        }
+        __syncwarp();
+        int *t = cur;
+        cur = nxt;
+        nxt = t;
+        nf = nn;
+        if (nf > FRONT_CAP) {
+            ok = false;
+            break;
+        }
+    }
+    return ok && nu <= LST_CAP && nw <= LST_CAP;
+}
+
 // Neighbour cells and interaction lists, one warp per box (no waits).
 // Lanes 0-8 look up the 3x3 cells around the box (k = (dy + 1) * 3 + dx + 1:
 // the box at its level covering the cell, else the coarser leaf covering it,
-// else -1), lanes 9-17 those around its parent; then lanes 0-8 build U and W
-// for cells k = 0..8, lanes 9-17 V and lanes 18-26 X for the parent's cells;
-// warp scans give each lane its offsets in a chunk of lidx reserved by one
-// atomic, so the order inside every list is fixed.
-__global__ void nbr_lists_kernel(Tree T) {
-    const int lane = threadIdx.x & 31;
+// else -1), lanes 9-17 those around its parent.  Then lanes 9-17 form V and
+// lanes 18-26 X for the parent's cells (in registers); for a leaf, lanes 0-8
+// give the direct U entries (the box itself, coarser or same-level leaves)
+// and the internal same-level neighbours, from which the warp descends to
+// the finer U entries and the W entries (staged in shared memory).  One
+// atomic reserves the box's chunk of lidx; the order inside every list is
+// fixed.  A box whose lists overflow the staging falls back to a per-lane
+// walk, run once to count and once to write.
+constexpr int LIST_WARPS = 8;
+
+__global__ void __launch_bounds__(LIST_WARPS * 32) nbr_lists_kernel(Tree T) {
+    __shared__ int s_u[LIST_WARPS][LST_CAP], s_w[LIST_WARPS][LST_CAP];
+    __shared__ int s_front[LIST_WARPS][2 * FRONT_CAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int role = lane / 9, k = lane % 9;
+    const unsigned lt = (1u << lane) - 1u;
+    int *su = s_u[wib], *sw = s_w[wib], *front = s_front[wib];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int B = min(T.levoff[NLEV], T.Bmax);
     const unsigned epoch = *T.epoch;
-    for (int b = gw; b < B; b += nw) {
+    for (int b = gw; b < B; b += nwarps) {
         const int2 mb = T.bmeta[b];
         const int L = meta_level(mb);
+        const bool leaf = meta_leaf(mb);
         const int bx = mx_(mb.x), by = my_(mb.x);
         const int p = b == 0 ? -1 : T.bparent[b];
         int mine = -1;
@@ -660,20 +779,52 @@ __global__ void nbr_lists_kernel(Tree T) {
             const int j = lane - 9;
             mine = j == 4 ? p : cover(T, epoch, L - 1, (bx >> 1) + j % 3 - 1, (by >> 1) + j / 3 - 1);
         }
-        int nbb[9], nbp[9];
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            nbb[j] = __shfl_sync(0xffffffffu, mine, j);
-            nbp[j] = __shfl_sync(0xffffffffu, mine, 9 + j);
+        // lane (role, k): the box of cell k around b (role 0) or around its parent (roles 1, 2)
+        const int A = __shfl_sync(0xffffffffu, mine, role == 0 ? k : 9 + k);
+        // a cell whose box an earlier cell of the same group already had (k = 4 excluded)
+        const bool grp = role <= 2 && k != 4 && A >= 0;
+        const unsigned long long tag =
+            grp ? ((unsigned long long)role << 32) | (unsigned)A : (1ull << 40) + (unsigned)lane;
+        const bool dup = (__match_any_sync(0xffffffffu, tag) & lt) != 0u;
+        // V (lanes 9-17, up to 4 each) and X (lanes 18-26, up to 1 each) in registers
+        int ve[4] = {-1, -1, -1, -1};
+        int cv = 0, xe = -1;
+        if (role == 1 && p >= 0) lists_v(T, mb, A, k, ve, cv);
+        else if (role == 2 && p >= 0) {
+            int cx = 0;
+            lists_x(T, mb, A, k, dup, &xe, cx);
+            if (!cx) xe = -1;
         }
-        int cu = 0, cw = 0, cv = 0, cx = 0;
-        if (role == 0) lists_uw(T, b, mb, nbb, k, nullptr, nullptr, cu, cw);
-        else if (role == 1 && p >= 0) lists_v(T, mb, nbp, k, nullptr, cv);
-        else if (role == 2 && p >= 0) lists_x(T, mb, nbp, k, nullptr, cx);
-        const int iu = warp_incl_scan(cu), iw = warp_incl_scan(cw), iv = warp_incl_scan(cv), ix = warp_incl_scan(cx);
-        const int tu = __shfl_sync(0xffffffffu, iu, 31), tw = __shfl_sync(0xffffffffu, iw, 31);
-        const int tv = __shfl_sync(0xffffffffu, iv, 31), tx = __shfl_sync(0xffffffffu, ix, 31);
-        const int total = tu + tv + tw + tx;
+        // direct U entries and the frontier (lanes 0-8 of a leaf)
+        int du = -1, fr = -1;
+        if (leaf && role == 0) {
+            if (k == 4) du = b;
+            else if (A >= 0 && !dup) {
+                if (meta_leaf(T.bmeta[A])) du = A;
+                else fr = A;
+            }
+        }
+        const unsigned bu = __ballot_sync(0xffffffffu, du >= 0), bf = __ballot_sync(0xffffffffu, fr >= 0);
+        if (du >= 0) su[__popc(bu & lt)] = du;
+        if (fr >= 0) front[__popc(bf & lt)] = fr;
+        int nu = __popc(bu), nw = 0;
+        __syncwarp();
+        const bool staged = bf == 0u || descend(T, mb.x, L, front, __popc(bf), su, nu, sw, nw, lane);
+        int nbb[9];
+        if (!staged) {
+            // overflow: exact counts by the per-lane walk
+#pragma unroll
+            for (int j = 0; j < 9; ++j) nbb[j] = __shfl_sync(0xffffffffu, mine, j);
+            int cu = 0, cw = 0;
+            if (role == 0) lists_uw(T, b, mb, nbb, k, nullptr, nullptr, cu, cw);
+            nu = __shfl_sync(0xffffffffu, warp_incl_scan(cu), 31);
+            nw = __shfl_sync(0xffffffffu, warp_incl_scan(cw), 31);
+        }
+        const int iv = warp_incl_scan(cv);
+        const int tv = __shfl_sync(0xffffffffu, iv, 31);
+        const unsigned bx_ = __ballot_sync(0xffffffffu, xe >= 0);
+        const int tx = __popc(bx_);
+        const int total = nu + tv + nw + tx;
         int base = 0;
         if (lane == 0) {
             base = atomicAdd(T.pool, total);
@@ -685,22 +836,35 @@ __global__ void nbr_lists_kernel(Tree T) {
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base < 0) {
             if (lane < 5) T.lofs[5 * b + lane] = 0;
+            __syncwarp();
             continue;
         }
         if (lane == 0) {
             T.lofs[5 * b] = base;
-            T.lofs[5 * b + 1] = base + tu;
-            T.lofs[5 * b + 2] = base + tu + tv;
-            T.lofs[5 * b + 3] = base + tu + tv + tw;
+            T.lofs[5 * b + 1] = base + nu;
+            T.lofs[5 * b + 2] = base + nu + tv;
+            T.lofs[5 * b + 3] = base + nu + tv + nw;
             T.lofs[5 * b + 4] = base + total;
         }
-        if (total > 0) {
-            int d0, d1;
-            if (role == 0)
-                lists_uw(T, b, mb, nbb, k, T.lidx + base + (iu - cu), T.lidx + base + tu + tv + (iw - cw), d0, d1);
-            else if (role == 1 && p >= 0) lists_v(T, mb, nbp, k, T.lidx + base + tu + (iv - cv), d0);
-            else if (role == 2 && p >= 0) lists_x(T, mb, nbp, k, T.lidx + base + tu + tv + tw + (ix - cx), d0);
+        int *out = T.lidx + base;
+        {
+            int c = nu + iv - cv;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (ve[q] >= 0) out[c++] = ve[q];
         }
+        if (xe >= 0) out[nu + tv + nw + __popc(bx_ & lt)] = xe;
+        if (staged) {
+            for (int i = lane; i < nu; i += 32) out[i] = su[i];
+            for (int i = lane; i < nw; i += 32) out[nu + tv + i] = sw[i];
+        } else {
+            int cu = 0, cw = 0;
+            if (role == 0) lists_uw(T, b, mb, nbb, k, nullptr, nullptr, cu, cw);
+            const int iu = warp_incl_scan(cu), iw = warp_incl_scan(cw);
+            int d0, d1;
+            if (role == 0) lists_uw(T, b, mb, nbb, k, out + (iu - cu), out + nu + tv + (iw - cw), d0, d1);
+        }
+        __syncwarp();
     }
 }
 
@@ -930,15 +1094,11 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
     }
 }
 
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 struct LeafArgs {
     ExpArgs e;
     float2 *f;           // f[q - fbase]
+    const float2 *fa;    // fa[q - fbase] added to the final force, or null
     int64_t q0, fbase;
     float kr;
     int *ticket;
@@ -956,17 +1116,6 @@ struct LeafArgs {
 // sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the far kernel completes it).
 constexpr int NEAR_WARPS = 8;
 constexpr int NEAR_SRC = 128;
-
-__device__ __forceinline__ void p2p_pair(const float4 &z, const float4 &q, float &fx, float &fy) {
-    const float dx = z.x - q.x, dy = z.y - q.y;
-    // r^2 + 1e-30: a coincident pair (the target itself) has dx = dy = 0 and
-    // adds exactly 0; for any other pair of FP32 points the shift is far below
-    // one rounding of r^2
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
-    const float w = q.z * rcp_approx(r2);
-    fx = fmaf(w, dx, fx);
-    fy = fmaf(w, dy, fy);
-}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -996,18 +1145,22 @@ __device__ __forceinline__ int stage_chunk(const Tree &T, float4 *buf, int &ui, 
 }
 
 // Pairs of the targets tb + t + r * lps (r < R) with every S-th staged
-// source from h; R targets per lane amortise each shared-memory load.
+// source pair (2j, 2j + 1) from h; R targets per lane amortise each
+// shared-memory load, and each packed instruction covers two sources.
 template <int R>
 __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*buf)[NEAR_SRC], int tb, int ntc,
                                           int lps, int S, int us, int ue, int lane) {
     const int t = lane % lps, h = lane / lps;
-    float4 z[R];
-    float fx[R], fy[R];
+    f2x zx[R], zy[R], fx[R], fy[R];
+    int zi[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t + r * lps;
-        z[r] = i < ntc ? T.pts[tb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        fx[r] = fy[r] = 0.f;
+        const float4 z = i < ntc ? T.pts[tb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        zx[r] = pk2(z.x, z.x);
+        zy[r] = pk2(z.y, z.y);
+        zi[r] = __float_as_int(z.w);
+        fx[r] = fy[r] = 0ull;
     }
     int ui = us, off = 0, cur = 0;
     int cnt = stage_chunk(T, buf[0], ui, off, ue, lane);
@@ -1015,21 +1168,25 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
         // next chunk in flight while this one is summed
         const int nxt = ui < ue ? stage_chunk(T, buf[cur ^ 1], ui, off, ue, lane) : (cp_async_commit(), 0);
         cp_async_wait_one();
+        float4 *src = buf[cur];
+        // an odd chunk is padded with a massless source
+        if ((cnt & 1) && lane == 0) src[cnt] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
-        const float4 *src = buf[cur];
+        const int np = (cnt + 1) >> 1;
         if (S == 1) {
-#pragma unroll 4
-            for (int j = 0; j < cnt; ++j) {
-                const float4 q = src[j];
+#pragma unroll 2
+            for (int j = 0; j < np; ++j) {
+                const float4 q0 = src[2 * j], q1 = src[2 * j + 1];
+                const f2x qx = pk2(q0.x, q1.x), qy = pk2(q0.y, q1.y), qm = pk2(q0.z, q1.z);
 #pragma unroll
-                for (int r = 0; r < R; ++r) p2p_pair(z[r], q, fx[r], fy[r]);
+                for (int r = 0; r < R; ++r) p2p_pair2(zx[r], zy[r], qx, qy, qm, fx[r], fy[r]);
             }
         } else {
-#pragma unroll 2
-            for (int j = h; j < cnt; j += S) {
-                const float4 q = src[j];
+            for (int j = h; j < np; j += S) {
+                const float4 q0 = src[2 * j], q1 = src[2 * j + 1];
+                const f2x qx = pk2(q0.x, q1.x), qy = pk2(q0.y, q1.y), qm = pk2(q0.z, q1.z);
 #pragma unroll
-                for (int r = 0; r < R; ++r) p2p_pair(z[r], q, fx[r], fy[r]);
+                for (int r = 0; r < R; ++r) p2p_pair2(zx[r], zy[r], qx, qy, qm, fx[r], fy[r]);
             }
         }
         __syncwarp();
@@ -1038,21 +1195,20 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+        float ax, bx, ay, by;
+        upk2(fx[r], ax, bx);
+        upk2(fy[r], ay, by);
+        float sx = ax + bx, sy = ay + by;
         for (int o = lps; o < 32; o <<= 1) {
-            fx[r] += __shfl_xor_sync(0xffffffffu, fx[r], o);
-            fy[r] += __shfl_xor_sync(0xffffffffu, fy[r], o);
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
         }
-    }
-    if (h == 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = t + r * lps;
-            if (i < ntc) la.f[la.q0 + __float_as_int(z[r].w) - la.fbase] = make_float2(fx[r], fy[r]);
-        }
+        const int i = t + r * lps;
+        if (h == 0 && i < ntc) la.f[la.q0 + zi[r] - la.fbase] = make_float2(sx, sy);
     }
 }
 
-__global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
+__global__ void __launch_bounds__(NEAR_WARPS * 32, 5) near_kernel(LeafArgs la) {
     const Tree &T = la.e.T;
     __shared__ __align__(16) float4 stage[NEAR_WARPS][2][NEAR_SRC];
     const int lane = threadIdx.x & 31;
@@ -1071,7 +1227,7 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
             // fewest padded target slots: R targets on lps = 32 / S lanes
             int R = 2, S = 1, best = 64;
             for (int s2 = 1; s2 <= 32; s2 <<= 1) {
-                for (int r2 = 4; r2 >= 1; --r2) {
+                for (int r2 = 3; r2 >= 1; --r2) {
                     const int slots = r2 * (32 / s2);
                     if (slots >= ntc && slots < best) {
                         best = slots;
@@ -1081,8 +1237,7 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
                 }
             }
             const int lps = 32 / S;
-            if (R == 4) near_tile<4>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else if (R == 2) near_tile<2>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else near_tile<1>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
         }
@@ -1107,6 +1262,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
     __shared__ float2 loc[FAR_WARPS][PT + 1];
     __shared__ float2 ancl[FAR_WARPS][MAXLEV - 1][PT + 1];
     __shared__ float2 part_[FAR_WARPS][MAXLEV - 1][PT + 1];
+    __shared__ int s_anc[FAR_WARPS][MAXLEV - 1];
+    __shared__ float2 s_t[FAR_WARPS][MAXLEV - 1];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = la.e.binom[i];
     __syncthreads();
     const Tree &T = la.e.T;
@@ -1123,42 +1280,37 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
         const int Lb = mb.y & 255;
         const uint32_t kb = T.bkey[b];
         // ancestors of levels >= 2 (lane j: level Lb - j, key kb >> 2j), found by
-        // independent hash lookups; their partial locals staged in shared memory
+        // independent hash lookups, and the shift t_j = (c_leaf - c_A) / r_A
         const int nA = Lb >= 2 ? Lb - 1 : 0;
-        int anc = -1;
-        if (lane < nA) anc = lane == 0 ? b : hash_find(T, epoch, Lb - lane, kb >> (2 * lane));
-        {
-            int ancj[MAXLEV - 1];
-#pragma unroll
-            for (int j = 0; j < MAXLEV - 1; ++j) ancj[j] = __shfl_sync(0xffffffffu, anc, j);
-            for (int it = lane; it < nA * (p + 1); it += 32) {
-                const int j = it / (p + 1), l = it % (p + 1);
-                int A = -1;
-#pragma unroll
-                for (int jj = 0; jj < MAXLEV - 1; ++jj)
-                    if (jj == j) A = ancj[jj];
-                ancl[wib][j][l] = A >= 0 ? la.e.Lc[(size_t)A * (PT + 1) + l] : make_float2(0.f, 0.f);
-            }
+        if (lane < nA) {
+            s_anc[wib][lane] = lane == 0 ? b : hash_find(T, epoch, Lb - lane, kb >> (2 * lane));
+            const uint32_t ka = kb >> (2 * lane);
+            const float sc = ldexpf(1.0f, -lane);
+            const float sx = (float)((int)(2 * compact_bits(kb) + 1) - (int)(2 * compact_bits(ka) + 1) * (1 << lane));
+            const float sy =
+                (float)((int)(2 * compact_bits(kb >> 1) + 1) - (int)(2 * compact_bits(ka >> 1) + 1) * (1 << lane));
+            s_t[wib][lane] = make_float2(sx * sc, sy * sc);
+        }
+        __syncwarp();
+        // their partial local expansions (M2L + P2L) staged in shared memory
+        for (int it = lane; it < nA * (PT + 1); it += 32) {
+            const int j = it / (PT + 1), l = it - j * (PT + 1);
+            const int A = s_anc[wib][j];
+            ancl[wib][j][l] = A >= 0 && l <= p ? la.e.Lc[(size_t)A * (PT + 1) + l] : make_float2(0.f, 0.f);
         }
         __syncwarp();
         // incoming expansion of the leaf: items (ancestor j, coefficient m)
-        // spread over all lanes, then each coefficient summed over j in order
-        for (int it = lane; it < nA * p; it += 32) {
-            const int j = it / p, m = it % p + 1;
-            // t = (c_leaf - c_A) / r_A, A the ancestor j levels up
-            const uint32_t ka = kb >> (2 * j);
-            const float sx = (float)((int)(2 * compact_bits(kb) + 1) - (int)(2 * compact_bits(ka) + 1) * (1 << j));
-            const float sy = (float)((int)(2 * compact_bits(kb >> 1) + 1) - (int)(2 * compact_bits(ka >> 1) + 1) * (1 << j));
-            const float sc = 1.0f / (float)(1 << j);
-            const float2 t = make_float2(sx * sc, sy * sc);
-            float2 s = make_float2(0.f, 0.f), pw = make_float2(1.f, 0.f);
-            for (int l = m; l <= p; ++l) {
-                s = cadd(s, cscale(cmul(ancl[wib][j][l], pw), sbin[l * BN + m]));
-                pw = cmul(pw, t);
+        // spread over all lanes, each a Horner sum in t_j, then each
+        // coefficient summed over j in order:
+        //   b~_m(leaf) += 2^(-j m) sum_{l >= m} b~_l(A_j) C(l, m) t_j^(l-m)
+        for (int it = lane; it < nA * PT; it += 32) {
+            const int j = it / PT, m = it - j * PT + 1;
+            float2 sres = make_float2(0.f, 0.f);
+            if (m <= p) {
+                const float2 t = s_t[wib][j];
+                for (int l = p; l >= m; --l) sres = cadd(cmul(sres, t), cscale(ancl[wib][j][l], sbin[l * BN + m]));
             }
-            float scm = 1.0f;
-            for (int q = 0; q < m; ++q) scm *= sc;          // 2^(-j m)
-            part_[wib][j][m] = cscale(s, scm);
+            part_[wib][j][m] = make_float2(ldexpf(sres.x, -j * m), ldexpf(sres.y, -j * m));
         }
         __syncwarp();
         float2 mine = make_float2(0.f, 0.f);
@@ -1167,6 +1319,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
         if (lane <= PT) loc[wib][lane] = mine;
         __syncwarp();
         const BoxGeo g = box_geo_xy(rt, mb.x, Lb);
+        const float ir = 1.0f / g.r;
         const int s = T.bstart[b], e = T.bend[b];
         const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
         for (int tt = s + lane; tt < e; tt += 32) {
@@ -1174,7 +1327,6 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
             float2 E;
             // L2P: E = (1/r) sum_l l b~_l v^(l-1), v = (z - c) / r
             {
-                const float ir = 1.0f / g.r;
                 const float2 v = make_float2((z.x - g.cx) * ir, (z.y - g.cy) * ir);
                 float2 hs = make_float2(0.f, 0.f);
 #pragma unroll
@@ -1189,7 +1341,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
                 const int2 md_ = T.bmeta[Dx];
                 const BoxGeo gd = box_geo_xy(rt, md_.x, md_.y & 255);
                 const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
-                const float2 idz = crcp(dz);
+                const float id2 = rcp_approx(fmaf(dz.x, dz.x, dz.y * dz.y));
+                const float2 idz = make_float2(dz.x * id2, -dz.y * id2);
                 const float2 tt2 = cscale(idz, gd.r);
                 const float2 *md = la.e.M + (size_t)Dx * (PT + 1);
                 float2 hs = make_float2(0.f, 0.f);
@@ -1205,7 +1358,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
             float2 *fo = la.f + (la.q0 + o - la.fbase);
             const float2 nr = *fo;
             const float km = la.kr * z.z;
-            *fo = make_float2(km * (nr.x + E.x), km * (nr.y - E.y));
+            const float2 a = la.fa ? la.fa[la.q0 + o - la.fbase] : make_float2(0.f, 0.f);
+            *fo = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
         }
         __syncwarp();
     }
@@ -1373,10 +1527,11 @@ static ExpArgs exp_args(FmmPlan *pl, const Tree &T) {
     return a;
 }
 
-static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbase) {
+static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbase, const float2 *fa) {
     LeafArgs la;
     la.e = a;
     la.f = f;
+    la.fa = fa;
     la.q0 = pl->q0;
     la.fbase = fbase;
     la.kr = pl->kr;
@@ -1390,15 +1545,16 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
     const int n = pl->n;
     const float *ml = pl->g->mass.p + pl->q0;
     BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 8, s));
-    bbox_kernel<<<std::min<int64_t>(2 * ctx->num_sms, nblk(n, 256)), 256, 0, s>>>(
-        xl, n, pl->part.p, pl->counter.p, pl->root.p, pl->err.p, pl->epoch.p);
-    BGL_LAUNCH_CHECK();
-    keys_kernel<<<nblk(n, 256), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p);
-    BGL_LAUNCH_CHECK();
     cudaStream_t keep = ctx->stream;
     ctx->stream = s;
     try {
-        radix_sort_u32_ws(ctx, pl->sortws, pl->key.p, pl->idx.p, n, 32, xl, ml, pl->pts.p);
+        const OsHist h = radix_sort_u32_ws_begin(ctx, pl->sortws, n);
+        bbox_kernel<<<std::min<int64_t>(2 * ctx->num_sms, nblk(n, 256)), 256, 0, s>>>(
+            xl, n, pl->part.p, pl->counter.p, pl->root.p, pl->err.p, pl->epoch.p);
+        BGL_LAUNCH_CHECK();
+        keys_kernel<<<nblk(n, 256 * KEY_ITEMS), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p, h);
+        BGL_LAUNCH_CHECK();
+        radix_sort_u32_ws_scatter(ctx, pl->sortws, pl->key.p, pl->idx.p, n, xl, ml, pl->pts.p);
     } catch (...) {
         ctx->stream = keep;
         throw;
@@ -1452,11 +1608,12 @@ static void launch_far(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
 //   side:                +-- up -------+-- (lists) down ----+
 // ev (timing events, 7, may be null) forces one stream and marks the phases.
 template <int PT>
-static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev) {
+static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev,
+                     const float2 *fa = nullptr, cudaEvent_t fa_ready = nullptr) {
     cudaStream_t s = pl->g->ctx->stream;
     const Tree T = make_tree(pl);
     const ExpArgs a = exp_args(pl, T);
-    const LeafArgs la = leaf_args(pl, a, f, fbase);
+    const LeafArgs la = leaf_args(pl, a, f, fbase, fa);
     if (ev) BGL_CUDA(cudaEventRecord(ev[0], s));
     phase_points(pl, xl, s);
     if (ev) BGL_CUDA(cudaEventRecord(ev[1], s));
@@ -1471,6 +1628,7 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
         if (ev) BGL_CUDA(cudaEventRecord(ev[5], s));
         launch_near(pl, la, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[6], s));
+        if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
         launch_far<PT>(pl, la, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[7], s));
         return;
@@ -1486,18 +1644,21 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
     launch_down<PT>(pl, a, t);
     BGL_CUDA(cudaEventRecord(pl->ev[2], t));           // local expansions ready
     BGL_CUDA(cudaStreamWaitEvent(s, pl->ev[2], 0));
+    if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
     launch_far<PT>(pl, la, s);
 }
 
-static void evaluate_any(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev) {
-    if (pl->PT == 8) evaluate<8>(pl, xl, f, fbase, concurrent, ev);
-    else if (pl->PT == 16) evaluate<16>(pl, xl, f, fbase, concurrent, ev);
-    else evaluate<24>(pl, xl, f, fbase, concurrent, ev);
+static void evaluate_any(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev,
+                         const float2 *fa = nullptr, cudaEvent_t fa_ready = nullptr) {
+    if (pl->PT == 8) evaluate<8>(pl, xl, f, fbase, concurrent, ev, fa, fa_ready);
+    else if (pl->PT == 16) evaluate<16>(pl, xl, f, fbase, concurrent, ev, fa, fa_ready);
+    else evaluate<24>(pl, xl, f, fbase, concurrent, ev, fa, fa_ready);
 }
 
-void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase) {
+void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase, const float2 *fa,
+                   cudaEvent_t fa_ready) {
     if (pl->n <= 0) return;
-    evaluate_any(pl, xy + (pl->q0 - qbase), f, fbase, true, nullptr);
+    evaluate_any(pl, xy + (pl->q0 - qbase), f, fbase, true, nullptr, fa, fa_ready);
 }
 
 namespace {

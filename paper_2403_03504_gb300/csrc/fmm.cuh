@@ -11,10 +11,13 @@ struct FmmPlan;
 FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c);
 void fmm_destroy(FmmPlan *pl);
 
-// f[q - fbase] <- kr m_q sum_j m_j (p_q - p_j) / |p_q - p_j|^2 for every
-// position q of the component, with xy[q - qbase] the positions.  Launches
-// only (no host synchronisation), so it can be captured in a CUDA graph.
-void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase);
+// f[q - fbase] <- kr m_q sum_j m_j (p_q - p_j) / |p_q - p_j|^2 (+ fa[q - fbase]
+// when fa is not null) for every position q of the component, with
+// xy[q - qbase] the positions.  The kernel that adds fa first waits for the
+// event fa_ready (if not null) on the calling stream.  Launches only (no
+// host synchronisation), so it can be captured in a CUDA graph.
+void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase, const float2 *fa = nullptr,
+                   cudaEvent_t fa_ready = nullptr);
 
 // Counts and per-phase device times of `reps` evaluations (synchronises);
 // out[15]: boxes, leaves, depth, P2P pairs, M2L translations, M2P terms,

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "bgl_internal.cuh"
+#include "sort_hist.cuh"
 
 namespace bgl {
 
@@ -274,46 +275,20 @@ constexpr int OS_ITEMS = 8;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_MASK = (1u << 30) - 1u;
 constexpr long long OS_SPIN = 1ll << 24;
+constexpr int OS_LB = 8;           // look-back window (predecessor tiles per step)
 
-__global__ void os_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, uint32_t *hist, uint32_t *base,
-                               unsigned *counter) {
-    __shared__ uint32_t h[4][256];
-    __shared__ bool last;
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
+// digit histograms of the keys, OS_ITEMS per thread
+__global__ void __launch_bounds__(OS_THREADS) os_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, OsHist h) {
+    uint32_t k[OS_ITEMS];
+    unsigned valid = 0;
+    const int64_t i0 = (int64_t)blockIdx.x * OS_TILE + threadIdx.x;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) atomicAdd(&h[d][(k >> (8 * d)) & 0xFF], 1u);
+    for (int r = 0; r < OS_ITEMS; ++r) {
+        const int64_t i = i0 + (int64_t)r * OS_THREADS;
+        k[r] = i < n ? keys[i] : 0u;
+        if (i < n) valid |= 1u << r;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
-        if ((&h[0][0])[i]) atomicAdd(&hist[i], (&h[0][0])[i]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // exclusive scan of each digit histogram (thread = bin)
-    __shared__ uint32_t ws[8];
-    for (int d = 0; d < 4; ++d) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        uint32_t v = __ldcg(&hist[d * 256 + threadIdx.x]);
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) ws[warp] = x;
-        __syncthreads();
-        uint32_t pre = 0;
-        for (int w = 0; w < warp; ++w) pre += ws[w];
-        base[d * 256 + threadIdx.x] = pre + x - v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *counter = 0u;
+    os_block_hist<OS_ITEMS>(k, valid, h);
 }
 
 __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *__restrict__ kin,
@@ -384,18 +359,29 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
             st[d] = OS_INC | own;
         } else {
             st[(int64_t)tile * 256 + d] = OS_AGG | own;
-            for (int t = tile - 1; t >= 0; --t) {
-                uint32_t v;
-                long long it = 0;
-                while (((v = st[(int64_t)t * 256 + d]) & ~OS_MASK) == 0) {
-                    if (++it > OS_SPIN) {
-                        atomicOr(err, 1);
-                        break;
+            // look back OS_LB predecessors per step: their status words are
+            // loaded together, then taken newest first until an inclusive one
+            bool done = false;
+            for (int t = tile - 1; t >= 0 && !done; t -= OS_LB) {
+                uint32_t v[OS_LB];
+#pragma unroll
+                for (int w = 0; w < OS_LB; ++w) v[w] = t - w >= 0 ? (uint32_t)st[(int64_t)(t - w) * 256 + d] : (uint32_t)OS_INC;
+#pragma unroll
+                for (int w = 0; w < OS_LB; ++w) {
+                    if (done) break;
+                    long long it = 0;
+                    while ((v[w] & ~OS_MASK) == 0) {
+                        if (++it > OS_SPIN) {
+                            atomicOr(err, 1);
+                            v[w] = OS_INC;
+                            break;
+                        }
+                        __nanosleep(32);
+                        v[w] = st[(int64_t)(t - w) * 256 + d];
                     }
-                    __nanosleep(32);
+                    excl += v[w] & OS_MASK;
+                    if (v[w] & OS_INC) done = true;
                 }
-                excl += v & OS_MASK;
-                if (v & OS_INC) break;
             }
             __threadfence();
             st[(int64_t)tile * 256 + d] = OS_INC | (excl + own);
@@ -460,25 +446,31 @@ void SortWorkspace::reserve(Allocator *a, int64_t n, cudaStream_t s) {
     cap = n;
 }
 
-void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits,
-                       const float2 *gxy, const float *gmass, float4 *gpts) {
-    if (n <= 1 || bits <= 0) return;
+OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n) {
     BGL_REQUIRE(n <= ws.cap && n < (int64_t(1) << 30), "radix sort: workspace too small");
-    BGL_REQUIRE(bits == 32 && vals, "radix sort: the workspace sort takes 32-bit keys with values");
+    cudaStream_t s = c->stream;
+    const int64_t nt = os_tiles(n);
+    OsHist h;
+    h.hist = reinterpret_cast<uint32_t *>(ws.hist.p);
+    h.base = h.hist + 4 * 256;
+    unsigned *tickets = reinterpret_cast<unsigned *>(h.hist + 8 * 256);
+    h.counter = tickets + 4;
+    // counts, pass tickets and look-back status words start at zero
+    BGL_CUDA(cudaMemsetAsync(h.hist, 0, sizeof(uint32_t) * 4 * 256, s));
+    BGL_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * 4, s));
+    BGL_CUDA(cudaMemsetAsync(ws.tiles.p, 0, sizeof(uint32_t) * 4 * 256 * nt, s));
+    return h;
+}
+
+void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n,
+                               const float2 *gxy, const float *gmass, float4 *gpts) {
     cudaStream_t s = c->stream;
     const int64_t nt = os_tiles(n);
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws.hist.p);
     uint32_t *base = hist + 4 * 256;
     unsigned *tickets = reinterpret_cast<unsigned *>(hist + 8 * 256);
-    unsigned *counter = tickets + 4;
     int *err = reinterpret_cast<int *>(tickets + 5);
     uint32_t *status = reinterpret_cast<uint32_t *>(ws.tiles.p);
-    BGL_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * 256, s));
-    BGL_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * 5, s));
-    BGL_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t) * 4 * 256 * nt, s));
-    const int hblocks = (int)std::min<int64_t>(64, (n + 255) / 256);   // few blocks: fewer global atomics
-    os_hist_kernel<<<hblocks, 256, 0, s>>>(keys, n, hist, base, counter);
-    BGL_LAUNCH_CHECK();
     uint32_t *ka = keys, *kb = ws.keys.p, *va = vals, *vb = ws.vals.p;
     for (int d = 0; d < 4; ++d) {
         const bool g = d == 3 && gpts;
@@ -491,6 +483,16 @@ void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *
         std::swap(va, vb);
     }
     // four passes: the sorted keys (and values unless gathered) are back in keys / vals
+}
+
+void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits,
+                       const float2 *gxy, const float *gmass, float4 *gpts) {
+    if (n <= 1 || bits <= 0) return;
+    BGL_REQUIRE(bits == 32 && vals, "radix sort: the workspace sort takes 32-bit keys with values");
+    const OsHist h = radix_sort_u32_ws_begin(c, ws, n);
+    os_hist_kernel<<<(unsigned)os_tiles(n), OS_THREADS, 0, c->stream>>>(keys, n, h);
+    BGL_LAUNCH_CHECK();
+    radix_sort_u32_ws_scatter(c, ws, keys, vals, n, gxy, gmass, gpts);
 }
 
 int sort_workspace_error(bgl_ctx *c, SortWorkspace &ws) {

@@ -100,7 +100,7 @@ def test_fmm_small_leaf_sizes(path30k):
         assert e.max() <= ceiling(12), (leaf, e.max())
 
 
-@pytest.mark.parametrize("case", ["tiny", "coincident", "collinear", "far_clusters", "wide_range"])
+@pytest.mark.parametrize("case", ["tiny", "coincident", "collinear", "far_clusters", "wide_range", "edge_line"])
 def test_fmm_degenerate_geometries(ctx, case):
     bgl = _bgl()
     rng = np.random.default_rng(11)
@@ -116,6 +116,14 @@ def test_fmm_degenerate_geometries(ctx, case):
     elif case == "far_clusters":
         n = 6000                                 # deep tree around two tight clusters
         xy = np.concatenate([rng.normal(0, 1e-3, (n // 2, 2)), rng.normal(0, 1e-3, (n // 2, 2)) + [100.0, 40.0]])
+    elif case == "edge_line":
+        # two coarse leaves (the left half of the root) against a line of
+        # 40,000 points just right of the midline, refined to ~1,000 leaves:
+        # each coarse leaf touches over 500 fine ones (long U and W lists)
+        left = np.stack([rng.uniform(0.05, 0.45, 20), rng.uniform(0.0, 1.0, 20)], 1)
+        line = np.stack([np.full(40000, 0.5001), rng.uniform(0.0, 1.0, 40000)], 1)
+        xy = np.concatenate([[[0.0, 0.0], [1.0, 1.0]], left, line])
+        n = len(xy)
     else:
         n = 6000                                 # scales from 1e-3 to 1e3
         r = 10 ** rng.uniform(-3, 3, n)
