@@ -49,14 +49,13 @@ __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
     __shared__ float4 src[EX_STILE];
     const Tile t = tiles[blockIdx.x];
     const int64_t s_begin = comp_off[c0 + t.comp], s_end = comp_off[c0 + t.comp + 1];
-    f2x zx[EX_R], zy[EX_R];
-    float sx[EX_R], sy[EX_R], cx[EX_R], cy[EX_R];
+    float zx[EX_R], zy[EX_R], sx[EX_R], sy[EX_R], cx[EX_R], cy[EX_R];
 #pragma unroll
     for (int r = 0; r < EX_R; ++r) {
         int64_t q = t.t0 + threadIdx.x + r * EX_THREADS;
         float2 p = q < t.t1 ? xy[q - qbase] : make_float2(0.f, 0.f);
-        zx[r] = pk2(p.x, p.x);
-        zy[r] = pk2(p.y, p.y);
+        zx[r] = p.x;
+        zy[r] = p.y;
         sx[r] = sy[r] = cx[r] = cy[r] = 0.f;
     }
     for (int64_t s0 = s_begin; s0 < s_end; s0 += EX_STILE) {
@@ -66,32 +65,25 @@ __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
             float2 p = xy[s0 + k - qbase];
             src[k] = make_float4(p.x, p.y, mass[s0 + k], 0.f);
         }
-        // an odd stage is padded with a massless source
-        if ((cnt & 1) && threadIdx.x == 0) src[cnt] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        f2x ax[EX_R], ay[EX_R];
+        float ax[EX_R], ay[EX_R];
 #pragma unroll
-        for (int r = 0; r < EX_R; ++r) ax[r] = ay[r] = 0ull;
-        const int np = (cnt + 1) >> 1;
-#pragma unroll 2
-        for (int j = 0; j < np; ++j) {
-            const float4 q0 = src[2 * j], q1 = src[2 * j + 1];
-            const f2x qx = pk2(q0.x, q1.x), qy = pk2(q0.y, q1.y), qm = pk2(q0.z, q1.z);
+        for (int r = 0; r < EX_R; ++r) ax[r] = ay[r] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) {
+            const float4 q = src[j];
 #pragma unroll
-            for (int r = 0; r < EX_R; ++r) p2p_pair2(zx[r], zy[r], qx, qy, qm, ax[r], ay[r]);
+            for (int r = 0; r < EX_R; ++r) p2p_pair(zx[r], zy[r], q, ax[r], ay[r]);
         }
         // blocked accumulation: each stage's partial sum enters a
         // compensated (Kahan) running total
 #pragma unroll
         for (int r = 0; r < EX_R; ++r) {
-            float a0, a1, b0, b1;
-            upk2(ax[r], a0, a1);
-            upk2(ay[r], b0, b1);
-            float y = (a0 + a1) - cx[r];
+            float y = ax[r] - cx[r];
             float s = sx[r] + y;
             cx[r] = (s - sx[r]) - y;
             sx[r] = s;
-            y = (b0 + b1) - cy[r];
+            y = ay[r] - cy[r];
             s = sy[r] + y;
             cy[r] = (s - sy[r]) - y;
             sy[r] = s;

@@ -80,8 +80,7 @@ struct Tree {
     int *lofs;                // [5 * Bmax] per box: starts of U, V, W, X and the end, in lidx
     int *lidx;                // list entries (each box's lists in one chunk)
     int *pool;                // entries handed out so far (zero at the start of an evaluation)
-    unsigned long long *hkey; // box hash table: keys tagged with the evaluation epoch
-    int *hval;                //   and box indices
+    ulonglong2 *hkv;          // box hash table: {key tagged with the evaluation epoch, box index}
     int hmask;                // table size - 1 (a power of two)
     const unsigned *epoch;    // evaluation counter (1..2^24-1)
     int lcap;                 // capacity of lidx
@@ -164,8 +163,9 @@ __device__ __forceinline__ bool adjacent_xy(int ca, int La, int cb, int Lb) {
 //
 // Keys: epoch (24 bits) << 40 | level << 35 | Morton prefix (32 bits).  A
 // slot holding another epoch's key counts as empty, so the table is never
-// cleared; linear probing; the value array is written by the inserting
-// thread and read only by later kernels.
+// cleared; linear probing.  A slot is {key, value} in 16 bytes, so a probe
+// is one load; the value is written by the inserting thread and read only
+// by later kernels.
 __device__ __forceinline__ unsigned long long hash_key(unsigned epoch, int L, uint32_t prefix) {
     return ((unsigned long long)epoch << 40) | ((unsigned long long)L << 35) | (unsigned long long)prefix;
 }
@@ -177,17 +177,15 @@ __device__ __forceinline__ unsigned hash_slot(unsigned long long k, int mask) {
     return (unsigned)k & (unsigned)mask;
 }
 
-__device__ void hash_insert(const unsigned long long *hk_, int *hv, int mask, unsigned epoch, int L, uint32_t prefix,
-                            int box, int *err) {
-    unsigned long long *hk = const_cast<unsigned long long *>(hk_);
+__device__ void hash_insert(ulonglong2 *hkv, int mask, unsigned epoch, int L, uint32_t prefix, int box, int *err) {
     const unsigned long long k = hash_key(epoch, L, prefix);
     unsigned s = hash_slot(k, mask);
     for (int probe = 0; probe <= mask; ++probe) {
-        unsigned long long cur = hk[s];
+        unsigned long long cur = hkv[s].x;
         while ((cur >> 40) != epoch) {             // empty (stale): try to claim it
-            const unsigned long long prev = atomicCAS(&hk[s], cur, k);
+            const unsigned long long prev = atomicCAS(&hkv[s].x, cur, k);
             if (prev == cur) {
-                hv[s] = box;
+                hkv[s].y = (unsigned long long)(unsigned)box;
                 return;
             }
             cur = prev;
@@ -202,9 +200,9 @@ __device__ __forceinline__ int hash_find(const Tree &T, unsigned epoch, int L, u
     const unsigned long long k = hash_key(epoch, L, prefix);
     unsigned s = hash_slot(k, T.hmask);
     for (int probe = 0; probe <= T.hmask; ++probe) {
-        const unsigned long long cur = __ldcg(&T.hkey[s]);
-        if (cur == k) return __ldcg(&T.hval[s]);
-        if ((cur >> 40) != epoch) return -1;
+        const ulonglong2 cur = __ldcg(&T.hkv[s]);
+        if (cur.x == k) return (int)cur.y;
+        if ((cur.x >> 40) != epoch) return -1;
         s = (s + 1) & (unsigned)T.hmask;
     }
     return -1;
@@ -398,21 +396,29 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
     if (threadIdx.x < NLEV) tcnt[threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// exclusive scan of the (level, tile) counts; level offsets
-__global__ void tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax, int *err) {
-    constexpr int ITEMS = 8;
+// Exclusive scan of the (level, tile) counts (one block of SCAN_THREADS,
+// counts staged in shared memory with coalesced loads, SCAN_ITEMS
+// consecutive counts per thread); level offsets.
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 8;
+
+__global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax,
+                                                                 int *err) {
+    __shared__ int sv[SCAN_THREADS * SCAN_ITEMS];
     __shared__ int wsum[32];
     __shared__ int carry_s;
     const int total = NLEV * ntiles;
-    int carry = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < total; base += blockDim.x * ITEMS) {
-        int v[ITEMS];
+    int carry = 0;
+    for (int base = 0; base < total; base += SCAN_THREADS * SCAN_ITEMS) {
+        const int m = min(SCAN_THREADS * SCAN_ITEMS, total - base);
+        for (int i = threadIdx.x; i < SCAN_THREADS * SCAN_ITEMS; i += SCAN_THREADS) sv[i] = i < m ? tcnt[base + i] : 0;
+        __syncthreads();
+        int v[SCAN_ITEMS];
         int s = 0;
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            const int i = base + threadIdx.x * ITEMS + k;
-            v[k] = i < total ? tcnt[i] : 0;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            v[k] = sv[threadIdx.x * SCAN_ITEMS + k];
             s += v[k];
         }
         int x = s;
@@ -424,7 +430,7 @@ __global__ void tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax, i
         if (lane == 31) wsum[warp] = x;
         __syncthreads();
         if (warp == 0) {
-            const int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            const int w = wsum[lane];
             int t = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -437,12 +443,13 @@ __global__ void tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax, i
         __syncthreads();
         int e = carry + wsum[warp] + x - s;
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            const int i = base + threadIdx.x * ITEMS + k;
-            if (i < total) tcnt[i] = e;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            sv[threadIdx.x * SCAN_ITEMS + k] = e;
             e += v[k];
         }
         carry += carry_s;
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += SCAN_THREADS) tcnt[base + i] = sv[i];
         __syncthreads();
     }
     if (threadIdx.x <= NLEV) {
@@ -456,7 +463,14 @@ __global__ void tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax, i
 // contiguous points [t0 + w * PW, t0 + (w + 1) * PW) in rounds of 32, so a
 // box's rank in its level is the tile's level offset + the counts of the
 // earlier warps (one barrier) + the earlier rounds and lanes of its warp
-// (ballots).
+// (ballots).  With before_L(i) = boxes of level L that start before point
+// i, at point i:
+//   a box of level L starts (c(i) < L <= lambda(i)): index before_L(i);
+//     its parent is the box of level L - 1 holding point i: index
+//     before_{L-1}(i) if that one starts at i too, else before_{L-1}(i) - 1;
+//   the box of level L holding point i - 1 ends (c(i) < L <= lambda(i-1)):
+//     index before_L(i) - 1, end i; every box holding point n - 1 ends at n.
+// Each new box also takes its child slot in the parent.
 __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const int8_t *__restrict__ cl,
                                                                 const int8_t *__restrict__ lam,
                                                                 const int *__restrict__ tcnt, int ntiles, int Bmax) {
@@ -467,7 +481,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t0 = blockIdx.x * TREE_TILE;
     const unsigned lt = (1u << lane) - 1u;
-    int c[R], la[R];
+    int c[R], la[R], lp[R];
     uint32_t k[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -475,6 +489,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
         const bool ok = i < T.n;
         c[r] = ok ? cl[i] : 99;
         la[r] = ok ? lam[i] : -99;
+        lp[r] = ok && i > 0 ? lam[i - 1] : -99;      // leaf level of point i - 1
         k[r] = ok ? T.key[i] : 0u;
     }
     // per-warp totals of every level
@@ -485,9 +500,13 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
         if (lane == 0) wcount[L][warp] = tot;
     }
     __syncthreads();
-    int prev[R];
+    int pb[R];            // before_{L-1}(i), then whether a box of level L - 1 starts at i
+    bool pf[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) prev[r] = -1;
+    for (int r = 0; r < R; ++r) {
+        pb[r] = 0;
+        pf[r] = false;
+    }
     for (int L = 0; L < NLEV; ++L) {
         int base = tcnt[L * ntiles + blockIdx.x];
         for (int w = 0; w < warp; ++w) base += wcount[L][w];
@@ -496,55 +515,41 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
             const int i = t0 + warp * PW + r * 32 + lane;
             const bool f = c[r] < L && L <= la[r];
             const unsigned bl = __ballot_sync(0xffffffffu, f);
-            const int b = base + __popc(bl & lt);
-            if (f && b < Bmax) {
+            const int before = base + __popc(bl & lt);
+            if (f && before < Bmax) {
+                const int b = before;
+                const uint32_t P = prefix_at(k[r], L);
                 T.bstart[b] = i;
                 T.blevel[b] = L;
-                T.bkey[b] = prefix_at(k[r], L);
+                T.bkey[b] = P;
                 T.bleaf[b] = (int8_t)(L == la[r]);
-                T.bmeta[b] = make_int2(pack_xy(prefix_at(k[r], L)), L | ((L == la[r]) ? 256 : 0));
-                T.bparent[b] = (L >= 1 && L - 1 > c[r]) ? prev[r] : -1;
+                T.bmeta[b] = make_int2(pack_xy(P), L | ((L == la[r]) ? 256 : 0));
+                int par = -1;
+                if (L >= 1) {
+                    par = pf[r] ? pb[r] : pb[r] - 1;
+                    if (par >= 0 && par < b) ((int *)&T.bchild[par])[P & 3u] = b;
+                    else atomicOr(T.err, ERR_BOX_OVERFLOW);
+                }
+                T.bparent[b] = par;
             }
-            if (f) prev[r] = b;
+            // the box of level L holding point i - 1 ends at i
+            if (i < T.n && c[r] < L && L <= lp[r] && before >= 1 && before - 1 < Bmax) T.bend[before - 1] = i;
+            // every box holding the last point ends at n
+            if (i == T.n - 1 && L <= la[r] && before + (f ? 0 : -1) >= 0 && before + (f ? 0 : -1) < Bmax)
+                T.bend[before + (f ? 0 : -1)] = T.n;
+            pb[r] = before;
+            pf[r] = f;
             base += __popc(bl);
         }
     }
 }
 
-// box ends, parents found by search, child slots
-__global__ void tree_link_kernel(Tree T) {
+// every box into the hash table
+__global__ void tree_hash_kernel(Tree T) {
     const int B = min(T.levoff[NLEV], T.Bmax);
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-        const int L = T.blevel[b], s = T.bstart[b];
-        int end = T.n;
-        if (L > 0) {
-            const uint32_t P = T.bkey[b];
-            const int sh = 32 - 2 * L;
-            int lo = s + 1, hi = T.n;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if ((T.key[mid] >> sh) > P) hi = mid;
-                else lo = mid + 1;
-            }
-            end = lo;
-            int p = T.bparent[b];
-            if (p < 0) {
-                // last box of level L-1 starting at or before s
-                int a = T.levoff[L - 1], z = T.levoff[L];
-                while (a < z) {
-                    int mid = (a + z) >> 1;
-                    if (T.bstart[mid] <= s) a = mid + 1;
-                    else z = mid;
-                }
-                p = a - 1;
-                T.bparent[b] = p;
-            }
-            if (p >= 0 && p < b) ((int *)&T.bchild[p])[P & 3u] = b;
-            else atomicOr(T.err, ERR_BOX_OVERFLOW);
-        }
-        T.bend[b] = end;
-        hash_insert(T.hkey, T.hval, T.hmask, *T.epoch, L, T.bkey[b], b, T.err);
-    }
+    const unsigned epoch = *T.epoch;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+        hash_insert(T.hkv, T.hmask, epoch, T.blevel[b], T.bkey[b], b, T.err);
 }
 
 // ---------------------------------------------------------------- neighbour tables and lists
@@ -1145,22 +1150,21 @@ __device__ __forceinline__ int stage_chunk(const Tree &T, float4 *buf, int &ui, 
 }
 
 // Pairs of the targets tb + t + r * lps (r < R) with every S-th staged
-// source pair (2j, 2j + 1) from h; R targets per lane amortise each
-// shared-memory load, and each packed instruction covers two sources.
+// source from h; R targets per lane amortise each shared-memory load.
 template <int R>
 __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*buf)[NEAR_SRC], int tb, int ntc,
                                           int lps, int S, int us, int ue, int lane) {
     const int t = lane % lps, h = lane / lps;
-    f2x zx[R], zy[R], fx[R], fy[R];
+    float zx[R], zy[R], fx[R], fy[R];
     int zi[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t + r * lps;
         const float4 z = i < ntc ? T.pts[tb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        zx[r] = pk2(z.x, z.x);
-        zy[r] = pk2(z.y, z.y);
+        zx[r] = z.x;
+        zy[r] = z.y;
         zi[r] = __float_as_int(z.w);
-        fx[r] = fy[r] = 0ull;
+        fx[r] = fy[r] = 0.f;
     }
     int ui = us, off = 0, cur = 0;
     int cnt = stage_chunk(T, buf[0], ui, off, ue, lane);
@@ -1168,25 +1172,21 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
         // next chunk in flight while this one is summed
         const int nxt = ui < ue ? stage_chunk(T, buf[cur ^ 1], ui, off, ue, lane) : (cp_async_commit(), 0);
         cp_async_wait_one();
-        float4 *src = buf[cur];
-        // an odd chunk is padded with a massless source
-        if ((cnt & 1) && lane == 0) src[cnt] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
-        const int np = (cnt + 1) >> 1;
+        const float4 *src = buf[cur];
         if (S == 1) {
-#pragma unroll 2
-            for (int j = 0; j < np; ++j) {
-                const float4 q0 = src[2 * j], q1 = src[2 * j + 1];
-                const f2x qx = pk2(q0.x, q1.x), qy = pk2(q0.y, q1.y), qm = pk2(q0.z, q1.z);
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q = src[j];
 #pragma unroll
-                for (int r = 0; r < R; ++r) p2p_pair2(zx[r], zy[r], qx, qy, qm, fx[r], fy[r]);
+                for (int r = 0; r < R; ++r) p2p_pair(zx[r], zy[r], q, fx[r], fy[r]);
             }
         } else {
-            for (int j = h; j < np; j += S) {
-                const float4 q0 = src[2 * j], q1 = src[2 * j + 1];
-                const f2x qx = pk2(q0.x, q1.x), qy = pk2(q0.y, q1.y), qm = pk2(q0.z, q1.z);
+#pragma unroll 2
+            for (int j = h; j < cnt; j += S) {
+                const float4 q = src[j];
 #pragma unroll
-                for (int r = 0; r < R; ++r) p2p_pair2(zx[r], zy[r], qx, qy, qm, fx[r], fy[r]);
+                for (int r = 0; r < R; ++r) p2p_pair(zx[r], zy[r], q, fx[r], fy[r]);
             }
         }
         __syncwarp();
@@ -1195,10 +1195,7 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        float ax, bx, ay, by;
-        upk2(fx[r], ax, bx);
-        upk2(fy[r], ay, by);
-        float sx = ax + bx, sy = ay + by;
+        float sx = fx[r], sy = fy[r];
         for (int o = lps; o < 32; o <<= 1) {
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
@@ -1208,7 +1205,7 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
     }
 }
 
-__global__ void __launch_bounds__(NEAR_WARPS * 32, 5) near_kernel(LeafArgs la) {
+__global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
     const Tree &T = la.e.T;
     __shared__ __align__(16) float4 stage[NEAR_WARPS][2][NEAR_SRC];
     const int lane = threadIdx.x & 31;
@@ -1227,7 +1224,7 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32, 5) near_kernel(LeafArgs la) {
             // fewest padded target slots: R targets on lps = 32 / S lanes
             int R = 2, S = 1, best = 64;
             for (int s2 = 1; s2 <= 32; s2 <<= 1) {
-                for (int r2 = 3; r2 >= 1; --r2) {
+                for (int r2 = 6; r2 >= 1; --r2) {
                     const int slots = r2 * (32 / s2);
                     if (slots >= ntc && slots < best) {
                         best = slots;
@@ -1237,7 +1234,10 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32, 5) near_kernel(LeafArgs la) {
                 }
             }
             const int lps = 32 / S;
-            if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            if (R == 6) near_tile<6>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else            if (R == 5) near_tile<5>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else            if (R == 4) near_tile<4>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else            if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else if (R == 2) near_tile<2>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else near_tile<1>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
         }
@@ -1255,16 +1255,20 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32, 5) near_kernel(LeafArgs la) {
 // expansion and M2P over W, added to the near sum; F_rep = kr m_i
 // (near + conj(E_far)).
 constexpr int FAR_WARPS = 4;
+constexpr int FAR_W = 16;        // W entries staged in shared memory (longer lists read global memory)
 
 template <int PT>
-__global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
-    __shared__ float sbin[BN * BN];
+__global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
+    __shared__ float sbin[(PT + 1) * (PT + 1)];   // C(l, m), l, m <= PT
     __shared__ float2 loc[FAR_WARPS][PT + 1];
     __shared__ float2 ancl[FAR_WARPS][MAXLEV - 1][PT + 1];
     __shared__ float2 part_[FAR_WARPS][MAXLEV - 1][PT + 1];
     __shared__ int s_anc[FAR_WARPS][MAXLEV - 1];
     __shared__ float2 s_t[FAR_WARPS][MAXLEV - 1];
-    for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = la.e.binom[i];
+    __shared__ float4 s_wg[FAR_WARPS][FAR_W];             // W box centre and half-width
+    __shared__ float2 s_wm[FAR_WARPS][FAR_W][PT + 1];     // W box outgoing expansion
+    for (int i = threadIdx.x; i < (PT + 1) * (PT + 1); i += blockDim.x)
+        sbin[i] = la.e.binom[(i / (PT + 1)) * BN + i % (PT + 1)];
     __syncthreads();
     const Tree &T = la.e.T;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1279,6 +1283,17 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
         if (!meta_leaf(mb)) continue;
         const int Lb = mb.y & 255;
         const uint32_t kb = T.bkey[b];
+        const int s = T.bstart[b], e = T.bend[b];
+        const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
+        const int nW = we - ws;
+        const bool wst = nW <= FAR_W;
+        // a short W list: its boxes' geometry and expansions in shared memory
+        if (wst && lane < nW) {
+            const int Dx = T.lidx[ws + lane];
+            const int2 md_ = T.bmeta[Dx];
+            const BoxGeo gd = box_geo_xy(rt, md_.x, md_.y & 255);
+            s_wg[wib][lane] = make_float4(gd.cx, gd.cy, gd.r, __int_as_float(Dx));
+        }
         // ancestors of levels >= 2 (lane j: level Lb - j, key kb >> 2j), found by
         // independent hash lookups, and the shift t_j = (c_leaf - c_A) / r_A
         const int nA = Lb >= 2 ? Lb - 1 : 0;
@@ -1298,6 +1313,13 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
             const int A = s_anc[wib][j];
             ancl[wib][j][l] = A >= 0 && l <= p ? la.e.Lc[(size_t)A * (PT + 1) + l] : make_float2(0.f, 0.f);
         }
+        if (wst) {
+            for (int it = lane; it < nW * (PT + 1); it += 32) {
+                const int i = it / (PT + 1), k = it - i * (PT + 1);
+                const int Dx = __float_as_int(s_wg[wib][i].w);
+                s_wm[wib][i][k] = k <= p ? la.e.M[(size_t)Dx * (PT + 1) + k] : make_float2(0.f, 0.f);
+            }
+        }
         __syncwarp();
         // incoming expansion of the leaf: items (ancestor j, coefficient m)
         // spread over all lanes, each a Horner sum in t_j, then each
@@ -1308,7 +1330,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
             float2 sres = make_float2(0.f, 0.f);
             if (m <= p) {
                 const float2 t = s_t[wib][j];
-                for (int l = p; l >= m; --l) sres = cadd(cmul(sres, t), cscale(ancl[wib][j][l], sbin[l * BN + m]));
+                for (int l = p; l >= m; --l) sres = cadd(cmul(sres, t), cscale(ancl[wib][j][l], sbin[l * (PT + 1) + m]));
             }
             part_[wib][j][m] = make_float2(ldexpf(sres.x, -j * m), ldexpf(sres.y, -j * m));
         }
@@ -1320,8 +1342,6 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
         __syncwarp();
         const BoxGeo g = box_geo_xy(rt, mb.x, Lb);
         const float ir = 1.0f / g.r;
-        const int s = T.bstart[b], e = T.bend[b];
-        const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
         for (int tt = s + lane; tt < e; tt += 32) {
             const float4 z = T.pts[tt];
             float2 E;
@@ -1336,7 +1356,23 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) far_kernel(LeafArgs la) {
                 E = cscale(hs, ir);
             }
             // M2P: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
-            for (int k = ws; k < we; ++k) {
+            if (wst) {
+                for (int i = 0; i < nW; ++i) {
+                    const float4 gd = s_wg[wib][i];
+                    const float2 dz = make_float2(z.x - gd.x, z.y - gd.y);
+                    const float id2 = rcp_approx(fmaf(dz.x, dz.x, dz.y * dz.y));
+                    const float2 idz = make_float2(dz.x * id2, -dz.y * id2);
+                    const float2 tt2 = cscale(idz, gd.z);
+                    float2 hs = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int kk = PT; kk >= 1; --kk) {
+                        if (kk <= p) hs = cadd(cmul(hs, tt2), cscale(s_wm[wib][i][kk], (float)kk));
+                    }
+                    hs = cmul(hs, tt2);
+                    const float2 a0 = s_wm[wib][i][0];
+                    E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
+                }
+            } else for (int k = ws; k < we; ++k) {
                 const int Dx = T.lidx[k];
                 const int2 md_ = T.bmeta[Dx];
                 const BoxGeo gd = box_geo_xy(rt, md_.x, md_.y & 255);
@@ -1386,8 +1422,7 @@ struct FmmPlan {
     DevBuf<int2> bmeta;
     DevBuf<float2> M, Lc;
     DevBuf<int> arrive, tickets, err;
-    DevBuf<unsigned long long> hkey;
-    DevBuf<int> hval;
+    DevBuf<ulonglong2> hkv;
     DevBuf<unsigned> epoch;
     int hmask = 0;
     DevBuf<float> binom;
@@ -1452,10 +1487,9 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         int64_t hs = 1;
         while (hs < 2 * bmax) hs <<= 1;
         pl->hmask = (int)(hs - 1);
-        pl->hkey.reset(A, hs);
-        pl->hval.reset(A, hs);
+        pl->hkv.reset(A, hs);
         pl->epoch.reset(A, 1);
-        BGL_CUDA(cudaMemsetAsync(pl->hkey.p, 0, sizeof(unsigned long long) * hs, s));
+        BGL_CUDA(cudaMemsetAsync(pl->hkv.p, 0, sizeof(ulonglong2) * hs, s));
         BGL_CUDA(cudaMemsetAsync(pl->epoch.p, 0, sizeof(unsigned), s));
         pl->tickets.reset(A, 8);
         pl->err.reset(A, 1);
@@ -1503,8 +1537,7 @@ static Tree make_tree(FmmPlan *pl) {
     T.lofs = pl->lofs.p;
     T.lidx = pl->lidx.p;
     T.pool = pl->tickets.p + 3;
-    T.hkey = pl->hkey.p;
-    T.hval = pl->hval.p;
+    T.hkv = pl->hkv.p;
     T.hmask = pl->hmask;
     T.epoch = pl->epoch.p;
     T.lcap = pl->lcap;
@@ -1564,15 +1597,15 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
 
 // tree: boxes in level order, ends, parents, children
 static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
+    BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * pl->Bmax, s));
     tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, pl->n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
                                                           pl->ntiles);
     BGL_LAUNCH_CHECK();
-    tree_scan_kernel<<<1, 1024, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p);
+    tree_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p);
     BGL_LAUNCH_CHECK();
-    BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * pl->Bmax, s));
     tree_emit_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(T, pl->cl.p, pl->lam.p, pl->tcnt.p, pl->ntiles, pl->Bmax);
     BGL_LAUNCH_CHECK();
-    tree_link_kernel<<<pl->grid_p, 256, 0, s>>>(T);
+    tree_hash_kernel<<<pl->grid_p / 4, 256, 0, s>>>(T);
     BGL_LAUNCH_CHECK();
 }
 
