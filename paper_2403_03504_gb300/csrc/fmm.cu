@@ -1102,8 +1102,10 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
 
 struct LeafArgs {
     ExpArgs e;
-    float2 *f;           // f[q - fbase]
+    float2 *f;           // f[q - fbase]: near-field sums, then the final forces
     const float2 *fa;    // fa[q - fbase] added to the final force, or null
+    float2 *ef;          // far field E(z) of every sorted point
+    int *leafdone;       // per box: how many of the near and far kernels finished it (0 between evaluations)
     int64_t q0, fbase;
     float kr;
     int *ticket;
@@ -1205,6 +1207,31 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
     }
 }
 
+// The near and far fields of a leaf are computed by two kernels that may
+// run at the same time; each marks the leaf when its part is in memory, and
+// the second to finish writes the force of every target of the leaf:
+//   F_rep(i) = kr m_i (near(i) + conj(E(z_i))) (+ fa(i))
+__device__ __noinline__ void leaf_finish(const LeafArgs &la, int b, int s, int e, int lane) {
+    __threadfence();
+    __syncwarp();
+    int old = 0;
+    if (lane == 0) old = atomicAdd(&la.leafdone[b], 1);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != 1) return;
+    __threadfence();
+    for (int tt = s + lane; tt < e; tt += 32) {
+        const float4 z = la.e.T.pts[tt];
+        const int o = __float_as_int(z.w);
+        const int64_t q = la.q0 + o - la.fbase;
+        const float2 nr = __ldcg(&la.f[q]);
+        const float2 E = __ldcg(&la.ef[tt]);
+        const float km = la.kr * z.z;
+        const float2 a = la.fa ? la.fa[q] : make_float2(0.f, 0.f);
+        la.f[q] = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
+    }
+    if (lane == 0) la.leafdone[b] = 0;
+}
+
 __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
     const Tree &T = la.e.T;
     __shared__ __align__(16) float4 stage[NEAR_WARPS][2][NEAR_SRC];
@@ -1241,6 +1268,7 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
             else if (R == 2) near_tile<2>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else near_tile<1>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
         }
+        leaf_finish(la, b, s, e, lane);
     }
 }
 
@@ -1390,14 +1418,9 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                 const float2 a0 = md[0];
                 E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
             }
-            const int o = __float_as_int(z.w);
-            float2 *fo = la.f + (la.q0 + o - la.fbase);
-            const float2 nr = *fo;
-            const float km = la.kr * z.z;
-            const float2 a = la.fa ? la.fa[la.q0 + o - la.fbase] : make_float2(0.f, 0.f);
-            *fo = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
+            la.ef[tt] = E;
         }
-        __syncwarp();
+        leaf_finish(la, b, s, e, lane);
     }
 }
 
@@ -1421,7 +1444,8 @@ struct FmmPlan {
     DevBuf<int4> bchild;
     DevBuf<int2> bmeta;
     DevBuf<float2> M, Lc;
-    DevBuf<int> arrive, tickets, err;
+    DevBuf<int> arrive, tickets, err, leafdone;
+    DevBuf<float2> ef;
     DevBuf<ulonglong2> hkv;
     DevBuf<unsigned> epoch;
     int hmask = 0;
@@ -1484,6 +1508,8 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->M.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->Lc.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->arrive.reset(A, bmax);
+        pl->leafdone.reset(A, bmax);
+        pl->ef.reset(A, n);
         int64_t hs = 1;
         while (hs < 2 * bmax) hs <<= 1;
         pl->hmask = (int)(hs - 1);
@@ -1496,6 +1522,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->sortws.reserve(A, n, s);
         BGL_CUDA(cudaMemsetAsync(pl->counter.p, 0, sizeof(unsigned), s));
         BGL_CUDA(cudaMemsetAsync(pl->arrive.p, 0, sizeof(int) * bmax, s));
+        BGL_CUDA(cudaMemsetAsync(pl->leafdone.p, 0, sizeof(int) * bmax, s));
         BGL_CUDA(cudaMemsetAsync(pl->err.p, 0, sizeof(int), s));
         std::vector<float> bn(BN * BN, 0.f);
         for (int i = 0; i < BN; ++i) {
@@ -1569,6 +1596,8 @@ static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbas
     la.fbase = fbase;
     la.kr = pl->kr;
     la.ticket = pl->tickets.p + 2;
+    la.ef = pl->ef.p;
+    la.leafdone = pl->leafdone.p;
     return la;
 }
 
@@ -1635,10 +1664,12 @@ static void launch_far(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
     BGL_LAUNCH_CHECK();
 }
 
-// Whole evaluation.  With `concurrent`, the upward and downward passes run
-// on the plan's side stream while the near field runs on the main stream:
-//   main: points, tree --+-- lists ----+-- near ------------+-- far --
-//   side:                +-- up -------+-- (lists) down ----+
+// Whole evaluation.  With `concurrent`, the upward and downward passes and
+// the far field run on the plan's side stream while the near field runs on
+// the main stream; whichever of near and far finishes a leaf last writes
+// its forces:
+//   main: points, tree --+-- lists ----+-- near ---------------------+--
+//   side:                +-- up -------+-- (lists) down -- far ------+
 // ev (timing events, 7, may be null) forces one stream and marks the phases.
 template <int PT>
 static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev,
@@ -1659,9 +1690,9 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
         if (ev) BGL_CUDA(cudaEventRecord(ev[4], s));
         launch_down<PT>(pl, a, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[5], s));
+        if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
         launch_near(pl, la, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[6], s));
-        if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
         launch_far<PT>(pl, la, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[7], s));
         return;
@@ -1672,13 +1703,14 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
     launch_up<PT>(pl, a, t);
     phase_lists(pl, T, s);
     BGL_CUDA(cudaEventRecord(pl->ev[1], s));           // lists built
+    if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
     launch_near(pl, la, s);
     BGL_CUDA(cudaStreamWaitEvent(t, pl->ev[1], 0));
     launch_down<PT>(pl, a, t);
-    BGL_CUDA(cudaEventRecord(pl->ev[2], t));           // local expansions ready
+    if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(t, fa_ready, 0));
+    launch_far<PT>(pl, la, t);
+    BGL_CUDA(cudaEventRecord(pl->ev[2], t));           // far field done
     BGL_CUDA(cudaStreamWaitEvent(s, pl->ev[2], 0));
-    if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
-    launch_far<PT>(pl, la, s);
 }
 
 static void evaluate_any(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev,

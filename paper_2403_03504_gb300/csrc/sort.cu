@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(OS_THREADS) os_hist_kernel(const uint32_t *__r
     os_block_hist<OS_ITEMS>(k, valid, h);
 }
 
-__global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *__restrict__ kin,
+__global__ void __launch_bounds__(OS_THREADS, 2) os_scatter_kernel(const uint32_t *__restrict__ kin,
                                                                  const uint32_t *__restrict__ vin,
                                                                  uint32_t *__restrict__ kout,
                                                                  uint32_t *__restrict__ vout, int64_t n, int shift,
@@ -317,12 +317,18 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
     const int64_t wbase = t0 + (int64_t)warp * 32 * OS_ITEMS;
     uint32_t key[OS_ITEMS], val[OS_ITEMS];
     int32_t rank[OS_ITEMS];
+    // all loads in flight before the ranking (whose warp barriers would
+    // otherwise order them one after another)
+#pragma unroll
+    for (int r = 0; r < OS_ITEMS; ++r) {
+        const int64_t k = wbase + r * 32 + lane;
+        key[r] = k < n ? kin[k] : 0u;
+        val[r] = k < n ? vin[k] : 0u;
+    }
 #pragma unroll
     for (int r = 0; r < OS_ITEMS; ++r) {
         const int64_t k = wbase + r * 32 + lane;
         const bool ok = k < n;
-        key[r] = ok ? kin[k] : 0u;
-        val[r] = ok ? vin[k] : 0u;
         const unsigned d = ok ? ((key[r] >> shift) & 0xFF) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int before = __popc(peers & lt);
@@ -403,17 +409,38 @@ __global__ void __launch_bounds__(OS_THREADS) os_scatter_kernel(const uint32_t *
         sval[lp] = val[r];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < tcount; i += OS_THREADS) {
-        const uint32_t k = skey[i];
-        const unsigned d = (k >> shift) & 0xFF;
-        const uint32_t dst = gofs[d] + (uint32_t)(i - lstart[d]);
-        kout[dst] = k;
-        const uint32_t v = sval[i];
-        if (gpts) {   // last pass with a gather: the sorted record {x, y, m, index}
-            const float2 p = gxy[v];
-            gpts[dst] = make_float4(p.x, p.y, gmass[v], __int_as_float((int)v));
-        } else {
-            vout[dst] = v;
+    uint32_t dst[OS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < OS_ITEMS; ++r) {
+        const int i = r * OS_THREADS + threadIdx.x;
+        key[r] = i < tcount ? skey[i] : 0u;
+        val[r] = i < tcount ? sval[i] : 0u;
+        const unsigned d = (key[r] >> shift) & 0xFF;
+        dst[r] = gofs[d] + (uint32_t)(i - lstart[d]);
+    }
+    if (gpts) {
+        // last pass with a gather: the sorted record {x, y, m, index}, all
+        // gather loads issued before the stores
+        float2 p[OS_ITEMS];
+        float m[OS_ITEMS];
+#pragma unroll
+        for (int r = 0; r < OS_ITEMS; ++r) {
+            const bool ok = r * OS_THREADS + (int)threadIdx.x < tcount;
+            p[r] = ok ? gxy[val[r]] : make_float2(0.f, 0.f);
+            m[r] = ok ? gmass[val[r]] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < OS_ITEMS; ++r) {
+            if (r * OS_THREADS + (int)threadIdx.x >= tcount) continue;
+            kout[dst[r]] = key[r];
+            gpts[dst[r]] = make_float4(p[r].x, p[r].y, m[r], __int_as_float((int)val[r]));
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < OS_ITEMS; ++r) {
+            if (r * OS_THREADS + (int)threadIdx.x >= tcount) continue;
+            kout[dst[r]] = key[r];
+            vout[dst[r]] = val[r];
         }
     }
 }
