@@ -42,11 +42,17 @@ METRIC = "FA2 node-updates/s (FMM vs exact) at stated force error; layout p50/p9
 UNIT = "node-updates/s"
 CONFIG_NAME = "fmm-fa2-200k-tx"
 
-# P2P pair throughput peak: 152 SMs x 2070 MHz x 16 pairs/clk/SM (one MUFU
-# reciprocal per pair; 16 MUFU results per clock per SM; 7 FP32-pipe ops per
-# pair need 7/128 clk, so the MUFU is the binding unit)
-SMS, SM_MAX_MHZ, MUFU_PER_CLK = 152, 2070.0, 16.0
-PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * MUFU_PER_CLK
+# P2P pair throughput peak: a pair issues 8 instructions (7 FP32-pipe ops and
+# one MUFU reciprocal); an SM issues 4 warp instructions (128 lanes) per
+# clock, so 16 pairs/clk/SM.  The FP32 pipe alone would allow 128 / 7 = 18.3
+# and the MUFU reciprocal was measured at >= 15/clk/SM (a lower bound, from
+# dependent chains), so issue is the binding limit.
+SMS, SM_MAX_MHZ, PAIRS_PER_CLK = 152, 2070.0, 16.0
+PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * PAIRS_PER_CLK
+# DRAM bytes (read + write) of one near_kernel launch on this workload's
+# giant component, from the ncu capture summarised in
+# profiles/near_kernel_fmm_c2_giant.md (the working set is L2-resident)
+NEAR_TRAFFIC_BYTES = 12_450_560 + 256
 
 
 def env_rank():
@@ -190,6 +196,9 @@ def main():
     ap.add_argument("--exact-iters", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--timed-only", action="store_true",
+                    help="profiling case: warm-up and timed steps only (no end-to-end leg, no diagnostics); "
+                         "prints the device-resident step times")
     ap.add_argument("--kernels-only", action="store_true",
                     help="profiling case: FMM and exact repulsion on the giant component only")
     args = ap.parse_args()
@@ -263,7 +272,7 @@ def main():
         g.layout(p, out=h_xy.numpy())
         g.destroy()
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(args.warmup if args.timed_only else max(args.warmup, 3)):
         step_dev()
     ctx.sync()
 
@@ -286,6 +295,13 @@ def main():
         dist.barrier()
     launches = (bgl.launch_count() - launches0) // max(args.steps, 1)
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    if args.timed_only:
+        if rank == 0:
+            print(json.dumps({"timed_only": True, "step_ms": step_ms, "gpu_launches": int(launches)}), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     total_s = sum(step_ms) / 1e3
     upd = float(fa2_nodes) * args.iters * args.steps
     if dist:
@@ -358,8 +374,10 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "fmm near field (P2P, near_kernel)", "achieved": achieved / 1e9,
-                     "peak": PAIR_PEAK / 1e9, "unit": "Gpairs/s", "frac": achieved / PAIR_PEAK, "traffic": None,
-                     "peak_source": "152 SMs x 2070 MHz x 16 MUFU rcp/clk/SM (one rcp per pair)"},
+                     "peak": PAIR_PEAK / 1e9, "unit": "Gpairs/s", "frac": achieved / PAIR_PEAK,
+                     "traffic": NEAR_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "peak_source": "derived: 152 SMs x 2070 MHz x 128 issue lanes/clk / 8 instructions per pair "
+                                    "= 16 pairs/clk/SM (FP32 pipe 18.3, MUFU rcp >= 15 measured)"},
         "force_error": {"reference": "GPU FP32 exact sum at the final layout", **errs},
         "exact_fa2": {"value": exact_rate, "unit": UNIT, "iters": args.exact_iters, "nodes": giant},
         "fmm_p16_step_ms": 1e3 * p16_s,

@@ -226,9 +226,53 @@ bgl_status bgl_fa2_repulsion(bgl_graph *g, int64_t c, const bgl_params *p, const
 bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t iters, float *xy_inout,
                         double *stats_out);
 
+/* ------------------------------------------ resumable runs and checkpoints */
+
+/*
+ * A ForceAtlas2 run (Section 3.2) that lives on the graph between calls, so
+ * that a long layout can be advanced in pieces, inspected, checkpointed and
+ * resumed.  The graph holds at most one session; components must have been
+ * computed (bgl_components), and recomputing them ends the session.
+ *
+ * bgl_fa2_session_begin: starts a session on component c from the caller's
+ *   local positions xy_in[2 n_c] (x, y interleaved), with F_{-1} = 0,
+ *   s_G = 1 and a private copy of *p; replaces any earlier session.
+ * bgl_fa2_session_advance: runs `iters` more iterations; stats_out (3 * iters
+ *   doubles, may be NULL) receives swing, traction and s_G of each.  Advancing
+ *   by a then b iterations gives bitwise the positions of a + b iterations
+ *   in one call, and those of bgl_fa2_step with a + b iterations.
+ * bgl_fa2_session_positions: copies the current local positions to
+ *   xy_out[2 n_c]; iters_done (may be NULL) receives the iterations run.
+ * No session: BGL_ESTATE.  All three synchronise the context's stream.
+ */
+bgl_status bgl_fa2_session_begin(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in);
+bgl_status bgl_fa2_session_advance(bgl_graph *g, int32_t iters, double *stats_out);
+bgl_status bgl_fa2_session_positions(bgl_graph *g, float *xy_out, int64_t *iters_done);
+
+/*
+ * Checkpoint of the graph's session: everything the iteration needs to
+ * continue -- positions, F_{t-1}, s_G, the iteration count, the parameters
+ * and the FMM's choice of radix passes for its next sort -- in a host
+ * buffer owned by the caller, plus the identity of
+ * the component (graph sizes, component index and size, and a 64-bit hash of
+ * its node ids and adjacency).
+ * bgl_state_save: with buf = NULL stores the size needed in *len; otherwise
+ *   *len must be at least that size, the state is written to buf and *len
+ *   set to the bytes written.  No session: BGL_ESTATE.
+ * bgl_state_load: replaces the graph's session by the checkpoint in
+ *   buf[len].  The graph must be the one the checkpoint came from (rebuilt
+ *   from the same input and with components computed): anything else, a
+ *   short buffer or a foreign format returns BGL_EINVAL and leaves the
+ *   session unchanged.  Advancing a loaded session continues bitwise as the
+ *   saved one would have.
+ * The format is host-endian and tied to this library version.
+ */
+bgl_status bgl_state_save(bgl_graph *g, void *buf, size_t *len);
+bgl_status bgl_state_load(bgl_graph *g, const void *buf, size_t len);
+
 /* ---------------------------------------------------------------- profiling */
 
-#define BGL_FMM_NSTATS 15
+#define BGL_FMM_NSTATS 17
 
 /*
  * Profiling aid for the Fast Multipole repulsion (Section 3.2.1) on
@@ -244,7 +288,12 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
  *   downward pass (M2L, P2L, L2L), near field (P2P), far field (L2P, M2P);
  *   14 mean milliseconds of a whole evaluation in the schedule used inside
  *   ForceAtlas2 iterations (upward and downward passes overlapping the near
- *   field on a second stream).
+ *   field on a second stream);
+ *   15 largest |F_last - F_first| / largest |F_first| between the first
+ *   evaluation (radix sort over all 32 key bits) and the last one, whose sort
+ *   skips the two low passes when the previous tree was at most 8 levels
+ *   deep (then the trees are the same and only the order of points inside
+ *   a leaf differs); 16 the passes skipped by the last evaluation (0 or 2).
  * Synchronises the stream.
  */
 bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, int32_t reps,

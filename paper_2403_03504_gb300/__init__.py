@@ -103,6 +103,11 @@ def _load():
         "bgl_fa2_forces": ([VP, I64, ctypes.POINTER(Params), VP, VP], I32),
         "bgl_fa2_repulsion": ([VP, I64, ctypes.POINTER(Params), VP, VP], I32),
         "bgl_fa2_step": ([VP, I64, ctypes.POINTER(Params), I32, VP, VP], I32),
+        "bgl_fa2_session_begin": ([VP, I64, ctypes.POINTER(Params), VP], I32),
+        "bgl_fa2_session_advance": ([VP, I32, VP], I32),
+        "bgl_fa2_session_positions": ([VP, VP, P64], I32),
+        "bgl_state_save": ([VP, VP, ctypes.POINTER(ctypes.c_size_t)], I32),
+        "bgl_state_load": ([VP, VP, ctypes.c_size_t], I32),
         "bgl_fmm_stats": ([VP, I64, ctypes.POINTER(Params), VP, I32, VP], I32),
         "bgl_launch_count": ([], I64),
         "bgl_fa2_iteration_noalloc": ([VP, I64, VP, VP, VP, VP, VP, VP, VP, ctypes.POINTER(Params)], I32),
@@ -116,7 +121,7 @@ def _load():
 
 
 FMM_STATS = ("boxes", "leaves", "depth", "p2p_pairs", "m2l", "m2p", "p2l", "ms_points", "ms_tree", "ms_lists",
-             "ms_up", "ms_down", "ms_near", "ms_far", "ms_total")
+             "ms_up", "ms_down", "ms_near", "ms_far", "ms_total", "sortmode_rel_diff", "sort_skip")
 
 
 def launch_count() -> int:
@@ -354,3 +359,31 @@ class Graph:
         stats = np.zeros((max(iters, 1), 3))
         self.ctx.check(self._lib.bgl_fa2_step(self.h, c, ctypes.byref(p), iters, _hp(xy), _hp(stats)))
         return xy, stats[:iters]
+
+    # resumable ForceAtlas2 run and its checkpoint
+    def session_begin(self, c: int, p: Params, xy) -> None:
+        xy = _arr(xy, np.float32)
+        self._session_n = len(xy)
+        self.ctx.check(self._lib.bgl_fa2_session_begin(self.h, c, ctypes.byref(p), _hp(xy)))
+
+    def session_advance(self, iters: int):
+        stats = np.zeros((max(iters, 1), 3))
+        self.ctx.check(self._lib.bgl_fa2_session_advance(self.h, iters, _hp(stats)))
+        return stats[:iters]
+
+    def session_positions(self, n: int):
+        xy = np.zeros((n, 2), np.float32)
+        done = ctypes.c_int64(0)
+        self.ctx.check(self._lib.bgl_fa2_session_positions(self.h, _hp(xy), ctypes.byref(done)))
+        return xy, int(done.value)
+
+    def state_save(self) -> bytes:
+        need = ctypes.c_size_t(0)
+        self.ctx.check(self._lib.bgl_state_save(self.h, None, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        self.ctx.check(self._lib.bgl_state_save(self.h, buf, ctypes.byref(need)))
+        return buf.raw[:need.value]
+
+    def state_load(self, data: bytes) -> None:
+        buf = ctypes.create_string_buffer(data, len(data))
+        self.ctx.check(self._lib.bgl_state_load(self.h, buf, len(data)))

@@ -79,6 +79,22 @@ void Allocator::free(void *p) {
     live_.erase(it);
 }
 
+void check_params(const bgl_params *p) {
+    BGL_REQUIRE(p != nullptr, "params is NULL");
+    BGL_REQUIRE(p->kk_max_nodes >= 0 && p->kk_max_nodes <= 255, "kk_max_nodes must be in [0, 255]");
+    BGL_REQUIRE(p->fa2_iters >= 0, "fa2_iters must be >= 0");
+    BGL_REQUIRE(p->kr >= 0 && p->kg >= 0, "kr and kg must be >= 0");
+    BGL_REQUIRE(p->ks > 0 && p->ksmax > 0 && p->tau > 0, "ks, ksmax and tau must be > 0");
+    BGL_REQUIRE(p->repulsion >= BGL_REP_EXACT && p->repulsion <= BGL_REP_AUTO, "repulsion must be 0, 1 or 2");
+    BGL_REQUIRE(p->fmm_p >= 1 && p->fmm_p <= 24, "fmm_p must be in [1, 24]");
+    BGL_REQUIRE(p->leaf_size >= 1 && p->leaf_size <= 256, "leaf_size must be in [1, 256]");
+    BGL_REQUIRE(p->fmm_min_nodes >= 0, "fmm_min_nodes must be >= 0");
+    BGL_REQUIRE(p->swing_variant == 0 || p->swing_variant == 1, "swing_variant must be 0 or 1");
+    BGL_REQUIRE(p->kk_sweeps >= 0, "kk_sweeps must be >= 0");
+    BGL_REQUIRE(p->kk_l > 0, "kk_l must be > 0");
+    BGL_REQUIRE(p->kk_tol >= 0, "kk_tol must be >= 0");
+}
+
 }  // namespace bgl
 
 using namespace bgl;
@@ -105,22 +121,6 @@ bgl_status guarded(bgl_ctx *c, F &&fn) {
         if (c) c->last_error = "unknown failure";
         return BGL_ECUDA;
     }
-}
-
-void check_params(const bgl_params *p) {
-    BGL_REQUIRE(p != nullptr, "params is NULL");
-    BGL_REQUIRE(p->kk_max_nodes >= 0 && p->kk_max_nodes <= 255, "kk_max_nodes must be in [0, 255]");
-    BGL_REQUIRE(p->fa2_iters >= 0, "fa2_iters must be >= 0");
-    BGL_REQUIRE(p->kr >= 0 && p->kg >= 0, "kr and kg must be >= 0");
-    BGL_REQUIRE(p->ks > 0 && p->ksmax > 0 && p->tau > 0, "ks, ksmax and tau must be > 0");
-    BGL_REQUIRE(p->repulsion >= BGL_REP_EXACT && p->repulsion <= BGL_REP_AUTO, "repulsion must be 0, 1 or 2");
-    BGL_REQUIRE(p->fmm_p >= 1 && p->fmm_p <= 24, "fmm_p must be in [1, 24]");
-    BGL_REQUIRE(p->leaf_size >= 1 && p->leaf_size <= 256, "leaf_size must be in [1, 256]");
-    BGL_REQUIRE(p->fmm_min_nodes >= 0, "fmm_min_nodes must be >= 0");
-    BGL_REQUIRE(p->swing_variant == 0 || p->swing_variant == 1, "swing_variant must be 0 or 1");
-    BGL_REQUIRE(p->kk_sweeps >= 0, "kk_sweeps must be >= 0");
-    BGL_REQUIRE(p->kk_l > 0, "kk_l must be > 0");
-    BGL_REQUIRE(p->kk_tol >= 0, "kk_tol must be >= 0");
 }
 
 void check_offsets(int64_t n_tx, const int64_t *off, const char *what) {
@@ -378,6 +378,8 @@ bgl_status bgl_graph_destroy(bgl_graph *g) {
     bgl_ctx *c = g->ctx;
     return guarded(c, [&] {
         sync(c);
+        fa2_session_destroy(g->session);
+        g->session = nullptr;
         delete g;
     });
 }
@@ -385,6 +387,9 @@ bgl_status bgl_graph_destroy(bgl_graph *g) {
 bgl_status bgl_components(bgl_graph *g, int32_t *label_out, int64_t *n_comp) {
     if (!g) return BGL_EINVAL;
     return guarded(g->ctx, [&] {
+        // a session refers to the component arrays being rebuilt
+        fa2_session_destroy(g->session);
+        g->session = nullptr;
         components_device(g);
         if (label_out) {
             d2h(g->ctx, label_out, g->label.p, g->n);
@@ -495,6 +500,59 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
         d2h(g->ctx, reinterpret_cast<float2 *>(xy_inout), xy.p, n);
         if (stats_out) d2h(g->ctx, stats_out, st.p, 3 * (size_t)iters);
         sync(g->ctx);
+    });
+}
+
+bgl_status bgl_fa2_session_begin(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in) {
+    if (!g || !xy_in) return BGL_EINVAL;
+    return guarded(g->ctx, [&] {
+        check_params(p);
+        require_c(g, c);
+        Fa2Session *s = fa2_session_create(g, p, c, reinterpret_cast<const float2 *>(xy_in));
+        fa2_session_destroy(g->session);
+        g->session = s;
+    });
+}
+
+bgl_status bgl_fa2_session_advance(bgl_graph *g, int32_t iters, double *stats_out) {
+    if (!g) return BGL_EINVAL;
+    return guarded(g->ctx, [&] {
+        if (!g->session) fail(BGL_ESTATE, "no ForceAtlas2 session: call bgl_fa2_session_begin or bgl_state_load");
+        BGL_REQUIRE(iters >= 0, "iters must be >= 0");
+        fa2_session_advance(g->session, iters, stats_out);
+    });
+}
+
+bgl_status bgl_fa2_session_positions(bgl_graph *g, float *xy_out, int64_t *iters_done) {
+    if (!g || !xy_out) return BGL_EINVAL;
+    return guarded(g->ctx, [&] {
+        if (!g->session) fail(BGL_ESTATE, "no ForceAtlas2 session: call bgl_fa2_session_begin or bgl_state_load");
+        const int64_t k = fa2_session_positions(g->session, reinterpret_cast<float2 *>(xy_out));
+        if (iters_done) *iters_done = k;
+    });
+}
+
+bgl_status bgl_state_save(bgl_graph *g, void *buf, size_t *len) {
+    if (!g || !len) return BGL_EINVAL;
+    return guarded(g->ctx, [&] {
+        if (!g->session) fail(BGL_ESTATE, "no ForceAtlas2 session to save");
+        const size_t need = fa2_session_state_bytes(g->session);
+        if (!buf) {
+            *len = need;
+            return;
+        }
+        BGL_REQUIRE(*len >= need, "state: buffer too small (query the size with buf = NULL)");
+        fa2_session_save(g->session, buf);
+        *len = need;
+    });
+}
+
+bgl_status bgl_state_load(bgl_graph *g, const void *buf, size_t len) {
+    if (!g || !buf) return BGL_EINVAL;
+    return guarded(g->ctx, [&] {
+        Fa2Session *s = fa2_session_load(g, buf, len);
+        fa2_session_destroy(g->session);
+        g->session = s;
     });
 }
 

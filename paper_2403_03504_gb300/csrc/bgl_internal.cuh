@@ -22,6 +22,7 @@ struct Error : std::runtime_error {
 };
 
 [[noreturn]] void fail(bgl_status s, const std::string &msg);
+void check_params(const bgl_params *p);     // BGL_EINVAL on any parameter out of range
 void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 #define BGL_CUDA(call) ::bgl::check_cuda((call), #call, __FILE__, __LINE__)
 void count_launches(int64_t k);   // kernels launched through the library
@@ -111,8 +112,14 @@ struct bgl_ctx {
     int *h_flag = nullptr;        // pinned mirror
 };
 
+namespace bgl {
+struct Fa2Session;
+void fa2_session_destroy(Fa2Session *s);
+}  // namespace bgl
+
 struct bgl_graph {
     bgl_ctx *ctx = nullptr;
+    bgl::Fa2Session *session = nullptr;   // resumable ForceAtlas2 run (bgl_fa2_session_*)
     int64_t n_tx = 0, n_addr = 0, n = 0;
     int64_t n_dir = 0, n_undir = 0;
     bgl::DevBuf<uint64_t> addr;         // [n_addr] address keys in id order
@@ -154,7 +161,7 @@ void radix_sort_u32(bgl_ctx *c, uint32_t *keys, uint32_t *vals, int64_t n, int b
 // Preallocated temporaries for sorting up to `cap` 32-bit keys with values,
 // so that a sort can run inside a captured CUDA graph.
 struct SortWorkspace {
-    DevBuf<uint32_t> keys, vals;
+    DevBuf<uint32_t> keys, vals, keys2, vals2;   // two scratch buffers for the passes
     DevBuf<int32_t> hist, tiles;
     int64_t cap = 0;
     void reserve(Allocator *a, int64_t n, cudaStream_t s);
@@ -176,8 +183,13 @@ struct OsHist {
     unsigned *counter;   // arrival count of the blocks (reset by the last block)
 };
 OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n);
+// d_skip (device int, may be null = 0): the passes below *d_skip (0 or 2)
+// return at once, so the keys end up ordered by their top 32 - 8 * skip
+// bits only (stable: equal top bits keep the input order).  Read by each
+// pass when it starts.
 void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n,
-                               const float2 *gxy = nullptr, const float *gmass = nullptr, float4 *gpts = nullptr);
+                               const float2 *gxy = nullptr, const float *gmass = nullptr, float4 *gpts = nullptr,
+                               const int *d_skip = nullptr);
 
 int bits_for(uint64_t max_value);   // number of bits needed to hold max_value
 
@@ -208,6 +220,15 @@ void kk_distances(bgl_graph *g, int64_t c, int32_t *d_out_dev);
 // null): swing, traction, s_G per iteration of component c0.
 void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
                 double *d_stats);
+// Resumable ForceAtlas2 run on one component (fa2.cu): positions,
+// F_{t-1}, s_G and the iteration count stay on the device between calls.
+Fa2Session *fa2_session_create(bgl_graph *g, const bgl_params *p, int64_t c, const float2 *h_xy);
+void fa2_session_advance(Fa2Session *s, int iters, double *h_stats);
+int64_t fa2_session_positions(Fa2Session *s, float2 *h_xy);     // returns the iterations done
+size_t fa2_session_state_bytes(const Fa2Session *s);
+void fa2_session_save(Fa2Session *s, void *buf);
+Fa2Session *fa2_session_load(bgl_graph *g, const void *buf, size_t len);
+
 // one force evaluation on component c, xy and f indexed by q - comp_off[c];
 // what: 0 total force, 1 repulsion only
 void fa2_forces(bgl_graph *g, const bgl_params *p, const float2 *xy, float2 *f, int64_t c, int what);

@@ -19,6 +19,8 @@
 // The sequence has fixed launch shapes, so it is captured once into a CUDA
 // graph and replayed for every iteration.  Every sum has a fixed order, so
 // runs are bitwise reproducible.
+#include <cstring>
+
 #include "bgl_internal.cuh"
 #include "fmm.cuh"
 #include "p2p.cuh"
@@ -493,14 +495,13 @@ struct Fa2Run {
     }
 };
 
-void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
-                double *d_stats) {
-    if (c1 <= c0 || iters <= 0) return;
-    bgl_ctx *ctx = g->ctx;
+// One iteration of `run` captured into a CUDA graph (nothing may allocate
+// while the capture is open), replayed `iters` times on the context stream.
+static void run_iterations(Fa2Run &run, int iters, double *d_stats) {
+    bgl_ctx *ctx = run.g->ctx;
     cudaStream_t s = ctx->stream;
-    Fa2Run run(g, p, xy, qbase, c0, c1);
     BGL_CUDA(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
-    // capture one iteration, replay it
+    BGL_CUDA(cudaMemsetAsync(run.iter.p, 0, sizeof(int), s));
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const int64_t before = launch_count();
@@ -544,6 +545,192 @@ void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, in
     cudaGraphExecDestroy(exec);
     run.check_fmm();
     if (ctx->h_flag[1]) fail(BGL_ENUMERIC, "fa2: a position became non-finite");
+}
+
+void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
+                double *d_stats) {
+    if (c1 <= c0 || iters <= 0) return;
+    Fa2Run run(g, p, xy, qbase, c0, c1);
+    run_iterations(run, iters, d_stats);
+}
+
+// ---------------------------------------------------------------- resumable runs
+
+namespace {
+
+// 64-bit FNV-1a over a byte range
+uint64_t fnv1a(uint64_t h, const void *data, size_t len) {
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < len; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+// Identity of component c of g: its size, position in the component order,
+// node ids and adjacency rows (a checkpoint loads only into the same graph).
+uint64_t component_fingerprint(bgl_graph *g, int64_t c) {
+    const int64_t q0 = g->h_comp_off[c], q1 = g->h_comp_off[c + 1], n = q1 - q0;
+    std::vector<int32_t> nodes(n);
+    std::vector<int64_t> coff(n + 1);
+    cudaStream_t s = g->ctx->stream;
+    BGL_CUDA(cudaMemcpyAsync(nodes.data(), g->nodes.p + q0, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaMemcpyAsync(coff.data(), g->coff.p + q0, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaStreamSynchronize(s));
+    const int64_t e0 = coff[0], e1 = coff[n];
+    std::vector<int32_t> cadj(e1 - e0);
+    if (e1 > e0)
+        BGL_CUDA(cudaMemcpyAsync(cadj.data(), g->cadj.p + e0, sizeof(int32_t) * (e1 - e0), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaStreamSynchronize(s));
+    for (auto &o : coff) o -= e0;
+    uint64_t h = 0xcbf29ce484222325ull;
+    const int64_t head[4] = {g->n, g->n_undir, c, n};
+    h = fnv1a(h, head, sizeof(head));
+    h = fnv1a(h, nodes.data(), sizeof(int32_t) * n);
+    h = fnv1a(h, coff.data(), sizeof(int64_t) * (n + 1));
+    h = fnv1a(h, cadj.data(), sizeof(int32_t) * cadj.size());
+    return h;
+}
+
+// checkpoint layout: this header, then n float2 positions and n float2 F_{t-1}
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    int64_t n_nodes, n_undir, comp, comp_nodes;
+    uint64_t fingerprint;
+    int64_t iters_done;
+    double sg;
+    int32_t fmm_sortskip;          // FMM sort passes the next evaluation skips (-1: exact repulsion)
+    int32_t pad;
+    bgl_params params;
+};
+constexpr char STATE_MAGIC[8] = {'B', 'G', 'L', 'F', 'A', '2', 'S', 'T'};
+constexpr uint32_t STATE_VERSION = 1;
+
+}  // namespace
+
+struct Fa2Session {
+    bgl_graph *g = nullptr;
+    bgl_params p;                  // owned copy (the run keeps a pointer to it)
+    int64_t c = 0, q0 = 0, n = 0;
+    int64_t iters_done = 0;
+    uint64_t fingerprint = 0;
+    DevBuf<float2> xy;             // positions, xy[q - q0]
+    Fa2Run *run = nullptr;
+    ~Fa2Session() { delete run; }
+};
+
+static Fa2Session *session_new(bgl_graph *g, const bgl_params *p, int64_t c) {
+    Fa2Session *s = new Fa2Session();
+    try {
+        s->g = g;
+        s->p = *p;
+        s->c = c;
+        s->q0 = g->h_comp_off[c];
+        s->n = g->h_comp_off[c + 1] - s->q0;
+        s->xy.reset(g->ctx->alloc, std::max<int64_t>(s->n, 1));
+        s->run = new Fa2Run(g, &s->p, s->xy.p, s->q0, c, c + 1);
+        s->fingerprint = component_fingerprint(g, c);
+    } catch (...) {
+        delete s;
+        throw;
+    }
+    return s;
+}
+
+Fa2Session *fa2_session_create(bgl_graph *g, const bgl_params *p, int64_t c, const float2 *h_xy) {
+    Fa2Session *s = session_new(g, p, c);
+    try {
+        BGL_CUDA(cudaMemcpyAsync(s->xy.p, h_xy, sizeof(float2) * s->n, cudaMemcpyHostToDevice, g->ctx->stream));
+        BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
+    } catch (...) {
+        delete s;
+        throw;
+    }
+    return s;
+}
+
+void fa2_session_destroy(Fa2Session *s) { delete s; }
+
+void fa2_session_advance(Fa2Session *s, int iters, double *h_stats) {
+    if (iters <= 0) return;
+    bgl_ctx *ctx = s->g->ctx;
+    DevBuf<double> st;
+    if (h_stats) st.reset(ctx->alloc, 3 * (size_t)iters);
+    run_iterations(*s->run, iters, h_stats ? st.p : nullptr);
+    s->iters_done += iters;
+    if (h_stats) {
+        BGL_CUDA(cudaMemcpyAsync(h_stats, st.p, sizeof(double) * 3 * iters, cudaMemcpyDeviceToHost, ctx->stream));
+        BGL_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+}
+
+int64_t fa2_session_positions(Fa2Session *s, float2 *h_xy) {
+    cudaStream_t st = s->g->ctx->stream;
+    BGL_CUDA(cudaMemcpyAsync(h_xy, s->xy.p, sizeof(float2) * s->n, cudaMemcpyDeviceToHost, st));
+    BGL_CUDA(cudaStreamSynchronize(st));
+    return s->iters_done;
+}
+
+size_t fa2_session_state_bytes(const Fa2Session *s) { return sizeof(StateHeader) + 2 * sizeof(float2) * s->n; }
+
+void fa2_session_save(Fa2Session *s, void *buf) {
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, STATE_MAGIC, 8);
+    h.version = STATE_VERSION;
+    h.header_bytes = (uint32_t)sizeof(StateHeader);
+    h.n_nodes = s->g->n;
+    h.n_undir = s->g->n_undir;
+    h.comp = s->c;
+    h.comp_nodes = s->n;
+    h.fingerprint = s->fingerprint;
+    h.iters_done = s->iters_done;
+    h.params = s->p;
+    h.fmm_sortskip = s->run->fmm.empty() ? -1 : fmm_sortskip(s->run->fmm[0]);
+    cudaStream_t st = s->g->ctx->stream;
+    BGL_CUDA(cudaMemcpyAsync(&h.sg, s->run->sg.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    char *out = static_cast<char *>(buf);
+    float2 *xy = reinterpret_cast<float2 *>(out + sizeof(StateHeader));
+    BGL_CUDA(cudaMemcpyAsync(xy, s->xy.p, sizeof(float2) * s->n, cudaMemcpyDeviceToHost, st));
+    BGL_CUDA(cudaMemcpyAsync(xy + s->n, s->run->fprev.p, sizeof(float2) * s->n, cudaMemcpyDeviceToHost, st));
+    BGL_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(out, &h, sizeof(h));
+}
+
+Fa2Session *fa2_session_load(bgl_graph *g, const void *buf, size_t len) {
+    BGL_REQUIRE(len >= sizeof(StateHeader), "state: buffer shorter than the header");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, STATE_MAGIC, 8) != 0 || h.version != STATE_VERSION ||
+        h.header_bytes != sizeof(StateHeader))
+        fail(BGL_EINVAL, "state: not a ForceAtlas2 checkpoint of this library version");
+    if (!g->has_comp) fail(BGL_ESTATE, "state: run bgl_components before loading a checkpoint");
+    if (h.n_nodes != g->n || h.n_undir != g->n_undir || h.comp < 0 || h.comp >= g->n_comp ||
+        h.comp_nodes != g->h_comp_off[h.comp + 1] - g->h_comp_off[h.comp])
+        fail(BGL_EINVAL, "state: the checkpoint belongs to another graph");
+    BGL_REQUIRE(len >= sizeof(StateHeader) + 2 * sizeof(float2) * (size_t)h.comp_nodes,
+                "state: buffer shorter than the checkpoint");
+    check_params(&h.params);
+    Fa2Session *s = session_new(g, &h.params, h.comp);
+    try {
+        if (s->fingerprint != h.fingerprint) fail(BGL_EINVAL, "state: the checkpoint belongs to another graph");
+        const float2 *xy = reinterpret_cast<const float2 *>(static_cast<const char *>(buf) + sizeof(StateHeader));
+        cudaStream_t st = g->ctx->stream;
+        BGL_CUDA(cudaMemcpyAsync(s->xy.p, xy, sizeof(float2) * s->n, cudaMemcpyHostToDevice, st));
+        BGL_CUDA(cudaMemcpyAsync(s->run->fprev.p, xy + s->n, sizeof(float2) * s->n, cudaMemcpyHostToDevice, st));
+        BGL_CUDA(cudaMemcpyAsync(s->run->sg.p, &h.sg, sizeof(double), cudaMemcpyHostToDevice, st));
+        BGL_CUDA(cudaStreamSynchronize(st));
+        if ((h.fmm_sortskip >= 0) != !s->run->fmm.empty()) fail(BGL_EINVAL, "state: repulsion kind mismatch");
+        if (h.fmm_sortskip >= 0) fmm_set_sortskip(s->run->fmm[0], h.fmm_sortskip);
+        s->iters_done = h.iters_done;
+    } catch (...) {
+        delete s;
+        throw;
+    }
+    return s;
 }
 
 void fa2_forces(bgl_graph *g, const bgl_params *p, const float2 *xy, float2 *f, int64_t c, int what) {

@@ -11,28 +11,34 @@
 //
 // One evaluation (all launches, no host synchronisation):
 //   bbox      root square covering all points (FP32 min/max, FP64 geometry)
-//   keys      16-bit quantised x, y interleaved into 32-bit Morton keys
-//   sort      stable radix sort of (key, index); the last pass writes x, y, m in key order
+//   keys      16-bit quantised x, y interleaved into 32-bit Morton keys, with
+//             the digit histograms of the sort in the same pass
+//   sort      stable radix sort of (key, index), four onesweep passes; the
+//             last writes x, y, m in key order
 //   tree      adaptive quadtree: a box is split while it holds more than
 //             leaf_size points (and is above level 16).  The leaf level of
 //             point i is 1 + the deepest level at which some window of
 //             leaf_size + 1 consecutive sorted points around i shares a key
 //             prefix, so boxes are emitted in one pass, level by level, in
-//             Morton order within a level.
-//   nbr       3x3 neighbour table per box from its parent's table (the
-//             same-level box or the coarser leaf covering each adjacent cell)
-//   lists     U (adjacent leaves, near field), V (children of the parent's
-//             neighbours that are not adjacent: the "interacting cells" of
-//             Section 3.2.1), W and X (the adaptive-tree lists of Carrier,
-//             Greengard and Rokhlin that make every pair counted exactly once)
-//   up        P2M at leaves; M2M from the 4 children into the parent by the
-//             last child to finish (an atomic arrival count), so the whole
-//             upward pass is one launch
-//   down      M2L over V, P2L over X, L2L from the parent; boxes are taken in
-//             level order through a ticket counter and wait (bounded) for
-//             their parent's local expansion
-//   leaf      per leaf: L2P of its local expansion, M2P over W, and the direct
-//             P2P sum over the points of U staged in shared memory
+//             Morton order within a level, with their ends, parents and child
+//             slots; then every box goes into a hash table keyed by (level,
+//             Morton prefix)
+//   lists     per box, by hash lookups of the 3x3 cells around it and its
+//             parent: U (adjacent leaves, near field), V (children of the
+//             parent's neighbours that are not adjacent: the "interacting
+//             cells" of Section 3.2.1), W and X (the adaptive-tree lists of
+//             Carrier, Greengard and Rokhlin that make every pair counted
+//             exactly once)
+//   up        P2M from the points for boxes of up to 2048 points; M2M from
+//             the 4 children for the larger ones, by the last child to finish
+//   m2l       per box, independently: M2L over V + P2L over X (a partial
+//             incoming expansion)
+//   near      per leaf: the direct P2P sum over the points of U
+//   far       per leaf: the incoming expansion composed from the partial
+//             expansions of the leaf and all its ancestors (the L2L chain,
+//             one shift per ancestor), L2P at the targets, M2P over W
+// Near and far run concurrently (main and side stream); the second of the
+// two to finish a leaf writes its forces.
 // Every sum has a fixed order, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
@@ -353,7 +359,11 @@ __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy
 // level of its leaf; per tile and level: number of boxes that start in the tile
 __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t *__restrict__ key, int n, int S,
                                                                  int8_t *__restrict__ cl, int8_t *__restrict__ lam,
-                                                                 int *__restrict__ tcnt, int ntiles) {
+                                                                 int *__restrict__ tcnt, int ntiles,
+                                                                 const int *__restrict__ sortskip, int *gmax) {
+    // keys sorted on their top 16 bits only (two radix passes skipped):
+    // boxes stop at level 8
+    const int cap = *sortskip == 2 ? 8 : MAXLEV;
     __shared__ uint32_t sk[TREE_TILE + 2 * 256];
     __shared__ int8_t g[TREE_TILE + 256];
     __shared__ int cnt[NLEV];
@@ -375,6 +385,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
     int local[NLEV];
 #pragma unroll
     for (int L = 0; L < NLEV; ++L) local[L] = 0;
+    int gm = -1;
     for (int r = 0; r < TREE_TILE / TREE_THREADS; ++r) {
         int i = t0 + r * TREE_THREADS + threadIdx.x;
         if (i >= n) break;
@@ -383,7 +394,8 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
         int G = -1;
         // windows j in [i - S, i] (g is -1 where a window does not fit)
         for (int j = k - S; j <= k; ++j) G = max(G, (int)g[j]);
-        int la = min(MAXLEV, G + 1);
+        gm = max(gm, G);
+        int la = min(cap, G + 1);
         cl[i] = (int8_t)c;
         lam[i] = (int8_t)la;
 #pragma unroll
@@ -392,6 +404,9 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
 #pragma unroll
     for (int L = 0; L < NLEV; ++L)
         if (local[L]) atomicAdd(&cnt[L], local[L]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if ((threadIdx.x & 31) == 0 && gm >= 0) atomicMax(gmax, gm);
     __syncthreads();
     if (threadIdx.x < NLEV) tcnt[threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
@@ -402,8 +417,11 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 8;
 
+// Also picks the radix passes of the next evaluation: when no window of
+// leaf_size + 1 points shares 8 or more levels (the tree is at most 8 levels
+// deep), the next sort orders the top 16 key bits only.
 __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax,
-                                                                 int *err) {
+                                                                 int *err, const int *gmax, int *sortskip) {
     __shared__ int sv[SCAN_THREADS * SCAN_ITEMS];
     __shared__ int wsum[32];
     __shared__ int carry_s;
@@ -457,6 +475,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int 
         levoff[L] = L < NLEV ? tcnt[L * ntiles] : carry;
     }
     if (threadIdx.x == 0 && carry > Bmax) atomicOr(err, ERR_BOX_OVERFLOW);
+    if (threadIdx.x == 0) *sortskip = *gmax <= 7 ? 2 : 0;
 }
 
 // Boxes of the tile, level by level in point order.  Warp w owns the
@@ -1212,10 +1231,14 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
 // the second to finish writes the force of every target of the leaf:
 //   F_rep(i) = kr m_i (near(i) + conj(E(z_i))) (+ fa(i))
 __device__ __noinline__ void leaf_finish(const LeafArgs &la, int b, int s, int e, int lane) {
-    __threadfence();
+    // the warp barrier orders the lanes' writes before lane 0's fence, which
+    // makes them visible device-wide before the mark
     __syncwarp();
     int old = 0;
-    if (lane == 0) old = atomicAdd(&la.leafdone[b], 1);
+    if (lane == 0) {
+        __threadfence();
+        old = atomicAdd(&la.leafdone[b], 1);
+    }
     old = __shfl_sync(0xffffffffu, old, 0);
     if (old != 1) return;
     __threadfence();
@@ -1445,6 +1468,7 @@ struct FmmPlan {
     DevBuf<int2> bmeta;
     DevBuf<float2> M, Lc;
     DevBuf<int> arrive, tickets, err, leafdone;
+    DevBuf<int> sortskip;     // radix passes the next sort skips (0 or 2), set by the tree of the last evaluation
     DevBuf<float2> ef;
     DevBuf<ulonglong2> hkv;
     DevBuf<unsigned> epoch;
@@ -1509,6 +1533,8 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->Lc.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->arrive.reset(A, bmax);
         pl->leafdone.reset(A, bmax);
+        pl->sortskip.reset(A, 1);
+        BGL_CUDA(cudaMemsetAsync(pl->sortskip.p, 0, sizeof(int), s));
         pl->ef.reset(A, n);
         int64_t hs = 1;
         while (hs < 2 * bmax) hs <<= 1;
@@ -1616,7 +1642,7 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
         BGL_LAUNCH_CHECK();
         keys_kernel<<<nblk(n, 256 * KEY_ITEMS), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p, h);
         BGL_LAUNCH_CHECK();
-        radix_sort_u32_ws_scatter(ctx, pl->sortws, pl->key.p, pl->idx.p, n, xl, ml, pl->pts.p);
+        radix_sort_u32_ws_scatter(ctx, pl->sortws, pl->key.p, pl->idx.p, n, xl, ml, pl->pts.p, pl->sortskip.p);
     } catch (...) {
         ctx->stream = keep;
         throw;
@@ -1628,9 +1654,10 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
 static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
     BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * pl->Bmax, s));
     tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, pl->n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
-                                                          pl->ntiles);
+                                                          pl->ntiles, pl->sortskip.p, pl->tickets.p + 6);
     BGL_LAUNCH_CHECK();
-    tree_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p);
+    tree_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p,
+                                                pl->tickets.p + 6, pl->sortskip.p);
     BGL_LAUNCH_CHECK();
     tree_emit_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(T, pl->cl.p, pl->lam.p, pl->tcnt.p, pl->ntiles, pl->Bmax);
     BGL_LAUNCH_CHECK();
@@ -1767,6 +1794,7 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
     const float2 *xl = xy + (pl->q0 - qbase);
     const Tree T = make_tree(pl);
     DevBuf<float2> f(ctx->alloc, std::max(pl->n, 1));
+    std::vector<float2> f_first(pl->n), f_last(pl->n);
     cudaEvent_t ev[8], c0, c1;
     for (auto &e : ev) BGL_CUDA(cudaEventCreate(&e));
     BGL_CUDA(cudaEventCreate(&c0));
@@ -1782,6 +1810,8 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
                 BGL_CUDA(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
                 acc[k] += ms;
             }
+            if (r == 0 && pl->n > 0)
+                BGL_CUDA(cudaMemcpy(f_first.data(), f.p, sizeof(float2) * pl->n, cudaMemcpyDeviceToHost));
         }
         // the concurrent schedule used inside ForceAtlas2 iterations
         for (int r = 0; r < R; ++r) {
@@ -1802,6 +1832,16 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
     for (auto &e : ev) cudaEventDestroy(e);
     cudaEventDestroy(c0);
     cudaEventDestroy(c1);
+    // the first evaluation (sorting all key bits) against the last (with the
+    // radix passes the plan chose from the tree): largest difference relative
+    // to the largest force
+    const int skip_last = fmm_sortskip(pl);
+    if (pl->n > 0) BGL_CUDA(cudaMemcpy(f_last.data(), f.p, sizeof(float2) * pl->n, cudaMemcpyDeviceToHost));
+    double dmax = 0.0, fmax = 0.0;
+    for (int i = 0; i < pl->n; ++i) {
+        dmax = std::max(dmax, (double)std::hypot(f_last[i].x - f_first[i].x, f_last[i].y - f_first[i].y));
+        fmax = std::max(fmax, (double)std::hypot(f_first[i].x, f_first[i].y));
+    }
     DevBuf<unsigned long long> cnt(ctx->alloc, 6);
     BGL_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 6, s));
     count_kernel<<<pl->grid_p, 256, 0, s>>>(T, cnt.p);
@@ -1820,6 +1860,21 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
     out[5] = (double)h[1];
     out[6] = (double)h[2];
     for (int k = 0; k < 8; ++k) out[7 + k] = acc[k] / R;
+    out[15] = fmax > 0.0 ? dmax / fmax : 0.0;
+    out[16] = (double)skip_last;
+}
+
+int fmm_sortskip(FmmPlan *pl) {
+    int v = 0;
+    BGL_CUDA(cudaMemcpyAsync(&v, pl->sortskip.p, sizeof(int), cudaMemcpyDeviceToHost, pl->g->ctx->stream));
+    BGL_CUDA(cudaStreamSynchronize(pl->g->ctx->stream));
+    return v;
+}
+
+void fmm_set_sortskip(FmmPlan *pl, int skip) {
+    BGL_REQUIRE(skip == 0 || skip == 2, "fmm: sort pass skip must be 0 or 2");
+    BGL_CUDA(cudaMemcpyAsync(pl->sortskip.p, &skip, sizeof(int), cudaMemcpyHostToDevice, pl->g->ctx->stream));
+    BGL_CUDA(cudaStreamSynchronize(pl->g->ctx->stream));
 }
 
 int fmm_error(FmmPlan *pl) {

@@ -26,6 +26,12 @@ void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int6
 // and of a whole evaluation in the concurrent schedule.
 void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double *out);
 
+// Radix passes the plan's next sort skips (0 or 2): chosen on the device from
+// the depth of the previous evaluation's tree, so it is part of the state a
+// resumed run needs (reading and setting synchronise the stream).
+int fmm_sortskip(FmmPlan *pl);
+void fmm_set_sortskip(FmmPlan *pl, int skip);
+
 // Error bits raised on the device since the plan was made (synchronises):
 // 1 a bounded wait gave up, 2 list capacity exceeded, 4 box capacity
 // exceeded, 8 non-finite bounding box.

@@ -291,15 +291,27 @@ __global__ void __launch_bounds__(OS_THREADS) os_hist_kernel(const uint32_t *__r
     os_block_hist<OS_ITEMS>(k, valid, h);
 }
 
-__global__ void __launch_bounds__(OS_THREADS, 2) os_scatter_kernel(const uint32_t *__restrict__ kin,
-                                                                 const uint32_t *__restrict__ vin,
-                                                                 uint32_t *__restrict__ kout,
-                                                                 uint32_t *__restrict__ vout, int64_t n, int shift,
+// Buffers of pass d (0..3) when the first `skip` passes are skipped: the
+// first active pass reads the input, the last writes the output, the ones
+// between alternate between the two scratch pairs.
+struct OsBufs {
+    uint32_t *keys, *vals;      // input, and output of the last pass
+    uint32_t *k0, *v0, *k1, *v1; // scratch
+};
+
+__global__ void __launch_bounds__(OS_THREADS, 2) os_scatter_kernel(OsBufs bf, int d, const int *d_skip, int64_t n,
                                                                  const uint32_t *__restrict__ base,
                                                                  uint32_t *status, unsigned *ticket, int *err,
                                                                  const float2 *__restrict__ gxy,
                                                                  const float *__restrict__ gmass,
                                                                  float4 *__restrict__ gpts) {
+    const int skip = d_skip ? *d_skip : 0;
+    if (d < skip) return;
+    const int shift = 8 * d;
+    const uint32_t *__restrict__ kin = d == skip ? bf.keys : (((d - skip - 1) & 1) ? bf.k1 : bf.k0);
+    const uint32_t *__restrict__ vin = d == skip ? bf.vals : (((d - skip - 1) & 1) ? bf.v1 : bf.v0);
+    uint32_t *__restrict__ kout = d == 3 ? bf.keys : (((d - skip) & 1) ? bf.k1 : bf.k0);
+    uint32_t *__restrict__ vout = d == 3 ? bf.vals : (((d - skip) & 1) ? bf.v1 : bf.v0);
     __shared__ int32_t cnt[OS_WARPS][256];
     __shared__ uint32_t gofs[256];
     __shared__ int32_t lstart[256];
@@ -466,6 +478,8 @@ void SortWorkspace::reserve(Allocator *a, int64_t n, cudaStream_t s) {
     if (n <= cap) return;
     keys.reset(a, n);
     vals.reset(a, n);
+    keys2.reset(a, n);
+    vals2.reset(a, n);
     // hist: 4 x 256 digit counts, 4 x 256 digit bases, 4 tickets, 1 counter, error word
     hist.reset(a, 8 * 256 + 8);
     BGL_CUDA(cudaMemsetAsync(hist.p, 0, hist.bytes(), s));
@@ -490,7 +504,7 @@ OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n) {
 }
 
 void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n,
-                               const float2 *gxy, const float *gmass, float4 *gpts) {
+                               const float2 *gxy, const float *gmass, float4 *gpts, const int *d_skip) {
     cudaStream_t s = c->stream;
     const int64_t nt = os_tiles(n);
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws.hist.p);
@@ -498,18 +512,16 @@ void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, ui
     unsigned *tickets = reinterpret_cast<unsigned *>(hist + 8 * 256);
     int *err = reinterpret_cast<int *>(tickets + 5);
     uint32_t *status = reinterpret_cast<uint32_t *>(ws.tiles.p);
-    uint32_t *ka = keys, *kb = ws.keys.p, *va = vals, *vb = ws.vals.p;
+    const OsBufs bf{keys, vals, ws.keys.p, ws.vals.p, ws.keys2.p, ws.vals2.p};
     for (int d = 0; d < 4; ++d) {
         const bool g = d == 3 && gpts;
-        os_scatter_kernel<<<(unsigned)nt, OS_THREADS, 0, s>>>(ka, va, kb, vb, n, 8 * d, base + 256 * d,
+        os_scatter_kernel<<<(unsigned)nt, OS_THREADS, 0, s>>>(bf, d, d_skip, n, base + 256 * d,
                                                               status + (int64_t)d * 256 * nt, tickets + d, err,
                                                               g ? gxy : nullptr, g ? gmass : nullptr,
                                                               g ? gpts : nullptr);
         BGL_LAUNCH_CHECK();
-        std::swap(ka, kb);
-        std::swap(va, vb);
     }
-    // four passes: the sorted keys (and values unless gathered) are back in keys / vals
+    // the sorted keys (and values unless gathered) are back in keys / vals
 }
 
 void radix_sort_u32_ws(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n, int bits,

@@ -28,7 +28,8 @@ def lib():
 def test_header_declares_entry_points():
     names = _declared()
     for must in ("bgl_graph_build", "bgl_components", "bgl_split", "bgl_layout", "bgl_fa2_step",
-                 "bgl_kk_run", "bgl_graph_build_dev", "bgl_layout_dev"):
+                 "bgl_kk_run", "bgl_graph_build_dev", "bgl_layout_dev", "bgl_state_save", "bgl_state_load",
+                 "bgl_fa2_session_begin", "bgl_fa2_session_advance", "bgl_fa2_session_positions"):
         assert must in names
 
 
@@ -67,6 +68,9 @@ def test_params_defaults(lib):
 def test_null_arguments_are_rejected_without_a_gpu(lib):
     # entry points that validate before touching the device
     assert lib.bgl_ctx_create(0, None) == -1
+    assert lib.bgl_state_save(None, None, None) == -1
+    assert lib.bgl_state_load(None, None, 0) == -1
+    assert lib.bgl_fa2_session_advance(None, 1, None) == -1
     lib.bgl_graph_sizes.argtypes = [ctypes.c_void_p] * 5
     assert lib.bgl_graph_sizes(None, None, None, None, None) == -1
     lib.bgl_last_error.restype = ctypes.c_char_p

@@ -89,6 +89,22 @@ def test_fmm_is_bitwise_reproducible(path30k):
     assert np.array_equal(a, b)
 
 
+def test_fmm_sort_passes_follow_tree_depth(path30k):
+    """When a tree is at most 8 levels deep, the next evaluation of the same
+    plan sorts the Morton keys on their top 16 bits only (two radix passes
+    skipped): the tree is the same, only the order of points inside a leaf
+    differs, so the forces agree to rounding.  Deeper trees keep the full
+    sort, and then repeated evaluations are bitwise equal."""
+    bgl = _bgl()
+    p = bgl.params(repulsion=bgl.REP_FMM, fmm_p=8)
+    shallow = path30k.g.fmm_stats(0, p, synth.points(7, path30k.n, "uniform", scale=50.0), reps=2)
+    assert shallow["depth"] <= 8 and shallow["sort_skip"] == 2
+    assert shallow["sortmode_rel_diff"] <= 1e-5
+    deep = path30k.g.fmm_stats(0, p, synth.points(5, path30k.n, "clustered", scale=20.0), reps=2)
+    assert deep["depth"] > 8 and deep["sort_skip"] == 0
+    assert deep["sortmode_rel_diff"] == 0.0
+
+
 def test_fmm_small_leaf_sizes(path30k):
     bgl = _bgl()
     xy = synth.points(5, path30k.n, "clustered", scale=20.0)
