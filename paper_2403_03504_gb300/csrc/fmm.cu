@@ -1238,10 +1238,11 @@ __device__ __noinline__ void leaf_finish(const LeafArgs &la, int b, int s, int e
     if (lane == 0) {
         __threadfence();
         old = atomicAdd(&la.leafdone[b], 1);
+        if (old == 1) __threadfence();     // acquire: the other kernel's results are visible
     }
     old = __shfl_sync(0xffffffffu, old, 0);
     if (old != 1) return;
-    __threadfence();
+    __syncwarp();
     for (int tt = s + lane; tt < e; tt += 32) {
         const float4 z = la.e.T.pts[tt];
         const int o = __float_as_int(z.w);
@@ -1285,9 +1286,9 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
             }
             const int lps = 32 / S;
             if (R == 6) near_tile<6>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else            if (R == 5) near_tile<5>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else            if (R == 4) near_tile<4>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else            if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else if (R == 5) near_tile<5>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else if (R == 4) near_tile<4>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+            else if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else if (R == 2) near_tile<2>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else near_tile<1>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
         }

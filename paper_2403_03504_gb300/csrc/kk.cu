@@ -3,17 +3,20 @@
 //
 // A group of lanes lays out one component of at most 255 nodes:
 //  1. all-pairs hop distances by a BFS from every node (lane s runs the BFS
-//     of sources s, s+32, ...) into a uint8 matrix in shared memory; with
-//     unit edge weights this equals the Floyd-Warshall result the paper
-//     names, at O(n (n + E)) instead of O(n^3) work;
+//     of sources s, s+32, ...) into a uint8 matrix -- in shared memory for
+//     components of up to 64 nodes, in global memory (one BFS row per lane
+//     staged in shared memory) for larger ones, so that a few large
+//     components do not take all of an SM's shared memory; with unit edge
+//     weights this equals the Floyd-Warshall result the paper names, at
+//     O(n (n + E)) instead of O(n^3) work;
 //  2. optional initial positions (SplitMix64 per node id) scaled by
 //     l * diameter / 2;
 //  3. Gauss-Seidel sweeps: for m = 0..n-1 the lanes sum the gradient and
-//     Hessian of the KK energy over all i != m (lane-strided FP32 terms,
-//     xor-butterfly reduction so every lane holds identical sums), take a
-//     safeguarded 2x2 Newton-Raphson step (kk_step, FP32; the FP64 rate of
-//     GB300 is a small fraction of its FP32 rate) and move p_m in shared
-//     memory.
+//     Hessian of the KK energy over all i != m (each lane over its own
+//     consecutive nodes, positions in registers; xor-butterfly reduction so
+//     every lane holds identical sums), take a safeguarded 2x2
+//     Newton-Raphson step (kk_step, FP32; the FP64 rate of GB300 is a small
+//     fraction of its FP32 rate) and the owner lane moves p_m.
 // Small components share a warp: lane groups of 4, 8, 16 or 32 lanes by
 // component size class, each group laying out its own component.
 #include <algorithm>
@@ -70,19 +73,25 @@ __device__ __forceinline__ bool kk_step(float gx, float gy, float a, float b, fl
     const float e1 = l1 > 1e-12f * big ? l1 : fmaxf(fabsf(l1), fl);
     const float e2 = l2 > 1e-12f * big ? l2 : fmaxf(fabsf(l2), fl);
     float sx, sy;
+    // correctly rounded reciprocals (__frcp_rn) instead of divisions, and
+    // rsqrtf for the length cap: cheaper, and the step is a safeguarded
+    // Newton move whose rounding the sweeps do not amplify
+    const float ie1 = __frcp_rn(e1), ie2 = __frcp_rn(e2);
     if (dd == 0.0f) {
-        sx = -gx / e1;
-        sy = -gy / e1;
+        sx = -gx * ie1;
+        sy = -gy * ie1;
     } else {
-        const float p1x = ((h + dd) * gx + b * gy) / (2.0f * dd);
-        const float p1y = (b * gx + (dd - h) * gy) / (2.0f * dd);
-        sx = -(p1x / e1 + (gx - p1x) / e2);
-        sy = -(p1y / e1 + (gy - p1y) / e2);
+        const float i2d = __frcp_rn(2.0f * dd);
+        const float p1x = ((h + dd) * gx + b * gy) * i2d;
+        const float p1y = (b * gx + (dd - h) * gy) * i2d;
+        sx = -(p1x * ie1 + (gx - p1x) * ie2);
+        sy = -(p1y * ie1 + (gy - p1y) * ie2);
     }
-    const float len = sqrtf(sx * sx + sy * sy);
-    if (len > l) {
-        sx *= l / len;
-        sy *= l / len;
+    const float len2 = sx * sx + sy * sy;
+    if (len2 > l * l) {
+        const float sc = l * rsqrtf(len2);
+        sx *= sc;
+        sy *= sc;
     }
     *dx = sx;
     *dy = sy;
@@ -105,10 +114,19 @@ struct KKArgs {
     float tol;
     int init;
     int32_t *d_out;        // optional int32 distance matrix of component c0
+    uint8_t *gdist;        // distances in global memory (null: in shared memory)
+    const int64_t *gdist_off;  // [nc] start of component c0 + k's matrix in gdist
 };
 
-// One group of G lanes per component (G = 4, 8, 16 or 32).
-template <int G>
+// Distance rows are padded to a multiple of 8 bytes (padding 255).
+__host__ __device__ __forceinline__ int kk_row_stride(int n) { return (n + 7) & ~7; }
+constexpr size_t KK_TABLE_BYTES = 2 * 256 * sizeof(float);
+
+// One group of G lanes per component (G = 4, 8, 16 or 32); lane gl owns the
+// nodes gl + j G (j < CPL): their positions live in its registers, and their
+// distances to the current node m are read one step ahead (the next row's
+// loads are in flight during the current step).
+template <int G, int CPL>
 __global__ void kk_kernel(KKArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -116,19 +134,56 @@ __global__ void kk_kernel(KKArgs a) {
     const int gl = threadIdx.x % G;                  // lane in the group
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((lane / G) * G));
     const int64_t c = a.c0 + (int64_t)blockIdx.x * a.gpb + grp;
+    const bool live = c < a.c0 + a.nc;
+    const int64_t q0 = live ? a.comp_off[c] : 0;
+    const int n = live ? (int)(a.comp_off[c + 1] - q0) : 0;
+    const int ds = kk_row_stride(n);                 // row stride of the distance matrix
+    const bool glob = a.gdist != nullptr;
+    const int dsm = kk_row_stride(a.maxn);
+    const size_t gbytes = glob ? (size_t)dsm : (size_t)a.maxn * dsm;
+    // per-block table: s_k[d] = d^-2, s_l[d] = l d (0 for d = 0 and d = 255)
+    float *s_k = reinterpret_cast<float *>(smem), *s_l = s_k + 256;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const bool ok = i != 0 && i != 255;
+        s_k[i] = ok ? 1.0f / (float)(i * i) : 0.f;
+        s_l[i] = ok ? a.l * (float)i : 0.f;
+    }
+    __syncthreads();
     if (c >= a.c0 + a.nc) return;
-    const int64_t q0 = a.comp_off[c];
-    const int n = (int)(a.comp_off[c + 1] - q0);
-    const size_t dbytes = ((size_t)a.maxn * a.maxn + 15) & ~size_t(15);
-    unsigned char *base = smem + (size_t)grp * (dbytes + 8 * (size_t)a.maxn);
-    uint8_t *dist = base;
-    float *px = reinterpret_cast<float *>(base + dbytes);
-    float *py = px + a.maxn;
+    unsigned char *base = smem + KK_TABLE_BYTES + (size_t)grp * ((gbytes + 15) / 16 * 16);
+    uint8_t *dist = glob ? a.gdist + a.gdist_off[c - a.c0] : base;
 
     // 1. BFS from every node (Section 3.1: all-pairs shortest paths, unit weights)
-    for (int s = gl; s < n; s += G) {
-        uint8_t *row = dist + (size_t)s * n;
-        for (int v = 0; v < n; ++v) row[v] = 255;
+    if (glob) {
+        // large component: one source at a time, the group expanding each
+        // level together in a shared row, which then goes to global memory
+        uint8_t *row = base;
+        for (int s = 0; s < n; ++s) {
+            for (int v = gl; v < ds; v += G) row[v] = v == s ? 0 : 255;
+            __syncwarp(gmask);
+            for (int k = 0; k < 254; ++k) {
+                bool grew = false;
+                for (int v = gl; v < n; v += G) {
+                    if (row[v] != k) continue;
+                    for (int64_t e = a.coff[q0 + v]; e < a.coff[q0 + v + 1]; ++e) {
+                        const int w = (int)(a.cadj[e] - q0);
+                        if (row[w] == 255) {
+                            row[w] = (uint8_t)(k + 1);   // lanes reaching w write the same value
+                            grew = true;
+                        }
+                    }
+                }
+                __syncwarp(gmask);
+                if (!__any_sync(gmask, grew)) break;
+            }
+            for (int v = gl; v < ds; v += G) dist[(size_t)s * ds + v] = row[v];
+            __syncwarp(gmask);
+        }
+        __threadfence_block();
+    }
+    for (int s = gl; !glob && s < n; s += G) {
+        uint8_t *row = dist + (size_t)s * ds;
+        for (int v = 0; v < ds; ++v) row[v] = 255;
         row[s] = 0;
         for (int k = 0; k < 254; ++k) {
             bool grew = false;
@@ -148,56 +203,82 @@ __global__ void kk_kernel(KKArgs a) {
     __syncwarp(gmask);
     int diam = 0;
     for (int i = gl; i < n * n; i += G) {
-        int d = dist[i];
+        int d = dist[(size_t)(i / n) * ds + i % n];
         if (d != 255 && d > diam) diam = d;
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) diam = max(diam, __shfl_xor_sync(gmask, diam, o));
 
     if (a.d_out && c == a.c0) {
-        for (int i = gl; i < n * n; i += G) a.d_out[i] = dist[i] == 255 ? -1 : (int32_t)dist[i];
-    }
-
-    // 2. positions
-    const float scale = a.l * (float)diam * 0.5f;
-    for (int v = gl; v < n; v += G) {
-        float2 p;
-        if (a.init) {
-            p = initial_position(a.seed, a.nodes[q0 + v]);
-            p.x *= scale;
-            p.y *= scale;
-        } else {
-            p = a.xy[q0 + v - a.qbase];
+        for (int i = gl; i < n * n; i += G) {
+            const int d = dist[(size_t)(i / n) * ds + i % n];
+            a.d_out[i] = d == 255 ? -1 : d;
         }
-        px[v] = p.x;
-        py[v] = p.y;
     }
-    __syncwarp(gmask);
 
-    // 3. Gauss-Seidel Newton-Raphson sweeps
+    // 2. positions of the lane's nodes
+    const float scale = a.l * (float)diam * 0.5f;
+    float px[CPL], py[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+        const int v = gl + j * G;
+        float2 p = make_float2(0.f, 0.f);
+        if (v < n) {
+            if (a.init) {
+                p = initial_position(a.seed, a.nodes[q0 + v]);
+                p.x *= scale;
+                p.y *= scale;
+            } else {
+                p = a.xy[q0 + v - a.qbase];
+            }
+        }
+        px[j] = p.x;
+        py[j] = p.y;
+    }
+
+    // 3. Gauss-Seidel Newton-Raphson sweeps.  k_mi = d^-2 and l_mi = l d come
+    // from the block's table (0 for d = 0: the node itself; and for the 255
+    // padding of a row), so the pair terms need no branch.
+    uint8_t dn[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? dist[gl + j * G] : 255;
     for (int sw = 0; sw < a.sweeps; ++sw) {
         float gmax = 0.f;
         for (int m = 0; m < n; ++m) {
-            const float xm = px[m], ym = py[m];
-            const uint8_t *drow = dist + (size_t)m * n;
+            uint8_t d[CPL];
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) d[j] = dn[j];
+            // next row (m + 1, or row 0 for the next sweep) in flight
+            const uint8_t *nrow = dist + (size_t)(m + 1 < n ? m + 1 : 0) * ds;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? nrow[gl + j * G] : 255;
+            // position of node m from its owner lane
+            const int owner = m % G, slot = m / G;
+            float ox = px[0], oy = py[0];
+#pragma unroll
+            for (int j = 1; j < CPL; ++j)
+                if (slot == j) {
+                    ox = px[j];
+                    oy = py[j];
+                }
+            const int src = (lane / G) * G + owner;
+            const float xm = __shfl_sync(gmask, ox, src), ym = __shfl_sync(gmask, oy, src);
             float gx = 0.f, gy = 0.f, hxx = 0.f, hxy = 0.f, hyy = 0.f;
-            for (int i = gl; i < n; i += G) {
-                int d = drow[i];
-                if (i == m || d == 0 || d == 255) continue;
-                float dx = xm - px[i], dy = ym - py[i];
-                float r2 = dx * dx + dy * dy;
-                if (r2 == 0.f) continue;
-                float fd = (float)d;
-                float k = 1.0f / (fd * fd);
-                float lm = a.l * fd;
-                float rinv = rsqrtf(r2);
-                float t = lm * rinv;              // l_mi / r
-                float u = t * rinv * rinv;        // l_mi / r^3
-                gx += k * dx * (1.f - t);
-                gy += k * dy * (1.f - t);
-                hxx += k * (1.f - u * dy * dy);
-                hyy += k * (1.f - u * dx * dx);
-                hxy += k * u * dx * dy;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                if (j * G >= n) break;                   // the group's component has no node there
+                const float k = s_k[d[j]], lm = s_l[d[j]];
+                const float dx = xm - px[j], dy = ym - py[j];
+                const float r2 = fmaf(dx, dx, dy * dy);
+                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                const float t = lm * rinv;              // l_mi / r
+                const float u = t * rinv * rinv;        // l_mi / r^3
+                const float kdx = k * dx, kdy = k * dy;
+                gx = fmaf(kdx, 1.f - t, gx);
+                gy = fmaf(kdy, 1.f - t, gy);
+                hxx += k - u * kdy * dy;
+                hyy += k - u * kdx * dx;
+                hxy = fmaf(u * kdx, dy, hxy);
             }
             gx = group_sum<G>(gx, gmask);
             gy = group_sum<G>(gy, gmask);
@@ -206,20 +287,30 @@ __global__ void kk_kernel(KKArgs a) {
             hyy = group_sum<G>(hyy, gmask);
             gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
             float dxm, dym;
-            if (kk_step(gx, gy, hxx, hxy, hyy, a.l, &dxm, &dym) && gl == 0) {
-                px[m] = xm + dxm;
-                py[m] = ym + dym;
+            // every lane holds the same sums, so every lane takes the same step
+            if (kk_step(gx, gy, hxx, hxy, hyy, a.l, &dxm, &dym) && gl == owner) {
+#pragma unroll
+                for (int j = 0; j < CPL; ++j)
+                    if (slot == j) {
+                        px[j] = xm + dxm;
+                        py[j] = ym + dym;
+                    }
             }
-            __syncwarp(gmask);
         }
         if (a.tol > 0.f && gmax < a.tol) break;
     }
-    for (int v = gl; v < n; v += G) a.xy[q0 + v - a.qbase] = make_float2(px[v], py[v]);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j)
+        if (gl + j * G < n) a.xy[q0 + gl + j * G - a.qbase] = make_float2(px[j], py[j]);
 }
 
-size_t kk_warp_bytes(int maxn) {
-    return (((size_t)maxn * maxn + 15) & ~size_t(15)) + 8 * (size_t)maxn;
+size_t kk_group_bytes(int maxn, bool glob) {
+    const size_t d = glob ? (size_t)kk_row_stride(maxn) : (size_t)maxn * kk_row_stride(maxn);
+    return (d + 15) / 16 * 16;
 }
+
+// components above this size keep their distance matrix in global memory
+constexpr int KK_SMEM_MAX_N = 64;
 
 }  // namespace
 
@@ -231,18 +322,35 @@ void init_positions(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t q0, i
     BGL_LAUNCH_CHECK();
 }
 
-template <int G>
+template <int G, int CPL>
 static void kk_launch_group(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1,
                             bool init, int sweeps, int32_t *d_out) {
     if (c1 <= c0) return;
     int maxn = (int)(g->h_comp_off[c0 + 1] - g->h_comp_off[c0]);   // components sorted by size, descending
-    BGL_REQUIRE(maxn <= 255, "kk: components must have at most 255 nodes");
+    BGL_REQUIRE(maxn <= G * CPL && maxn <= 255, "kk: component larger than its size class");
     if (maxn < 1) maxn = 1;
-    const size_t gb = kk_warp_bytes(maxn);
+    const bool glob = maxn > KK_SMEM_MAX_N;
+    const size_t gb = kk_group_bytes(maxn, glob);
     const int max_groups = 256 / G;
     const int gpb = (int)std::min<size_t>(max_groups, std::max<size_t>(1, (size_t)(200 * 1024) / gb));
-    const size_t smem = gb * gpb;
-    BGL_CUDA(cudaFuncSetAttribute(kk_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    const size_t smem = KK_TABLE_BYTES + gb * gpb;
+    // global distance matrices: n_c x stride(n_c) bytes per component
+    DevBuf<uint8_t> gdist;
+    DevBuf<int64_t> gdist_off;
+    if (glob) {
+        std::vector<int64_t> off(c1 - c0);
+        int64_t tot = 0;
+        for (int64_t c = c0; c < c1; ++c) {
+            const int64_t nc = g->h_comp_off[c + 1] - g->h_comp_off[c];
+            off[c - c0] = tot;
+            tot += nc * kk_row_stride((int)nc);
+        }
+        gdist.reset(g->ctx->alloc, std::max<int64_t>(tot, 8));
+        gdist_off.reset(g->ctx->alloc, off.size());
+        BGL_CUDA(cudaMemcpyAsync(gdist_off.p, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice,
+                                 g->ctx->stream));
+    }
+    BGL_CUDA(cudaFuncSetAttribute(kk_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     KKArgs a;
     a.comp_off = g->comp_off.p;
     a.coff = g->coff.p;
@@ -260,9 +368,13 @@ static void kk_launch_group(bgl_graph *g, const bgl_params *p, float2 *xy, int64
     a.tol = (float)p->kk_tol;
     a.init = init ? 1 : 0;
     a.d_out = d_out;
+    a.gdist = glob ? gdist.p : nullptr;
+    a.gdist_off = glob ? gdist_off.p : nullptr;
     const int64_t blocks = (a.nc + gpb - 1) / gpb;
-    kk_kernel<G><<<(unsigned)blocks, G * gpb, smem, g->ctx->stream>>>(a);
+    kk_kernel<G, CPL><<<(unsigned)blocks, G * gpb, smem, g->ctx->stream>>>(a);
     BGL_LAUNCH_CHECK();
+    // the scratch goes back to the caching allocator only once the kernel is done
+    if (glob) BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
 }
 
 // first component index in [c0, c1) with at most `size` nodes (sizes descend)
@@ -276,21 +388,22 @@ static int64_t first_at_most(const bgl_graph *g, int64_t c0, int64_t c1, int64_t
     return lo;
 }
 
-// Components in size classes, each with lane groups of its size:
-// > 16 nodes: 32 lanes, 9..16: 16, 5..8: 8, <= 4: 4.
+// Components in size classes: (128, 255] nodes 32 lanes x up to 8 nodes
+// each, (64, 128] 32 x 4, (32, 64] 32 x 2, (16, 32] 16 x 2, (8, 16] 8 x 2,
+// (4, 8] 4 x 2, <= 4 4 x 1; distances in global memory above 64 nodes.
 static void kk_launch(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init,
                       int sweeps, int32_t *d_out) {
     if (c1 <= c0) return;
-    if (d_out) {   // one component, distances exported
-        kk_launch_group<32>(g, p, xy, qbase, c0, c1, init, sweeps, d_out);
-        return;
-    }
-    const int64_t a16 = first_at_most(g, c0, c1, 16), a8 = first_at_most(g, c0, c1, 8),
-                  a4 = first_at_most(g, c0, c1, 4);
-    kk_launch_group<32>(g, p, xy, qbase, c0, a16, init, sweeps, nullptr);
-    kk_launch_group<16>(g, p, xy, qbase, a16, a8, init, sweeps, nullptr);
-    kk_launch_group<8>(g, p, xy, qbase, a8, a4, init, sweeps, nullptr);
-    kk_launch_group<4>(g, p, xy, qbase, a4, c1, init, sweeps, nullptr);
+    const int64_t a128 = first_at_most(g, c0, c1, 128), a64 = first_at_most(g, c0, c1, 64),
+                  a32 = first_at_most(g, c0, c1, 32), a16 = first_at_most(g, c0, c1, 16),
+                  a8 = first_at_most(g, c0, c1, 8), a4 = first_at_most(g, c0, c1, 4);
+    kk_launch_group<32, 8>(g, p, xy, qbase, c0, a128, init, sweeps, d_out);
+    kk_launch_group<32, 4>(g, p, xy, qbase, a128, a64, init, sweeps, d_out);
+    kk_launch_group<32, 2>(g, p, xy, qbase, a64, a32, init, sweeps, d_out);
+    kk_launch_group<16, 2>(g, p, xy, qbase, a32, a16, init, sweeps, d_out);
+    kk_launch_group<8, 2>(g, p, xy, qbase, a16, a8, init, sweeps, d_out);
+    kk_launch_group<4, 2>(g, p, xy, qbase, a8, a4, init, sweeps, d_out);
+    kk_launch_group<4, 1>(g, p, xy, qbase, a4, c1, init, sweeps, d_out);
 }
 
 void kk_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init) {
