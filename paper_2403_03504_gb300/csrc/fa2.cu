@@ -16,8 +16,8 @@
 //                     order) and updates s_G = min(tau trc / swg, 1.5 s_G)
 //   K4 update         s_n = ks s_G / (1 + s_G sqrt|F_t - F_{t-1}|), capped at
 //                     ksmax / |F_t|; p_n += s_n F_t; F_{t-1} <- F_t
-// The sequence has fixed launch shapes, so it is captured once into a CUDA
-// graph and replayed for every iteration.  Every sum has a fixed order, so
+// The sequence has fixed launch shapes, so it is captured once as the body of
+// a device-side WHILE loop in a CUDA graph: one launch runs all iterations.  Every sum has a fixed order, so
 // runs are bitwise reproducible.
 #include <cstring>
 
@@ -328,6 +328,7 @@ struct Fa2Run {
     DevBuf<double> sg;
     DevBuf<unsigned> counter;
     DevBuf<int> iter;
+    DevBuf<int> loop;              // iterations done by the device-side loop of one graph launch
     DevBuf<HeavyChunk> chunks;
     DevBuf<float2> chunk_part;
     DevBuf<int> chunk_arrive;
@@ -378,6 +379,7 @@ struct Fa2Run {
         BGL_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned), s));
         iter.reset(A, 1);
         BGL_CUDA(cudaMemsetAsync(iter.p, 0, sizeof(int), s));
+        loop.reset(A, 1);
         // nodes of high degree: chunks of HEAVY_CHUNK adjacency entries
         DevBuf<int32_t> flag(A, n), fscan(A, n), tot(A, 1);
         heavy_flag_kernel<<<nblocks(n, 256), 256, 0, s>>>(g->coff.p, q0, n, flag.p);
@@ -495,47 +497,79 @@ struct Fa2Run {
     }
 };
 
-// One iteration of `run` captured into a CUDA graph (nothing may allocate
-// while the capture is open), replayed `iters` times on the context stream.
+namespace {
+
+// End of a loop iteration: count it and keep looping while below `iters`.
+__global__ void loop_ctrl_kernel(cudaGraphConditionalHandle h, int *count, int iters) {
+    const int k = ++*count;
+    cudaGraphSetConditional(h, k < iters ? 1u : 0u);
+}
+
+}  // namespace
+
+// All `iters` iterations of `run` in one graph launch: the graph holds a
+// WHILE conditional node whose body is one captured iteration followed by a
+// one-thread kernel that counts the iterations and clears the condition
+// after the last, so the loop runs on the device without the host.
+// Nothing may allocate while the capture is open.
 static void run_iterations(Fa2Run &run, int iters, double *d_stats) {
+    if (iters <= 0) return;
     bgl_ctx *ctx = run.g->ctx;
     cudaStream_t s = ctx->stream;
     BGL_CUDA(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
     BGL_CUDA(cudaMemsetAsync(run.iter.p, 0, sizeof(int), s));
+    BGL_CUDA(cudaMemsetAsync(run.loop.p, 0, sizeof(int), s));
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    const int64_t before = launch_count();
-    BGL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    ctx->alloc->forbid = true;
+    BGL_CUDA(cudaGraphCreate(&graph, 0));
+    int64_t kernels = 0;
     try {
-        run.iteration(d_stats);
-    } catch (...) {
+        cudaGraphConditionalHandle h;
+        BGL_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        BGL_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        const int64_t before = launch_count();
+        BGL_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        ctx->alloc->forbid = true;
+        try {
+            run.iteration(d_stats);
+            loop_ctrl_kernel<<<1, 1, 0, s>>>(h, run.loop.p, iters);
+            BGL_LAUNCH_CHECK();
+        } catch (...) {
+            ctx->alloc->forbid = false;
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(s, &tmp);
+            throw;
+        }
         ctx->alloc->forbid = false;
-        cudaGraph_t tmp = nullptr;
-        cudaStreamEndCapture(s, &tmp);
-        if (tmp) cudaGraphDestroy(tmp);
+        cudaGraph_t captured = nullptr;
+        BGL_CUDA(cudaStreamEndCapture(s, &captured));
+        // captured launches run only when the graph does
+        count_launches(before - launch_count());
+        size_t nn = 0;
+        BGL_CUDA(cudaGraphGetNodes(body, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) BGL_CUDA(cudaGraphGetNodes(body, nodes.data(), &nn));
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            BGL_CUDA(cudaGraphNodeGetType(nd, &t));
+            if (t == cudaGraphNodeTypeKernel) ++kernels;
+        }
+        BGL_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    } catch (...) {
+        cudaGraphDestroy(graph);
         throw;
     }
-    ctx->alloc->forbid = false;
-    BGL_CUDA(cudaStreamEndCapture(s, &graph));
-    // captured launches run only when the graph is replayed
-    count_launches(before - launch_count());
-    size_t nn = 0;
-    int64_t kernels = 0;
-    BGL_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (nn) BGL_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
-    for (auto nd : nodes) {
-        cudaGraphNodeType t;
-        BGL_CUDA(cudaGraphNodeGetType(nd, &t));
-        if (t == cudaGraphNodeTypeKernel) ++kernels;
-    }
-    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
-    BGL_CUDA(e);
     count_launches(kernels * iters);
     try {
-        for (int it = 0; it < iters; ++it) BGL_CUDA(cudaGraphLaunch(exec, s));
+        BGL_CUDA(cudaGraphLaunch(exec, s));
     } catch (...) {
         cudaGraphExecDestroy(exec);
         throw;
