@@ -110,6 +110,9 @@ struct bgl_ctx {
     std::string last_error;
     int *d_flag = nullptr;        // device error/flag words (4 ints)
     int *h_flag = nullptr;        // pinned mirror
+    // autotuner choices: exact-repulsion targets per thread by log2 of the pairs
+    std::mutex tune_mu;
+    std::map<int, int> tune_exact;
 };
 
 namespace bgl {

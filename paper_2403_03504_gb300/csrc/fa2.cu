@@ -29,9 +29,7 @@ namespace bgl {
 
 namespace {
 
-constexpr int EX_THREADS = 256;
-constexpr int EX_R = 2;                        // targets per thread
-constexpr int EX_TILE = EX_THREADS * EX_R;     // targets per block
+constexpr int EX_THREADS = 256;                // a tile is EX_THREADS x R targets, R = 1, 2 or 4 (autotuned)
 constexpr int EX_STILE = 1024;                 // sources per shared-memory stage
 constexpr int HEAVY_DEG = 128;
 constexpr int HEAVY_CHUNK = 2048;              // adjacency entries per block for high-degree nodes
@@ -45,6 +43,7 @@ struct Tile {
 
 
 // K1 (exact): repulsion of every target in the tile from every node of its component
+template <int EX_R>
 __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
     const Tile *__restrict__ tiles, const int64_t *__restrict__ comp_off, int64_t c0, const float2 *__restrict__ xy,
     const float *__restrict__ mass, int64_t qbase, float kr, const float2 *__restrict__ fa, float2 *__restrict__ f) {
@@ -308,6 +307,89 @@ inline unsigned nblocks(int64_t n, int t) { return (unsigned)std::max<int64_t>(1
 
 }  // namespace
 
+static void launch_exact(int r, int ntiles, const Tile *tiles, const int64_t *comp_off, int64_t c0, const float2 *xy,
+                         const float *mass, int64_t qbase, float kr, const float2 *fa, float2 *f, cudaStream_t s) {
+    if (r == 1)
+        exact_repulsion_kernel<1><<<ntiles, EX_THREADS, 0, s>>>(tiles, comp_off, c0, xy, mass, qbase, kr, fa, f);
+    else if (r == 4)
+        exact_repulsion_kernel<4><<<ntiles, EX_THREADS, 0, s>>>(tiles, comp_off, c0, xy, mass, qbase, kr, fa, f);
+    else
+        exact_repulsion_kernel<2><<<ntiles, EX_THREADS, 0, s>>>(tiles, comp_off, c0, xy, mass, qbase, kr, fa, f);
+    BGL_LAUNCH_CHECK();
+}
+
+// tiles of EX_THREADS * r targets over the given components (indices >= c0)
+static std::vector<Tile> exact_tiles(const bgl_graph *g, int64_t c0, const std::vector<int64_t> &comps, int r) {
+    std::vector<Tile> ex;
+    const int64_t tile = (int64_t)EX_THREADS * r;
+    for (int64_t c : comps) {
+        const int64_t a = g->h_comp_off[c], b = g->h_comp_off[c + 1];
+        for (int64_t t = a; t < b; t += tile) ex.push_back(Tile{(int32_t)(c - c0), 0, t, std::min(b, t + tile)});
+    }
+    return ex;
+}
+
+// Autotuner of the exact tiles: the first time a context meets a set of
+// exact components of a given scale (log2 of the pairs of one evaluation),
+// each R in {1, 2, 4} is timed on one evaluation (after one warm-up launch),
+// and the fastest is kept for that scale.  Small sets (under 2^24 pairs)
+// take R = 2 untimed.
+static int exact_tile_choice(bgl_graph *g, const bgl_params *p, const std::vector<int64_t> &comps) {
+    if (comps.empty()) return 2;
+    double pairs = 0.0;
+    for (int64_t c : comps) {
+        const double n = (double)(g->h_comp_off[c + 1] - g->h_comp_off[c]);
+        pairs += n * n;
+    }
+    if (pairs < (double)(1 << 24)) return 2;
+    const int scale = (int)std::log2(pairs);
+    bgl_ctx *ctx = g->ctx;
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tune_exact.find(scale);
+        if (it != ctx->tune_exact.end()) return it->second;
+    }
+    cudaStream_t s = ctx->stream;
+    const int64_t c0 = comps.front();
+    const int64_t q0 = g->h_comp_off[c0], q1 = g->h_comp_off[comps.back() + 1];
+    DevBuf<float2> xy(ctx->alloc, q1 - q0), f(ctx->alloc, q1 - q0);
+    init_positions(g, p, xy.p, q0, q1);
+    cudaEvent_t e0, e1;
+    BGL_CUDA(cudaEventCreate(&e0));
+    BGL_CUDA(cudaEventCreate(&e1));
+    int best = 2;
+    float best_ms = 1e30f;
+    try {
+        for (int r : {1, 2, 4}) {
+            const std::vector<Tile> ex = exact_tiles(g, c0, comps, r);
+            DevBuf<Tile> tiles(ctx->alloc, ex.size());
+            BGL_CUDA(cudaMemcpyAsync(tiles.p, ex.data(), sizeof(Tile) * ex.size(), cudaMemcpyHostToDevice, s));
+            launch_exact(r, (int)ex.size(), tiles.p, g->comp_off.p, c0, xy.p, g->mass.p, q0, (float)p->kr, nullptr,
+                         f.p, s);
+            BGL_CUDA(cudaEventRecord(e0, s));
+            launch_exact(r, (int)ex.size(), tiles.p, g->comp_off.p, c0, xy.p, g->mass.p, q0, (float)p->kr, nullptr,
+                         f.p, s);
+            BGL_CUDA(cudaEventRecord(e1, s));
+            BGL_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BGL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = r;
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    ctx->tune_exact[scale] = best;
+    return best;
+}
+
 bool use_fmm(const bgl_params *p, int64_t n) {
     if (p->repulsion == BGL_REP_FMM) return true;
     if (p->repulsion == BGL_REP_EXACT) return false;
@@ -321,6 +403,7 @@ struct Fa2Run {
     float2 *xy;
     int64_t qbase, c0, c1, q0, q1;
     DevBuf<Tile> ex_tiles, red_tiles;
+    int ex_r = 2;                 // targets per thread of the exact tiles
     DevBuf<int64_t> red_tile_off;
     int n_ex_tiles = 0, n_red_tiles = 0;
     DevBuf<float2> f, fprev, fa;
@@ -346,6 +429,7 @@ struct Fa2Run {
         q1 = g->h_comp_off[c1];
         const int64_t n = q1 - q0;
         std::vector<Tile> ex, red;
+        std::vector<int64_t> ex_comps;
         std::vector<int64_t> roff(1, 0);
         for (int64_t c = c0; c < c1; ++c) {
             int64_t a = g->h_comp_off[c], b = g->h_comp_off[c + 1];
@@ -353,11 +437,13 @@ struct Fa2Run {
                 fmm.push_back(fmm_create(g, p, c));
                 fmm_comp.push_back(c);
             } else {
-                for (int64_t t = a; t < b; t += EX_TILE) ex.push_back(Tile{(int32_t)(c - c0), 0, t, std::min(b, t + EX_TILE)});
+                ex_comps.push_back(c);
             }
             for (int64_t t = a; t < b; t += RED_TILE) red.push_back(Tile{(int32_t)(c - c0), 0, t, std::min(b, t + RED_TILE)});
             roff.push_back((int64_t)red.size());
         }
+        ex_r = exact_tile_choice(g, p, ex_comps);
+        ex = exact_tiles(g, c0, ex_comps, ex_r);
         n_ex_tiles = (int)ex.size();
         n_red_tiles = (int)red.size();
         ex_tiles.reset(A, ex.size());
@@ -460,11 +546,8 @@ struct Fa2Run {
             fmm_repulsion(fmm[k], xy, qbase, f.p, q0, att ? fa.p : nullptr, att ? ev_fa : nullptr);
         if (att) BGL_CUDA(cudaStreamWaitEvent(s, ev_fa, 0));
         if (n_ex_tiles > 0) {
-            exact_repulsion_kernel<<<n_ex_tiles, EX_THREADS, 0, s>>>(ex_tiles.p, g->comp_off.p, c0, xy, g->mass.p,
-                                                                     qbase, (float)p->kr,
-                                                                     att ? fa.p - (q0 - qbase) : nullptr,
-                                                                     f.p - (q0 - qbase));
-            BGL_LAUNCH_CHECK();
+            launch_exact(ex_r, n_ex_tiles, ex_tiles.p, g->comp_off.p, c0, xy, g->mass.p, qbase, (float)p->kr,
+                         att ? fa.p - (q0 - qbase) : nullptr, f.p - (q0 - qbase), s);
         }
     }
 
