@@ -7,8 +7,10 @@ contraction) with numpy-facing functions, and composes them into the whole
 layout of Section 4 (``layout``) in plain Python.
 
 Paper map: Section 2 -> graph_build / undirected_csr; Section 4 ->
-components / component_order / layout; Section 3.1 -> bfs_apsp,
-floyd_warshall, kk_*; Section 3.2 -> fa2_forces, fa2_energy, fa2_run.
+components / component_order / layout, and the assembly of the component
+layouts into one frame -> assemble (meta_keys, meta_tree, tree_distances,
+kkw_*); Section 3.1 -> bfs_apsp, floyd_warshall, kk_*; Section 3.2 ->
+fa2_forces, fa2_energy, fa2_run.
 """
 from __future__ import annotations
 
@@ -63,6 +65,10 @@ def _load():
                 "orc_fa2_run": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D, _D, _D, _D, ctypes.c_int32,
                                  _I64, _VP, _VP, _VP, _VP], None),
                 "orc_threads": ([], ctypes.c_int),
+                "orc_kkw_energy": ([_I64, _VP, _VP, _VP], _D),
+                "orc_kkw_grad_hess": ([_I64, _VP, _VP, _VP, _I64, _VP], None),
+                "orc_kkw_run": ([_I64, _VP, _VP, _VP, _D, _I64, _VP], _I64),
+                "orc_tree_distances": ([_I64, _VP, _VP, _VP], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -333,3 +339,161 @@ def layout(g: Graph, kk_max_nodes=50, fa2_iters=50, kr=1.0, kg=1.0, ks=0.1, ksma
         xy[vs, 0] = x
         xy[vs, 1] = y
     return xy
+
+
+# ---------------------------------------------------------------- Section 4: assembly
+
+KAPPA = 1.0                       # the "constant" added to every meta-edge length
+META_SALT = 0x5851F42D4C957F2D    # separates the order stream from the position streams
+
+
+def kkw_energy(x, y, d) -> float:
+    return float(_load().orc_kkw_energy(len(x), _p(_c(x, np.float64)), _p(_c(y, np.float64)), _p(_c(d, np.float64))))
+
+
+def kkw_grad_hess(x, y, d, m):
+    out = np.zeros(5)
+    _load().orc_kkw_grad_hess(len(x), _p(_c(x, np.float64)), _p(_c(y, np.float64)), _p(_c(d, np.float64)), m,
+                              _p(out))
+    return out
+
+
+def kkw_run(x, y, d, cap, sweeps):
+    """Returns (x, y, energy_per_sweep); inputs are not modified."""
+    x = np.array(x, np.float64)
+    y = np.array(y, np.float64)
+    e = np.zeros(max(sweeps, 1))
+    _load().orc_kkw_run(len(x), _p(x), _p(y), _p(_c(d, np.float64)), cap, sweeps, _p(e))
+    return x, y, e[:sweeps].copy()
+
+
+def tree_distances(parent, length):
+    parent = _c(parent, np.int64)
+    m = len(parent)
+    d = np.zeros((m, m))
+    _load().orc_tree_distances(m, _p(parent), _p(_c(length, np.float64)), _p(d))
+    return d
+
+
+def meta_keys(seed, n):
+    """Random order of the components (Section 4): key of component c is the
+    first SplitMix64 output from state (seed ^ META_SALT) ^ (c * 0x9E3779B97F4A7C15)."""
+    keys = np.zeros(n, np.uint64)
+    base = (int(seed) ^ META_SALT) & 0xFFFFFFFFFFFFFFFF
+    for c in range(n):
+        st = base ^ ((c * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF)
+        keys[c] = splitmix64_stream(st, 1)[0]
+    return keys
+
+
+def meta_tree(sizes):
+    """Each item after the first is linked to the largest earlier item (the
+    first of equals); returns parent indices (-1 for item 0)."""
+    parent = np.full(len(sizes), -1, np.int64)
+    best = 0
+    for k in range(1, len(sizes)):
+        parent[k] = best
+        if sizes[k] > sizes[best]:
+            best = k
+    return parent
+
+
+def assemble(off, adj, comp_off, nodes, xy, K, seed=0, sweeps=200, kappa=KAPPA):
+    """Assembly of per-component layouts into one frame (Section 4).
+
+    1. Rescale: each component is centred on its centroid and scaled so that
+       its mean edge length is 1 (no edges: scale 1); its radius is the
+       largest distance of a node from the centroid after scaling.
+    2. Order: components sorted by meta_keys (random order).
+    3. Levels: the ordered items are cut into consecutive chunks of at most
+       K; in a chunk each item links to the largest earlier one (size =
+       nodes), with edge length r_a + r_b + kappa (half the diameters plus a
+       constant); Kamada-Kawai on the chunk's weighted tree (path lengths as
+       distances, init SplitMix64 by item index with seed + level + 1,
+       scaled by half the largest distance, steps capped at the mean edge
+       length) gives item centres; the chunk is centred on their mean and
+       becomes one item of the next level with radius max(|centre| + r) and
+       size the sum.  Repeat until one item is left.
+    4. Compose: a node's position is its scaled local position plus the
+       offset of every item containing it.
+    Returns dict(xy, rank, parent0, scale, centroid, radius, levels) where
+    levels[L] = dict(parent, length, centres, offsets, radius, size)."""
+    C = len(comp_off) - 1
+    xy = np.asarray(xy, np.float64)
+    scale = np.ones(C)
+    centroid = np.zeros((C, 2))
+    radius = np.zeros(C)
+    sizes = np.diff(comp_off).astype(np.int64)
+    local = np.zeros_like(xy)
+    for c in range(C):
+        vs = nodes[comp_off[c]:comp_off[c + 1]]
+        p = xy[vs]
+        tot, cnt = 0.0, 0
+        for v in vs:
+            for w in adj[off[v]:off[v + 1]]:
+                if w > v:
+                    tot += float(np.hypot(*(xy[v] - xy[w])))
+                    cnt += 1
+        if cnt > 0 and tot > 0.0:
+            scale[c] = cnt / tot
+        centroid[c] = p.mean(0)
+        q = (p - centroid[c]) * scale[c]
+        local[vs] = q
+        radius[c] = float(np.max(np.hypot(q[:, 0], q[:, 1]))) if len(vs) > 0 else 0.0
+    order = np.lexsort((np.arange(C), meta_keys(seed, C)))   # by key, then index
+    rank = np.empty(C, np.int64)
+    rank[order] = np.arange(C)
+    item_r = radius[order].copy()
+    item_n = sizes[order].copy()
+    levels = []
+    parent0 = None
+    level = 0
+    while len(item_r) > 1 or level == 0:
+        m_all = len(item_r)
+        parent = np.full(m_all, -1, np.int64)
+        length = np.zeros(m_all)
+        offsets = np.zeros((m_all, 2))
+        centres = np.zeros((m_all, 2))
+        nxt_r, nxt_n = [], []
+        for a in range(0, m_all, K):
+            b = min(m_all, a + K)
+            m = b - a
+            par = meta_tree(item_n[a:b])
+            ln = np.zeros(m)
+            for k in range(1, m):
+                ln[k] = item_r[a + k] + item_r[a + par[k]] + kappa
+            parent[a:b] = np.where(par >= 0, par + a, -1)
+            length[a:b] = ln
+            if m == 1:
+                q = np.zeros((1, 2))
+            else:
+                d = tree_distances(par, ln)
+                x, y = init_positions(seed + level + 1, np.arange(a, b))
+                half = d.max() / 2.0
+                cap = ln[1:].mean()
+                x, y, _ = kkw_run(x * half, y * half, d, cap, sweeps)
+                q = np.stack([x, y], 1)
+            centres[a:b] = q
+            ctr = q.mean(0)
+            offsets[a:b] = q - ctr
+            nxt_r.append(float(np.max(np.hypot(*(q - ctr).T) + item_r[a:b])))
+            nxt_n.append(int(item_n[a:b].sum()))
+        levels.append(dict(parent=parent, length=length, centres=centres, offsets=offsets,
+                           radius=item_r.copy(), size=item_n.copy()))
+        if level == 0:
+            parent0 = parent
+        item_r = np.array(nxt_r)
+        item_n = np.array(nxt_n, np.int64)
+        level += 1
+        if len(item_r) == 1:
+            break
+    out = local.copy()
+    for c in range(C):
+        vs = nodes[comp_off[c]:comp_off[c + 1]]
+        idx = rank[c]
+        shift = np.zeros(2)
+        for L in range(len(levels)):
+            shift += levels[L]["offsets"][idx]
+            idx //= K
+        out[vs] += shift
+    return dict(xy=out, rank=rank, parent0=parent0, scale=scale, centroid=centroid, radius=radius, levels=levels)

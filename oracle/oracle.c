@@ -475,6 +475,94 @@ int64_t orc_kk_run(int64_t n, double *x, double *y, const int32_t *d, double l, 
 }
 
 /* ------------------------------------------------------------------ */
+/* Section 4: assembly of the component layouts                          */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Kamada-Kawai on a graph whose pair distances d_ij are real (the path
+ * lengths of the weighted tree of components): energy
+ *   E = sum_{i<j} d_ij^-2 (|p_i - p_j| - d_ij)^2,
+ * i.e. the Section 3.1 energy with l d_ij replaced by the weighted d_ij.
+ */
+double orc_kkw_energy(int64_t n, const double *x, const double *y, const double *d)
+{
+    double e = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dij = d[i * n + j];
+            if (!(dij > 0.0)) continue;
+            double t = hypot(x[i] - x[j], y[i] - y[j]) - dij;
+            e += t * t / (dij * dij);
+        }
+    return e;
+}
+
+/* half-gradient and half-Hessian with respect to p_m, as orc_kk_grad_hess
+   with k = d_mi^-2 and l_mi = d_mi */
+void orc_kkw_grad_hess(int64_t n, const double *x, const double *y, const double *d, int64_t m, double *out)
+{
+    double gx = 0, gy = 0, hxx = 0, hxy = 0, hyy = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (i == m) continue;
+        double dmi = d[m * n + i];
+        if (!(dmi > 0.0)) continue;
+        double dx = x[m] - x[i], dy = y[m] - y[i];
+        double r = sqrt(dx * dx + dy * dy);
+        if (r == 0.0) continue;
+        double k = 1.0 / (dmi * dmi);
+        double r3 = r * r * r;
+        gx += k * (dx - dmi * dx / r);
+        gy += k * (dy - dmi * dy / r);
+        hxx += k * (1.0 - dmi * dy * dy / r3);
+        hyy += k * (1.0 - dmi * dx * dx / r3);
+        hxy += k * dmi * dx * dy / r3;
+    }
+    out[0] = gx; out[1] = gy; out[2] = hxx; out[3] = hxy; out[4] = hyy;
+}
+
+/* Gauss-Seidel sweeps of the safeguarded Newton step (orc_kk_step), steps
+   capped at `cap`; returns the node steps skipped */
+int64_t orc_kkw_run(int64_t n, double *x, double *y, const double *d, double cap, int64_t sweeps, double *energy)
+{
+    int64_t skipped = 0;
+    for (int64_t s = 0; s < sweeps; ++s) {
+        for (int64_t m = 0; m < n; ++m) {
+            double o[5], dxm, dym;
+            orc_kkw_grad_hess(n, x, y, d, m, o);
+            if (!orc_kk_step(o, cap, &dxm, &dym)) { ++skipped; continue; }
+            x[m] += dxm;
+            y[m] += dym;
+        }
+        if (energy) energy[s] = orc_kkw_energy(n, x, y, d);
+    }
+    return skipped;
+}
+
+/*
+ * Path lengths in a tree given by parent links (parent[k] < k, -1 for the
+ * root k = 0) and edge lengths len[k] (edge k - parent[k]): d[i * m + j],
+ * by walking from every node, plainly O(m^2).
+ */
+void orc_tree_distances(int64_t m, const int64_t *parent, const double *len, double *d)
+{
+    for (int64_t i = 0; i < m * m; ++i) d[i] = -1.0;
+    for (int64_t s = 0; s < m; ++s) {
+        d[s * m + s] = 0.0;
+        /* repeat relaxations along tree edges until nothing changes */
+        int changed = 1;
+        while (changed) {
+            changed = 0;
+            for (int64_t k = 1; k < m; ++k) {
+                int64_t p = parent[k];
+                double a = d[s * m + k], b = d[s * m + p];
+                if (b >= 0.0 && a < 0.0) { d[s * m + k] = b + len[k]; changed = 1; }
+                if (a >= 0.0 && b < 0.0) { d[s * m + p] = a + len[k]; changed = 1; }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Section 3.2: ForceAtlas2 forces                                      */
 /* ------------------------------------------------------------------ */
 

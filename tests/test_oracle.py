@@ -418,3 +418,125 @@ def test_layout_c1_shapes():
     label, _ = oracle.components(g.off, g.adj)
     iso = np.diff(g.off) == 0
     assert np.all(xy[iso] == 0)
+
+
+# ------------------------------------------------------------- Section 4 assembly
+
+def test_meta_tree_golden():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "meta_tree.json")) as f:
+        gold = json.load(f)
+    assert oracle.meta_tree(np.array(gold["sizes"])).tolist() == gold["parents"]
+
+
+def test_meta_tree_brute_force():
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        sizes = rng.integers(1, 6, rng.integers(1, 12))
+        par = oracle.meta_tree(sizes)
+        for k in range(1, len(sizes)):
+            best = max(sizes[:k])
+            assert par[k] == min(j for j in range(k) if sizes[j] == best)
+
+
+def test_tree_distances_vs_scipy():
+    sp = pytest.importorskip("scipy.sparse.csgraph")
+    from scipy.sparse import coo_matrix
+    rng = np.random.default_rng(5)
+    for m in (1, 2, 7, 30):
+        parent = np.array([-1] + [int(rng.integers(0, k)) for k in range(1, m)])
+        length = np.concatenate([[0.0], rng.uniform(0.5, 4.0, m - 1)])
+        d = oracle.tree_distances(parent, length)
+        if m > 1:
+            a = coo_matrix((length[1:], (np.arange(1, m), parent[1:])), shape=(m, m)).tocsr()
+            ref = sp.shortest_path(a, directed=False)
+        else:
+            ref = np.zeros((1, 1))
+        assert np.allclose(d, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_kkw_equals_kk_on_integer_distances():
+    # with l = 1 and hop distances the weighted energy is the Section 3.1 energy
+    sizes, u, v = synth.forest(23, 3, 6.0, 30.0)
+    g = oracle.graph_from_edges(int(sizes.sum()), u, v)
+    label, _ = oracle.components(g.off, g.adj)
+    comp_off, _, nodes = oracle.component_order(label)
+    vs = nodes[comp_off[0]:comp_off[1]]
+    loff, ladj = oracle.subgraph(g.off, g.adj, vs)
+    d = oracle.bfs_apsp(loff, ladj)
+    x, y = oracle.init_positions(2, vs)
+    sc = d.max() / 2
+    a = oracle.kk_run(x * sc, y * sc, d, 1.0, 15)
+    b = oracle.kkw_run(x * sc, y * sc, d.astype(np.float64), 1.0, 15)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_kkw_gradient_vs_finite_differences():
+    rng = np.random.default_rng(8)
+    parent = np.array([-1, 0, 0, 1, 1, 2])
+    length = np.array([0.0, 2.0, 3.5, 1.0, 4.0, 2.5])
+    d = oracle.tree_distances(parent, length)
+    x, y = rng.normal(0, 3, 6), rng.normal(0, 3, 6)
+    h = 1e-6
+    for m in range(6):
+        g = oracle.kkw_grad_hess(x, y, d, m)
+        for axis, gi in ((x, 0), (y, 1)):
+            axis[m] += h
+            ep = oracle.kkw_energy(x, y, d)
+            axis[m] -= 2 * h
+            em = oracle.kkw_energy(x, y, d)
+            axis[m] += h
+            # g is half the gradient
+            assert abs((ep - em) / (2 * h) / 2 - g[gi]) <= 1e-5 * (1 + abs(g[gi]))
+
+
+def test_kkw_weighted_path_is_realised_exactly():
+    parent = np.array([-1, 0, 1, 2])
+    length = np.array([0.0, 2.0, 3.0, 0.5])
+    d = oracle.tree_distances(parent, length)
+    x, y = oracle.init_positions(4, np.arange(4))
+    x, y, e = oracle.kkw_run(x * 3, y * 3, d, length[1:].mean(), 300)
+    assert e[-1] <= 1e-18 + 1e-12 * e[0]
+    r = np.hypot(x[:, None] - x[None], y[:, None] - y[None])
+    assert np.allclose(r, d, rtol=1e-6, atol=1e-8)
+
+
+def _forest_layout(seed, n_comp, lo, hi):
+    sizes, u, v = synth.forest(seed, n_comp, lo, hi)
+    g = oracle.graph_from_edges(int(sizes.sum()), u, v)
+    label, _ = oracle.components(g.off, g.adj)
+    comp_off, _, nodes = oracle.component_order(label)
+    xy = np.random.default_rng(seed).normal(0, 5, (g.n_nodes, 2))
+    return g, comp_off, nodes, xy
+
+
+def test_assembly_keeps_component_shapes_at_unit_mean_edge():
+    g, comp_off, nodes, xy = _forest_layout(31, 40, 1.0, 25.0)
+    out = oracle.assemble(g.off, g.adj, comp_off, nodes, xy, K=8, sweeps=50)
+    for c in range(len(comp_off) - 1):
+        vs = nodes[comp_off[c]:comp_off[c + 1]]
+        # a translation of the rescaled component: differences scale exactly
+        diff_in = xy[vs] - xy[vs[0]]
+        diff_out = out["xy"][vs] - out["xy"][vs[0]]
+        assert np.allclose(diff_out, diff_in * out["scale"][c], rtol=1e-9, atol=1e-9)
+        lens = [np.hypot(*(out["xy"][a] - out["xy"][b])) for a in vs for b in g.adj[g.off[a]:g.off[a + 1]] if b > a]
+        if lens:
+            assert abs(np.mean(lens) - 1.0) <= 1e-12
+    # the order is a permutation sorted by the keys
+    keys = oracle.meta_keys(0, len(comp_off) - 1)
+    order = np.argsort(out["rank"])
+    assert sorted(out["rank"].tolist()) == list(range(len(comp_off) - 1))
+    assert np.all(np.diff(keys[order].astype(np.float64)) >= 0)
+    assert len(out["levels"]) >= 2           # 40 components in chunks of 8: more than one level
+
+
+def test_assembly_of_two_components_places_them_at_the_edge_length():
+    # two components: one meta-edge, KK on two nodes reaches its length exactly
+    u = np.array([0, 1, 3, 4, 5]); v = np.array([1, 2, 4, 5, 3])
+    g = oracle.graph_from_edges(6, u, v)
+    label, _ = oracle.components(g.off, g.adj)
+    comp_off, _, nodes = oracle.component_order(label)
+    xy = np.random.default_rng(2).normal(0, 1, (6, 2))
+    out = oracle.assemble(g.off, g.adj, comp_off, nodes, xy, K=50, sweeps=100)
+    cen = [out["xy"][nodes[comp_off[c]:comp_off[c + 1]]].mean(0) for c in range(2)]
+    want = out["radius"][0] + out["radius"][1] + oracle.KAPPA
+    assert abs(np.hypot(*(cen[0] - cen[1])) - want) <= 1e-9 * want
