@@ -94,6 +94,9 @@ typedef struct bgl_params {
     int32_t kk_sweeps;      /* KK sweeps                                         default 200 */
     double kk_l;            /* KK edge length l                                  default 1 */
     double kk_tol;          /* KK early-stop gradient norm, 0 = fixed sweeps     default 0 */
+    int32_t assemble;       /* 1: bgl_layout assembles the component layouts into one frame
+                               (Section 4, see bgl_assemble); 0: each in its own frame default 0 */
+    int32_t pad0;
 } bgl_params;
 
 /* ---------------------------------------------------------------- context */
@@ -225,6 +228,36 @@ bgl_status bgl_fa2_repulsion(bgl_graph *g, int64_t c, const bgl_params *p, const
  * iteration. */
 bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t iters, float *xy_inout,
                         double *stats_out);
+
+/* ---------------------------------------------------------------- assembly */
+
+/*
+ * Assembly of per-component layouts into one frame (Section 4): each
+ * component is centred on its centroid and rescaled to mean edge length 1
+ * (components without edges keep their scale); the components are put in a
+ * random order (SplitMix64 key per component index, seed p->seed); in
+ * consecutive runs ("pieces") of at most p->kk_max_nodes, each is linked to
+ * the largest earlier one of its run (the first of equals), by an edge of
+ * length r_a + r_b + 1 (r = largest distance of a node from the centroid
+ * after rescaling, i.e. half the diameter); Kamada-Kawai (p->kk_sweeps
+ * sweeps of Section 3.1's safeguarded Newton step, with the weighted path
+ * lengths as distances, steps capped at the run's mean edge length) places
+ * the run's components; each run, centred on the mean of its components'
+ * centres, becomes one item of the next level, which repeats until one item
+ * is left.  A node's position is its rescaled local position plus the
+ * offsets of the items holding it.
+ *
+ * xy_in[2 n_nodes]: per-component layouts in node-id order (as bgl_layout
+ * returns them); xy_out[2 n_nodes]: the assembled frame.  Optional outputs
+ * (NULL to skip), per component in component order: rank_out[n_comp] its
+ * place in the random order; parent_out[n_comp] (indexed by rank) the rank of
+ * the component it is linked to in its run, -1 for a run's first;
+ * scale_out, radius_out[n_comp]; centre_out[2 n_comp] (indexed by rank) its
+ * centre in its run's Kamada-Kawai layout before centring.  Needs
+ * bgl_components.  Synchronises the stream.
+ */
+bgl_status bgl_assemble(bgl_graph *g, const bgl_params *p, const float *xy_in, float *xy_out, int64_t *rank_out,
+                        int64_t *parent_out, float *scale_out, float *radius_out, float *centre_out);
 
 /* ------------------------------------------ resumable runs and checkpoints */
 

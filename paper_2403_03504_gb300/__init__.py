@@ -50,6 +50,8 @@ class Params(ctypes.Structure):
         ("kk_sweeps", ctypes.c_int32),
         ("kk_l", ctypes.c_double),
         ("kk_tol", ctypes.c_double),
+        ("assemble", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -107,6 +109,7 @@ def _load():
         "bgl_fa2_session_advance": ([VP, I32, VP], I32),
         "bgl_fa2_session_positions": ([VP, VP, P64], I32),
         "bgl_state_save": ([VP, VP, ctypes.POINTER(ctypes.c_size_t)], I32),
+        "bgl_assemble": ([VP, ctypes.POINTER(Params), VP, VP, VP, VP, VP, VP, VP], I32),
         "bgl_state_load": ([VP, VP, ctypes.c_size_t], I32),
         "bgl_fmm_stats": ([VP, I64, ctypes.POINTER(Params), VP, I32, VP], I32),
         "bgl_launch_count": ([], I64),
@@ -359,6 +362,22 @@ class Graph:
         stats = np.zeros((max(iters, 1), 3))
         self.ctx.check(self._lib.bgl_fa2_step(self.h, c, ctypes.byref(p), iters, _hp(xy), _hp(stats)))
         return xy, stats[:iters]
+
+    def assemble(self, p: Params, xy):
+        """Assembly of per-component layouts (node-id order) into one frame
+        (Section 4); returns (xy, info) with per-component rank, parent (by
+        rank), scale, radius and level-0 centres (by rank)."""
+        xy = _arr(xy, np.float32)
+        nc = self.n_comp
+        out = np.zeros_like(xy)
+        rank = np.zeros(nc, np.int64)
+        parent = np.zeros(nc, np.int64)
+        scale = np.zeros(nc, np.float32)
+        radius = np.zeros(nc, np.float32)
+        centre = np.zeros((nc, 2), np.float32)
+        self.ctx.check(self._lib.bgl_assemble(self.h, ctypes.byref(p), _hp(xy), _hp(out), _hp(rank), _hp(parent),
+                                              _hp(scale), _hp(radius), _hp(centre)))
+        return out, dict(rank=rank, parent=parent, scale=scale, radius=radius, centre=centre)
 
     # resumable ForceAtlas2 run and its checkpoint
     def session_begin(self, c: int, p: Params, xy) -> None:

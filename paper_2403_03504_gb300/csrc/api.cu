@@ -93,6 +93,7 @@ void check_params(const bgl_params *p) {
     BGL_REQUIRE(p->kk_sweeps >= 0, "kk_sweeps must be >= 0");
     BGL_REQUIRE(p->kk_l > 0, "kk_l must be > 0");
     BGL_REQUIRE(p->kk_tol >= 0, "kk_tol must be >= 0");
+    BGL_REQUIRE(p->assemble == 0 || p->assemble == 1, "assemble must be 0 or 1");
 }
 
 }  // namespace bgl
@@ -169,11 +170,19 @@ void layout_device(bgl_graph *g, const bgl_params *p, float *d_xy_out) {
         init_positions(g, p, xy.p, 0, q_fa2);
         fa2_layout(g, p, xy.p, 0, 0, g->n_fa2, p->fa2_iters, nullptr);
     }
-    if (g->n > 0) {
+    if (g->n > 0 && p->assemble) {
+        assemble_device(g, p, xy.p, reinterpret_cast<float2 *>(d_xy_out), nullptr);
+    } else if (g->n > 0) {
         scatter_xy_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, c->stream>>>(xy.p, g->nodes.p, g->n,
                                                                                  reinterpret_cast<float2 *>(d_xy_out));
         BGL_LAUNCH_CHECK();
     }
+}
+
+__global__ void gather_xy_kernel(const float2 *__restrict__ xy_nodes, const int32_t *__restrict__ nodes, int64_t n,
+                                 float2 *__restrict__ out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = xy_nodes[nodes[q]];
 }
 
 }  // namespace
@@ -500,6 +509,39 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
         d2h(g->ctx, reinterpret_cast<float2 *>(xy_inout), xy.p, n);
         if (stats_out) d2h(g->ctx, stats_out, st.p, 3 * (size_t)iters);
         sync(g->ctx);
+    });
+}
+
+bgl_status bgl_assemble(bgl_graph *g, const bgl_params *p, const float *xy_in, float *xy_out, int64_t *rank_out,
+                        int64_t *parent_out, float *scale_out, float *radius_out, float *centre_out) {
+    if (!g || !xy_in || !xy_out) return BGL_EINVAL;
+    return guarded(g->ctx, [&] {
+        check_params(p);
+        require_comp(g);
+        bgl_ctx *c = g->ctx;
+        DevBuf<float2> in(c->alloc, std::max<int64_t>(g->n, 1)), comp(c->alloc, std::max<int64_t>(g->n, 1)),
+            out(c->alloc, std::max<int64_t>(g->n, 1));
+        h2d(c, in.p, reinterpret_cast<const float2 *>(xy_in), g->n);
+        if (g->n > 0) {
+            gather_xy_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, c->stream>>>(in.p, g->nodes.p, g->n, comp.p);
+            BGL_LAUNCH_CHECK();
+        }
+        AssemblyOut info;
+        assemble_device(g, p, comp.p, out.p, &info);
+        d2h(c, reinterpret_cast<float2 *>(xy_out), out.p, g->n);
+        sync(c);
+        const int64_t C = g->n_comp;
+        if (C > 0 && !info.rank.empty()) {
+            if (rank_out) std::copy(info.rank.begin(), info.rank.end(), rank_out);
+            if (parent_out) std::copy(info.parent0.begin(), info.parent0.end(), parent_out);
+            if (scale_out) std::copy(info.scale.begin(), info.scale.end(), scale_out);
+            if (radius_out) std::copy(info.radius.begin(), info.radius.end(), radius_out);
+            if (centre_out)
+                for (int64_t i = 0; i < C; ++i) {
+                    centre_out[2 * i] = info.centre0[i].x;
+                    centre_out[2 * i + 1] = info.centre0[i].y;
+                }
+        }
     });
 }
 

@@ -223,6 +223,19 @@ void kk_distances(bgl_graph *g, int64_t c, int32_t *d_out_dev);
 // null): swing, traction, s_G per iteration of component c0.
 void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
                 double *d_stats);
+// Assembly of the component layouts into one frame (assemble.cu, Section 4):
+// xy_comp[q] the per-component layout at component-order position q,
+// xy_out the assembled frame in node-id order; info (may be null) receives
+// per-component results for parity checks.
+struct AssemblyOut {
+    int levels = 0;
+    std::vector<int64_t> rank, parent0;
+    std::vector<float> scale, radius;
+    std::vector<float2> centre0;
+};
+void assemble_device(bgl_graph *g, const bgl_params *p, const float2 *xy_comp, float2 *xy_out_nodes,
+                     AssemblyOut *info);
+
 // Resumable ForceAtlas2 run on one component (fa2.cu): positions,
 // F_{t-1}, s_G and the iteration count stay on the device between calls.
 Fa2Session *fa2_session_create(bgl_graph *g, const bgl_params *p, int64_t c, const float2 *h_xy);
