@@ -422,6 +422,22 @@ def main():
     torch.cuda.synchronize()
     p16_s = time.perf_counter() - t0
 
+    # the assembly into one frame (Section 4): the same layout with and without it
+    p_asm = bgl.params(**{k: getattr(p, k) for k, _ in bgl.Params._fields_})
+    p_asm.assemble = 1
+    asm_ms = []
+    for params_k in (p, p_asm, p, p_asm):
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a_ev.record(stream)
+        g0.layout_dev(params_k, d_xy)
+        with torch.cuda.stream(stream):
+            b_ev.record(stream)
+        torch.cuda.synchronize()
+        asm_ms.append(a_ev.elapsed_time(b_ev))
+    assembly = {"ms": 0.5 * ((asm_ms[1] - asm_ms[0]) + (asm_ms[3] - asm_ms[2])), "components": int(len(coff) - 1),
+                "kk_max_nodes": int(p.kk_max_nodes)}
+
     clocks = clk.summary()
     if rank != 0:
         if dist:
@@ -449,6 +465,7 @@ def main():
         "force_error": {"reference": "GPU FP32 exact sum at the final layout", **errs},
         "exact_fa2": {"value": exact_rate, "unit": UNIT, "iters": args.exact_iters, "nodes": giant},
         "fmm_p16_step_ms": 1e3 * p16_s,
+        "assembly": assembly,
         "fmm_profile": stats,
         "clocks": clocks,
         "cpu_baseline": cpu,
