@@ -40,15 +40,16 @@ constexpr float KAPPA = 1.0f;                              // added to every met
 constexpr uint64_t META_SALT = 0x5851F42D4C957F2Dull;      // order stream, apart from position streams
 constexpr int ASM_MAX_K = 255;
 
-// per component (component order): centroid, scale, radius
-__global__ void __launch_bounds__(256) comp_stats_kernel(const float2 *__restrict__ xy, const int64_t *__restrict__ comp_off,
-                                                         const int64_t *__restrict__ coff,
-                                                         const int32_t *__restrict__ cadj, double2 *centroid,
-                                                         float *scale, float *radius, int64_t *size) {
-    const int64_t c = blockIdx.x;
+// per component (component order) from c0 on, one block each: centroid,
+// scale, radius.  Edge lengths in FP32, sums in FP64 (a fixed order).
+__global__ void __launch_bounds__(1024) comp_stats_kernel(const float2 *__restrict__ xy, const int64_t *__restrict__ comp_off,
+                                                          int64_t c0, const int64_t *__restrict__ coff,
+                                                          const int32_t *__restrict__ cadj, double2 *centroid,
+                                                          float *scale, float *radius, int64_t *size) {
+    const int64_t c = c0 + blockIdx.x;
     const int64_t q0 = comp_off[c], q1 = comp_off[c + 1];
-    __shared__ double red[3][8];
-    __shared__ float redf[8];
+    __shared__ double red[3][32];
+    __shared__ float redf[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double sx = 0.0, sy = 0.0, sl = 0.0;
     for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
@@ -57,7 +58,8 @@ __global__ void __launch_bounds__(256) comp_stats_kernel(const float2 *__restric
         sy += p.y;
         for (int64_t e = coff[q]; e < coff[q + 1]; ++e) {
             const float2 o = xy[cadj[e]];
-            sl += hypot((double)p.x - (double)o.x, (double)p.y - (double)o.y);
+            const float dx = p.x - o.x, dy = p.y - o.y;
+            sl += (double)sqrtf(fmaf(dx, dx, dy * dy));
         }
     }
 #pragma unroll
@@ -136,8 +138,12 @@ struct ChunkArgs {
     int sweeps;
 };
 
-// One warp per chunk.
+// One warp per chunk; with K <= ASM_SMEM_K the chunk's distance matrix is
+// kept in dynamic shared memory (K * K floats per warp), else in a.dist.
+constexpr int ASM_SMEM_K = 64;
+
 __global__ void __launch_bounds__(128) chunk_kernel(ChunkArgs a) {
+    extern __shared__ float s_dist[];
     __shared__ int s_par[4][ASM_MAX_K + 1];
     __shared__ float s_len[4][ASM_MAX_K + 1];
     __shared__ float s_root[4][ASM_MAX_K + 1];       // path length from the chunk's first item
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(128) chunk_kernel(ChunkArgs a) {
     for (int k = lane; k < m; k += 32) a.parent[a0 + k] = par[k] >= 0 ? a0 + par[k] : -1;
     // path lengths d(s, k): along the parent links, d(s, k) = d(s, par k) + len k
     // unless k is an ancestor of s (then root[s] - root[k])
-    float *d = a.dist + chunk * (int64_t)a.K * a.K;
+    float *d = a.K <= ASM_SMEM_K ? s_dist + (size_t)wib * a.K * a.K : a.dist + chunk * (int64_t)a.K * a.K;
     float dmax = 0.f;
     for (int s = lane; s < m; s += 32) {
         float *row = d + (int64_t)s * m;
@@ -296,9 +302,19 @@ void assemble_device(bgl_graph *g, const bgl_params *p, const float2 *xy_comp, f
     DevBuf<double2> centroid(A, C);
     DevBuf<float> scale(A, C), radius(A, C);
     DevBuf<int64_t> size(A, C), rank(A, C);
-    comp_stats_kernel<<<(unsigned)C, 256, 0, s>>>(xy_comp, g->comp_off.p, g->coff.p, g->cadj.p, centroid.p, scale.p,
-                                                 radius.p, size.p);
-    BGL_LAUNCH_CHECK();
+    // components in descending size: the large ones get 1024 threads
+    int64_t nbig = 0;
+    while (nbig < C && g->h_comp_off[nbig + 1] - g->h_comp_off[nbig] > 4096) ++nbig;
+    if (nbig > 0) {
+        comp_stats_kernel<<<(unsigned)nbig, 1024, 0, s>>>(xy_comp, g->comp_off.p, 0, g->coff.p, g->cadj.p, centroid.p,
+                                                         scale.p, radius.p, size.p);
+        BGL_LAUNCH_CHECK();
+    }
+    if (C > nbig) {
+        comp_stats_kernel<<<(unsigned)(C - nbig), 128, 0, s>>>(xy_comp, g->comp_off.p, nbig, g->coff.p, g->cadj.p,
+                                                              centroid.p, scale.p, radius.p, size.p);
+        BGL_LAUNCH_CHECK();
+    }
     DevBuf<uint64_t> keys(A, C);
     DevBuf<uint32_t> order(A, C);
     meta_keys_kernel<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(C, p->seed, keys.p, order.p);
@@ -318,7 +334,11 @@ void assemble_device(bgl_graph *g, const bgl_params *p, const float2 *xy_comp, f
     meta_items_kernel<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(C, order.p, radius.p, size.p, rank.p, ir.p, in.p);
     BGL_LAUNCH_CHECK();
     const int64_t max_chunks = (C + K - 1) / K;
-    DevBuf<float> dist(A, max_chunks * (int64_t)K * K);
+    const bool sdist = K <= ASM_SMEM_K;
+    DevBuf<float> dist(A, sdist ? 1 : max_chunks * (int64_t)K * K);
+    const size_t chunk_smem = sdist ? sizeof(float) * 4 * (size_t)K * K : 0;
+    // the static arrays plus this can pass the 48 KB default
+    BGL_CUDA(cudaFuncSetAttribute(chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chunk_smem));
     for (int L = 0; L < levels; ++L) {
         const int64_t m = counts[L], chunks = (m + K - 1) / K;
         ChunkArgs a;
@@ -334,7 +354,7 @@ void assemble_device(bgl_graph *g, const bgl_params *p, const float2 *xy_comp, f
         a.centre = L == 0 ? centre0.p : nullptr;
         a.seed = p->seed + (uint64_t)L + 1;
         a.sweeps = p->kk_sweeps;
-        chunk_kernel<<<(unsigned)((chunks + 3) / 4), 128, 0, s>>>(a);
+        chunk_kernel<<<(unsigned)((chunks + 3) / 4), 128, chunk_smem, s>>>(a);
         BGL_LAUNCH_CHECK();
         std::swap(ir, nr);
         std::swap(in, nnext);
