@@ -259,6 +259,54 @@ bgl_status bgl_fa2_step(bgl_graph *g, int64_t c, const bgl_params *p, int32_t it
 bgl_status bgl_assemble(bgl_graph *g, const bgl_params *p, const float *xy_in, float *xy_out, int64_t *rank_out,
                         int64_t *parent_out, float *scale_out, float *radius_out, float *centre_out);
 
+/* ----------------------------------------------------------------- serving */
+
+/*
+ * Layouts of neighbourhoods of a resident graph, served with continuous
+ * batching.  The paper lays out transaction graphs "for a certain time
+ * period" (Section 4); a service answers many such requests for parts of one
+ * large graph.  A request (seed node, hops k) asks for the k-hop
+ * neighbourhood of the seed -- every node within k undirected hops and every
+ * edge among them, node ids renumbered 0..n-1 in ascending resident id --
+ * laid out as bgl_layout does with the request's parameters (KK for
+ * components of at most kk_max_nodes nodes, ForceAtlas2 otherwise;
+ * p->assemble for one frame).
+ *
+ * bgl_graph_khop: the neighbourhood itself (synchronous, on g's stream):
+ *   *n_nodes = its size, or -1 if it has more than max_nodes nodes (then
+ *   nothing else is written); node_ids[n] (may be NULL) the resident ids in
+ *   ascending order; *n_edges and u, v[m] (may be NULL) the induced edges in
+ *   local ids, each once.  Call it with NULL arrays to learn the sizes.
+ * bgl_server_create: `slots` workers (1..64), each with its own context on
+ *   the resident graph's device; a request enters the layout stage when the
+ *   estimated HBM footprint of all requests in that stage, its own included,
+ *   is at most hbm_budget bytes (a request alone is always admitted);
+ *   waiting requests keep their arrival order.  The resident graph must stay
+ *   alive and unchanged until bgl_server_destroy.
+ * bgl_server_submit: queues a request (p is copied); *id identifies it.
+ * bgl_server_wait: blocks until the request is done; returns its status
+ *   (BGL_EINVAL if the neighbourhood exceeds max_nodes); *n_nodes its size;
+ *   times[3] (may be NULL) the steady-clock seconds of submission, admission
+ *   to the layout stage and completion (coordinates in host memory);
+ *   bytes[2] (may be NULL) the estimated footprint and the measured peak of
+ *   device memory of its layout stage.
+ * bgl_server_fetch: copies the result (node_ids[n] resident ids, xy[2n]) and
+ *   forgets the request; NULL arrays only forget it.
+ * bgl_server_stats: the largest estimated in-flight footprint so far.
+ * bgl_server_destroy: finishes the queued requests and stops the workers.
+ * A request's result does not depend on the other requests in flight.
+ */
+typedef struct bgl_server bgl_server;
+bgl_status bgl_graph_khop(bgl_graph *g, int64_t seed, int32_t hops, int64_t max_nodes, int64_t *n_nodes,
+                          int32_t *node_ids, int64_t *n_edges, int32_t *u, int32_t *v);
+bgl_status bgl_server_create(bgl_graph *resident, int32_t slots, int64_t hbm_budget, bgl_server **out);
+bgl_status bgl_server_submit(bgl_server *srv, int64_t seed, int32_t hops, int64_t max_nodes, const bgl_params *p,
+                             int64_t *id);
+bgl_status bgl_server_wait(bgl_server *srv, int64_t id, int64_t *n_nodes, double *times, int64_t *bytes);
+bgl_status bgl_server_fetch(bgl_server *srv, int64_t id, int32_t *node_ids, float *xy);
+bgl_status bgl_server_stats(bgl_server *srv, int64_t *inflight_max_bytes);
+bgl_status bgl_server_destroy(bgl_server *srv);
+
 /* ------------------------------------------ resumable runs and checkpoints */
 
 /*

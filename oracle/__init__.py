@@ -497,3 +497,32 @@ def assemble(off, adj, comp_off, nodes, xy, K, seed=0, sweeps=200, kappa=KAPPA):
             idx //= K
         out[vs] += shift
     return dict(xy=out, rank=rank, parent0=parent0, scale=scale, centroid=centroid, radius=radius, levels=levels)
+
+
+# ---------------------------------------------------------------- neighbourhoods (serving requests)
+
+def khop(off, adj, seed, k):
+    """Nodes within k undirected hops of seed (ascending ids) and the edges
+    among them in local ids (u < v, each once), by a plain breadth-first
+    search; for small graphs."""
+    dist = {int(seed): 0}
+    frontier = [int(seed)]
+    for h in range(k):
+        nxt = []
+        for x in frontier:
+            for w in adj[off[x]:off[x + 1]]:
+                w = int(w)
+                if w not in dist:
+                    dist[w] = h + 1
+                    nxt.append(w)
+        frontier = nxt
+    ids = np.array(sorted(dist), np.int64)
+    local = {int(g): i for i, g in enumerate(ids)}
+    edges = set()
+    for g in ids:
+        for w in adj[off[g]:off[g + 1]]:
+            w = int(w)
+            if w in local and local[w] != local[int(g)]:
+                a, b = sorted((local[int(g)], local[w]))
+                edges.add((a, b))
+    return ids, sorted(edges)

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["BglError", "Context", "Graph", "Params", "params", "build", "lib_path", "launch_count", "FMM_STATS",
+__all__ = ["BglError", "Context", "Graph", "Params", "Server", "params", "build", "lib_path", "launch_count", "FMM_STATS",
            "REP_EXACT", "REP_FMM", "REP_AUTO"]
 
 REP_EXACT, REP_FMM, REP_AUTO = 0, 1, 2
@@ -110,6 +110,13 @@ def _load():
         "bgl_fa2_session_positions": ([VP, VP, P64], I32),
         "bgl_state_save": ([VP, VP, ctypes.POINTER(ctypes.c_size_t)], I32),
         "bgl_assemble": ([VP, ctypes.POINTER(Params), VP, VP, VP, VP, VP, VP, VP], I32),
+        "bgl_graph_khop": ([VP, I64, I32, I64, P64, VP, P64, VP, VP], I32),
+        "bgl_server_create": ([VP, I32, I64, PP], I32),
+        "bgl_server_submit": ([VP, I64, I32, I64, ctypes.POINTER(Params), P64], I32),
+        "bgl_server_wait": ([VP, I64, P64, VP, VP], I32),
+        "bgl_server_fetch": ([VP, I64, VP, VP], I32),
+        "bgl_server_stats": ([VP, P64], I32),
+        "bgl_server_destroy": ([VP], I32),
         "bgl_state_load": ([VP, VP, ctypes.c_size_t], I32),
         "bgl_fmm_stats": ([VP, I64, ctypes.POINTER(Params), VP, I32, VP], I32),
         "bgl_launch_count": ([], I64),
@@ -125,6 +132,50 @@ def _load():
 
 FMM_STATS = ("boxes", "leaves", "depth", "p2p_pairs", "m2l", "m2p", "p2l", "ms_points", "ms_tree", "ms_lists",
              "ms_up", "ms_down", "ms_near", "ms_far", "ms_total", "sortmode_rel_diff", "sort_skip")
+
+
+class Server:
+    """Continuous-batching layout server on a resident graph (bgl_server_*)."""
+
+    def __init__(self, graph: "Graph", slots: int = 4, hbm_budget: int = 64 << 30):
+        self._lib = _load()
+        self.graph = graph
+        h = ctypes.c_void_p()
+        graph.ctx.check(self._lib.bgl_server_create(graph.h, slots, hbm_budget, ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, seed: int, hops: int, p: "Params", max_nodes: int = 1 << 30) -> int:
+        rid = ctypes.c_int64()
+        st = self._lib.bgl_server_submit(self.h, seed, hops, max_nodes, ctypes.byref(p), ctypes.byref(rid))
+        if st != 0:
+            raise BglError(st, "bgl_server_submit")
+        return rid.value
+
+    def wait(self, rid: int):
+        """Blocks; returns (status, n_nodes, times[3], bytes[2])."""
+        n = ctypes.c_int64()
+        t = np.zeros(3)
+        b = np.zeros(2, np.int64)
+        st = self._lib.bgl_server_wait(self.h, rid, ctypes.byref(n), _hp(t), _hp(b))
+        return st, n.value, t, b
+
+    def fetch(self, rid: int, n: int):
+        ids = np.zeros(max(n, 1), np.int32)
+        xy = np.zeros((max(n, 1), 2), np.float32)
+        st = self._lib.bgl_server_fetch(self.h, rid, _hp(ids), _hp(xy))
+        if st != 0:
+            raise BglError(st, "bgl_server_fetch")
+        return ids[:n], xy[:n]
+
+    def inflight_max(self) -> int:
+        v = ctypes.c_int64()
+        self._lib.bgl_server_stats(self.h, ctypes.byref(v))
+        return v.value
+
+    def close(self):
+        if self.h:
+            self._lib.bgl_server_destroy(self.h)
+            self.h = None
 
 
 def launch_count() -> int:
@@ -378,6 +429,20 @@ class Graph:
         self.ctx.check(self._lib.bgl_assemble(self.h, ctypes.byref(p), _hp(xy), _hp(out), _hp(rank), _hp(parent),
                                               _hp(scale), _hp(radius), _hp(centre)))
         return out, dict(rank=rank, parent=parent, scale=scale, radius=radius, centre=centre)
+
+    def khop(self, seed: int, hops: int, max_nodes: int):
+        """k-hop neighbourhood: (resident node ids, u, v) or None if larger than max_nodes."""
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx.check(self._lib.bgl_graph_khop(self.h, seed, hops, max_nodes, ctypes.byref(n), None,
+                                                ctypes.byref(m), None, None))
+        if n.value < 0:
+            return None
+        ids = np.zeros(n.value, np.int32)
+        u = np.zeros(max(m.value, 1), np.int32)
+        v = np.zeros(max(m.value, 1), np.int32)
+        self.ctx.check(self._lib.bgl_graph_khop(self.h, seed, hops, max_nodes, ctypes.byref(n), _hp(ids),
+                                                ctypes.byref(m), _hp(u), _hp(v)))
+        return ids, u[:m.value], v[:m.value]
 
     # resumable ForceAtlas2 run and its checkpoint
     def session_begin(self, c: int, p: Params, xy) -> None:

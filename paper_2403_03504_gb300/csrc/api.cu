@@ -50,6 +50,8 @@ void *Allocator::alloc(size_t bytes) {
             free_.erase(it);
             cached_ -= sz;
             live_[p] = sz;
+            live_bytes_ += sz;
+            peak_bytes_ = std::max(peak_bytes_, live_bytes_);
             return p;
         }
     }
@@ -67,6 +69,8 @@ void *Allocator::alloc(size_t bytes) {
     }
     std::lock_guard<std::mutex> lk(mu_);
     live_[p] = bytes;
+    live_bytes_ += bytes;
+    peak_bytes_ = std::max(peak_bytes_, live_bytes_);
     return p;
 }
 
@@ -76,6 +80,7 @@ void Allocator::free(void *p) {
     if (it == live_.end()) return;
     free_.emplace(it->second, p);
     cached_ += it->second;
+    live_bytes_ -= it->second;
     live_.erase(it);
 }
 
@@ -155,6 +160,17 @@ void require_c(const bgl_graph *g, int64_t c) {
     BGL_REQUIRE(c >= 0 && c < g->n_comp, "component index out of range");
 }
 
+
+__global__ void gather_xy_kernel(const float2 *__restrict__ xy_nodes, const int32_t *__restrict__ nodes, int64_t n,
+                                 float2 *__restrict__ out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = xy_nodes[nodes[q]];
+}
+
+}  // namespace
+
+namespace bgl {
+
 // Full layout into a device array in node-id order.
 void layout_device(bgl_graph *g, const bgl_params *p, float *d_xy_out) {
     check_params(p);
@@ -179,13 +195,7 @@ void layout_device(bgl_graph *g, const bgl_params *p, float *d_xy_out) {
     }
 }
 
-__global__ void gather_xy_kernel(const float2 *__restrict__ xy_nodes, const int32_t *__restrict__ nodes, int64_t n,
-                                 float2 *__restrict__ out) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) out[q] = xy_nodes[nodes[q]];
-}
-
-}  // namespace
+}  // namespace bgl
 
 extern "C" {
 

@@ -49,6 +49,13 @@ class Allocator {
     void *alloc(size_t bytes);
     void free(void *p);
     size_t cached_bytes() const { return cached_; }
+    size_t live_bytes() const { return live_bytes_; }
+    // largest live total since the last reset_peak
+    size_t peak_bytes() const { return peak_bytes_; }
+    void reset_peak() {
+        std::lock_guard<std::mutex> lk(mu_);
+        peak_bytes_ = live_bytes_;
+    }
     void release_cache();
     // set while a stream capture is open: allocating then would bake a
     // block that is freed after the capture into the replayed graph
@@ -60,6 +67,7 @@ class Allocator {
     std::multimap<size_t, void *> free_;      // size -> block
     std::map<void *, size_t> live_;           // block -> size
     size_t cached_ = 0;
+    size_t live_bytes_ = 0, peak_bytes_ = 0;
 };
 
 // Device array owned through the context allocator.
@@ -244,6 +252,10 @@ int64_t fa2_session_positions(Fa2Session *s, float2 *h_xy);     // returns the i
 size_t fa2_session_state_bytes(const Fa2Session *s);
 void fa2_session_save(Fa2Session *s, void *buf);
 Fa2Session *fa2_session_load(bgl_graph *g, const void *buf, size_t len);
+
+// the whole layout (split, KK, ForceAtlas2, assembly if asked) into a device
+// array in node-id order (api.cu)
+void layout_device(bgl_graph *g, const bgl_params *p, float *d_xy_out);
 
 // one force evaluation on component c, xy and f indexed by q - comp_off[c];
 // what: 0 total force, 1 repulsion only

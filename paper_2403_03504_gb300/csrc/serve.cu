@@ -1,0 +1,455 @@
+// Serving layouts of neighbourhoods of a resident graph.
+//
+// A request names a seed node and a hop count k: its subgraph is the
+// k-hop neighbourhood of the seed in the resident graph (every node within
+// k undirected hops and every edge between two of them), laid out with the
+// method of Section 4 (KK for small components, ForceAtlas2 with FMM or exact
+// repulsion for large ones).  The server keeps the resident graph in HBM and
+// runs `slots` workers, each with its own context (stream, allocator,
+// extraction scratch), so the work of several requests overlaps on the
+// device.  A request is admitted to the layout stage when the estimated HBM
+// footprint of everything in flight, its own included, fits the budget (a
+// lone request is always admitted); requests that arrive meanwhile wait in
+// arrival order.  Results do not depend on what else runs: every kernel is
+// deterministic and per-request state is private to its worker.
+//
+// k-hop extraction on the device: frontier expansion edge-parallel (a
+// thread per frontier edge, its frontier node by binary search over the
+// degree prefix sums), visited marks stamped with a per-worker counter (never
+// cleared), then the visited nodes sorted by id (local id = rank, so the
+// subgraph does not depend on the order of discovery) and the induced edges
+// listed per node in adjacency order.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+
+#include "bgl_internal.cuh"
+
+namespace bgl {
+
+namespace {
+
+constexpr int KH_TPB = 256;
+
+inline unsigned kh_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + KH_TPB - 1) / KH_TPB); }
+
+__global__ void kh_seed_kernel(int32_t *stamp, int32_t *vis, int32_t seed, int32_t epoch) {
+    stamp[seed] = epoch;
+    vis[0] = seed;
+}
+
+__global__ void kh_deg_kernel(const int32_t *__restrict__ front, int64_t nf, const int64_t *__restrict__ off,
+                              int64_t *__restrict__ deg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nf) deg[i] = off[front[i] + 1] - off[front[i]];
+}
+
+// one thread per edge of the frontier; new nodes appended to vis[base ..]
+__global__ void kh_expand_kernel(const int32_t *__restrict__ front, int64_t nf, const int64_t *__restrict__ dscan,
+                                 int64_t E, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                 int32_t *stamp, int32_t epoch, int32_t *vis, int64_t base, int64_t cap,
+                                 unsigned long long *cnt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int64_t lo = 0, hi = nf;           // largest i with dscan[i] <= e
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (dscan[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    const int32_t f = front[lo];
+    const int32_t w = adj[off[f] + (e - dscan[lo])];
+    if (stamp[w] == epoch) return;
+    if (atomicExch(&stamp[w], epoch) == epoch) return;
+    const unsigned long long idx = atomicAdd(cnt, 1ull);
+    if (base + (int64_t)idx < cap) vis[base + idx] = w;
+}
+
+__global__ void kh_local_kernel(const int32_t *__restrict__ vis, int64_t n, int32_t *__restrict__ local) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) local[vis[r]] = (int32_t)r;
+}
+
+// induced edges (r, local[w]) with local[w] > r: counts, then the lists
+__global__ void kh_edge_count_kernel(const int32_t *__restrict__ vis, int64_t n, const int64_t *__restrict__ off,
+                                     const int32_t *__restrict__ adj, const int32_t *__restrict__ stamp,
+                                     int32_t epoch, const int32_t *__restrict__ local, int64_t *__restrict__ cnt) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int32_t v = vis[r];
+    int64_t k = 0;
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+        const int32_t w = adj[e];
+        if (stamp[w] == epoch && local[w] > r) ++k;
+    }
+    cnt[r] = k;
+}
+
+__global__ void kh_edge_fill_kernel(const int32_t *__restrict__ vis, int64_t n, const int64_t *__restrict__ off,
+                                    const int32_t *__restrict__ adj, const int32_t *__restrict__ stamp, int32_t epoch,
+                                    const int32_t *__restrict__ local, const int64_t *__restrict__ start,
+                                    int32_t *__restrict__ u, int32_t *__restrict__ v) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int32_t g = vis[r];
+    int64_t k = start[r];
+    for (int64_t e = off[g]; e < off[g + 1]; ++e) {
+        const int32_t w = adj[e];
+        if (stamp[w] == epoch && local[w] > r) {
+            u[k] = (int32_t)r;
+            v[k] = local[w];
+            ++k;
+        }
+    }
+}
+
+}  // namespace
+
+// Scratch of one extracting context: visited stamps and local ids over the
+// resident graph's nodes, the visit list (at most cap entries).
+struct KhopScratch {
+    DevBuf<int32_t> stamp, local, vis;
+    DevBuf<int64_t> deg, dscan, tot;
+    DevBuf<unsigned long long> cnt;
+    int32_t epoch = 0;
+    int64_t cap = 0;
+    void reserve(bgl_ctx *c, int64_t n_res, int64_t cap_) {
+        if (stamp.n < (size_t)n_res) {
+            stamp.reset(c->alloc, n_res);
+            local.reset(c->alloc, n_res);
+            BGL_CUDA(cudaMemsetAsync(stamp.p, 0, sizeof(int32_t) * n_res, c->stream));
+            epoch = 0;
+        }
+        if (cap < cap_) {
+            vis.reset(c->alloc, cap_ + 1);
+            deg.reset(c->alloc, cap_ + 1);
+            dscan.reset(c->alloc, cap_ + 1);
+            cap = cap_;
+        }
+        if (!tot.p) tot.reset(c->alloc, 1);
+        if (!cnt.p) cnt.reset(c->alloc, 1);
+    }
+};
+
+// k-hop neighbourhood of `seed` in R (undirected CSR R->off, R->adj) on the
+// stream of ctx.  Returns its node count, or -1 if it has more than cap
+// nodes; on success vis[0 .. n) holds the node ids in ascending order and
+// (u, v)[0 .. m) the induced edges in local ids.
+static int64_t khop_extract(bgl_ctx *ctx, const bgl_graph *R, KhopScratch &ws, int64_t seed, int hops, int64_t cap,
+                            DevBuf<int32_t> &u, DevBuf<int32_t> &v, int64_t &m) {
+    BGL_REQUIRE(seed >= 0 && seed < R->n, "khop: seed out of range");
+    BGL_REQUIRE(hops >= 0, "khop: hops must be >= 0");
+    BGL_REQUIRE(cap >= 1, "khop: max_nodes must be >= 1");
+    cudaStream_t s = ctx->stream;
+    ws.reserve(ctx, R->n, cap);
+    const int32_t epoch = ++ws.epoch;
+    kh_seed_kernel<<<1, 1, 0, s>>>(ws.stamp.p, ws.vis.p, (int32_t)seed, epoch);
+    BGL_LAUNCH_CHECK();
+    int64_t total = 1, f0 = 0, nf = 1;
+    for (int h = 0; h < hops && nf > 0; ++h) {
+        kh_deg_kernel<<<kh_blocks(nf), KH_TPB, 0, s>>>(ws.vis.p + f0, nf, R->off.p, ws.deg.p);
+        BGL_LAUNCH_CHECK();
+        scan_exclusive_i64(ctx, ws.deg.p, ws.dscan.p, nf, ws.tot.p);
+        int64_t E = 0;
+        BGL_CUDA(cudaMemcpyAsync(&E, ws.tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        BGL_CUDA(cudaMemsetAsync(ws.cnt.p, 0, sizeof(unsigned long long), s));
+        BGL_CUDA(cudaStreamSynchronize(s));
+        if (E == 0) break;
+        kh_expand_kernel<<<kh_blocks(E), KH_TPB, 0, s>>>(ws.vis.p + f0, nf, ws.dscan.p, E, R->off.p, R->adj.p,
+                                                         ws.stamp.p, epoch, ws.vis.p, total, cap, ws.cnt.p);
+        BGL_LAUNCH_CHECK();
+        unsigned long long add = 0;
+        BGL_CUDA(cudaMemcpyAsync(&add, ws.cnt.p, sizeof(add), cudaMemcpyDeviceToHost, s));
+        BGL_CUDA(cudaStreamSynchronize(s));
+        if (total + (int64_t)add > cap) return -1;
+        f0 = total;
+        nf = (int64_t)add;
+        total += nf;
+    }
+    const int64_t n = total;
+    // ascending node ids: local id = rank
+    DevBuf<uint32_t> keys(ctx->alloc, n);
+    BGL_CUDA(cudaMemcpyAsync(keys.p, ws.vis.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    radix_sort_u32(ctx, keys.p, nullptr, n, std::max(1, bits_for((uint64_t)R->n)));
+    BGL_CUDA(cudaMemcpyAsync(ws.vis.p, keys.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    kh_local_kernel<<<kh_blocks(n), KH_TPB, 0, s>>>(ws.vis.p, n, ws.local.p);
+    BGL_LAUNCH_CHECK();
+    DevBuf<int64_t> ecnt(ctx->alloc, n), estart(ctx->alloc, n), etot(ctx->alloc, 1);
+    kh_edge_count_kernel<<<kh_blocks(n), KH_TPB, 0, s>>>(ws.vis.p, n, R->off.p, R->adj.p, ws.stamp.p, epoch,
+                                                         ws.local.p, ecnt.p);
+    BGL_LAUNCH_CHECK();
+    scan_exclusive_i64(ctx, ecnt.p, estart.p, n, etot.p);
+    m = 0;
+    BGL_CUDA(cudaMemcpyAsync(&m, etot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaStreamSynchronize(s));
+    u.reset(ctx->alloc, std::max<int64_t>(m, 1));
+    v.reset(ctx->alloc, std::max<int64_t>(m, 1));
+    kh_edge_fill_kernel<<<kh_blocks(n), KH_TPB, 0, s>>>(ws.vis.p, n, R->off.p, R->adj.p, ws.stamp.p, epoch,
+                                                        ws.local.p, estart.p, u.p, v.p);
+    BGL_LAUNCH_CHECK();
+    return n;
+}
+
+// HBM footprint of laying out a subgraph of n nodes and m undirected edges:
+// graph and component arrays, layout state, FMM plan (boxes, lists,
+// expansions, sort workspace) and the caching allocator's slack
+int64_t serve_footprint(int64_t n, int64_t m) { return 640 * n + 96 * m + (int64_t(16) << 20); }
+
+struct ServeRequest {
+    int64_t seed = 0, cap = 0;
+    int hops = 0;
+    bgl_params p;
+    bgl_status status = BGL_OK;
+    std::string error;
+    bool done = false;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int64_t footprint = 0, peak = 0;
+    std::vector<int32_t> nodes;
+    std::vector<float> xy;
+};
+
+struct Server {
+    bgl_graph *R = nullptr;
+    int64_t budget = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_mem, cv_done;
+    std::deque<int64_t> queue;
+    std::map<int64_t, std::unique_ptr<ServeRequest>> reqs;
+    int64_t next_id = 1, inflight = 0, inflight_max = 0;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    std::vector<bgl_ctx *> ctxs;
+    std::string init_error;
+};
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void serve_one(Server *S, bgl_ctx *ctx, KhopScratch &ws, ServeRequest *r) {
+    DevBuf<int32_t> u, v;
+    int64_t m = 0;
+    const int64_t n = khop_extract(ctx, S->R, ws, r->seed, r->hops, r->cap, u, v, m);
+    if (n < 0) fail(BGL_EINVAL, "neighbourhood larger than max_nodes");
+    const int64_t fp = serve_footprint(n, m);
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_mem.wait(lk, [&] { return S->inflight == 0 || S->inflight + fp <= S->budget || S->stop; });
+        S->inflight += fp;
+        S->inflight_max = std::max(S->inflight_max, S->inflight);
+    }
+    r->footprint = fp;
+    r->t_admit = now_s();
+    ctx->alloc->reset_peak();
+    const size_t live0 = ctx->alloc->live_bytes();
+    try {
+        std::unique_ptr<bgl_graph> sub(new bgl_graph());
+        sub->ctx = ctx;
+        graph_from_edges_device(sub.get(), n, m, u.p, v.p);
+        u.release();
+        v.release();
+        components_device(sub.get());
+        DevBuf<float2> xy(ctx->alloc, std::max<int64_t>(n, 1));
+        layout_device(sub.get(), &r->p, reinterpret_cast<float *>(xy.p));
+        r->nodes.resize(n);
+        r->xy.resize(2 * n);
+        BGL_CUDA(cudaMemcpyAsync(r->nodes.data(), ws.vis.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        BGL_CUDA(cudaMemcpyAsync(r->xy.data(), xy.p, sizeof(float2) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        BGL_CUDA(cudaStreamSynchronize(ctx->stream));
+        r->peak = (int64_t)(ctx->alloc->peak_bytes() - std::min(live0, ctx->alloc->peak_bytes()));
+    } catch (...) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->inflight -= fp;
+        S->cv_mem.notify_all();
+        throw;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->inflight -= fp;
+    S->cv_mem.notify_all();
+}
+
+static void worker_loop(Server *S, bgl_ctx *ctx) {
+    cudaSetDevice(ctx->device);
+    KhopScratch ws;
+    for (;;) {
+        ServeRequest *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+            if (S->stop && S->queue.empty()) return;
+            const int64_t id = S->queue.front();
+            S->queue.pop_front();
+            r = S->reqs[id].get();
+        }
+        bgl_status st = BGL_OK;
+        std::string msg;
+        try {
+            serve_one(S, ctx, ws, r);
+        } catch (const Error &e) {
+            st = e.status;
+            msg = e.what();
+        } catch (const std::exception &e) {
+            st = BGL_ECUDA;
+            msg = e.what();
+        }
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->status = st;
+        r->error = msg;
+        r->t_done = now_s();
+        r->done = true;
+        S->cv_done.notify_all();
+    }
+}
+
+}  // namespace bgl
+
+using namespace bgl;
+
+extern "C" {
+
+struct bgl_server {
+    Server s;
+};
+
+bgl_status bgl_server_create(bgl_graph *resident, int32_t slots, int64_t hbm_budget, bgl_server **out) {
+    if (!resident || !out || slots < 1 || slots > 64 || hbm_budget <= 0) return BGL_EINVAL;
+    *out = nullptr;
+    bgl_server *srv = new (std::nothrow) bgl_server();
+    if (!srv) return BGL_ENOMEM;
+    srv->s.R = resident;
+    srv->s.budget = hbm_budget;
+    for (int i = 0; i < slots; ++i) {
+        bgl_ctx *c = nullptr;
+        const bgl_status st = bgl_ctx_create(resident->ctx->device, &c);
+        if (st != BGL_OK) {
+            bgl_server_destroy(srv);
+            return st;
+        }
+        srv->s.ctxs.push_back(c);
+    }
+    // the resident graph must be complete before other streams read it
+    if (cudaStreamSynchronize(resident->ctx->stream) != cudaSuccess) {
+        bgl_server_destroy(srv);
+        return BGL_ECUDA;
+    }
+    for (bgl_ctx *c : srv->s.ctxs) srv->s.workers.emplace_back(worker_loop, &srv->s, c);
+    *out = srv;
+    return BGL_OK;
+}
+
+bgl_status bgl_server_submit(bgl_server *srv, int64_t seed, int32_t hops, int64_t max_nodes, const bgl_params *p,
+                             int64_t *id) {
+    if (!srv || !p || !id) return BGL_EINVAL;
+    if (seed < 0 || seed >= srv->s.R->n || hops < 0 || max_nodes < 1) return BGL_EINVAL;
+    try {
+        check_params(p);
+    } catch (const Error &e) {
+        return e.status;
+    }
+    std::unique_ptr<ServeRequest> r(new ServeRequest());
+    r->seed = seed;
+    r->hops = hops;
+    r->cap = max_nodes;
+    r->p = *p;
+    r->t_submit = now_s();
+    std::lock_guard<std::mutex> lk(srv->s.mu);
+    if (srv->s.stop) return BGL_ESTATE;
+    *id = srv->s.next_id++;
+    srv->s.reqs[*id] = std::move(r);
+    srv->s.queue.push_back(*id);
+    srv->s.cv_work.notify_one();
+    return BGL_OK;
+}
+
+bgl_status bgl_server_wait(bgl_server *srv, int64_t id, int64_t *n_nodes, double *times, int64_t *bytes) {
+    if (!srv) return BGL_EINVAL;
+    std::unique_lock<std::mutex> lk(srv->s.mu);
+    auto it = srv->s.reqs.find(id);
+    if (it == srv->s.reqs.end()) return BGL_EINVAL;
+    ServeRequest *r = it->second.get();
+    srv->s.cv_done.wait(lk, [&] { return r->done; });
+    if (n_nodes) *n_nodes = (int64_t)r->nodes.size();
+    if (times) {
+        times[0] = r->t_submit;
+        times[1] = r->t_admit;
+        times[2] = r->t_done;
+    }
+    if (bytes) {
+        bytes[0] = r->footprint;
+        bytes[1] = r->peak;
+    }
+    return r->status;
+}
+
+bgl_status bgl_server_fetch(bgl_server *srv, int64_t id, int32_t *node_ids, float *xy) {
+    if (!srv) return BGL_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->s.mu);
+    auto it = srv->s.reqs.find(id);
+    if (it == srv->s.reqs.end() || !it->second->done) return BGL_EINVAL;
+    ServeRequest *r = it->second.get();
+    const bgl_status st = r->status;
+    if (st == BGL_OK) {
+        if (node_ids) std::copy(r->nodes.begin(), r->nodes.end(), node_ids);
+        if (xy) std::copy(r->xy.begin(), r->xy.end(), xy);
+    }
+    srv->s.reqs.erase(it);
+    return st;
+}
+
+bgl_status bgl_server_stats(bgl_server *srv, int64_t *inflight_max_bytes) {
+    if (!srv) return BGL_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->s.mu);
+    if (inflight_max_bytes) *inflight_max_bytes = srv->s.inflight_max;
+    return BGL_OK;
+}
+
+bgl_status bgl_server_destroy(bgl_server *srv) {
+    if (!srv) return BGL_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->s.mu);
+        srv->s.stop = true;
+        srv->s.cv_work.notify_all();
+        srv->s.cv_mem.notify_all();
+    }
+    for (auto &t : srv->s.workers) t.join();
+    for (bgl_ctx *c : srv->s.ctxs) bgl_ctx_destroy(c);
+    delete srv;
+    return BGL_OK;
+}
+
+bgl_status bgl_graph_khop(bgl_graph *g, int64_t seed, int32_t hops, int64_t max_nodes, int64_t *n_nodes,
+                          int32_t *node_ids, int64_t *n_edges, int32_t *u, int32_t *v) {
+    if (!g || !n_nodes) return BGL_EINVAL;
+    bgl_ctx *c = g->ctx;
+    try {
+        cudaSetDevice(c->device);
+        KhopScratch ws;
+        DevBuf<int32_t> du, dv;
+        int64_t m = 0;
+        const int64_t n = khop_extract(c, g, ws, seed, hops, max_nodes, du, dv, m);
+        *n_nodes = n;
+        if (n_edges) *n_edges = n < 0 ? 0 : m;
+        if (n >= 0) {
+            if (node_ids)
+                BGL_CUDA(cudaMemcpyAsync(node_ids, ws.vis.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream));
+            if (u && m)
+                BGL_CUDA(cudaMemcpyAsync(u, du.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));
+            if (v && m)
+                BGL_CUDA(cudaMemcpyAsync(v, dv.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));
+        }
+        BGL_CUDA(cudaStreamSynchronize(c->stream));
+        c->last_error.clear();
+        return BGL_OK;
+    } catch (const Error &e) {
+        c->last_error = e.what();
+        return e.status;
+    } catch (const std::exception &e) {
+        c->last_error = e.what();
+        return BGL_ECUDA;
+    }
+}
+
+}  // extern "C"

@@ -540,3 +540,20 @@ def test_assembly_of_two_components_places_them_at_the_edge_length():
     cen = [out["xy"][nodes[comp_off[c]:comp_off[c + 1]]].mean(0) for c in range(2)]
     want = out["radius"][0] + out["radius"][1] + oracle.KAPPA
     assert abs(np.hypot(*(cen[0] - cen[1])) - want) <= 1e-9 * want
+
+
+def test_khop_vs_scipy_distances():
+    sp = pytest.importorskip("scipy.sparse.csgraph")
+    from scipy.sparse import csr_matrix
+    tx = synth.tx_lists(**synth.C1)
+    g = oracle.graph_build(tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    a = csr_matrix((np.ones(len(g.adj)), g.adj, g.off), shape=(g.n_nodes, g.n_nodes))
+    rng = np.random.default_rng(1)
+    for seed in rng.choice(g.n_nodes, 5, replace=False):
+        dist = sp.shortest_path(a, unweighted=True, indices=int(seed))
+        for k in (0, 1, 2, 3):
+            ids, edges = oracle.khop(g.off, g.adj, int(seed), k)
+            assert np.array_equal(ids, np.flatnonzero(dist <= k))
+            inside = set(ids.tolist())
+            m = sum(1 for x in ids for w in g.adj[g.off[x]:g.off[x + 1]] if int(w) in inside and int(w) != int(x)) // 2
+            assert len(edges) == m
