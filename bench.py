@@ -55,6 +55,82 @@ PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * PAIRS_PER_CLK
 NEAR_TRAFFIC_BYTES = 12_450_560 + 256
 
 
+def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, slots=4, budget=120 << 30):
+    """Poisson arrivals (rate per second) of k-hop layout requests (k uniform
+    in 1..4, seeds uniform over the graph's address nodes, redrawn until the
+    neighbourhood has min_nodes..max_nodes nodes) served by a bgl Server;
+    returns latency percentiles (arrival -> coordinates on the host),
+    throughput and sizes."""
+    import ctypes
+    lib = bgl._load()
+    rng = np.random.default_rng(seed)
+    sizes = g.sizes()
+    lo_id, hi_id = sizes["n_nodes"] - sizes["n_addr"], sizes["n_nodes"]
+    reqs = []
+    n_c, m_c = ctypes.c_int64(), ctypes.c_int64()
+    while len(reqs) < n_requests:
+        sd, k = int(rng.integers(lo_id, hi_id)), int(rng.integers(1, 5))
+        g.ctx.check(lib.bgl_graph_khop(g.h, sd, k, max_nodes, ctypes.byref(n_c), None, ctypes.byref(m_c), None, None))
+        if min_nodes <= n_c.value <= max_nodes:
+            reqs.append((sd, k, n_c.value))
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    p = bgl.params(seed=0, fa2_iters=iters, repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=64, kk_max_nodes=50)
+    srv = bgl.Server(g, slots=slots, hbm_budget=budget)
+    t0 = time.perf_counter()
+    arrive = t0 + np.cumsum(gaps)
+    ids = []
+    for (sd, k, _), ta in zip(reqs, arrive):
+        dt = ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(sd, k, p, max_nodes=max_nodes))
+    lat, sub, done, fps, peaks = [], [], [], [], []
+    for rid in ids:
+        st, n, t, b = srv.wait(rid)
+        if st != 0:
+            raise RuntimeError(f"serving request failed with status {st}")
+        srv.fetch(rid, n)
+        sub.append(t[0])
+        done.append(t[2])
+        lat.append(t[2] - t[0])
+        fps.append(int(b[0]))
+        peaks.append(int(b[1]))
+    inflight = srv.inflight_max()
+    srv.close()
+    lat_ms = 1e3 * np.array(lat)
+    wall = max(done) - min(sub)            # the server's steady clock
+    nodes = np.array([r[2] for r in reqs])
+    return {
+        "requests": n_requests, "rate_per_s": rate, "hops": "uniform 1..4", "fa2_iters": iters,
+        "nodes_min": int(nodes.min()), "nodes_p50": int(np.median(nodes)), "nodes_max": int(nodes.max()),
+        "latency_ms_p50": float(np.percentile(lat_ms, 50)), "latency_ms_p99": float(np.percentile(lat_ms, 99)),
+        "latency_ms_max": float(lat_ms.max()), "layouts_per_s": n_requests / wall,
+        "node_updates_per_s": float(nodes.sum()) * iters / wall, "slots": slots, "hbm_budget_bytes": int(budget),
+        "inflight_footprint_max_bytes": int(inflight), "peak_over_estimate_max": float(max(
+            pk / fp for pk, fp in zip(peaks, fps)))}
+
+
+def run_serve(args, rank, world, dist, local):
+    """Serving on the 3M-transaction graph (seed 4, ~1e7 nodes): Poisson
+    stream of 50 requests/s for k-hop neighbourhoods of 100 to 2e6 nodes,
+    300 ForceAtlas2 iterations with FMM (KK for components of <= 50 nodes)."""
+    import synth
+    import paper_2403_03504_gb300 as bgl
+    tx = synth.tx_lists(**synth.C4)
+    ctx = bgl.Context(local)
+    g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    n = args.requests or 100
+    out = serve_session(bgl, g, n, 50.0, 5, 300, 100, 2_000_000, slots=args.slots)
+    if rank == 0:
+        print(json.dumps({"metric": "served k-hop layouts: latency (arrival -> coordinates on the host)",
+                          "value": out["latency_ms_p99"], "unit": "ms (p99)", "higher_is_better": False,
+                          "n_gpus": world, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "serve-khop-3m-tx", "n_tx": tx.n_tx, "seed": 4,
+                                     "n_nodes": g.sizes()["n_nodes"]}, "serving": out}), flush=True)
+    g.destroy()
+    ctx.close()
+
+
 def run_c3(args, rank, world, dist, local):
     """Batched components: 100,000 forest components of 3-200 nodes (KK, at
     most 200 nodes) and 2,000 of 200-5,000 nodes (ForceAtlas2 with exact
@@ -259,8 +335,11 @@ def main():
     ap.add_argument("--exact-iters", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: the headline 200k-transaction graph; c3: 1e5 small + 2e3 mid-size components")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "serve"],
+                    help="c2: the headline 200k-transaction graph; c3: 1e5 small + 2e3 mid-size components; "
+                         "serve: k-hop layout requests on the 3M-transaction graph")
+    ap.add_argument("--requests", type=int, default=0, help="serving requests (0: 40 in the c2 line, 100 for serve)")
+    ap.add_argument("--slots", type=int, default=4, help="serving workers")
     ap.add_argument("--timed-only", action="store_true",
                     help="profiling case: warm-up and timed steps only (no end-to-end leg, no diagnostics); "
                          "prints the device-resident step times")
@@ -288,6 +367,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.workload == "c3":
         run_c3(args, rank, world, dist, local)
+        return
+    if args.workload == "serve":
+        run_serve(args, rank, world, dist, local)
         return
     tx = synth.tx_lists(**synth.C2)
     stream = torch.cuda.Stream(device=dev)
@@ -438,6 +520,9 @@ def main():
     assembly = {"ms": 0.5 * ((asm_ms[1] - asm_ms[0]) + (asm_ms[3] - asm_ms[2])), "components": int(len(coff) - 1),
                 "kk_max_nodes": int(p.kk_max_nodes)}
 
+    # served layouts of k-hop neighbourhoods of this graph (latency)
+    serving = serve_session(bgl, g0, args.requests or 40, 50.0, 2, 300, 100, 2_000_000, slots=4, budget=64 << 30)
+
     clocks = clk.summary()
     if rank != 0:
         if dist:
@@ -466,6 +551,7 @@ def main():
         "exact_fa2": {"value": exact_rate, "unit": UNIT, "iters": args.exact_iters, "nodes": giant},
         "fmm_p16_step_ms": 1e3 * p16_s,
         "assembly": assembly,
+        "serving": serving,
         "fmm_profile": stats,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -56,11 +56,15 @@ void *Allocator::alloc(size_t bytes) {
         }
     }
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    // stream-ordered: a new block does not synchronise the device, so
+    // contexts that allocate while others compute (the serving workers) do
+    // not stall each other; every entry point ends with a stream
+    // synchronisation, so a cached block is complete before any reuse
+    cudaError_t e = stream_ ? cudaMallocAsync(&p, bytes, *stream_) : cudaMalloc(&p, bytes);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         release_cache();
-        e = cudaMalloc(&p, bytes);
+        e = stream_ ? cudaMallocAsync(&p, bytes, *stream_) : cudaMalloc(&p, bytes);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -238,7 +242,7 @@ bgl_status bgl_ctx_create(int device, bgl_ctx **out) {
         BGL_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
         BGL_CUDA(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
         c->stream = c->own_stream;
-        c->alloc = new Allocator(device);
+        c->alloc = new Allocator(device, &c->stream);
         BGL_CUDA(cudaMalloc(&c->d_flag, 4 * sizeof(int)));
         BGL_CUDA(cudaMemset(c->d_flag, 0, 4 * sizeof(int)));
         BGL_CUDA(cudaMallocHost(&c->h_flag, 4 * sizeof(int)));

@@ -44,7 +44,9 @@ int64_t launch_count();
 // layouts of similar graphs do not call cudaMalloc/cudaFree.
 class Allocator {
   public:
-    explicit Allocator(int device) : device_(device) {}
+    // stream (may be null): new blocks come from the device's stream-ordered
+    // pool on *stream; null: cudaMalloc
+    explicit Allocator(int device, cudaStream_t *stream = nullptr) : device_(device), stream_(stream) {}
     ~Allocator();
     void *alloc(size_t bytes);
     void free(void *p);
@@ -63,6 +65,7 @@ class Allocator {
 
   private:
     int device_;
+    cudaStream_t *stream_ = nullptr;
     std::mutex mu_;
     std::multimap<size_t, void *> free_;      // size -> block
     std::map<void *, size_t> live_;           // block -> size

@@ -196,7 +196,7 @@ static int64_t khop_extract(bgl_ctx *ctx, const bgl_graph *R, KhopScratch &ws, i
 // HBM footprint of laying out a subgraph of n nodes and m undirected edges:
 // graph and component arrays, layout state, FMM plan (boxes, lists,
 // expansions, sort workspace) and the caching allocator's slack
-int64_t serve_footprint(int64_t n, int64_t m) { return 640 * n + 96 * m + (int64_t(16) << 20); }
+int64_t serve_footprint(int64_t n, int64_t m) { return 768 * n + 96 * m + (int64_t(16) << 20); }
 
 struct ServeRequest {
     int64_t seed = 0, cap = 0;
