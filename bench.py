@@ -494,6 +494,17 @@ def main():
         f_f = g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=pp), giant_xy)
         rms = float(np.sqrt(np.mean(np.sum((f_f - f_ex) ** 2, 1)) / np.mean(np.sum(f_ex ** 2, 1))))
         errs[f"p{pp}_rms_rel"] = rms
+    # M2L precision study at p = 12: FP32 CUDA cores versus BF16 tensor cores
+    m2l_prec = {"fmm_p": 12, "reference": "GPU FP32 exact sum at the final layout"}
+    for name, bf in (("fp32", 0), ("bf16", 1)):
+        pq = bgl.params(repulsion=bgl.REP_FMM, fmm_p=12, m2l_bf16=bf)
+        f_f = g0.fa2_repulsion(0, pq, giant_xy)
+        m2l_prec[f"{name}_rms_rel"] = float(np.sqrt(np.mean(np.sum((f_f - f_ex) ** 2, 1)) /
+                                                    np.mean(np.sum(f_ex ** 2, 1))))
+        st = g0.fmm_stats(0, pq, giant_xy, reps=5)
+        m2l_prec[f"{name}_ms_down"] = st["ms_down"]
+        m2l_prec[f"{name}_ms_total"] = st["ms_total"]
+    m2l_prec["m2l_translations"] = stats["m2l"]
     p16 = bgl.params(seed=0, fa2_iters=args.iters, repulsion=bgl.REP_AUTO, fmm_p=16)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -550,6 +561,7 @@ def main():
         "force_error": {"reference": "GPU FP32 exact sum at the final layout", **errs},
         "exact_fa2": {"value": exact_rate, "unit": UNIT, "iters": args.exact_iters, "nodes": giant},
         "fmm_p16_step_ms": 1e3 * p16_s,
+        "m2l_precision": m2l_prec,
         "assembly": assembly,
         "serving": serving,
         "fmm_profile": stats,

@@ -96,7 +96,8 @@ typedef struct bgl_params {
     double kk_tol;          /* KK early-stop gradient norm, 0 = fixed sweeps     default 0 */
     int32_t assemble;       /* 1: bgl_layout assembles the component layouts into one frame
                                (Section 4, see bgl_assemble); 0: each in its own frame default 0 */
-    int32_t pad0;
+    int32_t m2l_bf16;       /* 1: FMM M2L translations in BF16 on the tensor cores (FP32
+                               accumulate, per-box scaling; fmm_p <= 15)          default 0 */
 } bgl_params;
 
 /* ---------------------------------------------------------------- context */

@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
         ("kk_l", ctypes.c_double),
         ("kk_tol", ctypes.c_double),
         ("assemble", ctypes.c_int32),
-        ("pad0", ctypes.c_int32),
+        ("m2l_bf16", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -103,6 +103,7 @@ void check_params(const bgl_params *p) {
     BGL_REQUIRE(p->kk_l > 0, "kk_l must be > 0");
     BGL_REQUIRE(p->kk_tol >= 0, "kk_tol must be >= 0");
     BGL_REQUIRE(p->assemble == 0 || p->assemble == 1, "assemble must be 0 or 1");
+    BGL_REQUIRE(p->m2l_bf16 == 0 || p->m2l_bf16 == 1, "m2l_bf16 must be 0 or 1");
 }
 
 }  // namespace bgl

@@ -42,6 +42,7 @@
 // Every sum has a fixed order, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "fmm.cuh"
 #include "p2p.cuh"
@@ -933,7 +934,173 @@ struct ExpArgs {
     int *ticket;
     const float *binom;   // [BN * BN]
     int p;
+    const float *vout;    // BF16 M2L: the translated expansion of every V entry (null: M2L in FP32 here)
+    const int *vbase;     //   row of box b's first V entry in vout
 };
+
+// ---------------------------------------------------------------- M2L on tensor cores (BF16)
+//
+// A V entry of offset class c translates the source's scaled outgoing
+// expansion by a fixed matrix T_c (scaled coefficients make it the same at
+// every level): in real form, rows (l, re/im) for l = 0..p, columns (k,
+// re/im), blocks [[t_r, -t_i], [t_i, t_r]] of
+//   t(l, 0) = -w^-l / l,  t(l, k) = (-1)^k C(l+k-1, k-1) w^-(l+k),  l >= 1,
+// w = 2 (dx + i dy); row l = 0 is zero (b~_0 is not used).  With p <= 15 the
+// matrix fits 32 x 32.  The entries are bucketed by class; a warp takes 8
+// entries of one class at a time: B = their source vectors, each divided by
+// its largest component (per-box scaling) and rounded to BF16; A = T_c in
+// BF16 (precomputed as mma fragments); mma.m16n8k16 with FP32 accumulate,
+// 2 row tiles x 2 depth tiles; the results, multiplied back by the scales,
+// go to row vbase[b] + j of vout for the j-th V entry of box b.  The M2L +
+// P2L kernel then sums a box's rows in list order, so the result does not
+// depend on the bucketing order.
+constexpr int VCLS = 49;              // offset classes (dx, dy) in [-3, 3]^2, 40 of them used
+constexpr int VROWS = 32;             // rows of a translated expansion in vout
+
+// rows of vout for every box's V entries (the order of boxes in vout is
+// immaterial: each box reads back its own rows)
+__global__ void vbase_kernel(Tree T, int *vtot, int cap, int *vbase) {
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const int nv = T.lofs[5 * b + 2] - T.lofs[5 * b + 1];
+        int base = 0;
+        if (nv > 0) {
+            base = atomicAdd(vtot, nv);
+            if (base + nv > cap) {
+                atomicOr(T.err, ERR_LIST_OVERFLOW);
+                base = 0;
+            }
+        }
+        vbase[b] = base;
+    }
+}
+
+__global__ void vclass_count_kernel(Tree T, int *count) {
+    __shared__ int sc[VCLS];
+    for (int i = threadIdx.x; i < VCLS; i += blockDim.x) sc[i] = 0;
+    __syncthreads();
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+        for (int e = T.lofs[5 * b + 1]; e < T.lofs[5 * b + 2]; ++e) atomicAdd(&sc[T.lidx[e] & 63], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < VCLS; i += blockDim.x)
+        if (sc[i]) atomicAdd(&count[i], sc[i]);
+}
+
+// bucket starts (exclusive scan of the 49 counts, rounded up to tiles of 8);
+// the padding slots of every bucket hold {-1, -1}
+__global__ void vclass_scan_kernel(const int *count, int *start, int *cursor, int cap, int2 *pairs, int *err) {
+    if (threadIdx.x != 0) return;
+    int acc = 0;
+    for (int c = 0; c < VCLS; ++c) {
+        start[c] = acc;
+        cursor[c] = acc;
+        const int padded = (count[c] + 7) & ~7;
+        for (int j = acc + count[c]; j < acc + padded && j < cap; ++j) pairs[j] = make_int2(-1, -1);
+        acc += padded;
+    }
+    start[VCLS] = acc;
+    if (acc > cap) atomicOr(err, ERR_LIST_OVERFLOW);
+}
+
+// pairs[pos] = {V entry index in lidx, its row in vout}
+__global__ void vclass_scatter_kernel(Tree T, int *cursor, const int *vbase, int cap, int2 *pairs) {
+    const int B = min(T.levoff[NLEV], T.Bmax);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const int vs = T.lofs[5 * b + 1], ve = T.lofs[5 * b + 2];
+        for (int e = vs; e < ve; ++e) {
+            const int pos = atomicAdd(&cursor[T.lidx[e] & 63], 1);
+            if (pos < cap) pairs[pos] = make_int2(e, vbase[b] + (e - vs));
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// one warp per tile of 8 entries of one class
+__global__ void __launch_bounds__(256) m2l_bf16_kernel(Tree T, const float2 *__restrict__ M, int PT1, int p,
+                                                       const int *__restrict__ start, const int2 *__restrict__ pairs,
+                                                       const uint4 *__restrict__ tfrag, int cap, float *vout) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    // buckets past the capacity were not filled (the overflow is flagged): translate nothing
+    const int total = start[VCLS] <= cap ? start[VCLS] : 0;
+    const int gid = lane >> 2, tig = lane & 3;
+    for (int t0 = gw * 8; t0 < total; t0 += nw * 8) {
+        // class of this tile (tiles never straddle buckets)
+        int c = 0;
+        while (c + 1 < VCLS && start[c + 1] <= t0) ++c;
+        const int2 pr = pairs[t0 + gid];            // entry of column gid (-1: padding)
+        const bool live = pr.x >= 0 && pr.x < T.lcap && pr.y >= 0 && pr.y < cap;
+        const int e = live ? pr.y : -1;              // its row in vout
+        const int D = live ? (T.lidx[pr.x] >> 6) : -1;
+        // B fragments: rows k = kt * 16 + tig * 2 (+1, +8, +9) of column gid
+        float v[2][4];
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt) {
+            const int k0 = kt * 8 + tig, k1 = k0 + 4;       // coefficient indices
+            const float2 a0 = (D >= 0 && k0 <= p) ? M[(size_t)D * PT1 + k0] : make_float2(0.f, 0.f);
+            const float2 a1 = (D >= 0 && k1 <= p) ? M[(size_t)D * PT1 + k1] : make_float2(0.f, 0.f);
+            v[kt][0] = a0.x;
+            v[kt][1] = a0.y;
+            v[kt][2] = a1.x;
+            v[kt][3] = a1.y;
+        }
+        // per-column scale: the largest component (the 4 lanes of a column)
+        float mx = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mx = fmaxf(mx, fabsf(v[kt][j]));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        const float inv = mx > 0.f ? 1.0f / mx : 0.f;
+        uint32_t b[2][2];
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt) {
+            b[kt][0] = pack_bf16x2(v[kt][0] * inv, v[kt][1] * inv);
+            b[kt][1] = pack_bf16x2(v[kt][2] * inv, v[kt][3] * inv);
+        }
+        float acc[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[mt][j] = 0.f;
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt) {
+                const uint4 af = tfrag[((size_t)(c * 2 + mt) * 2 + kt) * 32 + lane];
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                    "{%8, %9}, {%0, %1, %2, %3};\n"
+                    : "+f"(acc[mt][0]), "+f"(acc[mt][1]), "+f"(acc[mt][2]), "+f"(acc[mt][3])
+                    : "r"(af.x), "r"(af.y), "r"(af.z), "r"(af.w), "r"(b[kt][0]), "r"(b[kt][1]));
+            }
+        }
+        // C: rows mt * 16 + gid (+8), columns tig * 2, tig * 2 + 1; scale back per column
+        int ec[2];
+        float sc[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            ec[j] = __shfl_sync(0xffffffffu, e, (tig * 2 + j) * 4);
+            sc[j] = __shfl_sync(0xffffffffu, mx, (tig * 2 + j) * 4);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (ec[j] < 0) continue;
+            float *o = vout + (size_t)ec[j] * VROWS;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                o[mt * 16 + gid] = acc[mt][j] * sc[j];
+                o[mt * 16 + gid + 8] = acc[mt][2 + j] * sc[j];
+            }
+        }
+    }
+}
 
 // Outgoing expansions of the boxes of level >= 2 (the only ones any list
 // uses).  A box of at most P2M_MAX points gets its expansion directly from
@@ -1064,7 +1231,16 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
         for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
         // M2L: b~_l += w^-l ( -a~_0 / l + sum_k (-1)^k a~_k w^-k C(l+k-1, k-1) ), w = 2 (dx + i dy)
         const int vs = T.lofs[5 * b + 1], ve = T.lofs[5 * b + 2];
-        for (int e = vs + lane; e < ve; e += 32) {
+        if (a.vout) {
+            // translated on the tensor cores: lane l sums coefficient l over the entries in order
+            if (lane >= 1 && lane <= p)
+                for (int e = vs; e < ve; ++e) {
+                    const float *o = a.vout + (size_t)(a.vbase[b] + (e - vs)) * VROWS + 2 * lane;
+                    acc[0].x += o[0];
+                    acc[0].y += o[1];
+                }
+        }
+        for (int e = vs + lane; !a.vout && e < ve; e += 32) {
             const int ent = T.lidx[e];
             const int D = ent >> 6, cls = ent & 63;
             const float2 w = make_float2(2.0f * (float)(cls / 7 - 3), 2.0f * (float)(cls % 7 - 3));
@@ -1113,8 +1289,16 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
                 }
             }
         }
+        float2 tc = make_float2(0.f, 0.f);
+        if (a.vout) {
+            // acc[0] of lane l holds its coefficient's tensor-core sum
+            tc = acc[0];
+            acc[0] = make_float2(0.f, 0.f);
+        }
         warp_reduce<PT>(acc);
-        if (lane <= p) a.Lc[(size_t)b * (PT + 1) + lane] = lane == 0 ? make_float2(0.f, 0.f) : pick<PT>(acc, lane);
+        if (lane <= p)
+            a.Lc[(size_t)b * (PT + 1) + lane] =
+                lane == 0 ? make_float2(0.f, 0.f) : cadd(pick<PT>(acc, lane), tc);
     }
 }
 
@@ -1452,6 +1636,74 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 
 }  // namespace
 
+// float -> bf16 bits, round to nearest even (finite inputs)
+static uint16_t bf16_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(r >> 16);
+}
+
+// mma.m16n8k16 A fragments (row-major 16 x 16 tiles, BF16) of the real M2L
+// matrices of the 49 offset classes for expansion order p <= 15; layout
+// [class][row tile][depth tile][lane] -> 4 x 32 bits
+static std::vector<uint4> m2l_fragments(int p) {
+    std::vector<uint4> out((size_t)VCLS * 2 * 2 * 32);
+    std::vector<double> R(32 * 32);
+    std::vector<double> binom(64 * 64, 0.0);
+    for (int i = 0; i < 64; ++i) {
+        binom[i * 64] = 1.0;
+        for (int k = 1; k <= i; ++k)
+            binom[i * 64 + k] = binom[(i - 1) * 64 + k - 1] + (k <= i - 1 ? binom[(i - 1) * 64 + k] : 0.0);
+    }
+    for (int c = 0; c < VCLS; ++c) {
+        std::fill(R.begin(), R.end(), 0.0);
+        const double wr = 2.0 * (c / 7 - 3), wi = 2.0 * (c % 7 - 3);
+        const double w2 = wr * wr + wi * wi;
+        if (w2 > 0.0) {
+            // powers of 1/w
+            std::vector<double> pr(2 * p + 2), pi(2 * p + 2);
+            pr[0] = 1.0;
+            pi[0] = 0.0;
+            const double ir = wr / w2, ii = -wi / w2;
+            for (int j = 1; j <= 2 * p + 1; ++j) {
+                pr[j] = pr[j - 1] * ir - pi[j - 1] * ii;
+                pi[j] = pr[j - 1] * ii + pi[j - 1] * ir;
+            }
+            for (int l = 1; l <= p; ++l) {
+                for (int k = 0; k <= p; ++k) {
+                    double tr, ti;
+                    if (k == 0) {
+                        tr = -pr[l] / l;
+                        ti = -pi[l] / l;
+                    } else {
+                        const double cf = ((k & 1) ? -1.0 : 1.0) * binom[(l + k - 1) * 64 + (k - 1)];
+                        tr = cf * pr[l + k];
+                        ti = cf * pi[l + k];
+                    }
+                    R[(2 * l) * 32 + 2 * k] = tr;
+                    R[(2 * l) * 32 + 2 * k + 1] = -ti;
+                    R[(2 * l + 1) * 32 + 2 * k] = ti;
+                    R[(2 * l + 1) * 32 + 2 * k + 1] = tr;
+                }
+            }
+        }
+        auto pk = [&](int r, int col) {
+            return (uint32_t)bf16_bits((float)R[r * 32 + col]) |
+                   ((uint32_t)bf16_bits((float)R[r * 32 + col + 1]) << 16);
+        };
+        for (int mt = 0; mt < 2; ++mt)
+            for (int kt = 0; kt < 2; ++kt)
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int gid = lane >> 2, tig = lane & 3;
+                    const int r0 = mt * 16 + gid, r1 = r0 + 8, c0 = kt * 16 + tig * 2;
+                    out[(((size_t)c * 2 + mt) * 2 + kt) * 32 + lane] =
+                        make_uint4(pk(r0, c0), pk(r1, c0), pk(r0, c0 + 8), pk(r1, c0 + 8));
+                }
+    }
+    return out;
+}
+
 struct FmmPlan {
     bgl_graph *g = nullptr;
     int64_t c = 0, q0 = 0;
@@ -1470,6 +1722,13 @@ struct FmmPlan {
     DevBuf<float2> M, Lc;
     DevBuf<int> arrive, tickets, err, leafdone;
     DevBuf<int> sortskip;     // radix passes the next sort skips (0 or 2), set by the tree of the last evaluation
+    // BF16 tensor-core M2L
+    bool bf16 = false;
+    int vcap = 0;
+    DevBuf<uint4> tfrag;      // [VCLS][2][2][32] mma fragments of the translation matrices
+    DevBuf<int> vbase, vclass;    // [Bmax]; counts, starts, cursors of the class buckets
+    DevBuf<int2> vpairs;      // [vcap]
+    DevBuf<float> vout;       // [vcap * VROWS]
     DevBuf<float2> ef;
     DevBuf<ulonglong2> hkv;
     DevBuf<unsigned> epoch;
@@ -1536,6 +1795,21 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->leafdone.reset(A, bmax);
         pl->sortskip.reset(A, 1);
         BGL_CUDA(cudaMemsetAsync(pl->sortskip.p, 0, sizeof(int), s));
+        if (p->m2l_bf16) {
+            BGL_REQUIRE(pl->p <= 15, "fmm: the BF16 tensor-core M2L takes expansion orders up to 15");
+            pl->bf16 = true;
+            // V entries: at most 27 per box, with at most n / 2 + 4096 boxes (beyond that
+            // the overflow is flagged and the evaluation fails); whole tiles of 8
+            pl->vcap = (int)(std::min<int64_t>(std::min<int64_t>(pl->lcap, 27 * ((int64_t)n / 2 + 4096)) + 8 * VCLS,
+                                               (int64_t)1 << 30) & ~int64_t(7));
+            pl->vbase.reset(A, bmax);
+            pl->vclass.reset(A, 3 * VCLS + 1);
+            pl->vpairs.reset(A, pl->vcap);
+            pl->vout.reset(A, (size_t)pl->vcap * VROWS);
+            std::vector<uint4> frag = m2l_fragments(pl->p);
+            pl->tfrag.reset(A, frag.size());
+            BGL_CUDA(cudaMemcpyAsync(pl->tfrag.p, frag.data(), sizeof(uint4) * frag.size(), cudaMemcpyHostToDevice, s));
+        }
         pl->ef.reset(A, n);
         int64_t hs = 1;
         while (hs < 2 * bmax) hs <<= 1;
@@ -1611,6 +1885,8 @@ static ExpArgs exp_args(FmmPlan *pl, const Tree &T) {
     a.ticket = pl->tickets.p + 1;
     a.binom = pl->binom.p;
     a.p = pl->p;
+    a.vout = pl->bf16 ? pl->vout.p : nullptr;
+    a.vbase = pl->bf16 ? pl->vbase.p : nullptr;
     return a;
 }
 
@@ -1679,6 +1955,21 @@ static void launch_up(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
 }
 template <int PT>
 static void launch_down(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
+    if (pl->bf16) {
+        int *cnt = pl->vclass.p, *start = cnt + VCLS, *cursor = start + VCLS + 1;
+        BGL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * VCLS, s));
+        vbase_kernel<<<pl->grid_p / 4, 256, 0, s>>>(a.T, pl->tickets.p + 7, pl->vcap, pl->vbase.p);
+        BGL_LAUNCH_CHECK();
+        vclass_count_kernel<<<pl->grid_p / 4, 256, 0, s>>>(a.T, cnt);
+        BGL_LAUNCH_CHECK();
+        vclass_scan_kernel<<<1, 32, 0, s>>>(cnt, start, cursor, pl->vcap, pl->vpairs.p, pl->err.p);
+        BGL_LAUNCH_CHECK();
+        vclass_scatter_kernel<<<pl->grid_p / 4, 256, 0, s>>>(a.T, cursor, pl->vbase.p, pl->vcap, pl->vpairs.p);
+        BGL_LAUNCH_CHECK();
+        m2l_bf16_kernel<<<pl->grid_p, 256, 0, s>>>(a.T, a.M, PT + 1, pl->p, start, pl->vpairs.p, pl->tfrag.p, pl->vcap,
+                                                   pl->vout.p);
+        BGL_LAUNCH_CHECK();
+    }
     m2l_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
     BGL_LAUNCH_CHECK();
 }

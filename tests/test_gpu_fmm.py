@@ -116,6 +116,36 @@ def test_fmm_small_leaf_sizes(path30k):
         assert e.max() <= ceiling(12), (leaf, e.max())
 
 
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_fmm_bf16_m2l_error(path30k, kind):
+    """M2L translations in BF16 on the tensor cores (FP32 accumulate, every
+    source expansion scaled by its largest component before rounding).  BF16
+    keeps 8 significant bits, unit roundoff u = 2^-8; the translated
+    expansion of one V entry then carries a relative error of a few u, which
+    bounds the far-field part of each force: RMS over the component at most
+    1e-2 and the per-node error (in units of the node's total repulsion
+    scale) at most 5e-2.  The result differs from the FP32 M2L, is never
+    more accurate than it, and is bitwise reproducible (each entry's
+    translation and each box's sum in list order are fixed)."""
+    bgl = _bgl()
+    xy = synth.points(11, path30k.n, kind, scale=50.0)
+    exact = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy)
+    sample = np.random.default_rng(4).choice(path30k.n, 300, replace=False)
+    f32 = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=12), xy)
+    p16 = bgl.params(repulsion=bgl.REP_FMM, fmm_p=12, m2l_bf16=1)
+    f16 = path30k.g.fa2_repulsion(0, p16, xy)
+    assert np.all(np.isfinite(f16))
+    assert not np.array_equal(f16, f32)
+    e16, r16 = _errors(f16, exact, xy, path30k, sample)
+    _, r32 = _errors(f32, exact, xy, path30k, sample)
+    assert r16 <= 1e-2, (kind, r16)
+    assert e16.max() <= 5e-2, (kind, e16.max())
+    assert r16 >= r32, (kind, r16, r32)
+    assert np.array_equal(f16, path30k.g.fa2_repulsion(0, p16, xy))
+    with pytest.raises(RuntimeError):
+        path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=16, m2l_bf16=1), xy)
+
+
 @pytest.mark.parametrize("case", ["tiny", "coincident", "collinear", "far_clusters", "wide_range", "edge_line"])
 def test_fmm_degenerate_geometries(ctx, case):
     bgl = _bgl()
