@@ -903,27 +903,41 @@ __device__ __forceinline__ float2 crcp(float2 a) {
     return make_float2(a.x * d, -a.y * d);
 }
 
+// Warp sum of the 2 (PT + 1) floats of a (real and imaginary parts
+// interleaved, float f = part f & 1 of coefficient f / 2), scattered: on
+// return out[c] of lane L holds the total of float 32 c + L.  Recursive
+// halving: at each step a lane keeps one half of its values, sends the
+// other half to its partner and adds what it receives, so a chunk of 32
+// floats takes 16 + 8 + 4 + 2 + 1 = 31 shuffles (a butterfly on every
+// float takes 5 per float).  The order of the additions is fixed.
 template <int PT>
-__device__ __forceinline__ void warp_reduce(float2 (&a)[PT + 1]) {
+__host__ __device__ constexpr int scatter_chunks() { return (2 * (PT + 1) + 31) / 32; }
+
+template <int PT>
+__device__ __forceinline__ void warp_sum_scatter(const float2 (&a)[PT + 1], int lane, float (&out)[scatter_chunks<PT>()]) {
+    constexpr int NF = 2 * (PT + 1);
 #pragma unroll
-    for (int k = 0; k <= PT; ++k) {
+    for (int c = 0; c < scatter_chunks<PT>(); ++c) {
+        float v[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a[k].x += __shfl_xor_sync(0xffffffffu, a[k].x, o);
-            a[k].y += __shfl_xor_sync(0xffffffffu, a[k].y, o);
+        for (int i = 0; i < 32; ++i) {
+            const int f = 32 * c + i;
+            v[i] = f < NF ? ((f & 1) ? a[f >> 1].y : a[f >> 1].x) : 0.f;
         }
+#pragma unroll
+        for (int h = 16; h > 0; h >>= 1) {
+            const bool up = (lane & h) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float send = up ? v[i] : v[i + h];
+                const float keep = up ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+        }
+        out[c] = v[0];
     }
 }
 
-// value of a[lane] for lane <= PT (register array, compile-time indices)
-template <int PT>
-__device__ __forceinline__ float2 pick(const float2 (&a)[PT + 1], int lane) {
-    float2 r = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k <= PT; ++k)
-        if (k == lane) r = a[k];
-    return r;
-}
 
 struct ExpArgs {
     Tree T;
@@ -1003,15 +1017,29 @@ __global__ void vclass_scan_kernel(const int *count, int *start, int *cursor, in
     if (acc > cap) atomicOr(err, ERR_LIST_OVERFLOW);
 }
 
-// pairs[pos] = {V entry index in lidx, its row in vout}
+// pairs[pos] = {V entry index in lidx, its row in vout}; slots are claimed
+// per block (shared counters, one global atomic per class and round)
 __global__ void vclass_scatter_kernel(Tree T, int *cursor, const int *vbase, int cap, int2 *pairs) {
+    __shared__ int sc[VCLS], sb[VCLS];
     const int B = min(T.levoff[NLEV], T.Bmax);
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-        const int vs = T.lofs[5 * b + 1], ve = T.lofs[5 * b + 2];
+    for (int r0 = blockIdx.x * blockDim.x; r0 < B; r0 += gridDim.x * blockDim.x) {
+        for (int i = threadIdx.x; i < VCLS; i += blockDim.x) sc[i] = 0;
+        __syncthreads();
+        const int b = r0 + threadIdx.x;
+        const int vs = b < B ? T.lofs[5 * b + 1] : 0, ve = b < B ? T.lofs[5 * b + 2] : 0;
+        for (int e = vs; e < ve; ++e) atomicAdd(&sc[T.lidx[e] & 63], 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < VCLS; i += blockDim.x) {
+            sb[i] = sc[i] ? atomicAdd(&cursor[i], sc[i]) : 0;
+            sc[i] = 0;
+        }
+        __syncthreads();
         for (int e = vs; e < ve; ++e) {
-            const int pos = atomicAdd(&cursor[T.lidx[e] & 63], 1);
+            const int c = T.lidx[e] & 63;
+            const int pos = sb[c] + atomicAdd(&sc[c], 1);
             if (pos < cap) pairs[pos] = make_int2(e, vbase[b] + (e - vs));
         }
+        __syncthreads();
     }
 }
 
@@ -1104,7 +1132,7 @@ __global__ void __launch_bounds__(256) m2l_bf16_kernel(Tree T, const float2 *__r
 
 // Outgoing expansions of the boxes of level >= 2 (the only ones any list
 // uses).  A box of at most P2M_MAX points gets its expansion directly from
-// its points (P2M, one warp, fixed butterfly).  The few larger boxes near
+// its points (P2M, one warp, fixed-order warp sum).  The few larger boxes near
 // the root get theirs by M2M from their four children, computed by the last
 // child to finish (an arrival count per box), so no warp waits.
 constexpr int P2M_MAX = 2048;
@@ -1144,12 +1172,14 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
                 pw = cmul(pw, w);
             }
         }
-        warp_reduce<PT>(acc);
+        float tot[scatter_chunks<PT>()];
+        warp_sum_scatter<PT>(acc, lane, tot);
         // a~_0 = sum q, a~_k = -sum q w^k / k
-        if (lane <= p) {
-            float2 v = pick<PT>(acc, lane);
-            if (lane > 0) v = cscale(v, -1.0f / (float)lane);
-            a.M[(size_t)b * (PT + 1) + lane] = v;
+#pragma unroll
+        for (int c = 0; c < scatter_chunks<PT>(); ++c) {
+            const int f = 32 * c + lane, k = f >> 1;
+            if (k <= p) reinterpret_cast<float *>(a.M)[(size_t)b * (PT + 1) * 2 + f] =
+                k > 0 ? tot[c] * (-1.0f / (float)k) : tot[c];
         }
         __threadfence();
         int child = b;
@@ -1209,11 +1239,13 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
 
 // Incoming expansion of every box of level >= 2 from its own interaction
 // lists only (no parent term): M2L over V and P2L over X, one warp per box,
-// lanes over the V entries and over the points of X leaves, a fixed
-// butterfly to combine.  Boxes are independent, so the pass has no waits;
+// lanes over the V entries and over the points of X leaves, a
+// fixed-order warp sum to combine.  Boxes are independent, so the pass has no waits;
 // the parents' contributions are folded in at the leaves (far_kernel).
-template <int PT>
-__global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
+// (at PT = 8 the kernel fits 64 registers: four blocks per SM hide more of
+// the latency of the list and expansion loads)
+template <int PT, bool TC>
+__global__ void __launch_bounds__(256, PT == 8 ? 4 : 1) m2l_kernel(ExpArgs a) {
     __shared__ float sbin[BN * BN];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
     __syncthreads();
@@ -1231,7 +1263,7 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
         for (int k = 0; k <= PT; ++k) acc[k] = make_float2(0.f, 0.f);
         // M2L: b~_l += w^-l ( -a~_0 / l + sum_k (-1)^k a~_k w^-k C(l+k-1, k-1) ), w = 2 (dx + i dy)
         const int vs = T.lofs[5 * b + 1], ve = T.lofs[5 * b + 2];
-        if (a.vout) {
+        if constexpr (TC) {
             // translated on the tensor cores: lane l sums coefficient l over the entries in order
             if (lane >= 1 && lane <= p)
                 for (int e = vs; e < ve; ++e) {
@@ -1240,7 +1272,7 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
                     acc[0].y += o[1];
                 }
         }
-        for (int e = vs + lane; !a.vout && e < ve; e += 32) {
+        for (int e = vs + lane; !TC && e < ve; e += 32) {
             const int ent = T.lidx[e];
             const int D = ent >> 6, cls = ent & 63;
             const float2 w = make_float2(2.0f * (float)(cls / 7 - 3), 2.0f * (float)(cls % 7 - 3));
@@ -1290,15 +1322,23 @@ __global__ void __launch_bounds__(256) m2l_kernel(ExpArgs a) {
             }
         }
         float2 tc = make_float2(0.f, 0.f);
-        if (a.vout) {
+        if constexpr (TC) {
             // acc[0] of lane l holds its coefficient's tensor-core sum
             tc = acc[0];
             acc[0] = make_float2(0.f, 0.f);
         }
-        warp_reduce<PT>(acc);
-        if (lane <= p)
-            a.Lc[(size_t)b * (PT + 1) + lane] =
-                lane == 0 ? make_float2(0.f, 0.f) : cadd(pick<PT>(acc, lane), tc);
+        float tot[scatter_chunks<PT>()];
+        warp_sum_scatter<PT>(acc, lane, tot);
+#pragma unroll
+        for (int c = 0; c < scatter_chunks<PT>(); ++c) {
+            const int f = 32 * c + lane, k = f >> 1;
+            float v = tot[c];
+            if constexpr (TC) {
+                const float tx = __shfl_sync(0xffffffffu, tc.x, k & 31), ty = __shfl_sync(0xffffffffu, tc.y, k & 31);
+                v += (f & 1) ? ty : tx;
+            }
+            if (k <= p) reinterpret_cast<float *>(a.Lc)[(size_t)b * (PT + 1) * 2 + f] = k == 0 ? 0.f : v;
+        }
     }
 }
 
@@ -1970,7 +2010,10 @@ static void launch_down(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
                                                    pl->vout.p);
         BGL_LAUNCH_CHECK();
     }
-    m2l_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
+    if (pl->bf16)
+        m2l_kernel<PT, true><<<pl->grid_p, 256, 0, s>>>(a);
+    else
+        m2l_kernel<PT, false><<<pl->grid_p, 256, 0, s>>>(a);
     BGL_LAUNCH_CHECK();
 }
 static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
