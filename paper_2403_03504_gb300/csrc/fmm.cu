@@ -37,8 +37,9 @@
 //   far       per leaf: the incoming expansion composed from the partial
 //             expansions of the leaf and all its ancestors (the L2L chain,
 //             one shift per ancestor), L2P at the targets, M2P over W
-// Near and far run concurrently (main and side stream); the second of the
-// two to finish a leaf writes its forces.
+//   combine   per point: the force from the near sum and the far field
+// Near and far run concurrently (main and side stream); the combine pass
+// joins them.
 // Every sum has a fixed order, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
@@ -1242,10 +1243,10 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
 // lanes over the V entries and over the points of X leaves, a
 // fixed-order warp sum to combine.  Boxes are independent, so the pass has no waits;
 // the parents' contributions are folded in at the leaves (far_kernel).
-// (at PT = 8 the kernel fits 64 registers: four blocks per SM hide more of
-// the latency of the list and expansion loads)
+// (at PT = 8 the kernel fits 64 registers and at PT = 12 128: four and two
+// blocks per SM hide more of the latency of the list and expansion loads)
 template <int PT, bool TC>
-__global__ void __launch_bounds__(256, PT == 8 ? 4 : 1) m2l_kernel(ExpArgs a) {
+__global__ void __launch_bounds__(256, PT == 8 ? 4 : (PT == 12 ? 2 : 1)) m2l_kernel(ExpArgs a) {
     __shared__ float sbin[BN * BN];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
     __syncthreads();
@@ -1347,8 +1348,8 @@ struct LeafArgs {
     ExpArgs e;
     float2 *f;           // f[q - fbase]: near-field sums, then the final forces
     const float2 *fa;    // fa[q - fbase] added to the final force, or null
-    float2 *ef;          // far field E(z) of every sorted point
-    int *leafdone;       // per box: how many of the near and far kernels finished it (0 between evaluations)
+    float2 *ef;          // far field E(z) of every point, by component-local index
+    const float *mass;   // mass[o], component-local index
     int64_t q0, fbase;
     float kr;
     int *ticket;
@@ -1363,7 +1364,7 @@ struct LeafArgs {
 // lanes, lane l takes targets l % lps + r * lps of split l / lps; (R, S) is
 // chosen per leaf for the fewest padded target slots; the splits share the
 // sources and combine by a fixed butterfly.  Writes the raw sum
-// sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the far kernel completes it).
+// sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the combine pass completes it).
 constexpr int NEAR_WARPS = 8;
 constexpr int NEAR_SRC = 128;
 
@@ -1420,7 +1421,7 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
         __syncwarp();
         const float4 *src = buf[cur];
         if (S == 1) {
-#pragma unroll 4
+#pragma unroll 2
             for (int j = 0; j < cnt; ++j) {
                 const float4 q = src[j];
 #pragma unroll
@@ -1450,34 +1451,20 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
     }
 }
 
-// The near and far fields of a leaf are computed by two kernels that may
-// run at the same time; each marks the leaf when its part is in memory, and
-// the second to finish writes the force of every target of the leaf:
-//   F_rep(i) = kr m_i (near(i) + conj(E(z_i))) (+ fa(i))
-__device__ __noinline__ void leaf_finish(const LeafArgs &la, int b, int s, int e, int lane) {
-    // the warp barrier orders the lanes' writes before lane 0's fence, which
-    // makes them visible device-wide before the mark
-    __syncwarp();
-    int old = 0;
-    if (lane == 0) {
-        __threadfence();
-        old = atomicAdd(&la.leafdone[b], 1);
-        if (old == 1) __threadfence();     // acquire: the other kernel's results are visible
-    }
-    old = __shfl_sync(0xffffffffu, old, 0);
-    if (old != 1) return;
-    __syncwarp();
-    for (int tt = s + lane; tt < e; tt += 32) {
-        const float4 z = la.e.T.pts[tt];
-        const int o = __float_as_int(z.w);
-        const int64_t q = la.q0 + o - la.fbase;
-        const float2 nr = __ldcg(&la.f[q]);
-        const float2 E = __ldcg(&la.ef[tt]);
-        const float km = la.kr * z.z;
-        const float2 a = la.fa ? la.fa[q] : make_float2(0.f, 0.f);
-        la.f[q] = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
-    }
-    if (lane == 0) la.leafdone[b] = 0;
+// The near and far fields are computed by two kernels that may run at the
+// same time (the near sum into f, the far field into ef, both by the
+// point's component-local index); once both are done, one coalesced pass
+// writes the force of every point:
+//   F_rep(o) = kr m_o (near(o) + conj(E(z_o))) (+ fa(o))
+__global__ void combine_kernel(LeafArgs la, int n) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int64_t q = la.q0 + o - la.fbase;
+    const float2 nr = la.f[q];
+    const float2 E = la.ef[o];
+    const float km = la.kr * la.mass[o];
+    const float2 a = la.fa ? la.fa[q] : make_float2(0.f, 0.f);
+    la.f[q] = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
 }
 
 __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
@@ -1516,7 +1503,6 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
             else if (R == 2) near_tile<2>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
             else near_tile<1>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
         }
-        leaf_finish(la, b, s, e, lane);
     }
 }
 
@@ -1528,8 +1514,7 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
 //   b~_m(leaf) += 2^(-D m) sum_{l >= m} b~_l(A) C(l, m) t^(l-m),
 //   t = (c_leaf - c_A) / r_A, D = level(leaf) - level(A);
 // lane m computes coefficient m.  Then, a lane per target: L2P of that
-// expansion and M2P over W, added to the near sum; F_rep = kr m_i
-// (near + conj(E_far)).
+// expansion and M2P over W, the field E stored for the combine pass.
 constexpr int FAR_WARPS = 4;
 constexpr int FAR_W = 16;        // W entries staged in shared memory (longer lists read global memory)
 
@@ -1666,9 +1651,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                 const float2 a0 = md[0];
                 E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
             }
-            la.ef[tt] = E;
+            la.ef[__float_as_int(z.w)] = E;
         }
-        leaf_finish(la, b, s, e, lane);
     }
 }
 
@@ -1760,7 +1744,7 @@ struct FmmPlan {
     DevBuf<int4> bchild;
     DevBuf<int2> bmeta;
     DevBuf<float2> M, Lc;
-    DevBuf<int> arrive, tickets, err, leafdone;
+    DevBuf<int> arrive, tickets, err;
     DevBuf<int> sortskip;     // radix passes the next sort skips (0 or 2), set by the tree of the last evaluation
     // BF16 tensor-core M2L
     bool bf16 = false;
@@ -1797,7 +1781,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         BGL_REQUIRE(n64 < (int64_t(1) << 30), "fmm: component too large");
         pl->n = (int)n64;
         pl->p = p->fmm_p;
-        pl->PT = p->fmm_p <= 8 ? 8 : (p->fmm_p <= 16 ? 16 : 24);
+        pl->PT = p->fmm_p <= 8 ? 8 : (p->fmm_p <= 12 ? 12 : (p->fmm_p <= 16 ? 16 : 24));
         pl->S = p->leaf_size;
         pl->kr = (float)p->kr;
         const int n = std::max(pl->n, 1);
@@ -1832,7 +1816,6 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->M.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->Lc.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->arrive.reset(A, bmax);
-        pl->leafdone.reset(A, bmax);
         pl->sortskip.reset(A, 1);
         BGL_CUDA(cudaMemsetAsync(pl->sortskip.p, 0, sizeof(int), s));
         if (p->m2l_bf16) {
@@ -1863,7 +1846,6 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->sortws.reserve(A, n, s);
         BGL_CUDA(cudaMemsetAsync(pl->counter.p, 0, sizeof(unsigned), s));
         BGL_CUDA(cudaMemsetAsync(pl->arrive.p, 0, sizeof(int) * bmax, s));
-        BGL_CUDA(cudaMemsetAsync(pl->leafdone.p, 0, sizeof(int) * bmax, s));
         BGL_CUDA(cudaMemsetAsync(pl->err.p, 0, sizeof(int), s));
         std::vector<float> bn(BN * BN, 0.f);
         for (int i = 0; i < BN; ++i) {
@@ -1940,7 +1922,7 @@ static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbas
     la.kr = pl->kr;
     la.ticket = pl->tickets.p + 2;
     la.ef = pl->ef.p;
-    la.leafdone = pl->leafdone.p;
+    la.mass = pl->g->mass.p + pl->q0;
     return la;
 }
 
@@ -2025,12 +2007,15 @@ static void launch_far(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
     far_kernel<PT><<<2 * pl->grid_p, FAR_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
 }
+static void launch_combine(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
+    combine_kernel<<<nblk(pl->n, 256), 256, 0, s>>>(la, pl->n);
+    BGL_LAUNCH_CHECK();
+}
 
 // Whole evaluation.  With `concurrent`, the upward and downward passes and
 // the far field run on the plan's side stream while the near field runs on
-// the main stream; whichever of near and far finishes a leaf last writes
-// its forces:
-//   main: points, tree --+-- lists ----+-- near ---------------------+--
+// the main stream; the combine pass joins them:
+//   main: points, tree --+-- lists ----+-- near ---------------------+-- combine
 //   side:                +-- up -------+-- (lists) down -- far ------+
 // ev (timing events, 7, may be null) forces one stream and marks the phases.
 template <int PT>
@@ -2052,10 +2037,11 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
         if (ev) BGL_CUDA(cudaEventRecord(ev[4], s));
         launch_down<PT>(pl, a, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[5], s));
-        if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
         launch_near(pl, la, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[6], s));
         launch_far<PT>(pl, la, s);
+        if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
+        launch_combine(pl, la, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[7], s));
         return;
     }
@@ -2065,19 +2051,20 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
     launch_up<PT>(pl, a, t);
     phase_lists(pl, T, s);
     BGL_CUDA(cudaEventRecord(pl->ev[1], s));           // lists built
-    if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
     launch_near(pl, la, s);
     BGL_CUDA(cudaStreamWaitEvent(t, pl->ev[1], 0));
     launch_down<PT>(pl, a, t);
-    if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(t, fa_ready, 0));
     launch_far<PT>(pl, la, t);
     BGL_CUDA(cudaEventRecord(pl->ev[2], t));           // far field done
     BGL_CUDA(cudaStreamWaitEvent(s, pl->ev[2], 0));
+    if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
+    launch_combine(pl, la, s);
 }
 
 static void evaluate_any(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bool concurrent, cudaEvent_t *ev,
                          const float2 *fa = nullptr, cudaEvent_t fa_ready = nullptr) {
     if (pl->PT == 8) evaluate<8>(pl, xl, f, fbase, concurrent, ev, fa, fa_ready);
+    else if (pl->PT == 12) evaluate<12>(pl, xl, f, fbase, concurrent, ev, fa, fa_ready);
     else if (pl->PT == 16) evaluate<16>(pl, xl, f, fbase, concurrent, ev, fa, fa_ready);
     else evaluate<24>(pl, xl, f, fbase, concurrent, ev, fa, fa_ready);
 }
