@@ -21,8 +21,8 @@
 //             leaf_size + 1 consecutive sorted points around i shares a key
 //             prefix, so boxes are emitted in one pass, level by level, in
 //             Morton order within a level, with their ends, parents and child
-//             slots; then every box goes into a hash table keyed by (level,
-//             Morton prefix)
+//             slots, and each box goes into a hash table keyed by (level,
+//             Morton prefix) as it is emitted
 //   lists     per box, by hash lookups of the 3x3 cells around it and its
 //             parent: U (adjacent leaves, near field), V (children of the
 //             parent's neighbours that are not adjacent: the "interacting
@@ -379,11 +379,32 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
     if (threadIdx.x < NLEV) cnt[threadIdx.x] = 0;
     __syncthreads();
     // g(j) = lcp(key[j], key[j + S]) for windows j in [t0 - S, t0 + TILE)
-    for (int k = threadIdx.x; k < TREE_TILE + S; k += TREE_THREADS) {
+    const int ng = TREE_TILE + S;
+    for (int k = threadIdx.x; k < ng; k += TREE_THREADS) {
         int j = lo + k;
         g[k] = (j >= 0 && j + S < n) ? (int8_t)lcp_level(sk[k], sk[k + S]) : (int8_t)-1;
     }
     __syncthreads();
+    // maxima of g over runs of P entries, P the largest power of two <= S + 1
+    // (doubling: after the round of step h, g[k] = max g[k .. k + 2h - 1])
+    int P = 1;
+    while (2 * P <= S + 1) P *= 2;
+    constexpr int GM = (TREE_TILE + 256 + TREE_THREADS - 1) / TREE_THREADS;
+    for (int h = 1; h < P; h *= 2) {
+        int8_t v[GM];
+#pragma unroll
+        for (int m = 0; m < GM; ++m) {
+            const int k = threadIdx.x + m * TREE_THREADS;
+            v[m] = k < ng ? (int8_t)max((int)g[k], k + h < ng ? (int)g[k + h] : -1) : (int8_t)-1;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < GM; ++m) {
+            const int k = threadIdx.x + m * TREE_THREADS;
+            if (k < ng) g[k] = v[m];
+        }
+        __syncthreads();
+    }
     int local[NLEV];
 #pragma unroll
     for (int L = 0; L < NLEV; ++L) local[L] = 0;
@@ -393,9 +414,9 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
         if (i >= n) break;
         int k = i - lo;
         int c = i == 0 ? -1 : lcp_level(sk[k - 1], sk[k]);
-        int G = -1;
-        // windows j in [i - S, i] (g is -1 where a window does not fit)
-        for (int j = k - S; j <= k; ++j) G = max(G, (int)g[j]);
+        // windows j in [i - S, i] (g is -1 where a window does not fit): two
+        // runs of P cover them
+        const int G = max((int)g[k - S], (int)g[k - P + 1]);
         gm = max(gm, G);
         int la = min(cap, G + 1);
         cl[i] = (int8_t)c;
@@ -423,7 +444,8 @@ constexpr int SCAN_ITEMS = 8;
 // leaf_size + 1 points shares 8 or more levels (the tree is at most 8 levels
 // deep), the next sort orders the top 16 key bits only.
 __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax,
-                                                                 int *err, const int *gmax, int *sortskip) {
+                                                                 int *err, const int *gmax, int *sortskip,
+                                                                 int4 *bchild) {
     __shared__ int sv[SCAN_THREADS * SCAN_ITEMS];
     __shared__ int wsum[32];
     __shared__ int carry_s;
@@ -478,6 +500,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int 
     }
     if (threadIdx.x == 0 && carry > Bmax) atomicOr(err, ERR_BOX_OVERFLOW);
     if (threadIdx.x == 0) *sortskip = *gmax <= 7 ? 2 : 0;
+    // empty child slots of this evaluation's boxes (the emit kernel fills them)
+    for (int b = threadIdx.x; b < min(carry, Bmax); b += SCAN_THREADS) bchild[b] = make_int4(-1, -1, -1, -1);
 }
 
 // Boxes of the tile, level by level in point order.  Warp w owns the
@@ -491,7 +515,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int 
 //     before_{L-1}(i) if that one starts at i too, else before_{L-1}(i) - 1;
 //   the box of level L holding point i - 1 ends (c(i) < L <= lambda(i-1)):
 //     index before_L(i) - 1, end i; every box holding point n - 1 ends at n.
-// Each new box also takes its child slot in the parent.
+// Each new box also takes its child slot in the parent and its entry in
+// the hash table.  Levels above the deepest leaf level met in the tile
+// (of its points and of the point before it) hold no box start or end.
 __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const int8_t *__restrict__ cl,
                                                                 const int8_t *__restrict__ lam,
                                                                 const int *__restrict__ tcnt, int ntiles, int Bmax) {
@@ -499,6 +525,10 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
     constexpr int R = TREE_TILE / TREE_THREADS;        // rounds per warp
     constexpr int PW = TREE_TILE / NW;                 // points per warp
     __shared__ int wcount[NLEV][NW];
+    __shared__ int smax;
+    if (threadIdx.x == 0) smax = 0;
+    __syncthreads();
+    const unsigned epoch = *T.epoch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t0 = blockIdx.x * TREE_TILE;
     const unsigned lt = (1u << lane) - 1u;
@@ -513,8 +543,17 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
         lp[r] = ok && i > 0 ? lam[i - 1] : -99;      // leaf level of point i - 1
         k[r] = ok ? T.key[i] : 0u;
     }
+    {
+        int m = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) m = max(m, max(la[r], lp[r]));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) atomicMax(&smax, m);
+    }
+    __syncthreads();
+    const int Lmax = min(smax, NLEV - 1);
     // per-warp totals of every level
-    for (int L = 0; L < NLEV; ++L) {
+    for (int L = 0; L <= Lmax; ++L) {
         int tot = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) tot += __popc(__ballot_sync(0xffffffffu, c[r] < L && L <= la[r]));
@@ -528,7 +567,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
         pb[r] = 0;
         pf[r] = false;
     }
-    for (int L = 0; L < NLEV; ++L) {
+    for (int L = 0; L <= Lmax; ++L) {
         int base = tcnt[L * ntiles + blockIdx.x];
         for (int w = 0; w < warp; ++w) base += wcount[L][w];
 #pragma unroll
@@ -552,6 +591,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
                     else atomicOr(T.err, ERR_BOX_OVERFLOW);
                 }
                 T.bparent[b] = par;
+                hash_insert(T.hkv, T.hmask, epoch, L, P, b, T.err);
             }
             // the box of level L holding point i - 1 ends at i
             if (i < T.n && c[r] < L && L <= lp[r] && before >= 1 && before - 1 < Bmax) T.bend[before - 1] = i;
@@ -565,13 +605,6 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
     }
 }
 
-// every box into the hash table
-__global__ void tree_hash_kernel(Tree T) {
-    const int B = min(T.levoff[NLEV], T.Bmax);
-    const unsigned epoch = *T.epoch;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
-        hash_insert(T.hkv, T.hmask, epoch, T.blevel[b], T.bkey[b], b, T.err);
-}
 
 // ---------------------------------------------------------------- neighbour tables and lists
 
@@ -1951,16 +1984,13 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
 
 // tree: boxes in level order, ends, parents, children
 static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
-    BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * pl->Bmax, s));
     tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, pl->n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
                                                           pl->ntiles, pl->sortskip.p, pl->tickets.p + 6);
     BGL_LAUNCH_CHECK();
     tree_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p,
-                                                pl->tickets.p + 6, pl->sortskip.p);
+                                                pl->tickets.p + 6, pl->sortskip.p, pl->bchild.p);
     BGL_LAUNCH_CHECK();
     tree_emit_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(T, pl->cl.p, pl->lam.p, pl->tcnt.p, pl->ntiles, pl->Bmax);
-    BGL_LAUNCH_CHECK();
-    tree_hash_kernel<<<pl->grid_p / 4, 256, 0, s>>>(T);
     BGL_LAUNCH_CHECK();
 }
 
