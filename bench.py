@@ -52,7 +52,7 @@ PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * PAIRS_PER_CLK
 # DRAM bytes (read + write) of one near_kernel launch on this workload's
 # giant component, from the ncu capture summarised in
 # profiles/near_kernel_fmm_c2_giant.md (the working set is L2-resident)
-NEAR_TRAFFIC_BYTES = 12_450_560 + 256
+NEAR_TRAFFIC_BYTES = 11_209_216 + 0
 
 
 def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, slots=4, budget=120 << 30):
@@ -345,6 +345,11 @@ def main():
                          "prints the device-resident step times")
     ap.add_argument("--kernels-only", action="store_true",
                     help="profiling case: FMM and exact repulsion on the giant component only")
+    ap.add_argument("--positions", default="",
+                    help="with --kernels-only: giant-component positions from this .npy file "
+                         "(written by --save-positions) instead of N(0, 300^2) points")
+    ap.add_argument("--save-positions", default="",
+                    help="write the giant component's final positions of the timed layout to this .npy file")
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -391,7 +396,11 @@ def main():
     if args.kernels_only:
         # a few launches of each repulsion kernel on the 5.5e5-node giant component
         coff, _, nodes = g0.component_nodes()
-        xy0 = np.random.default_rng(0).normal(0, 300, (int(coff[1] - coff[0]), 2)).astype(np.float32)
+        if args.positions:
+            xy0 = np.ascontiguousarray(np.load(args.positions), dtype=np.float32)
+            assert xy0.shape == (int(coff[1] - coff[0]), 2), xy0.shape
+        else:
+            xy0 = np.random.default_rng(0).normal(0, 300, (int(coff[1] - coff[0]), 2)).astype(np.float32)
         for _ in range(3):
             g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=args.p), xy0)
         g0.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy0)
@@ -478,6 +487,8 @@ def main():
     # ---------------------------------------------------------------- diagnostics (not timed)
     xy_final = d_xy.cpu().numpy()
     giant_xy = np.ascontiguousarray(xy_final[nodes[coff[0]:coff[1]]])
+    if args.save_positions:
+        np.save(args.save_positions, giant_xy)
     stats = g0.fmm_stats(0, p, giant_xy, reps=5)
     leaf_s = stats["ms_near"] / 1e3
     achieved = stats["p2p_pairs"] / leaf_s

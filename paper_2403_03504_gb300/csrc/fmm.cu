@@ -444,8 +444,7 @@ constexpr int SCAN_ITEMS = 8;
 // leaf_size + 1 points shares 8 or more levels (the tree is at most 8 levels
 // deep), the next sort orders the top 16 key bits only.
 __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax,
-                                                                 int *err, const int *gmax, int *sortskip,
-                                                                 int4 *bchild) {
+                                                                 int *err, const int *gmax, int *sortskip) {
     __shared__ int sv[SCAN_THREADS * SCAN_ITEMS];
     __shared__ int wsum[32];
     __shared__ int carry_s;
@@ -500,8 +499,6 @@ __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int 
     }
     if (threadIdx.x == 0 && carry > Bmax) atomicOr(err, ERR_BOX_OVERFLOW);
     if (threadIdx.x == 0) *sortskip = *gmax <= 7 ? 2 : 0;
-    // empty child slots of this evaluation's boxes (the emit kernel fills them)
-    for (int b = threadIdx.x; b < min(carry, Bmax); b += SCAN_THREADS) bchild[b] = make_int4(-1, -1, -1, -1);
 }
 
 // Boxes of the tile, level by level in point order.  Warp w owns the
@@ -1489,8 +1486,14 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
 // point's component-local index); once both are done, one coalesced pass
 // writes the force of every point:
 //   F_rep(o) = kr m_o (near(o) + conj(E(z_o))) (+ fa(o))
+// It also empties the child slots of this evaluation's boxes for the next
+// tree (the emit kernel fills only the slots of children that exist; the
+// plan starts with all slots empty).
 __global__ void combine_kernel(LeafArgs la, int n) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const Tree &T = la.e.T;
+    for (int b = o, B = min(T.levoff[NLEV], T.Bmax); b < B; b += gridDim.x * blockDim.x)
+        T.bchild[b] = make_int4(-1, -1, -1, -1);
     if (o >= n) return;
     const int64_t q = la.q0 + o - la.fbase;
     const float2 nr = la.f[q];
@@ -1611,7 +1614,9 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
             for (int it = lane; it < nW * (PT + 1); it += 32) {
                 const int i = it / (PT + 1), k = it - i * (PT + 1);
                 const int Dx = __float_as_int(s_wg[wib][i].w);
-                s_wm[wib][i][k] = k <= p ? la.e.M[(size_t)Dx * (PT + 1) + k] : make_float2(0.f, 0.f);
+                // k a~_k (a~_0 for k = 0): the weights of the M2P Horner sum
+                const float2 mk = k <= p ? la.e.M[(size_t)Dx * (PT + 1) + k] : make_float2(0.f, 0.f);
+                s_wm[wib][i][k] = k == 0 ? mk : cscale(mk, (float)k);
             }
         }
         __syncwarp();
@@ -1632,7 +1637,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
         float2 mine = make_float2(0.f, 0.f);
         if (lane >= 1 && lane <= p)
             for (int j = 0; j < nA; ++j) mine = cadd(mine, part_[wib][j][lane]);
-        if (lane <= PT) loc[wib][lane] = mine;
+        if (lane <= PT) loc[wib][lane] = cscale(mine, (float)lane);     // l b~_l, the L2P weights
         __syncwarp();
         const BoxGeo g = box_geo_xy(rt, mb.x, Lb);
         const float ir = 1.0f / g.r;
@@ -1645,7 +1650,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                 float2 hs = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int l = PT; l >= 1; --l) {
-                    if (l <= p) hs = cadd(cmul(hs, v), cscale(loc[wib][l], (float)l));
+                    if (l <= p) hs = cadd(cmul(hs, v), loc[wib][l]);
                 }
                 E = cscale(hs, ir);
             }
@@ -1660,7 +1665,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                     float2 hs = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int kk = PT; kk >= 1; --kk) {
-                        if (kk <= p) hs = cadd(cmul(hs, tt2), cscale(s_wm[wib][i][kk], (float)kk));
+                        if (kk <= p) hs = cadd(cmul(hs, tt2), s_wm[wib][i][kk]);
                     }
                     hs = cmul(hs, tt2);
                     const float2 a0 = s_wm[wib][i][0];
@@ -1843,6 +1848,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->bkey.reset(A, bmax);
         pl->bleaf.reset(A, bmax);
         pl->bchild.reset(A, bmax);
+        BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * bmax, s));
         pl->bmeta.reset(A, bmax);
         pl->lofs.reset(A, 5 * bmax);
         pl->lidx.reset(A, pl->lcap);
@@ -1988,7 +1994,7 @@ static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
                                                           pl->ntiles, pl->sortskip.p, pl->tickets.p + 6);
     BGL_LAUNCH_CHECK();
     tree_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p,
-                                                pl->tickets.p + 6, pl->sortskip.p, pl->bchild.p);
+                                                pl->tickets.p + 6, pl->sortskip.p);
     BGL_LAUNCH_CHECK();
     tree_emit_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(T, pl->cl.p, pl->lam.p, pl->tcnt.p, pl->ntiles, pl->Bmax);
     BGL_LAUNCH_CHECK();
@@ -2234,6 +2240,12 @@ int fmm_error(FmmPlan *pl) {
     BGL_CUDA(cudaMemcpyAsync(&e, pl->err.p, sizeof(int), cudaMemcpyDeviceToHost, pl->g->ctx->stream));
     BGL_CUDA(cudaStreamSynchronize(pl->g->ctx->stream));
     if (sort_workspace_error(pl->g->ctx, pl->sortws)) e |= ERR_SPIN;
+    // a failed evaluation may have stopped before its combine pass: empty
+    // every child slot again so that the plan stays usable
+    if (e) {
+        BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * pl->Bmax, pl->g->ctx->stream));
+        BGL_CUDA(cudaStreamSynchronize(pl->g->ctx->stream));
+    }
     return e;
 }
 
