@@ -80,6 +80,21 @@ def test_fmm_error_within_ceiling_and_decreasing(path30k, kind):
     assert rms <= 1e-5, rms                                   # p = 24 reaches the FP32 direct-sum level
 
 
+@pytest.mark.parametrize("p", [8, 16])
+def test_fmm_force_sum_vanishes(path30k, p):
+    """The exact repulsion is antisymmetric, so its sum over the component is
+    0; the FMM's residual |sum_i F(i)| / sum_i |F(i)| stays within its error
+    ceiling (and the exact sum's own residual is at the FP32 level)."""
+    bgl = _bgl()
+    xy = synth.points(9, path30k.n, "clustered", scale=30.0)
+    exact = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy).astype(np.float64)
+    f = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=p), xy).astype(np.float64)
+    res = np.hypot(*f.sum(0)) / np.sum(np.hypot(*f.T))
+    res_exact = np.hypot(*exact.sum(0)) / np.sum(np.hypot(*exact.T))
+    assert res_exact <= 1e-5, res_exact
+    assert res <= ceiling(p), (p, res)
+
+
 def test_fmm_is_bitwise_reproducible(path30k):
     bgl = _bgl()
     xy = synth.points(3, path30k.n, "clustered", scale=10.0)
