@@ -195,8 +195,14 @@ struct OsHist {
     uint32_t *hist;      // 4 x 256 digit counts
     uint32_t *base;      // 4 x 256 exclusive digit bases (written by the last block)
     unsigned *counter;   // arrival count of the blocks (reset by the last block)
+    unsigned *tickets;   // 4 pass tickets
+    uint32_t *status;    // 4 x ntiles x 256 look-back status words
+    int64_t ntiles;      // tiles of 256 x 8 keys
 };
-OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n);
+// With clear = false the caller zeroes hist and tickets in a kernel that
+// runs before its histogram kernel, and each block of the histogram kernel
+// (one per tile) zeroes its tile's status words (os_clear_status).
+OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n, bool clear = true);
 // d_skip (device int, may be null = 0): the passes below *d_skip (0 or 2)
 // return at once, so the keys end up ordered by their top 32 - 8 * skip
 // bits only (stable: equal top bits keep the input order).  Read by each

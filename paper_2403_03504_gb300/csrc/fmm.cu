@@ -234,9 +234,15 @@ __device__ int cover(const Tree &T, unsigned epoch, int L, int cx, int cy) {
 // ---------------------------------------------------------------- bbox, keys, gather
 
 __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__restrict__ part, unsigned *counter,
-                            Root *root, int *err, unsigned *epoch) {
+                            Root *root, int *err, unsigned *epoch, int *tickets, OsHist h) {
     __shared__ float4 wred[32];
     __shared__ bool last;
+    // this evaluation's work tickets, digit counts and sort pass tickets start at zero
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) h.hist[i] = 0u;
+        if (threadIdx.x < 8) tickets[threadIdx.x] = 0;
+        if (threadIdx.x < 4) h.tickets[threadIdx.x] = 0u;
+    }
     float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
@@ -351,6 +357,8 @@ __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy
             valid |= 1u << r;
         }
     }
+    static_assert(256 * KEY_ITEMS == 2048, "a key block is one radix tile");
+    os_clear_status(h, blockIdx.x);
     os_block_hist<KEY_ITEMS>(k, valid, h);
 }
 
@@ -1970,13 +1978,13 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
     bgl_ctx *ctx = pl->g->ctx;
     const int n = pl->n;
     const float *ml = pl->g->mass.p + pl->q0;
-    BGL_CUDA(cudaMemsetAsync(pl->tickets.p, 0, sizeof(int) * 8, s));
     cudaStream_t keep = ctx->stream;
     ctx->stream = s;
     try {
-        const OsHist h = radix_sort_u32_ws_begin(ctx, pl->sortws, n);
+        // tickets, digit counts and look-back words are zeroed by bbox_kernel and keys_kernel
+        const OsHist h = radix_sort_u32_ws_begin(ctx, pl->sortws, n, false);
         bbox_kernel<<<std::min<int64_t>(2 * ctx->num_sms, nblk(n, 256)), 256, 0, s>>>(
-            xl, n, pl->part.p, pl->counter.p, pl->root.p, pl->err.p, pl->epoch.p);
+            xl, n, pl->part.p, pl->counter.p, pl->root.p, pl->err.p, pl->epoch.p, pl->tickets.p, h);
         BGL_LAUNCH_CHECK();
         keys_kernel<<<nblk(n, 256 * KEY_ITEMS), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p, h);
         BGL_LAUNCH_CHECK();

@@ -487,7 +487,7 @@ void SortWorkspace::reserve(Allocator *a, int64_t n, cudaStream_t s) {
     cap = n;
 }
 
-OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n) {
+OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n, bool clear) {
     BGL_REQUIRE(n <= ws.cap && n < (int64_t(1) << 30), "radix sort: workspace too small");
     cudaStream_t s = c->stream;
     const int64_t nt = os_tiles(n);
@@ -496,6 +496,10 @@ OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n) {
     h.base = h.hist + 4 * 256;
     unsigned *tickets = reinterpret_cast<unsigned *>(h.hist + 8 * 256);
     h.counter = tickets + 4;
+    h.tickets = tickets;
+    h.status = reinterpret_cast<uint32_t *>(ws.tiles.p);
+    h.ntiles = nt;
+    if (!clear) return h;
     // counts, pass tickets and look-back status words start at zero
     BGL_CUDA(cudaMemsetAsync(h.hist, 0, sizeof(uint32_t) * 4 * 256, s));
     BGL_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * 4, s));

@@ -50,4 +50,11 @@ __device__ void os_block_hist(const uint32_t (&key)[ITEMS], unsigned valid, OsHi
     if (threadIdx.x == 0) *h.counter = 0u;
 }
 
+// The look-back status words of tile `tile` for the four passes to zero
+// (every thread of a 256-thread block calls it).
+__device__ __forceinline__ void os_clear_status(const OsHist &h, int64_t tile) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) h.status[((int64_t)d * h.ntiles + tile) * 256 + threadIdx.x] = 0u;
+}
+
 }  // namespace bgl
