@@ -557,8 +557,24 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
     }
     __syncthreads();
     const int Lmax = min(smax, NLEV - 1);
+    // levels at which a box starts or ends among the warp's points (a box of
+    // level L starts at i for c(i) < L <= lambda(i), one holding point i - 1
+    // ends there for c(i) < L <= lambda(i - 1), and every box holding the
+    // last point ends at n); at the other levels the warp has nothing to do
+    unsigned lm = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int lo = c[r] + 1, hi = max(la[r], lp[r]);
+        if (lo <= hi && hi < NLEV) lm |= ((2u << hi) - 1u) & ~((1u << lo) - 1u);
+        if (t0 + warp * PW + r * 32 + lane == T.n - 1 && la[r] >= 0) lm |= (2u << la[r]) - 1u;
+    }
+    lm = __reduce_or_sync(0xffffffffu, lm);
     // per-warp totals of every level
     for (int L = 0; L <= Lmax; ++L) {
+        if (!((lm >> L) & 1u)) {
+            if (lane == 0) wcount[L][warp] = 0;
+            continue;
+        }
         int tot = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) tot += __popc(__ballot_sync(0xffffffffu, c[r] < L && L <= la[r]));
@@ -575,6 +591,15 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
     for (int L = 0; L <= Lmax; ++L) {
         int base = tcnt[L * ntiles + blockIdx.x];
         for (int w = 0; w < warp; ++w) base += wcount[L][w];
+        if (!((lm >> L) & 1u)) {
+            // no start or end at this level: before_L(i) = base for every point
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                pb[r] = base;
+                pf[r] = false;
+            }
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = t0 + warp * PW + r * 32 + lane;
