@@ -19,6 +19,7 @@
 // The sequence has fixed launch shapes, so it is captured once as the body of
 // a device-side WHILE loop in a CUDA graph: one launch runs all iterations.  Every sum has a fixed order, so
 // runs are bitwise reproducible.
+#include <cstdlib>
 #include <cstring>
 
 #include "bgl_internal.cuh"
@@ -596,6 +597,57 @@ __global__ void loop_ctrl_kernel(cudaGraphConditionalHandle h, int *count, int i
 
 }  // namespace
 
+// With BGL_HOST_LOOP=1 in the environment, the iterations are launched
+// from the host as one captured-iteration graph each instead of a device-side
+// loop: profilers that cannot look inside graphs with conditional nodes can
+// then see every kernel.  The results are the same.
+static bool host_loop() {
+    const char *v = std::getenv("BGL_HOST_LOOP");
+    return v && v[0] == '1';
+}
+
+static void run_iterations_host(Fa2Run &run, int iters, double *d_stats) {
+    bgl_ctx *ctx = run.g->ctx;
+    cudaStream_t s = ctx->stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int64_t before = launch_count();
+    BGL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ctx->alloc->forbid = true;
+    try {
+        run.iteration(d_stats);
+    } catch (...) {
+        ctx->alloc->forbid = false;
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(s, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        throw;
+    }
+    ctx->alloc->forbid = false;
+    BGL_CUDA(cudaStreamEndCapture(s, &graph));
+    const int64_t per_iter = launch_count() - before;
+    count_launches(-per_iter);
+    try {
+        BGL_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    } catch (...) {
+        cudaGraphDestroy(graph);
+        throw;
+    }
+    cudaGraphDestroy(graph);
+    try {
+        for (int k = 0; k < iters; ++k) BGL_CUDA(cudaGraphLaunch(exec, s));
+    } catch (...) {
+        cudaGraphExecDestroy(exec);
+        throw;
+    }
+    count_launches(per_iter * iters);
+    BGL_CUDA(cudaMemcpyAsync(ctx->h_flag + 1, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BGL_CUDA(cudaStreamSynchronize(s));
+    cudaGraphExecDestroy(exec);
+    run.check_fmm();
+    if (ctx->h_flag[1]) fail(BGL_ENUMERIC, "fa2: a position became non-finite");
+}
+
 // All `iters` iterations of `run` in one graph launch: the graph holds a
 // WHILE conditional node whose body is one captured iteration followed by a
 // one-thread kernel that counts the iterations and clears the condition
@@ -608,6 +660,10 @@ static void run_iterations(Fa2Run &run, int iters, double *d_stats) {
     BGL_CUDA(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
     BGL_CUDA(cudaMemsetAsync(run.iter.p, 0, sizeof(int), s));
     BGL_CUDA(cudaMemsetAsync(run.loop.p, 0, sizeof(int), s));
+    if (host_loop()) {
+        run_iterations_host(run, iters, d_stats);
+        return;
+    }
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     BGL_CUDA(cudaGraphCreate(&graph, 0));

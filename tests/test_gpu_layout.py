@@ -186,6 +186,23 @@ def test_fa2_three_iterations_from_random_start(c1):
     assert np.allclose(stats, ostats, rtol=1e-4)
 
 
+def test_fa2_host_loop_equals_device_loop(c1, monkeypatch):
+    """BGL_HOST_LOOP=1 launches the captured iteration once per iteration from
+    the host instead of the device-side loop; positions and statistics are
+    bitwise the same (exact and FMM repulsion)."""
+    bgl = _bgl()
+    vs, loff, ladj, mass = c1.comp(0)
+    x, y = oracle.init_positions(0, vs)
+    xy = np.stack([x, y], 1).astype(np.float32)
+    for p in (bgl.params(repulsion=bgl.REP_EXACT), bgl.params(repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=16)):
+        monkeypatch.delenv("BGL_HOST_LOOP", raising=False)
+        a, sa = c1.g.fa2_step(0, p, 7, xy)
+        monkeypatch.setenv("BGL_HOST_LOOP", "1")
+        b, sb = c1.g.fa2_step(0, p, 7, xy)
+        monkeypatch.delenv("BGL_HOST_LOOP", raising=False)
+        assert np.array_equal(a, b) and np.array_equal(sa, sb)
+
+
 def test_fa2_ten_iterations_match_oracle(c1):
     # ten fresh iterations (F_-1 = 0, s_G = 1) from a relaxed layout: the
     # oracle's 50-iteration result, rounded to FP32
