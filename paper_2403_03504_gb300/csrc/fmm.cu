@@ -1199,7 +1199,7 @@ __global__ void __launch_bounds__(256) m2l_bf16_kernel(Tree T, const float2 *__r
 // its points (P2M, one warp, fixed-order warp sum).  The few larger boxes near
 // the root get theirs by M2M from their four children, computed by the last
 // child to finish (an arrival count per box), so no warp waits.
-constexpr int P2M_MAX = 2048;
+constexpr int P2M_MAX = 512;
 
 template <int PT>
 __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
@@ -1416,6 +1416,8 @@ struct LeafArgs {
     int64_t q0, fbase;
     float kr;
     int *ticket;
+    int *heavy, *nheavy;  // leaves whose W list the far_heavy kernel takes, and their count
+    int heavy_cap;
 };
 
 // Near field: the direct sum over the points of U for every target of a
@@ -1586,6 +1588,28 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
 // expansion and M2P over W, the field E stored for the combine pass.
 constexpr int FAR_WARPS = 4;
 constexpr int FAR_W = 16;        // W entries staged in shared memory (longer lists read global memory)
+constexpr int FAR_HEAVY = 32;    // longer W lists: the M2P goes to far_heavy_kernel (eight warps per leaf)
+
+// M2P of W entry k at z: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
+template <int PT>
+__device__ __forceinline__ float2 m2p_term(const Tree &T, const Root *rt, const float2 *M, int p, int k, float4 z) {
+    const int Dx = T.lidx[k];
+    const int2 md_ = T.bmeta[Dx];
+    const BoxGeo gd = box_geo_xy(rt, md_.x, md_.y & 255);
+    const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
+    const float id2 = rcp_approx(fmaf(dz.x, dz.x, dz.y * dz.y));
+    const float2 idz = make_float2(dz.x * id2, -dz.y * id2);
+    const float2 tt2 = cscale(idz, gd.r);
+    const float2 *md = M + (size_t)Dx * (PT + 1);
+    float2 hs = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int kk = PT; kk >= 1; --kk) {
+        if (kk <= p) hs = cadd(cmul(hs, tt2), cscale(md[kk], (float)kk));
+    }
+    hs = cmul(hs, tt2);
+    const float2 a0 = md[0];
+    return cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz);
+}
 
 template <int PT>
 __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
@@ -1617,6 +1641,13 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
         const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
         const int nW = we - ws;
         const bool wst = nW <= FAR_W;
+        // a long W list is left to far_heavy_kernel, which spreads it over eight warps
+        const bool heavy = nW > FAR_HEAVY;
+        if (heavy && lane == 0) {
+            const int h = atomicAdd(la.nheavy, 1);
+            if (h < la.heavy_cap) la.heavy[h] = b;
+            else atomicOr(T.err, ERR_LIST_OVERFLOW);
+        }
         // a short W list: its boxes' geometry and expansions in shared memory
         if (wst && lane < nW) {
             const int Dx = T.lidx[ws + lane];
@@ -1688,7 +1719,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                 E = cscale(hs, ir);
             }
             // M2P: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
-            if (wst) {
+            if (heavy) {
+            } else if (wst) {
                 for (int i = 0; i < nW; ++i) {
                     const float4 gd = s_wg[wib][i];
                     const float2 dz = make_float2(z.x - gd.x, z.y - gd.y);
@@ -1704,25 +1736,50 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                     const float2 a0 = s_wm[wib][i][0];
                     E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
                 }
-            } else for (int k = ws; k < we; ++k) {
-                const int Dx = T.lidx[k];
-                const int2 md_ = T.bmeta[Dx];
-                const BoxGeo gd = box_geo_xy(rt, md_.x, md_.y & 255);
-                const float2 dz = make_float2(z.x - gd.cx, z.y - gd.cy);
-                const float id2 = rcp_approx(fmaf(dz.x, dz.x, dz.y * dz.y));
-                const float2 idz = make_float2(dz.x * id2, -dz.y * id2);
-                const float2 tt2 = cscale(idz, gd.r);
-                const float2 *md = la.e.M + (size_t)Dx * (PT + 1);
-                float2 hs = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int kk = PT; kk >= 1; --kk) {
-                    if (kk <= p) hs = cadd(cmul(hs, tt2), cscale(md[kk], (float)kk));
-                }
-                hs = cmul(hs, tt2);
-                const float2 a0 = md[0];
-                E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
-            }
+            } else for (int k = ws; k < we; ++k) E = cadd(E, m2p_term<PT>(T, rt, la.e.M, p, k, z));
             la.ef[__float_as_int(z.w)] = E;
+        }
+    }
+}
+
+// The M2P of the leaves with more than FAR_HEAVY W entries (a leaf next to a
+// finely divided region can have hundreds, which one warp would take alone
+// long after the rest of the far field is done): one block of eight warps
+// per leaf, warp w taking the entries w, w + 8, ..., lanes over 32 targets
+// at a time; warp 0 then adds the eight partial sums in order to the L2P
+// value that far_kernel stored.
+constexpr int HEAVY_WARPS = 8;
+
+template <int PT>
+__global__ void __launch_bounds__(HEAVY_WARPS * 32) far_heavy_kernel(LeafArgs la) {
+    __shared__ float2 part[HEAVY_WARPS][32];
+    const Tree &T = la.e.T;
+    const Root *rt = T.root;
+    const int p = la.e.p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nh = min(*la.nheavy, la.heavy_cap);
+    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int b = la.heavy[h];
+        const int s = T.bstart[b], e = T.bend[b];
+        const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
+        for (int t0 = s; t0 < e; t0 += 32) {
+            const int tt = t0 + lane;
+            float2 acc = make_float2(0.f, 0.f);
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tt < e) {
+                z = T.pts[tt];
+                for (int k = ws + warp; k < we; k += HEAVY_WARPS) acc = cadd(acc, m2p_term<PT>(T, rt, la.e.M, p, k, z));
+            }
+            part[warp][lane] = acc;
+            __syncthreads();
+            if (warp == 0 && tt < e) {
+                const int o = __float_as_int(z.w);
+                float2 E = la.ef[o];
+#pragma unroll
+                for (int w = 0; w < HEAVY_WARPS; ++w) E = cadd(E, part[w][lane]);
+                la.ef[o] = E;
+            }
+            __syncthreads();
         }
     }
 }
@@ -1825,6 +1882,7 @@ struct FmmPlan {
     DevBuf<int2> vpairs;      // [vcap]
     DevBuf<float> vout;       // [vcap * VROWS]
     DevBuf<float2> ef;
+    DevBuf<int> heavy;        // [Bmax] leaves handed to far_heavy_kernel
     DevBuf<ulonglong2> hkv;
     DevBuf<unsigned> epoch;
     int hmask = 0;
@@ -1906,6 +1964,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
             BGL_CUDA(cudaMemcpyAsync(pl->tfrag.p, frag.data(), sizeof(uint4) * frag.size(), cudaMemcpyHostToDevice, s));
         }
         pl->ef.reset(A, n);
+        pl->heavy.reset(A, bmax);
         int64_t hs = 1;
         while (hs < 2 * bmax) hs <<= 1;
         pl->hmask = (int)(hs - 1);
@@ -1995,6 +2054,9 @@ static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbas
     la.ticket = pl->tickets.p + 2;
     la.ef = pl->ef.p;
     la.mass = pl->g->mass.p + pl->q0;
+    la.heavy = pl->heavy.p;
+    la.nheavy = pl->tickets.p + 4;
+    la.heavy_cap = pl->Bmax;
     return la;
 }
 
@@ -2074,6 +2136,8 @@ static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
 template <int PT>
 static void launch_far(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
     far_kernel<PT><<<2 * pl->grid_p, FAR_WARPS * 32, 0, s>>>(la);
+    BGL_LAUNCH_CHECK();
+    far_heavy_kernel<PT><<<pl->g->ctx->num_sms, HEAVY_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
 }
 static void launch_combine(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
