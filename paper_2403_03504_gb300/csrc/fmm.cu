@@ -1588,7 +1588,7 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
 // expansion and M2P over W, the field E stored for the combine pass.
 constexpr int FAR_WARPS = 4;
 constexpr int FAR_W = 16;        // W entries staged in shared memory (longer lists read global memory)
-constexpr int FAR_HEAVY = 32;    // longer W lists: the M2P goes to far_heavy_kernel (eight warps per leaf)
+constexpr int FAR_HEAVY = 16;    // longer W lists: the M2P goes to far_heavy_kernel (sixteen warps per leaf)
 
 // M2P of W entry k at z: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
 template <int PT>
@@ -1641,7 +1641,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
         const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
         const int nW = we - ws;
         const bool wst = nW <= FAR_W;
-        // a long W list is left to far_heavy_kernel, which spreads it over eight warps
+        // a W list longer than the staging is left to far_heavy_kernel, which spreads it over warps
         const bool heavy = nW > FAR_HEAVY;
         if (heavy && lane == 0) {
             const int h = atomicAdd(la.nheavy, 1);
@@ -1743,12 +1743,12 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
 }
 
 // The M2P of the leaves with more than FAR_HEAVY W entries (a leaf next to a
-// finely divided region can have hundreds, which one warp would take alone
-// long after the rest of the far field is done): one block of eight warps
-// per leaf, warp w taking the entries w, w + 8, ..., lanes over 32 targets
-// at a time; warp 0 then adds the eight partial sums in order to the L2P
-// value that far_kernel stored.
-constexpr int HEAVY_WARPS = 8;
+// finely divided region can have hundreds, which one warp reading them from
+// global memory would take alone long after the rest of the far field is
+// done): one block of HEAVY_WARPS warps per leaf, warp w taking the entries
+// w, w + HEAVY_WARPS, ..., lanes over 32 targets at a time; warp 0 then adds
+// the partial sums in warp order to the L2P value that far_kernel stored.
+constexpr int HEAVY_WARPS = 16;
 
 template <int PT>
 __global__ void __launch_bounds__(HEAVY_WARPS * 32) far_heavy_kernel(LeafArgs la) {
