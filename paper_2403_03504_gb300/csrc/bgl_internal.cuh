@@ -197,7 +197,7 @@ struct OsHist {
     unsigned *counter;   // arrival count of the blocks (reset by the last block)
     unsigned *tickets;   // 4 pass tickets
     uint32_t *status;    // 4 x ntiles x 256 look-back status words
-    int64_t ntiles;      // tiles of 256 x 8 keys
+    int64_t ntiles;      // tiles of 256 x 16 keys
 };
 // With clear = false the caller zeroes hist and tickets in a kernel that
 // runs before its histogram kernel, and each block of the histogram kernel

@@ -331,7 +331,7 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
 
 // Morton keys (KEY_ITEMS per thread) and, in the same pass, the digit
 // histograms of the radix sort that orders them
-constexpr int KEY_ITEMS = 8;
+constexpr int KEY_ITEMS = 16;
 
 __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
                                                    uint32_t *__restrict__ key, uint32_t *__restrict__ idx, OsHist h) {
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy
             valid |= 1u << r;
         }
     }
-    static_assert(256 * KEY_ITEMS == 2048, "a key block is one radix tile");
+    static_assert(256 * KEY_ITEMS == 4096, "a key block is one radix tile (256 threads x 16 keys)");
     os_clear_status(h, blockIdx.x);
     os_block_hist<KEY_ITEMS>(k, valid, h);
 }

@@ -271,7 +271,7 @@ void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
 
 constexpr int OS_THREADS = 256;
 constexpr int OS_WARPS = OS_THREADS / 32;
-constexpr int OS_ITEMS = 8;
+constexpr int OS_ITEMS = 16;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_MASK = (1u << 30) - 1u;
 constexpr long long OS_SPIN = 1ll << 24;
