@@ -354,7 +354,7 @@ bgl_status bgl_state_load(bgl_graph *g, const void *buf, size_t len);
 
 /* ---------------------------------------------------------------- profiling */
 
-#define BGL_FMM_NSTATS 17
+#define BGL_FMM_NSTATS 18
 
 /*
  * Profiling aid for the Fast Multipole repulsion (Section 3.2.1) on
@@ -375,7 +375,9 @@ bgl_status bgl_state_load(bgl_graph *g, const void *buf, size_t len);
  *   evaluation (radix sort over all 32 key bits) and the last one, whose sort
  *   skips the two low passes when the previous tree was at most 8 levels
  *   deep (then the trees are the same and only the order of points inside
- *   a leaf differs); 16 the passes skipped by the last evaluation (0 or 2).
+ *   a leaf differs); 16 the passes skipped by the last evaluation (0 or 2);
+ *   17 leaves whose W list is longer than the 16 entries the far-field
+ *   kernel stages (their M2P runs on sixteen warps per leaf).
  * Synchronises the stream.
  */
 bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, int32_t reps,

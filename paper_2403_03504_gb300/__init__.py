@@ -131,7 +131,7 @@ def _load():
 
 
 FMM_STATS = ("boxes", "leaves", "depth", "p2p_pairs", "m2l", "m2p", "p2l", "ms_points", "ms_tree", "ms_lists",
-             "ms_up", "ms_down", "ms_near", "ms_far", "ms_total", "sortmode_rel_diff", "sort_skip")
+             "ms_up", "ms_down", "ms_near", "ms_far", "ms_total", "sortmode_rel_diff", "sort_skip", "w_heavy")
 
 
 class Server:

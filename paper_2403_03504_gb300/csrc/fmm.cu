@@ -2213,7 +2213,7 @@ namespace {
 // interaction counts: P2P pairs, M2P and P2L point-box terms
 __global__ void count_kernel(Tree T, unsigned long long *out) {
     const int B = min(T.levoff[NLEV], T.Bmax);
-    unsigned long long p2p = 0, m2p = 0, p2l = 0, leaves = 0, depth = 0, m2l = 0;
+    unsigned long long p2p = 0, m2p = 0, p2l = 0, leaves = 0, depth = 0, m2l = 0, heavy = 0;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
         depth = max(depth, (unsigned long long)T.blevel[b]);
         m2l += (unsigned long long)(T.lofs[5 * b + 2] - T.lofs[5 * b + 1]);
@@ -2232,6 +2232,7 @@ __global__ void count_kernel(Tree T, unsigned long long *out) {
         }
         p2p += nt * ns;
         m2p += nt * (unsigned long long)(T.lofs[5 * b + 3] - T.lofs[5 * b + 2]);
+        heavy += (T.lofs[5 * b + 3] - T.lofs[5 * b + 2]) > FAR_HEAVY ? 1ull : 0ull;
     }
     atomicAdd(&out[0], p2p);
     atomicAdd(&out[1], m2p);
@@ -2239,6 +2240,7 @@ __global__ void count_kernel(Tree T, unsigned long long *out) {
     atomicAdd(&out[3], leaves);
     atomicMax(&out[4], depth);
     atomicAdd(&out[5], m2l);
+    atomicAdd(&out[6], heavy);
 }
 
 }  // namespace
@@ -2297,11 +2299,11 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
         dmax = std::max(dmax, (double)std::hypot(f_last[i].x - f_first[i].x, f_last[i].y - f_first[i].y));
         fmax = std::max(fmax, (double)std::hypot(f_first[i].x, f_first[i].y));
     }
-    DevBuf<unsigned long long> cnt(ctx->alloc, 6);
-    BGL_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 6, s));
+    DevBuf<unsigned long long> cnt(ctx->alloc, 7);
+    BGL_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 7, s));
     count_kernel<<<pl->grid_p, 256, 0, s>>>(T, cnt.p);
     BGL_LAUNCH_CHECK();
-    unsigned long long h[6];
+    unsigned long long h[7];
     int lev[NLEV + 1];
     BGL_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     BGL_CUDA(cudaMemcpyAsync(lev, pl->levoff.p, sizeof(lev), cudaMemcpyDeviceToHost, s));
@@ -2317,6 +2319,7 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
     for (int k = 0; k < 8; ++k) out[7 + k] = acc[k] / R;
     out[15] = fmax > 0.0 ? dmax / fmax : 0.0;
     out[16] = (double)skip_last;
+    out[17] = (double)h[6];
 }
 
 int fmm_sortskip(FmmPlan *pl) {

@@ -131,6 +131,28 @@ def test_fmm_small_leaf_sizes(path30k):
         assert e.max() <= ceiling(12), (leaf, e.max())
 
 
+def test_fmm_long_w_lists(path30k):
+    """Coarse leaves next to a finely divided cluster get long W lists (more
+    than the 16 entries the far-field kernel stages); their M2P runs in the
+    heavy-leaf kernel, sixteen warps per leaf.  The forces of those leaves'
+    points stay within the error ceiling, at p = 8 and p = 16."""
+    bgl = _bgl()
+    rng = np.random.default_rng(12)
+    n = path30k.n
+    xy = np.empty((n, 2), np.float32)
+    xy[:2000] = rng.uniform(0, 100, (2000, 2))                 # sparse: coarse leaves
+    xy[2000:] = 50.0 + rng.uniform(0, 1, (n - 2000, 2))          # dense: deep subdivision
+    exact = path30k.g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy)
+    sample = np.concatenate([rng.choice(2000, 250, replace=False), 2000 + rng.choice(n - 2000, 50, replace=False)])
+    for p in (8, 16):
+        prm = bgl.params(repulsion=bgl.REP_FMM, fmm_p=p)
+        st = path30k.g.fmm_stats(0, prm, xy, reps=1)
+        assert st["w_heavy"] > 0, st
+        f = path30k.g.fa2_repulsion(0, prm, xy)
+        e, _ = _errors(f, exact, xy, path30k, sample)
+        assert e.max() <= ceiling(p), (p, e.max(), ceiling(p))
+
+
 @pytest.mark.parametrize("kind", ["uniform", "clustered"])
 def test_fmm_bf16_m2l_error(path30k, kind):
     """M2L translations in BF16 on the tensor cores (FP32 accumulate, every
