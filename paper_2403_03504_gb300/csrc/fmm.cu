@@ -1585,10 +1585,12 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
 //   b~_m(leaf) += 2^(-D m) sum_{l >= m} b~_l(A) C(l, m) t^(l-m),
 //   t = (c_leaf - c_A) / r_A, D = level(leaf) - level(A);
 // lane m computes coefficient m.  Then, a lane per target: L2P of that
-// expansion and M2P over W, the field E stored for the combine pass.
+// expansion and M2P over W (W boxes staged in shared memory), the field E
+// stored for the combine pass; a longer W list is far_heavy_kernel's.
 constexpr int FAR_WARPS = 4;
-constexpr int FAR_W = 16;        // W entries staged in shared memory (longer lists read global memory)
+constexpr int FAR_W = 16;        // W entries staged in shared memory
 constexpr int FAR_HEAVY = 16;    // longer W lists: the M2P goes to far_heavy_kernel (sixteen warps per leaf)
+static_assert(FAR_HEAVY <= FAR_W, "every W list the far kernel keeps fits its staging");
 
 // M2P of W entry k at z: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
 template <int PT>
@@ -1640,9 +1642,9 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
         const int s = T.bstart[b], e = T.bend[b];
         const int ws = T.lofs[5 * b + 2], we = T.lofs[5 * b + 3];
         const int nW = we - ws;
-        const bool wst = nW <= FAR_W;
         // a W list longer than the staging is left to far_heavy_kernel, which spreads it over warps
         const bool heavy = nW > FAR_HEAVY;
+        const bool wst = !heavy;
         if (heavy && lane == 0) {
             const int h = atomicAdd(la.nheavy, 1);
             if (h < la.heavy_cap) la.heavy[h] = b;
@@ -1719,8 +1721,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                 E = cscale(hs, ir);
             }
             // M2P: E += (a~_0 - sum_k k a~_k t^k) / (z - c_D), t = r_D / (z - c_D)
-            if (heavy) {
-            } else if (wst) {
+            // (a list longer than the staging is far_heavy_kernel's)
+            if (!heavy) {
                 for (int i = 0; i < nW; ++i) {
                     const float4 gd = s_wg[wib][i];
                     const float2 dz = make_float2(z.x - gd.x, z.y - gd.y);
@@ -1736,7 +1738,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
                     const float2 a0 = s_wm[wib][i][0];
                     E = cadd(E, cmul(make_float2(a0.x - hs.x, a0.y - hs.y), idz));
                 }
-            } else for (int k = ws; k < we; ++k) E = cadd(E, m2p_term<PT>(T, rt, la.e.M, p, k, z));
+            }
             la.ef[__float_as_int(z.w)] = E;
         }
     }
