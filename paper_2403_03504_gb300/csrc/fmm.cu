@@ -13,8 +13,10 @@
 //   bbox      root square covering all points (FP32 min/max, FP64 geometry)
 //   keys      16-bit quantised x, y interleaved into 32-bit Morton keys, with
 //             the digit histograms of the sort in the same pass
-//   sort      stable radix sort of (key, index), four onesweep passes; the
-//             last writes x, y, m in key order
+//   sort      stable radix sort of (key, index), four onesweep passes over
+//             tiles of 4,096 keys (the two low ones skipped when the last
+//             tree was at most 8 levels deep); the last writes x, y, m in
+//             key order
 //   tree      adaptive quadtree: a box is split while it holds more than
 //             leaf_size points (and is above level 16).  The leaf level of
 //             point i is 1 + the deepest level at which some window of
@@ -29,14 +31,15 @@
 //             cells" of Section 3.2.1), W and X (the adaptive-tree lists of
 //             Carrier, Greengard and Rokhlin that make every pair counted
 //             exactly once)
-//   up        P2M from the points for boxes of up to 2048 points; M2M from
+//   up        P2M from the points for boxes of up to 512 points; M2M from
 //             the 4 children for the larger ones, by the last child to finish
 //   m2l       per box, independently: M2L over V + P2L over X (a partial
 //             incoming expansion)
 //   near      per leaf: the direct P2P sum over the points of U
 //   far       per leaf: the incoming expansion composed from the partial
 //             expansions of the leaf and all its ancestors (the L2L chain,
-//             one shift per ancestor), L2P at the targets, M2P over W
+//             one shift per ancestor), L2P at the targets, M2P over W (a W
+//             list longer than 16 entries: far_heavy, 16 warps per leaf)
 //   combine   per point: the force from the near sum and the far field
 // Near and far run concurrently (main and side stream); the combine pass
 // joins them.
