@@ -55,6 +55,20 @@ PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * PAIRS_PER_CLK
 NEAR_TRAFFIC_BYTES = 11_209_216 + 0
 
 
+def reduce_units_time(dist, units: float, seconds: float, device=None):
+    """Whole-job totals over the ranks: the units all ranks processed and the
+    slowest rank's time (every rank calls it; without a process group, the
+    rank's own numbers)."""
+    if dist is None:
+        return units, seconds
+    import torch
+    t = torch.tensor([units, seconds], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    return float(t[0]), float(tmax[1])
+
+
 def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, slots=4, budget=120 << 30):
     """Poisson arrivals (rate per second) of k-hop layout requests (k uniform
     in 1..4, seeds uniform over the graph's address nodes, redrawn until the
@@ -173,12 +187,15 @@ def run_c3(args, rank, world, dist, local):
     for _ in range(max(args.warmup, 3)):
         g.layout_dev(p, d_xy)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     launches0 = bgl.launch_count()
     step_ms = timed(p, args.steps)
     launches = (bgl.launch_count() - launches0) // max(args.steps, 1)
     kk_ms = timed(p_kk, args.steps)
-    total_s = sum(step_ms) / 1e3
-    value = fa2_nodes * iters * args.steps / total_s
+    upd, total_s = reduce_units_time(dist, float(fa2_nodes) * iters * args.steps, sum(step_ms) / 1e3,
+                                     torch.device("cuda", local))
+    value = upd / total_s
     if rank == 0:
         print(json.dumps({
             "metric": "C3 batched layout: FA2 node-updates/s (exact repulsion) with KK on 1e5 components",
@@ -370,11 +387,11 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if args.workload == "c3":
-        run_c3(args, rank, world, dist, local)
-        return
-    if args.workload == "serve":
-        run_serve(args, rank, world, dist, local)
+    if args.workload in ("c3", "serve"):
+        (run_c3 if args.workload == "c3" else run_serve)(args, rank, world, dist, local)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
         return
     tx = synth.tx_lists(**synth.C2)
     stream = torch.cuda.Stream(device=dev)
@@ -462,25 +479,22 @@ def main():
             dist.destroy_process_group()
         return
     total_s = sum(step_ms) / 1e3
-    upd = float(fa2_nodes) * args.iters * args.steps
-    if dist:
-        t = torch.tensor([upd, total_s], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        upd, total_s = float(t[0]), float(tmax[1])
+    upd_rank = float(fa2_nodes) * args.iters * args.steps
+    upd, total_s = reduce_units_time(dist, upd_rank, total_s, dev)
     value = upd / total_s
 
     # ---------------------------------------------------------------- timed: end to end (host buffers)
     step_e2e()
     e2e_times = []
+    if dist:
+        dist.barrier()
     for k in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         step_e2e()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times)
-    e2e_value = float(fa2_nodes) * args.iters * args.steps / e2e_s
+    e2e_upd, e2e_s = reduce_units_time(dist, upd_rank, sum(e2e_times), dev)
+    e2e_value = e2e_upd / e2e_s
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = h_xy.numel() * 4 + 8 * (len(coff))          # coordinates + component offsets
 
