@@ -534,7 +534,9 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
     constexpr int PW = TREE_TILE / NW;                 // points per warp
     __shared__ int wcount[NLEV][NW];
     __shared__ int smax;
+    __shared__ int stc[NLEV];          // the tile's offset at every level, loaded once
     if (threadIdx.x == 0) smax = 0;
+    if (threadIdx.x < NLEV) stc[threadIdx.x] = tcnt[threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
     const unsigned epoch = *T.epoch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -592,7 +594,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const i
         pf[r] = false;
     }
     for (int L = 0; L <= Lmax; ++L) {
-        int base = tcnt[L * ntiles + blockIdx.x];
+        int base = stc[L];
         for (int w = 0; w < warp; ++w) base += wcount[L][w];
         if (!((lm >> L) & 1u)) {
             // no start or end at this level: before_L(i) = base for every point
