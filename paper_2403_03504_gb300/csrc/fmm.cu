@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy
             valid |= 1u << r;
         }
     }
-    static_assert(256 * KEY_ITEMS == 4096, "a key block is one radix tile (256 threads x 16 keys)");
+    static_assert(256 * KEY_ITEMS == OS_TILE, "a key block is one radix tile");
     os_clear_status(h, blockIdx.x);
     os_block_hist<KEY_ITEMS>(k, valid, h);
 }

@@ -269,10 +269,8 @@ void radix_sort(bgl_ctx *c, K *keys, uint32_t *vals, int64_t n, int bits) {
 // memory so each digit run is written with coalesced stores.  Waits are
 // bounded; a wait that gives up records an error bit and the tile carries on.
 
-constexpr int OS_THREADS = 256;
+// OS_THREADS, OS_ITEMS, OS_TILE: sort_hist.cuh (a caller's histogram kernel uses the same tiles)
 constexpr int OS_WARPS = OS_THREADS / 32;
-constexpr int OS_ITEMS = 16;
-constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_MASK = (1u << 30) - 1u;
 constexpr long long OS_SPIN = 1ll << 24;
 constexpr int OS_LB = 8;           // look-back window (predecessor tiles per step)

@@ -4,6 +4,12 @@
 
 namespace bgl {
 
+// Radix tiles: OS_THREADS threads x OS_ITEMS keys.  A caller's histogram
+// kernel (os_block_hist, os_clear_status) runs one block per tile.
+constexpr int OS_THREADS = 256;
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
+
 // Adds the block's keys (key[r] for the bits r of `valid`) to the four 8-bit
 // digit histograms of h (shared-memory counts, then one global atomic per
 // non-empty bin); the last block to arrive writes the exclusive digit bases
