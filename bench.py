@@ -145,6 +145,62 @@ def run_serve(args, rank, world, dist, local):
     ctx.close()
 
 
+def run_precision(args, rank, world, dist, local):
+    """Precision study at scale: the 3M-transaction graph (seed 4, ~1e7 nodes),
+    200 ForceAtlas2 iterations with FMM p = 12 on its giant component, then,
+    at those positions, the repulsion with the M2L in FP32 and in BF16 on the
+    tensor cores, each against the FP64 oracle's exact sum on 10,000 sampled
+    nodes and against the GPU's FP32 exact sum on every node."""
+    import synth
+    import oracle
+    import paper_2403_03504_gb300 as bgl
+    if rank != 0:
+        return
+    tx = synth.tx_lists(**synth.C4)
+    ctx = bgl.Context(local)
+    g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    g.components(labels=False)
+    coff, _, nodes = g.component_nodes()
+    vs = nodes[coff[0]:coff[1]]
+    n = len(vs)
+    off, _ = g.csr()
+    mass = (np.diff(off)[vs] + 1).astype(np.float64)
+    x0, y0 = oracle.init_positions(0, vs)
+    xy0 = np.stack([x0, y0], 1).astype(np.float32)
+    t0 = time.perf_counter()
+    xy, _ = g.fa2_step(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=12), 200, xy0)
+    run_s = time.perf_counter() - t0
+    exact = g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_EXACT), xy).astype(np.float64)
+    sample = np.sort(np.random.default_rng(0).choice(n, 10_000, replace=False))
+    t1 = time.perf_counter()
+    o = oracle.fa2_forces(xy[:, 0], xy[:, 1], mass, np.zeros(n + 1, np.int64), np.zeros(0, np.int32),
+                          1.0, 1.0, targets=sample)
+    oracle_s = time.perf_counter() - t1
+    ref = o["frep"]
+    den = np.sqrt(np.mean(np.sum(ref ** 2, 1)))
+    out = {"n_tx": tx.n_tx, "giant_nodes": n, "fmm_p": 12, "fa2_iters": 200, "fa2_seconds": run_s,
+           "oracle_sample": int(len(sample)), "oracle_seconds": oracle_s, "oracle_cores": oracle.threads(),
+           "gpu_exact_vs_oracle_rms": float(np.sqrt(np.mean(np.sum((exact[sample] - ref) ** 2, 1))) / den)}
+    for name, bf in (("fp32", 0), ("bf16", 1)):
+        pq = bgl.params(repulsion=bgl.REP_FMM, fmm_p=12, m2l_bf16=bf)
+        f = g.fa2_repulsion(0, pq, xy).astype(np.float64)
+        e = np.hypot(*(f[sample] - ref).T) / o["srep"]
+        out[name] = {
+            "rms_rel_vs_oracle": float(np.sqrt(np.mean(np.sum((f[sample] - ref) ** 2, 1))) / den),
+            "max_norm_err_vs_oracle": float(e.max()),
+            "rms_rel_vs_gpu_exact": float(np.sqrt(np.mean(np.sum((f - exact) ** 2, 1)) /
+                                                  np.mean(np.sum(exact ** 2, 1)))),
+            "ms_down": g.fmm_stats(0, pq, xy, reps=3)["ms_down"],
+        }
+        out[name]["ms_total"] = g.fmm_stats(0, pq, xy, reps=3)["ms_total"]
+    print(json.dumps({"metric": "FMM M2L precision at scale: RMS relative repulsion error vs the FP64 oracle",
+                      "value": out["bf16"]["rms_rel_vs_oracle"], "unit": "relative RMS (BF16 M2L)",
+                      "higher_is_better": False, "n_gpus": world, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "precision-3m-tx", "seed": 4}, "precision": out}), flush=True)
+    g.destroy()
+    ctx.close()
+
+
 def run_c3(args, rank, world, dist, local):
     """Batched components: 100,000 forest components of 3-200 nodes (KK, at
     most 200 nodes) and 2,000 of 200-5,000 nodes (ForceAtlas2 with exact
@@ -352,9 +408,10 @@ def main():
     ap.add_argument("--exact-iters", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "serve"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "serve", "precision"],
                     help="c2: the headline 200k-transaction graph; c3: 1e5 small + 2e3 mid-size components; "
-                         "serve: k-hop layout requests on the 3M-transaction graph")
+                         "serve: k-hop layout requests on the 3M-transaction graph; "
+                         "precision: FP32 against BF16 M2L on the 3M-transaction graph's giant component")
     ap.add_argument("--requests", type=int, default=0, help="serving requests (0: 40 in the c2 line, 100 for serve)")
     ap.add_argument("--slots", type=int, default=4, help="serving workers")
     ap.add_argument("--timed-only", action="store_true",
@@ -387,8 +444,8 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if args.workload in ("c3", "serve"):
-        (run_c3 if args.workload == "c3" else run_serve)(args, rank, world, dist, local)
+    if args.workload in ("c3", "serve", "precision"):
+        {"c3": run_c3, "serve": run_serve, "precision": run_precision}[args.workload](args, rank, world, dist, local)
         if dist:
             dist.barrier()
             dist.destroy_process_group()
