@@ -50,8 +50,8 @@ CONFIG_NAME = "fmm-fa2-200k-tx"
 SMS, SM_MAX_MHZ, PAIRS_PER_CLK = 152, 2070.0, 16.0
 PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * PAIRS_PER_CLK
 # DRAM bytes (read + write) of one near_kernel launch on this workload's
-# giant component, from the ncu capture summarised in
-# profiles/near_kernel_fmm_c2_giant.md (the working set is L2-resident)
+# giant component at its final layout, from an ncu capture of that launch
+# (the working set is L2-resident)
 NEAR_TRAFFIC_BYTES = 11_209_216 + 0
 
 

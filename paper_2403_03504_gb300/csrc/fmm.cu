@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t
     }
     __syncthreads();
     // maxima of g over runs of P entries, P the largest power of two <= S + 1
-    // (doubling: after the round of step h, g[k] = max g[k .. k + 2h - 1])
+    // (doubling: after the pass with step h, g[k] = max g[k .. k + 2h - 1])
     int P = 1;
     while (2 * P <= S + 1) P *= 2;
     constexpr int GM = (TREE_TILE + 256 + TREE_THREADS - 1) / TREE_THREADS;
