@@ -60,6 +60,7 @@ def _load():
                 "orc_kk_energy": ([_I64, _VP, _VP, _VP, _D], _D),
                 "orc_kk_grad_hess": ([_I64, _VP, _VP, _VP, _D, _I64, _VP], None),
                 "orc_kk_run": ([_I64, _VP, _VP, _VP, _D, _I64, _D, _VP, _VP], _I64),
+                "orc_kk_step": ([_VP, _D, _VP, _VP], ctypes.c_int),
                 "orc_fa2_forces": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D, _I64, _VP] + [_VP] * 8, None),
                 "orc_fa2_energy": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D], _D),
                 "orc_fa2_run": ([_I64, _VP, _VP, _VP, _VP, _VP, _D, _D, _D, _D, _D, ctypes.c_int32,
@@ -223,6 +224,16 @@ def kk_grad_hess(x, y, d, l, m):
     out = np.zeros(5)
     _load().orc_kk_grad_hess(len(x), _p(x), _p(y), _p(d), l, m, _p(out))
     return out
+
+
+def kk_step(g, H, l):
+    """The safeguarded 2x2 Newton step of one node (Section 3.1): g the
+    half-gradient (2,), H the half-Hessian (2, 2), l the step-length cap.
+    Returns (step (2,), moved)."""
+    o = np.array([g[0], g[1], H[0][0], H[0][1], H[1][1]], np.float64)
+    dx, dy = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    moved = _load().orc_kk_step(_p(o), float(l), ctypes.byref(dx), ctypes.byref(dy))
+    return np.array([dx.value, dy.value]), bool(moved)
 
 
 def kk_run(x, y, d, l=1.0, sweeps=200, tol=0.0):

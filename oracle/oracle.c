@@ -42,7 +42,11 @@
  *     are replaced by max(|l|, 0.1 max|l|), and steps are no longer than l
  *     (a safeguarded Newton-Raphson step: the plain step diverges from
  *     random starts where H is indefinite).
- * "parity unpinned": none (every function has a pin in tests/test_oracle.py).
+ * "parity unpinned": none.  Every function has a pin in tests/test_oracle.py;
+ * the safeguarded KK step (orc_kk_step) by hand-worked 2x2 cases
+ * (tests/golden/kk_newton_step.json: plain, shortened, indefinite, floored,
+ * zero), both swing/traction variants by a hand-worked iteration of a
+ * three-node path with unequal masses (tests/golden/fa2_swing_variants.json).
  */
 #include <math.h>
 #include <stdint.h>
@@ -407,9 +411,9 @@ void orc_kk_grad_hess(int64_t n, const double *x, const double *y, const int32_t
  * step is shorter than l this is the plain Newton step; elsewhere the
  * directions of non-positive curvature are treated as positive (the plain
  * step there climbs the energy and throws nodes away from random starts).
- * H = 0 gives no step (returns 0).
+ * H = 0 gives no step (returns 0).  o = {g_x, g_y, H_xx, H_xy, H_yy}.
  */
-static int orc_kk_step(const double *o, double l, double *dxm, double *dym)
+int orc_kk_step(const double *o, double l, double *dxm, double *dym)
 {
     double gx = o[0], gy = o[1], a = o[2], b = o[3], c = o[4];
     double tr = 0.5 * (a + c);

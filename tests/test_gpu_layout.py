@@ -1,9 +1,11 @@
 """GPU parity of the layout kernels against the FP64 oracle.
 
-Kamada-Kawai (Section 3.1): BFS distances bit-exact; one sweep of Newton
+Kamada-Kawai (Section 3.1): BFS distances bit-exact; ten sweeps of Newton
 steps within 1e-3 of the component diameter; ten sweeps from the oracle's
-minimum stay there; 200 sweeps from random starts end stationary and (where
-the chaotic early sweeps do not part ways) at the oracle's energy.  ForceAtlas2 (Section 3.2): forces within 1e-5 of
+minimum stay there; 200 sweeps from random starts end stationary and at the
+oracle's energy.  A component may differ only where the oracle itself,
+started from one-ulp moves of the same FP32 start, ends that far away too
+(tests/kk_sensitivity.py).  ForceAtlas2 (Section 3.2): forces within 1e-5 of
 the sum of contribution magnitudes (FP32 direct sum), positions within 1e-3
 of the bounding-box diagonal after 10 iterations, and long runs compared by
 layout energy and edge-length statistics (the iteration is chaotic)."""
@@ -14,6 +16,7 @@ import os
 import numpy as np
 import pytest
 
+import kk_sensitivity
 import oracle
 import synth
 
@@ -93,11 +96,15 @@ def _kk_components(b, lo=2, hi=255, step=1):
     return np.flatnonzero((sizes >= lo) & (sizes <= hi))[::step]
 
 
-def test_kk_one_sweep_matches_oracle(c1, forest):
-    """One Gauss-Seidel sweep of Newton steps from the same FP32 start."""
+def test_kk_ten_sweeps_match_oracle(c1, forest):
+    """Ten Gauss-Seidel sweeps from the same FP32 start: positions within
+    1e-3 of the diameter for every component, unless the oracle itself,
+    started from one-ulp moves of that start, ends farther than 1e-4 of the
+    diameter from its unperturbed run (the early sweeps from random starts
+    amplify rounding a thousandfold there)."""
     bgl = _bgl()
-    p = bgl.params(kk_sweeps=1)
-    errs = []
+    p = bgl.params(kk_sweeps=10)
+    checked, excused = 0, []
     for b in (c1, forest):
         for c in _kk_components(b, step=2):
             vs, loff, ladj, _ = b.comp(c)
@@ -105,10 +112,16 @@ def test_kk_one_sweep_matches_oracle(c1, forest):
             x, y = _kk_start(5, vs, d)
             xy = np.stack([x, y], 1).astype(np.float32)
             got = b.g.kk_run(int(c), p, xy)
-            ox, oy, _, _, _ = oracle.kk_run(xy[:, 0].astype(np.float64), xy[:, 1].astype(np.float64), d, 1.0, 1)
-            errs.append(np.max(np.hypot(got[:, 0] - ox, got[:, 1] - oy)) / max(1, d.max()))
-    errs = np.array(errs)
-    assert np.max(errs) <= 1e-3, np.sort(errs)[-5:]
+            ox, oy, _, _, _ = oracle.kk_run(xy[:, 0].astype(np.float64), xy[:, 1].astype(np.float64), d, 1.0, 10)
+            diam = max(1, int(d.max()))
+            err = np.max(np.hypot(got[:, 0] - ox, got[:, 1] - oy)) / diam
+            checked += 1
+            if err <= 1e-3:
+                continue
+            _, spread, _ = kk_sensitivity.oracle_spread(xy[:, 0], xy[:, 1], d, 10)
+            assert spread / diam > 1e-4, (int(c), len(vs), err, spread / diam)
+            excused.append(int(c))
+    assert checked > 200 and len(excused) < checked // 2, (checked, excused)
 
 
 def test_kk_stays_at_the_oracle_minimum(forest):
@@ -127,13 +140,15 @@ def test_kk_stays_at_the_oracle_minimum(forest):
 
 
 def test_kk_full_run_reaches_the_oracle_minimum(forest):
-    """200 sweeps from the same start: the GPU run is stationary and, except
-    where the early sweeps part ways (the iteration is chaotic from random
-    starts), ends at the oracle's energy."""
+    """200 sweeps from the same start: the GPU run is stationary and ends at
+    the oracle's energy (1e-4 relative) on every component, unless the
+    oracle itself, from one-ulp moves of the start, ends at another energy
+    (the larger components, where rounding decides which minimum the early
+    sweeps fall into)."""
     bgl = _bgl()
     p = bgl.params(kk_sweeps=200)
-    rel = []
-    for c in _kk_components(forest, lo=3, hi=120, step=4):
+    checked, excused = 0, []
+    for c in _kk_components(forest, lo=3, hi=255, step=4):
         vs, loff, ladj, _ = forest.comp(c)
         d = oracle.bfs_apsp(loff, ladj)
         x, y = _kk_start(5, vs, d)
@@ -143,10 +158,13 @@ def test_kk_full_run_reaches_the_oracle_minimum(forest):
         eg = oracle.kk_energy(got[:, 0], got[:, 1], d, 1.0)
         gmax = max(np.hypot(*oracle.kk_grad_hess(got[:, 0], got[:, 1], d, 1.0, m)[:2]) for m in range(len(vs)))
         assert gmax <= 1e-3 * max(1.0, e[-1]), (c, gmax)
-        rel.append((eg - e[-1]) / max(e[-1], 1e-12))
-    rel = np.array(rel)
-    assert np.mean(np.abs(rel) <= 1e-4) >= 0.8, np.sort(rel)
-    assert abs(np.mean(rel)) <= 0.01, np.mean(rel)
+        checked += 1
+        if kk_sensitivity.energy_close(eg, e[-1]):
+            continue
+        _, _, other = kk_sensitivity.oracle_spread(xy[:, 0], xy[:, 1], d, 200)
+        assert other, (int(c), len(vs), eg, e[-1])
+        excused.append(int(c))
+    assert checked > 60 and len(excused) <= checked // 4, (checked, excused)
 
 
 # ------------------------------------------------------------------ FA2 forces
@@ -295,8 +313,9 @@ def test_layout_c1_against_oracle(c1):
         src, dst = c1.og.src[sub], c1.og.dst[sub]
     for a, b in zip(_edge_stats(xy, E), _edge_stats(oxy, E)):
         assert abs(a - b) <= 0.02 * b
-    # KK components: stationary, and mostly at the oracle's energy minimum
-    same = []
+    # KK components (at most 50 nodes, where the oracle's minimum does not
+    # depend on rounding of the start): stationary and at the oracle's
+    # energy, every one of them
     for c in np.flatnonzero((sizes >= 2) & (sizes <= 50)):
         vs, loff, ladj, _ = c1.comp(c)
         d = oracle.bfs_apsp(loff, ladj)
@@ -304,5 +323,4 @@ def test_layout_c1_against_oracle(c1):
         eo = oracle.kk_energy(oxy[vs, 0], oxy[vs, 1], d)
         gmax = max(np.hypot(*oracle.kk_grad_hess(xy[vs, 0], xy[vs, 1], d, 1.0, m)[:2]) for m in range(len(vs)))
         assert gmax <= 1e-3 * max(1.0, eo), (c, gmax)
-        same.append(abs(eg - eo) <= 1e-4 * max(eo, 1e-9) + 1e-9)
-    assert np.mean(same) >= 0.8, np.mean(same)
+        assert kk_sensitivity.energy_close(eg, eo), (int(c), len(vs), eg, eo)

@@ -12,6 +12,7 @@ import os
 import numpy as np
 import pytest
 
+import kk_sensitivity
 import oracle
 import synth
 
@@ -305,6 +306,26 @@ def test_fa2_two_node_iterations_golden():
     assert np.all(st.y == 0)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fa2_swing_variants_golden(variant):
+    """One iteration of a three-node path with unequal masses from a given
+    F_{t-1} and s_G, worked by hand: pins the printed (unweighted) sums and
+    ForceAtlas2's mass-weighted sums with halved traction."""
+    gd = _golden("fa2_swing_variants.json")
+    s, e = gd["setup"], gd["expected"]
+    g = oracle.graph_from_edges(3, [a for a, _ in s["edges"]], [b for _, b in s["edges"]])
+    assert np.array_equal(np.diff(g.off) + 1.0, s["mass"])
+    st = oracle.FA2State(np.array(s["x"]), np.array(s["y"]), np.array(s["fprev_x"], float),
+                         np.array(s["fprev_y"], float), s["sg"])
+    st, stats = oracle.fa2_run(None, None, s["mass"], g.off, g.adj, 1, s["kr"], s["kg"], s["ks"], s["ksmax"],
+                               s["tau"], variant=variant, state=st)
+    ev = e[f"variant{variant}"]
+    assert np.allclose(stats[0], ev["stats"], rtol=1e-14, atol=0)
+    assert np.allclose(st.x, ev["x"], rtol=1e-14, atol=0)
+    assert np.allclose(st.fpx, e["F_x"], rtol=1e-14, atol=0)
+    assert np.all(st.y == 0) and np.all(st.fpy == 0)
+
+
 def test_fa2_speed_cap_limits_displacement():
     # with ksmax = 0.01 every node moves exactly 0.01 in the first iteration
     vs, off, adj, mass = _comp_c1()
@@ -351,6 +372,18 @@ def test_kk_gradient_hessian_finite_differences():
         hxy = (E(k, k) - E(k, -k) - E(-k, k) + E(-k, -k)) / (4 * k * k) / 2
         assert np.allclose(o[:2], [gx, gy], rtol=1e-6, atol=1e-8)
         assert np.allclose(o[2:], [hxx, hxy, hyy], rtol=1e-4, atol=1e-5)
+
+
+@pytest.mark.parametrize("case", range(len(_golden("kk_newton_step.json")["cases"])))
+def test_kk_newton_step_golden(case):
+    """The safeguarded 2x2 Newton step against hand-worked cases: the plain
+    step, the step shortened to l, eigenvalues replaced where H is
+    indefinite, the floor at 0.1 max|l|, and no step for H = 0."""
+    c = _golden("kk_newton_step.json")["cases"][case]
+    step, moved = oracle.kk_step(c["g"], c["H"], c["l"])
+    assert moved == c["moved"], c["name"]
+    if moved:
+        assert np.allclose(step, c["step"], rtol=1e-14, atol=1e-16), (c["name"], step)
 
 
 def test_kk_two_nodes_reach_distance_l():
@@ -406,6 +439,56 @@ def test_kk_stationary_and_monotone_on_small_components():
         e0 = oracle.kk_energy(x0 * sc, y0 * sc, d, 1.0)
         assert e[-1] <= e0
         assert np.all(np.abs(np.diff(e[-20:])) <= 1e-9 * e[-1] + 1e-12)
+
+
+def _kk_fp32_start(seed, vs, d):
+    x, y = oracle.init_positions(seed, vs)
+    sc = np.float32(d.max() / 2)
+    return (x.astype(np.float32) * sc).astype(np.float32), (y.astype(np.float32) * sc).astype(np.float32)
+
+
+def test_kk_small_components_do_not_hinge_on_rounding():
+    """On the KK components of the 1,000-transaction graph (at most 50 nodes),
+    200 oracle sweeps from one-ulp moves of the FP32 start end at the same
+    energy as from the start itself: a GPU run must match every one."""
+    tx = synth.tx_lists(**synth.C1)
+    g = oracle.graph_build(tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    label, _ = oracle.components(g.off, g.adj)
+    comp_off, _, nodes = oracle.component_order(label)
+    sizes = np.diff(comp_off)
+    comps = np.flatnonzero((sizes >= 2) & (sizes <= 50))
+    assert len(comps) > 100
+    for c in comps:
+        vs = nodes[comp_off[c]:comp_off[c + 1]]
+        loff, ladj = oracle.subgraph(g.off, g.adj, vs)
+        d = oracle.bfs_apsp(loff, ladj)
+        x, y = _kk_fp32_start(1, vs, d)
+        _, _, other = kk_sensitivity.oracle_spread(x, y, d, 200)
+        assert not other, (int(c), len(vs))
+
+
+def test_kk_large_components_hinge_on_rounding():
+    """The reading that KK from random starts is chaotic, shown on the oracle
+    alone: among forest components of 150-200 nodes, a one-ulp move of the
+    FP32 start sends at least a quarter of the 200-sweep runs to another
+    energy minimum (so an FP32 run cannot be held to the oracle's minimum
+    there), while the small ones above never move."""
+    sizes, u, v = synth.forest(17, 300, 3.0, 200.0)
+    g = oracle.graph_from_edges(int(sizes.sum()), u, v)
+    label, _ = oracle.components(g.off, g.adj)
+    comp_off, _, nodes = oracle.component_order(label)
+    sz = np.diff(comp_off)
+    comps = np.flatnonzero(sz >= 150)[::2]
+    assert len(comps) >= 8
+    moved = 0
+    for c in comps:
+        vs = nodes[comp_off[c]:comp_off[c + 1]]
+        loff, ladj = oracle.subgraph(g.off, g.adj, vs)
+        d = oracle.bfs_apsp(loff, ladj)
+        x, y = _kk_fp32_start(5, vs, d)
+        _, _, other = kk_sensitivity.oracle_spread(x, y, d, 200)
+        moved += other
+    assert moved >= len(comps) / 4, (moved, len(comps))
 
 
 # ------------------------------------------------------------- Section 4 whole layout
