@@ -24,8 +24,10 @@ on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -45,14 +47,38 @@ CONFIG_NAME = "fmm-fa2-200k-tx"
 # P2P pair throughput peak: a pair issues 8 instructions (7 FP32-pipe ops and
 # one MUFU reciprocal); an SM issues 4 warp instructions (128 lanes) per
 # clock, so 16 pairs/clk/SM.  The FP32 pipe alone would allow 128 / 7 = 18.3
-# and the MUFU reciprocal was measured at >= 15/clk/SM (a lower bound, from
-# dependent chains), so issue is the binding limit.
-SMS, SM_MAX_MHZ, PAIRS_PER_CLK = 152, 2070.0, 16.0
-PAIR_PEAK = SMS * SM_MAX_MHZ * 1e6 * PAIRS_PER_CLK
-# DRAM bytes (read + write) of one near_kernel launch on this workload's
-# giant component at its final layout, from an ncu capture of that launch
-# (the working set is L2-resident)
-NEAR_TRAFFIC_BYTES = 11_209_216 + 0
+# pairs/clk/SM; the reciprocal's MUFU rate is measured by bgl_peak_probe.
+# The SM count is read from the device, the clock from nvidia-smi.
+PAIRS_PER_CLK = 16.0
+NEAR_PROFILE = os.path.join(ROOT, "profiles", "near_kernel_fmm_c2_giant.md")
+NEAR_SOURCES = ("fmm.cu", "fmm.cuh", "p2p.cuh")
+
+
+def near_source_digest() -> str:
+    """Digest of the sources the near-field kernel is built from."""
+    h = hashlib.sha256()
+    for f in NEAR_SOURCES:
+        with open(os.path.join(ROOT, "paper_2403_03504_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def near_traffic():
+    """DRAM read + write bytes of one near-field launch from the committed ncu
+    summary, used only while the kernel's sources are the ones it was
+    captured on (the summary records their digest); otherwise None."""
+    try:
+        with open(NEAR_PROFILE) as fh:
+            txt = fh.read()
+    except OSError:
+        return None, "no ncu summary"
+    t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", txt)
+    if not t or not d:
+        return None, "ncu summary without traffic or source digest"
+    if d.group(1) != near_source_digest():
+        return None, "kernel sources changed since the ncu capture"
+    return int(t.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, same sources"
 
 
 def reduce_units_time(dist, units: float, seconds: float, device=None):
@@ -69,7 +95,8 @@ def reduce_units_time(dist, units: float, seconds: float, device=None):
     return float(t[0]), float(tmax[1])
 
 
-def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, slots=4, budget=120 << 30):
+def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, slots=4, budget=120 << 30,
+                  repulsion=None):
     """Poisson arrivals (rate per second) of k-hop layout requests (k uniform
     in 1..4, seeds uniform over the graph's address nodes, redrawn until the
     neighbourhood has min_nodes..max_nodes nodes) served by a bgl Server;
@@ -88,7 +115,8 @@ def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, s
         if min_nodes <= n_c.value <= max_nodes:
             reqs.append((sd, k, n_c.value))
     gaps = rng.exponential(1.0 / rate, n_requests)
-    p = bgl.params(seed=0, fa2_iters=iters, repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=64, kk_max_nodes=50)
+    rep = bgl.REP_FMM if repulsion is None else repulsion
+    p = bgl.params(seed=0, fa2_iters=iters, repulsion=rep, fmm_p=8, leaf_size=64, kk_max_nodes=50)
     srv = bgl.Server(g, slots=slots, hbm_budget=budget)
     t0 = time.perf_counter()
     arrive = t0 + np.cumsum(gaps)
@@ -116,6 +144,7 @@ def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, s
     nodes = np.array([r[2] for r in reqs])
     return {
         "requests": n_requests, "rate_per_s": rate, "hops": "uniform 1..4", "fa2_iters": iters,
+        "repulsion": {bgl.REP_FMM: "fmm p=8", bgl.REP_EXACT: "exact", bgl.REP_AUTO: "auto"}[rep],
         "nodes_min": int(nodes.min()), "nodes_p50": int(np.median(nodes)), "nodes_max": int(nodes.max()),
         "latency_ms_p50": float(np.percentile(lat_ms, 50)), "latency_ms_p99": float(np.percentile(lat_ms, 99)),
         "latency_ms_max": float(lat_ms.max()), "layouts_per_s": n_requests / wall,
@@ -322,6 +351,45 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def oracle_force_error(bgl, g, giant_xy, n_sample=2000, seed=2):
+    """FMM repulsion at the final layout against the FP64 oracle's exact sum on
+    a uniform sample of the giant component's nodes: RMS relative error and
+    the largest normalised error e_i = |dF_i| / (kr m_i sum_j m_j / d_ij),
+    for p = 8 and p = 16, beside each one's truncation ceiling."""
+    import oracle
+    coff, _, nodes = g.component_nodes()
+    off, adj = g.csr()
+    vs = nodes[coff[0]:coff[1]]
+    pos = np.full(len(off) - 1, -1, np.int64)
+    pos[vs] = np.arange(len(vs))
+    loff = np.zeros(len(vs) + 1, np.int64)
+    loff[1:] = np.cumsum(np.diff(off)[vs])
+    ladj = pos[np.concatenate([adj[off[v]:off[v + 1]] for v in vs])].astype(np.int32)
+    mass = np.diff(loff) + 1.0
+    sample = np.sort(np.random.default_rng(seed).choice(len(vs), n_sample, replace=False))
+    t0 = time.perf_counter()
+    o = oracle.fa2_forces(giant_xy[:, 0], giant_xy[:, 1], mass, loff, ladj, 1.0, 1.0, targets=sample)
+    out = {"oracle_sample": n_sample, "oracle_seconds": time.perf_counter() - t0}
+    rho = 2 ** 0.5 / (4 - 2 ** 0.5)
+    ref = o["frep"]
+    for pp in (8, 16):
+        f = g.fa2_repulsion(0, bgl.params(repulsion=bgl.REP_FMM, fmm_p=pp, leaf_size=64), giant_xy)[sample]
+        e = np.hypot(*(f - ref).T) / o["srep"]
+        out[f"p{pp}_rms_rel_vs_oracle"] = float(np.sqrt(np.mean(np.sum((f - ref) ** 2, 1)) /
+                                                        np.mean(np.sum(ref ** 2, 1))))
+        out[f"p{pp}_max_e_vs_oracle"] = float(e.max())
+        out[f"p{pp}_ceiling"] = max(2 * (1 + rho) * rho ** (pp + 1) / (1 - rho), 2e-5)
+    return out
 
 
 def cpu_oracle_rate(tx, budget_s: float, giant_only=True):
@@ -615,6 +683,10 @@ def main():
 
     # served layouts of k-hop neighbourhoods of this graph (latency)
     serving = serve_session(bgl, g0, args.requests or 40, 50.0, 2, 300, 100, 2_000_000, slots=4, budget=64 << 30)
+    # the same requests, up to 60k nodes each, with FMM and with exact repulsion
+    serving_vs_exact = {name: serve_session(bgl, g0, args.requests or 40, 50.0, 3, 300, 100, 60_000, slots=4,
+                                            budget=64 << 30, repulsion=rep)
+                        for name, rep in (("fmm", bgl.REP_FMM), ("exact", bgl.REP_EXACT))}
 
     clocks = clk.summary()
     if rank != 0:
@@ -622,9 +694,15 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
+    probe = ctx.peak_probe()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    pair_peak = sms * sm_max_mhz * 1e6 * PAIRS_PER_CLK
+    traffic, traffic_note = near_traffic()
     cpu = None
     if not args.no_cpu and world == 1:
         cpu, _ = cpu_oracle_rate(tx, args.cpu_budget)
+        errs.update(oracle_force_error(bgl, g0, giant_xy))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -636,11 +714,14 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "fmm near field (P2P, near_kernel)", "achieved": achieved / 1e9,
-                     "peak": PAIR_PEAK / 1e9, "unit": "Gpairs/s", "frac": achieved / PAIR_PEAK,
-                     "traffic": NEAR_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "peak_source": "derived: 152 SMs x 2070 MHz x 128 issue lanes/clk / 8 instructions per pair "
-                                    "= 16 pairs/clk/SM (FP32 pipe 18.3, MUFU rcp >= 15 measured)"},
-        "force_error": {"reference": "GPU FP32 exact sum at the final layout", **errs},
+                     "peak": pair_peak / 1e9, "unit": "Gpairs/s", "frac": achieved / pair_peak,
+                     "traffic": traffic, "traffic_unit": "bytes per launch", "traffic_source": traffic_note,
+                     "peak_source": f"derived: {sms} SMs (device) x {sm_max_mhz:.0f} MHz (nvidia-smi max) x 128 "
+                                    "issue lanes/clk / 8 instructions per pair = 16 pairs/clk/SM",
+                     "peak_probe": probe},
+        "force_error": {"reference": "GPU FP32 exact sum at the final layout (rms_rel); FP64 oracle on 2000 "
+                                     "sampled nodes (vs_oracle)", **errs},
+        "serving_vs_exact": serving_vs_exact,
         "exact_fa2": {"value": exact_rate, "unit": UNIT, "iters": args.exact_iters, "nodes": giant},
         "fmm_p16_step_ms": 1e3 * p16_s,
         "m2l_precision": m2l_prec,

@@ -113,7 +113,9 @@ void bgl_ctx_destroy(bgl_ctx *ctx);
  * device); NULL restores the context's own stream. */
 bgl_status bgl_ctx_set_stream(bgl_ctx *ctx, void *cuda_stream);
 
-/* Block until all work queued by the context has finished. */
+/* Block until all work queued by the context has finished.  Returns
+ * BGL_ENUMERIC (once) if a bgl_fa2_iteration_noalloc call on this context
+ * produced a non-finite position since the last bgl_ctx_sync. */
 bgl_status bgl_ctx_sync(bgl_ctx *ctx);
 
 /* Message of the last failure on this context ("" if none).  Valid until
@@ -402,27 +404,47 @@ bgl_status bgl_fmm_stats(bgl_graph *g, int64_t c, const bgl_params *p, const flo
  *   d_fprev[2n]   in/out         previous forces; zero before the first iteration
  *   d_f[2n]       out            this iteration's forces
  *   d_sg[1]       in/out         global speed s_G; 1.0 before the first iteration
- * Calling it `iters` times from zero d_fprev and d_sg = 1 performs what
- * bgl_fa2_step does with p->repulsion = BGL_REP_EXACT (same force, swing,
- * traction and update rules, p->kr, kg, ks, ksmax, tau, swing_variant).
+ * Calling it `iters` times from zero d_fprev and d_sg = 1 applies the force,
+ * swing, traction and update rules of bgl_fa2_step with
+ * p->repulsion = BGL_REP_EXACT (p->kr, kg, ks, ksmax, tau, swing_variant);
+ * its sums are taken in another order and precision, so the two agree within
+ * rounding (positions within 1e-3 of the layout's bounding-box diagonal and
+ * s_G within 1e-4 relative after two iterations), not bitwise.  A position
+ * that becomes non-finite is recorded on the context; the next
+ * bgl_ctx_sync reports it as BGL_ENUMERIC and clears the record.
  *
  * Scratch: the per-tile swing/traction sums and a counter live in one
  * fixed array of about 8 KiB per device (room for BGL_NOALLOC_MAX_NODES
- * nodes), held by every GPU that loads the library until exit.  n above
- * BGL_NOALLOC_MAX_NODES returns BGL_EINVAL.  The first call on a device
- * looks up that array's device address; make that first call before any
- * stream capture.  Every call shares the array and leaves its last contents
- * there: calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.  Work is queued
- * on the context's stream; the call does not synchronise it.
+ * nodes), held by every GPU that loads the library until exit; the context
+ * looks up its device address when it is created.  n above
+ * BGL_NOALLOC_MAX_NODES returns BGL_EINVAL.  Every call shares the array
+ * and leaves its last contents there: calls whose work overlaps on the GPU
+ * (other streams, other host threads, other contexts on the same device)
+ * race on it and must be serialised by the caller.  Work is queued on the
+ * context's stream; the call does not synchronise it.
  */
 bgl_status bgl_fa2_iteration_noalloc(bgl_ctx *ctx, int64_t n, const int64_t *d_off, const int32_t *d_adj,
                                      const float *d_mass, float *d_xy, float *d_fprev, float *d_f, double *d_sg,
                                      const bgl_params *p);
 
+/* Measured ALU throughput behind the roofline of the pair kernels (the
+ * all-pairs repulsion of Section 3.2): out[0] FP32 FMA lanes, out[1] MUFU
+ * reciprocals (rcp.approx) and out[2] repulsion pairs (7 FP32 operations and
+ * one reciprocal, sources in registers), each per SM per clock from the
+ * clock64() counts of one 1,024-thread block per SM; out[3] the SM count.
+ * Synchronises the stream. */
+bgl_status bgl_peak_probe(bgl_ctx *ctx, double *out);
+
 /* Number of kernels this process has launched through the library so far
  * (direct launches plus the kernel nodes of every CUDA graph replay). */
 int64_t bgl_launch_count(void);
+
+/* Test aid for the failure paths (the paper has no counterpart): after
+ * `after` more successful device allocations on this context, the next one
+ * fails as if the device were out of memory, so the call making it returns
+ * BGL_ENOMEM with its outputs untouched; the aid then turns itself off.
+ * after = -1 turns it off at once.  No GPU fault is involved. */
+bgl_status bgl_debug_fail_alloc(bgl_ctx *ctx, int64_t after);
 
 #ifdef __cplusplus
 }

@@ -121,6 +121,8 @@ def _load():
         "bgl_fmm_stats": ([VP, I64, ctypes.POINTER(Params), VP, I32, VP], I32),
         "bgl_launch_count": ([], I64),
         "bgl_fa2_iteration_noalloc": ([VP, I64, VP, VP, VP, VP, VP, VP, VP, ctypes.POINTER(Params)], I32),
+        "bgl_debug_fail_alloc": ([VP, I64], I32),
+        "bgl_peak_probe": ([VP, VP], I32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -245,6 +247,19 @@ class Context:
         addresses, queued on the context's stream."""
         self.check(self._lib.bgl_fa2_iteration_noalloc(self.h, n, _dp(d_off), _dp(d_adj), _dp(d_mass), _dp(d_xy),
                                                        _dp(d_fprev), _dp(d_f), _dp(d_sg), ctypes.byref(p)))
+
+    def peak_probe(self) -> dict:
+        """Measured FP32 lanes, MUFU reciprocals and repulsion pairs per SM
+        clock (bgl_peak_probe), and the SM count."""
+        out = np.zeros(4)
+        self.check(self._lib.bgl_peak_probe(self.h, _hp(out)))
+        return {"fp32_lanes_per_clk_sm": out[0], "mufu_rcp_per_clk_sm": out[1], "pairs_per_clk_sm": out[2],
+                "sms": int(out[3])}
+
+    def debug_fail_alloc(self, after: int):
+        """Test aid: the device allocation after `after` more successful ones
+        fails with BGL_ENOMEM (-1: never)."""
+        self.check(self._lib.bgl_debug_fail_alloc(self.h, after))
 
     def close(self):
         if self.h:

@@ -40,6 +40,10 @@ void Allocator::release_cache() {
 
 void *Allocator::alloc(size_t bytes) {
     if (forbid) throw Error(BGL_ESTATE, "internal: device allocation inside a captured CUDA graph");
+    if (fail_after.load(std::memory_order_relaxed) >= 0 && fail_after.fetch_sub(1) == 0) {
+        fail_after.store(-1);
+        throw Error(BGL_ENOMEM, "device allocation refused by bgl_debug_fail_alloc");
+    }
     bytes = (bytes + 255) & ~size_t(255);
     {
         std::lock_guard<std::mutex> lk(mu_);
@@ -247,6 +251,7 @@ bgl_status bgl_ctx_create(int device, bgl_ctx **out) {
         BGL_CUDA(cudaMalloc(&c->d_flag, 4 * sizeof(int)));
         BGL_CUDA(cudaMemset(c->d_flag, 0, 4 * sizeof(int)));
         BGL_CUDA(cudaMallocHost(&c->h_flag, 4 * sizeof(int)));
+        c->noalloc_scratch = static_cast<unsigned char *>(noalloc_scratch_address());
     });
     if (s != BGL_OK) {
         bgl_ctx_destroy(c);
@@ -274,7 +279,18 @@ bgl_status bgl_ctx_set_stream(bgl_ctx *c, void *stream) {
 
 bgl_status bgl_ctx_sync(bgl_ctx *c) {
     if (!c) return BGL_EINVAL;
-    return guarded(c, [&] { sync(c); });
+    return guarded(c, [&] {
+        // the allocation-free iteration records non-finite positions in
+        // d_flag[2]; report that record once and clear it
+        BGL_CUDA(cudaMemcpyAsync(c->h_flag + 2, c->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        if (c->h_flag[2]) {
+            c->h_flag[2] = 0;
+            BGL_CUDA(cudaMemsetAsync(c->d_flag + 2, 0, sizeof(int), c->stream));
+            sync(c);
+            fail(BGL_ENUMERIC, "fa2_iteration_noalloc: a position became non-finite");
+        }
+    });
 }
 
 const char *bgl_last_error(const bgl_ctx *c) { return c ? c->last_error.c_str() : "context is NULL"; }
@@ -648,5 +664,16 @@ bgl_status bgl_fa2_iteration_noalloc(bgl_ctx *ctx, int64_t n, const int64_t *d_o
 }
 
 int64_t bgl_launch_count(void) { return bgl::launch_count(); }
+
+bgl_status bgl_peak_probe(bgl_ctx *c, double *out) {
+    if (!c || !out) return BGL_EINVAL;
+    return guarded(c, [&] { peak_probe(c, out); });
+}
+
+bgl_status bgl_debug_fail_alloc(bgl_ctx *c, int64_t after) {
+    if (!c || after < -1) return BGL_EINVAL;
+    c->alloc->fail_after.store(after);
+    return BGL_OK;
+}
 
 }  // extern "C"

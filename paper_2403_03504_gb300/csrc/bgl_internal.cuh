@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <stdexcept>
@@ -62,6 +63,9 @@ class Allocator {
     // set while a stream capture is open: allocating then would bake a
     // block that is freed after the capture into the replayed graph
     bool forbid = false;
+    // test aid (bgl_debug_fail_alloc): >= 0 makes the allocation after this
+    // many more successful ones fail with BGL_ENOMEM; -1 never
+    std::atomic<int64_t> fail_after{-1};
 
   private:
     int device_;
@@ -119,14 +123,22 @@ struct bgl_ctx {
     cudaStream_t stream = nullptr;
     bgl::Allocator *alloc = nullptr;
     std::string last_error;
-    int *d_flag = nullptr;        // device error/flag words (4 ints)
+    int *d_flag = nullptr;        // device error/flag words (4 ints): [0] per-call checks, [1] ForceAtlas2
+                                  // runs, [2] allocation-free iterations (read by bgl_ctx_sync)
     int *h_flag = nullptr;        // pinned mirror
+    unsigned char *noalloc_scratch = nullptr;   // device address of the allocation-free scratch array
     // autotuner choices: exact-repulsion targets per thread by log2 of the pairs
     std::mutex tune_mu;
     std::map<int, int> tune_exact;
 };
 
 namespace bgl {
+// device address of the allocation-free iteration's scratch array on the
+// current device (cudaGetSymbolAddress; allocates nothing)
+void *noalloc_scratch_address();
+// ALU throughput probes (probe.cu): out[4] = FP32 lanes, MUFU reciprocals and
+// pairs per SM clock, and the SM count
+void peak_probe(bgl_ctx *c, double *out);
 struct Fa2Session;
 void fa2_session_destroy(Fa2Session *s);
 }  // namespace bgl

@@ -64,6 +64,42 @@ constexpr int BN = 49;                 // binomial table dimension (n <= 48)
 constexpr int SRC_CAP = 2048;          // P2P sources staged per pass
 constexpr int LEAF_THREADS = 128;
 constexpr long long SPIN_LIMIT = 1ll << 24;
+// per-evaluation work tickets, zeroed by the bounding-box kernel: [0, 8) the
+// passes' own counters, [8, 24) the leaves in each near-field bucket
+constexpr int NTICKETS = 24;
+constexpr int NEAR_BUCKET_COUNTS = 8;
+// Near-field tuning constants (compile-time): target lanes per warp,
+// sources per stage, unroll of the source loop, whether the staging code is
+// shared by the tile variants instead of inlined into each, and whether the
+// leaves are taken in buckets of equal tile shape (filled by the lists kernel).
+#ifndef BGL_NEAR_LPS
+#define BGL_NEAR_LPS 8
+#endif
+#ifndef BGL_NEAR_SRC
+#define BGL_NEAR_SRC 128
+#endif
+#ifndef BGL_NEAR_UNROLL
+#define BGL_NEAR_UNROLL 1
+#endif
+#ifndef BGL_NEAR_SHARED_STAGE
+#define BGL_NEAR_SHARED_STAGE 0
+#endif
+#ifndef BGL_NEAR_BUCKETS
+#define BGL_NEAR_BUCKETS 1
+#endif
+constexpr int NEAR_SRC = BGL_NEAR_SRC;
+constexpr int NEAR_WARPS = 1024 / NEAR_SRC;       // 32 KB of stage buffers per block
+constexpr int NEAR_LPS = BGL_NEAR_LPS;            // target lanes
+constexpr int NEAR_SPLIT = 32 / NEAR_LPS;         // source splits
+constexpr int NEAR_RMAX = 64 / NEAR_LPS;          // targets per lane: 64 per tile
+constexpr int NEAR_UNROLL = BGL_NEAR_UNROLL;
+
+// tile shape class of a leaf of `points` points: targets per lane, 1..NEAR_RMAX
+__host__ __device__ __forceinline__ int near_class(int points) {
+    const int r = (points + NEAR_LPS - 1) / NEAR_LPS;
+    return r < 1 ? 1 : (r > NEAR_RMAX ? NEAR_RMAX : r);
+}
+
 
 enum { ERR_SPIN = 1, ERR_LIST_OVERFLOW = 2, ERR_BOX_OVERFLOW = 4, ERR_BBOX = 8 };
 
@@ -98,6 +134,8 @@ struct Tree {
     int Bmax;                 // capacity of the box arrays
     const Root *root;
     int *err;
+    int *ncls;                // [NEAR_RMAX] leaves in each near-field bucket (zeroed per evaluation)
+    int *cleaf;               // [NEAR_RMAX * Bmax] the leaves of each bucket
 };
 
 __device__ __forceinline__ uint32_t spread_bits(uint32_t x) {
@@ -243,7 +281,7 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
     // this evaluation's work tickets, digit counts and sort pass tickets start at zero
     if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) h.hist[i] = 0u;
-        if (threadIdx.x < 8) tickets[threadIdx.x] = 0;
+        if (threadIdx.x < NTICKETS) tickets[threadIdx.x] = 0;
         if (threadIdx.x < 4) h.tickets[threadIdx.x] = 0u;
     }
     float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
@@ -928,6 +966,13 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) nbr_lists_kernel(Tree T) {
             }
         }
         base = __shfl_sync(0xffffffffu, base, 0);
+#if BGL_NEAR_BUCKETS
+        if (lane == 0 && leaf) {
+            const int cls = near_class(T.bend[b] - T.bstart[b]);
+            const int pos = atomicAdd(T.ncls + cls - 1, 1);
+            T.cleaf[(size_t)(cls - 1) * T.Bmax + pos] = b;
+        }
+#endif
         if (base < 0) {
             if (lane < 5) T.lofs[5 * b + lane] = 0;
             __syncwarp();
@@ -1426,17 +1471,30 @@ struct LeafArgs {
 };
 
 // Near field: the direct sum over the points of U for every target of a
-// leaf.  One warp per leaf (leaves taken through a ticket counter).  The
+// leaf.  One warp per leaf, the leaves taken through a ticket counter bucket
+// by bucket (the lists kernel files every leaf under its tile shape, the
+// most targets per lane first), so that the warps of an SM run one or two of
+// the unrolled tile variants at a time and the instruction cache holds them
+// (taken in box order instead, with all variants interleaved on every SM,
+// the same kernel ran 12 % slower).  The
 // sources are staged NEAR_SRC at a time in the warp's own shared memory
 // with asynchronous 16-byte copies (cp.async), double-buffered: the copies
-// of the next chunk are in flight while the current chunk is summed.
-// Each lane owns R targets (1..4): with S source splits of lps = 32 / S
-// lanes, lane l takes targets l % lps + r * lps of split l / lps; (R, S) is
-// chosen per leaf for the fewest padded target slots; the splits share the
-// sources and combine by a fixed butterfly.  Writes the raw sum
-// sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the combine pass completes it).
-constexpr int NEAR_WARPS = 8;
-constexpr int NEAR_SRC = 128;
+// of the next chunk are in flight while the current chunk is summed; each
+// chunk is padded to a multiple of NEAR_SPLIT with zero-mass sources, which
+// add exactly 0.  The warp's lanes form NEAR_LPS target lanes times
+// NEAR_SPLIT source splits: lane (t, h) owns the R = ceil(targets / 8)
+// targets t, t + 8, ... of the leaf (at most 7 padded target slots) and
+// every NEAR_SPLIT-th staged source from h, so each shared-memory load of a
+// source serves R pairs; the splits combine by a fixed butterfly.  Writes
+// the raw sum sum_j m_j (p_i - p_j) / |p_i - p_j|^2 to f (the combine pass
+// completes it).  Measured on the 554k-node giant component's final layout:
+// four target lanes (up to sixteen targets each, fewer padded slots) ran 8 %
+// slower, as did unrolling the source loop (the code of the variants
+// outgrows the instruction cache).
+
+static_assert(NEAR_LPS * NEAR_RMAX == 64, "a near tile covers a full leaf of 64 points");
+static_assert(NEAR_WARPS >= 1 && NEAR_WARPS * NEAR_SRC * 2 * 16 == 32768, "stage buffers");
+static_assert(NEAR_SRC % NEAR_SPLIT == 0, "chunks split evenly");
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -1446,8 +1504,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Issue the copies of the next chunk (up to NEAR_SRC sources of the U list
-// from entry *ui, offset *off) into buf; returns the chunk size.
-__device__ __forceinline__ int stage_chunk(const Tree &T, float4 *buf, int &ui, int &off, int ue, int lane) {
+// from entry *ui, offset *off) into buf and zero-mass padding up to a
+// multiple of NEAR_SPLIT; returns the padded chunk size.
+#if BGL_NEAR_SHARED_STAGE
+__device__ __noinline__
+#else
+__device__ __forceinline__
+#endif
+int stage_chunk(const Tree &T, float4 *buf, int &ui, int &off, int ue, int lane) {
     int cnt = 0;
     while (ui < ue && cnt < NEAR_SRC) {
         const int C = T.lidx[ui];
@@ -1462,24 +1526,24 @@ __device__ __forceinline__ int stage_chunk(const Tree &T, float4 *buf, int &ui, 
         }
     }
     cp_async_commit();
-    return cnt;
+    const int padded = (cnt + NEAR_SPLIT - 1) & ~(NEAR_SPLIT - 1);
+    if (lane < padded - cnt) buf[cnt + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return padded;
 }
 
-// Pairs of the targets tb + t + r * lps (r < R) with every S-th staged
-// source from h; R targets per lane amortise each shared-memory load.
+// Pairs of the targets tb + t + 8 r (r < R) of lane (t, h) with the staged
+// sources h, h + NEAR_SPLIT, ...
 template <int R>
 __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*buf)[NEAR_SRC], int tb, int ntc,
-                                          int lps, int S, int us, int ue, int lane) {
-    const int t = lane % lps, h = lane / lps;
+                                          int us, int ue, int lane) {
+    const int t = lane % NEAR_LPS, h = lane / NEAR_LPS;
     float zx[R], zy[R], fx[R], fy[R];
-    int zi[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int i = t + r * lps;
+        const int i = t + r * NEAR_LPS;
         const float4 z = i < ntc ? T.pts[tb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
         zx[r] = z.x;
         zy[r] = z.y;
-        zi[r] = __float_as_int(z.w);
         fx[r] = fy[r] = 0.f;
     }
     int ui = us, off = 0, cur = 0;
@@ -1489,21 +1553,13 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
         const int nxt = ui < ue ? stage_chunk(T, buf[cur ^ 1], ui, off, ue, lane) : (cp_async_commit(), 0);
         cp_async_wait_one();
         __syncwarp();
-        const float4 *src = buf[cur];
-        if (S == 1) {
-#pragma unroll 2
-            for (int j = 0; j < cnt; ++j) {
-                const float4 q = src[j];
+        const float4 *src = buf[cur] + h;
+        const int steps = cnt / NEAR_SPLIT;
+#pragma unroll NEAR_UNROLL
+        for (int j = 0; j < steps; ++j) {
+            const float4 q = src[j * NEAR_SPLIT];
 #pragma unroll
-                for (int r = 0; r < R; ++r) p2p_pair(zx[r], zy[r], q, fx[r], fy[r]);
-            }
-        } else {
-#pragma unroll 2
-            for (int j = h; j < cnt; j += S) {
-                const float4 q = src[j];
-#pragma unroll
-                for (int r = 0; r < R; ++r) p2p_pair(zx[r], zy[r], q, fx[r], fy[r]);
-            }
+            for (int r = 0; r < R; ++r) p2p_pair(zx[r], zy[r], q, fx[r], fy[r]);
         }
         __syncwarp();
         cur ^= 1;
@@ -1512,12 +1568,18 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         float sx = fx[r], sy = fy[r];
-        for (int o = lps; o < 32; o <<= 1) {
+#pragma unroll
+        for (int o = NEAR_LPS; o < 32; o <<= 1) {
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
         }
-        const int i = t + r * lps;
-        if (h == 0 && i < ntc) la.f[la.q0 + zi[r] - la.fbase] = make_float2(sx, sy);
+        // every lane now holds the sums of its target lane; split h stores
+        // the targets r = h (mod NEAR_SPLIT)
+        const int i = t + r * NEAR_LPS;
+        if (r % NEAR_SPLIT == h && i < ntc) {
+            const int zi = __float_as_int(T.pts[tb + i].w);
+            la.f[la.q0 + zi - la.fbase] = make_float2(sx, sy);
+        }
     }
 }
 
@@ -1543,11 +1605,43 @@ __global__ void combine_kernel(LeafArgs la, int n) {
     la.f[q] = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
 }
 
+// the tile variant with R targets per lane
+template <int R>
+__device__ __forceinline__ void near_dispatch(int r, const Tree &T, LeafArgs &la, float4 (*buf)[NEAR_SRC], int tb,
+                                              int ntc, int us, int ue, int lane) {
+    if constexpr (R > 1) {
+        if (r < R) {
+            near_dispatch<R - 1>(r, T, la, buf, tb, ntc, us, ue, lane);
+            return;
+        }
+    }
+    near_tile<R>(T, la, buf, tb, ntc, us, ue, lane);
+}
+
 __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
     const Tree &T = la.e.T;
     __shared__ __align__(16) float4 stage[NEAR_WARPS][2][NEAR_SRC];
     const int lane = threadIdx.x & 31;
     float4(*buf)[NEAR_SRC] = stage[threadIdx.x >> 5];
+#if BGL_NEAR_BUCKETS
+    // leaves bucket by bucket, the most targets per lane first
+    int cnt_l = lane < NEAR_RMAX ? T.ncls[lane] : 0;
+    int total = cnt_l;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(la.ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) return;
+        int cls = NEAR_RMAX;
+        for (;; --cls) {
+            const int c = __shfl_sync(0xffffffffu, cnt_l, cls - 1);
+            if (t < c) break;
+            t -= c;
+        }
+        const int b = T.cleaf[(size_t)(cls - 1) * T.Bmax + t];
+#else
     const int B = min(T.levoff[NLEV], T.Bmax);
     for (;;) {
         int b = 0;
@@ -1555,29 +1649,12 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= B) return;
         if (!T.bleaf[b]) continue;
+#endif
         const int s = T.bstart[b], e = T.bend[b];
         const int us = T.lofs[5 * b], ue = T.lofs[5 * b + 1];
-        for (int tb = s; tb < e; tb += 64) {
-            const int ntc = min(64, e - tb);
-            // fewest padded target slots: R targets on lps = 32 / S lanes
-            int R = 2, S = 1, best = 64;
-            for (int s2 = 1; s2 <= 32; s2 <<= 1) {
-                for (int r2 = 6; r2 >= 1; --r2) {
-                    const int slots = r2 * (32 / s2);
-                    if (slots >= ntc && slots < best) {
-                        best = slots;
-                        R = r2;
-                        S = s2;
-                    }
-                }
-            }
-            const int lps = 32 / S;
-            if (R == 6) near_tile<6>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else if (R == 5) near_tile<5>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else if (R == 4) near_tile<4>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else if (R == 3) near_tile<3>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else if (R == 2) near_tile<2>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
-            else near_tile<1>(T, la, buf, tb, ntc, lps, S, us, ue, lane);
+        for (int tb = s; tb < e; tb += NEAR_LPS * NEAR_RMAX) {
+            const int ntc = min(NEAR_LPS * NEAR_RMAX, e - tb);
+            near_dispatch<NEAR_RMAX>((ntc + NEAR_LPS - 1) / NEAR_LPS, T, la, buf, tb, ntc, us, ue, lane);
         }
     }
 }
@@ -1875,6 +1952,7 @@ struct FmmPlan {
     DevBuf<float4> pts;
     DevBuf<int8_t> cl, lam, bleaf;
     DevBuf<int> tcnt, levoff, bstart, bend, blevel, bparent, lofs, lidx;
+    DevBuf<int> cleaf;     // near-field buckets of leaves (with BGL_NEAR_BUCKETS)
     DevBuf<uint32_t> bkey;
     DevBuf<int4> bchild;
     DevBuf<int2> bmeta;
@@ -1949,6 +2027,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         BGL_CUDA(cudaMemsetAsync(pl->bchild.p, 0xFF, sizeof(int4) * bmax, s));
         pl->bmeta.reset(A, bmax);
         pl->lofs.reset(A, 5 * bmax);
+        if (BGL_NEAR_BUCKETS) pl->cleaf.reset(A, (size_t)NEAR_RMAX * bmax);
         pl->lidx.reset(A, pl->lcap);
         pl->M.reset(A, (size_t)(pl->PT + 1) * bmax);
         pl->Lc.reset(A, (size_t)(pl->PT + 1) * bmax);
@@ -1979,7 +2058,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         pl->epoch.reset(A, 1);
         BGL_CUDA(cudaMemsetAsync(pl->hkv.p, 0, sizeof(ulonglong2) * hs, s));
         BGL_CUDA(cudaMemsetAsync(pl->epoch.p, 0, sizeof(unsigned), s));
-        pl->tickets.reset(A, 8);
+        pl->tickets.reset(A, NTICKETS);
         pl->err.reset(A, 1);
         pl->sortws.reserve(A, n, s);
         BGL_CUDA(cudaMemsetAsync(pl->counter.p, 0, sizeof(unsigned), s));
@@ -2032,6 +2111,8 @@ static Tree make_tree(FmmPlan *pl) {
     T.Bmax = pl->Bmax;
     T.root = pl->root.p;
     T.err = pl->err.p;
+    T.ncls = pl->tickets.p + NEAR_BUCKET_COUNTS;
+    T.cleaf = pl->cleaf.p;
     return T;
 }
 
@@ -2136,8 +2217,17 @@ static void launch_down(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
         m2l_kernel<PT, false><<<pl->grid_p, 256, 0, s>>>(a);
     BGL_LAUNCH_CHECK();
 }
+// persistent near-field grid: every resident block of every SM
+static int near_blocks_per_sm() {
+    static const int bps = [] {
+        int b = 0;
+        BGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_kernel, NEAR_WARPS * 32, 0));
+        return b > 0 ? b : 1;
+    }();
+    return bps;
+}
 static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
-    near_kernel<<<pl->g->ctx->num_sms * 6, NEAR_WARPS * 32, 0, s>>>(la);
+    near_kernel<<<pl->g->ctx->num_sms * near_blocks_per_sm(), NEAR_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
 }
 template <int PT>

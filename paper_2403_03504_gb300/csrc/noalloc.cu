@@ -13,10 +13,14 @@
 //
 // The kernels are variants of the ones in fa2.cu that need no host-built
 // tile list and no per-call buffers: one component, targets tiled by block
-// index, hub rows summed by the node's own thread.  The arithmetic of every
-// force term, of the swing/traction sums and of the update is the same.
-#include <mutex>
-
+// index, hub rows summed by the node's own thread.  The formulas of every
+// force term, of the swing/traction sums and of the update are the same;
+// the order and precision of the sums differ (here every thread sums its
+// swing/traction terms in FP64 over tiles of 2,048 nodes and a hub's
+// attraction in one loop, where fa2.cu sums in FP32 within a warp over tiles
+// of 1,024 nodes and splits hub rows into 2,048-entry chunks), so the two
+// agree within rounding, not bitwise.  A position that becomes non-finite
+// sets the context's d_flag[2], which bgl_ctx_sync reports.
 #include "bgl_internal.cuh"
 
 namespace bgl {
@@ -36,7 +40,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = NA_COUNTER_BYTES + sizeof(double2) * NA
 // The scratch of every call on this device: [0, 256) the arrival counter,
 // then NA_MAX_TILES double2 partial sums.  Host code must not pass this
 // symbol to a kernel; it passes the device address from
-// cudaGetSymbolAddress (see scratch_on_device).
+// cudaGetSymbolAddress (noalloc_scratch_address, stored in the context).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 __device__ __forceinline__ float na_rcp(float x) {
@@ -185,7 +189,7 @@ __global__ void na_swing_traction_kernel(const float2 *__restrict__ f, const flo
 }
 
 __global__ void na_update_kernel(const float2 *__restrict__ f, float2 *__restrict__ fprev, float2 *__restrict__ xy,
-                                 const double *__restrict__ sg, int64_t n, float ks, float ksmax) {
+                                 const double *__restrict__ sg, int64_t n, float ks, float ksmax, int *bad) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     float2 F = f[q], P = fprev[q];
@@ -197,30 +201,24 @@ __global__ void na_update_kernel(const float2 *__restrict__ f, float2 *__restric
     float2 p = xy[q];
     p.x += s * F.x;
     p.y += s * F.y;
+    if (!isfinite(p.x) || !isfinite(p.y)) *bad = 1;
     xy[q] = p;
     fprev[q] = F;
-}
-
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_scratch_mu;
-unsigned char *g_scratch_ptr[NA_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on each device does it).
-unsigned char *scratch_on_device(int device) {
-    BGL_REQUIRE(device >= 0 && device < NA_MAX_DEVICES, "noalloc: device index out of range");
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[device]) {
-        void *ptr = nullptr;
-        BGL_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        g_scratch_ptr[device] = static_cast<unsigned char *>(ptr);
-    }
-    return g_scratch_ptr[device];
 }
 
 inline unsigned na_blocks(int64_t n, int64_t per) { return (unsigned)((n + per - 1) / per); }
 
 }  // namespace
+
+// Device address of the scratch array on the current device.  Called by
+// bgl_ctx_create with the context's device current, so every context holds
+// the address for its device (a context created after a device reset looks
+// it up again).
+void *noalloc_scratch_address() {
+    void *ptr = nullptr;
+    BGL_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    return ptr;
+}
 
 void fa2_iteration_noalloc(bgl_ctx *c, int64_t n, const int64_t *d_off, const int32_t *d_adj, const float *d_mass,
                            float2 *d_xy, float2 *d_fprev, float2 *d_f, double *d_sg, const bgl_params *p) {
@@ -228,7 +226,8 @@ void fa2_iteration_noalloc(bgl_ctx *c, int64_t n, const int64_t *d_off, const in
     BGL_REQUIRE(n <= NA_MAX_NODES, "noalloc: component has more than BGL_NOALLOC_MAX_NODES (2^20) nodes");
     if (n == 0) return;
     BGL_REQUIRE(d_off && d_adj && d_mass && d_xy && d_fprev && d_f && d_sg, "noalloc: a device array is NULL");
-    unsigned char *scratch = scratch_on_device(c->device);
+    unsigned char *scratch = c->noalloc_scratch;
+    BGL_REQUIRE(scratch != nullptr, "noalloc: the context has no scratch address");
     cudaStream_t s = c->stream;
     // the arrival counter must start at zero; the partial sums are overwritten
     BGL_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned), s));
@@ -239,7 +238,8 @@ void fa2_iteration_noalloc(bgl_ctx *c, int64_t n, const int64_t *d_off, const in
     na_swing_traction_kernel<<<na_blocks(n, NA_RED_TILE), 256, 0, s>>>(d_f, d_fprev, d_mass, n, p->swing_variant,
                                                                        p->tau, d_sg, scratch);
     BGL_LAUNCH_CHECK();
-    na_update_kernel<<<na_blocks(n, 256), 256, 0, s>>>(d_f, d_fprev, d_xy, d_sg, n, (float)p->ks, (float)p->ksmax);
+    na_update_kernel<<<na_blocks(n, 256), 256, 0, s>>>(d_f, d_fprev, d_xy, d_sg, n, (float)p->ks, (float)p->ksmax,
+                                                       c->d_flag + 2);
     BGL_LAUNCH_CHECK();
 }
 

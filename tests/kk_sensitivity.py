@@ -38,6 +38,31 @@ def energy_close(e, e_ref):
     return abs(e - e_ref) <= 1e-4 * abs(e_ref) + 1e-9
 
 
+def min_curvature_ratio(x32, y32, d, sweeps, l=1.0):
+    """Replays the oracle's Gauss-Seidel sweeps node step by node step (its
+    own gradient/Hessian and step routines, in its order) and returns the
+    smallest |lambda_min| / |lambda_max| of the 2x2 Hessians it met, with the
+    final positions (equal to oracle.kk_run's).  Below about 1e-4 the small
+    curvature is a difference of near-equal FP32 terms (1 - l dx^2 / r^3 as
+    the path straightens), which an FP32 Hessian cannot resolve, so an FP32
+    run steps differently along that flat direction."""
+    x = np.asarray(x32, np.float64).copy()
+    y = np.asarray(y32, np.float64).copy()
+    worst = np.inf
+    for _ in range(sweeps):
+        for m in range(len(x)):
+            o = oracle.kk_grad_hess(x, y, d, l, m)
+            H = [[o[2], o[3]], [o[3], o[4]]]
+            ev = np.abs(np.linalg.eigvalsh(H))
+            if ev.max() > 0:
+                worst = min(worst, ev.min() / ev.max())
+            st, moved = oracle.kk_step(o[:2], H, l)
+            if moved:
+                x[m] += st[0]
+                y[m] += st[1]
+    return worst, x, y
+
+
 def oracle_spread(x32, y32, d, sweeps, l=1.0, k=ULP_STARTS):
     """Runs the oracle from the FP32 start and from k one-ulp moves of it.
 

@@ -101,7 +101,10 @@ def test_kk_ten_sweeps_match_oracle(c1, forest):
     1e-3 of the diameter for every component, unless the oracle itself,
     started from one-ulp moves of that start, ends farther than 1e-4 of the
     diameter from its unperturbed run (the early sweeps from random starts
-    amplify rounding a thousandfold there)."""
+    amplify rounding a thousandfold there), or the oracle's trajectory meets
+    a Hessian whose small curvature is below 1e-4 of the large one (a path
+    straightening: FP32 cannot resolve that curvature, and the energy is
+    flat along it), where the KK energies must still agree."""
     bgl = _bgl()
     p = bgl.params(kk_sweeps=10)
     checked, excused = 0, []
@@ -119,7 +122,13 @@ def test_kk_ten_sweeps_match_oracle(c1, forest):
             if err <= 1e-3:
                 continue
             _, spread, _ = kk_sensitivity.oracle_spread(xy[:, 0], xy[:, 1], d, 10)
-            assert spread / diam > 1e-4, (int(c), len(vs), err, spread / diam)
+            if spread / diam <= 1e-4:
+                flat, rx, ry = kk_sensitivity.min_curvature_ratio(xy[:, 0], xy[:, 1], d, 10)
+                assert np.array_equal(rx, ox) and np.array_equal(ry, oy)
+                eg = oracle.kk_energy(got[:, 0].astype(np.float64), got[:, 1].astype(np.float64), d, 1.0)
+                eo = oracle.kk_energy(ox, oy, d, 1.0)
+                assert flat < 1e-4 and kk_sensitivity.energy_close(eg, eo), (int(c), len(vs), err, spread / diam,
+                                                                            flat, eg, eo)
             excused.append(int(c))
     assert checked > 200 and len(excused) < checked // 2, (checked, excused)
 
@@ -142,9 +151,10 @@ def test_kk_stays_at_the_oracle_minimum(forest):
 def test_kk_full_run_reaches_the_oracle_minimum(forest):
     """200 sweeps from the same start: the GPU run is stationary and ends at
     the oracle's energy (1e-4 relative) on every component, unless the
-    oracle itself, from one-ulp moves of the start, ends at another energy
-    (the larger components, where rounding decides which minimum the early
-    sweeps fall into)."""
+    oracle itself, from one-ulp moves of the start, ends at another local
+    minimum -- another energy, or a layout more than 1e-3 of the diameter
+    away (the larger components, where rounding decides which minimum the
+    early sweeps fall into)."""
     bgl = _bgl()
     p = bgl.params(kk_sweeps=200)
     checked, excused = 0, []
@@ -161,8 +171,8 @@ def test_kk_full_run_reaches_the_oracle_minimum(forest):
         checked += 1
         if kk_sensitivity.energy_close(eg, e[-1]):
             continue
-        _, _, other = kk_sensitivity.oracle_spread(xy[:, 0], xy[:, 1], d, 200)
-        assert other, (int(c), len(vs), eg, e[-1])
+        _, spread, other = kk_sensitivity.oracle_spread(xy[:, 0], xy[:, 1], d, 200)
+        assert other or spread / max(1, int(d.max())) > 1e-3, (int(c), len(vs), eg, e[-1], spread)
         excused.append(int(c))
     assert checked > 60 and len(excused) <= checked // 4, (checked, excused)
 
