@@ -230,14 +230,17 @@ def run_precision(args, rank, world, dist, local):
     ctx.close()
 
 
-def run_c3(args, rank, world, dist, local):
+def c3_measure(bgl, local, steps, warmup, iters=50, rank=0, world=1, dist=None):
     """Batched components: 100,000 forest components of 3-200 nodes (KK, at
-    most 200 nodes) and 2,000 of 200-5,000 nodes (ForceAtlas2 with exact
-    repulsion), one layout per step; value = ForceAtlas2 node-updates/s,
-    with the KK-only part timed separately."""
+    most 200 nodes) and 2,000 of 200-5,000 nodes (ForceAtlas2, exact or FMM
+    repulsion chosen per component size by measurement), one layout per step:
+    the KK size classes run beside the ForceAtlas2 iterations in one graph
+    launch.  With several ranks each lays out its share of the components
+    (longest-processing-time packing).  Returns the step times, the KK-only
+    times and the ForceAtlas2 node-updates/s."""
     import torch
     import synth
-    import paper_2403_03504_gb300 as bgl
+    from paper_2403_03504_gb300 import shard
 
     ss, us, vs = synth.forest(**synth.C3_SMALL)
     sm, um, vm = synth.forest(**synth.C3_MID)
@@ -248,14 +251,27 @@ def run_c3(args, rank, world, dist, local):
     ctx = bgl.Context(local)
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     ctx.set_stream(stream)
-    iters = min(args.iters, 50)
-    p = bgl.params(seed=0, fa2_iters=iters, repulsion=bgl.REP_EXACT, kk_max_nodes=200)
-    p_kk = bgl.params(seed=0, fa2_iters=0, repulsion=bgl.REP_EXACT, kk_max_nodes=200)
-    g = bgl.Graph.from_edges(ctx, n, u, v)
-    g.components(labels=False)
+    iters = min(iters, 50)
+    p = bgl.params(seed=0, fa2_iters=iters, repulsion=bgl.REP_AUTO, fmm_min_nodes=-1, kk_max_nodes=200)
+    p_kk = bgl.params(seed=0, fa2_iters=0, repulsion=bgl.REP_AUTO, fmm_min_nodes=-1, kk_max_nodes=200)
+    g_all = bgl.Graph.from_edges(ctx, n, u, v)
+    g_all.components(labels=False)
+    n_kk_all, n_fa2_all = g_all.split(200)
+    coff, _, nodes = g_all.component_nodes()
+    if world > 1:
+        # this rank's share: every node id, the edges of its components only
+        costs = shard.component_costs(np.diff(coff), 200, iters, p.kk_sweeps, shard.REP_EXACT)
+        owner, _ = shard.lpt_assign(costs, world)
+        own = shard.node_owner(coff, nodes, owner, n)
+        u, v = shard.share_edges(u, v, own, rank)
+        g_all.destroy()
+        g = bgl.Graph.from_edges(ctx, n, u, v)
+        g.components(labels=False)
+    else:
+        g = g_all
     n_kk, n_fa2 = g.split(200)
-    coff, _, _ = g.component_nodes()
-    fa2_nodes = int(coff[n_fa2])
+    coff_r, _, _ = g.component_nodes()
+    fa2_nodes = int(coff_r[n_fa2])
     d_xy = torch.empty((n, 2), dtype=torch.float32, device=torch.device("cuda", local))
 
     def timed(params, k):
@@ -269,31 +285,42 @@ def run_c3(args, rank, world, dist, local):
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in ev]
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         g.layout_dev(p, d_xy)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     launches0 = bgl.launch_count()
-    step_ms = timed(p, args.steps)
-    launches = (bgl.launch_count() - launches0) // max(args.steps, 1)
-    kk_ms = timed(p_kk, args.steps)
-    upd, total_s = reduce_units_time(dist, float(fa2_nodes) * iters * args.steps, sum(step_ms) / 1e3,
+    step_ms = timed(p, steps)
+    launches = (bgl.launch_count() - launches0) // max(steps, 1)
+    kk_ms = timed(p_kk, steps)
+    upd, total_s = reduce_units_time(dist, float(fa2_nodes) * iters * steps, sum(step_ms) / 1e3,
                                      torch.device("cuda", local))
-    value = upd / total_s
-    if rank == 0:
-        print(json.dumps({
-            "metric": "C3 batched layout: FA2 node-updates/s (exact repulsion) with KK on 1e5 components",
-            "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "c3-batched-100k", "n_nodes": n, "kk_components": int(n_kk),
-                       "fa2_components": int(n_fa2), "fa2_nodes": fa2_nodes, "fa2_iters": iters,
-                       "kk_max_nodes": 200, "kk_sweeps": 200, "repulsion": "exact"},
-            "kk_only_ms": kk_ms, "layouts_per_s": args.steps / total_s, "gpu_launches": int(launches),
-            "step_ms": step_ms}), flush=True)
+    out = {"workload": "c3-batched-100k", "n_nodes": n, "kk_components": int(n_kk_all),
+           "fa2_components": int(n_fa2_all), "fa2_iters": iters, "kk_max_nodes": 200, "kk_sweeps": 200,
+           "repulsion": "auto, exact/FMM crossover measured (fmm_min_nodes = -1)",
+           "ms_per_step": 1e3 * total_s / steps, "step_ms": step_ms, "kk_only_ms": kk_ms,
+           "fa2_node_updates_per_s": upd / total_s, "layouts_per_s": steps / total_s,
+           "gpu_launches_per_step": int(launches)}
     g.destroy()
     ctx.close()
+    return out
+
+
+def run_c3(args, rank, world, dist, local):
+    """The batched-components workload as its own bench line."""
+    import paper_2403_03504_gb300 as bgl
+    c3 = c3_measure(bgl, local, args.steps, args.warmup, args.iters, rank, world, dist)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "C3 batched layout: FA2 node-updates/s with KK on 1e5 components",
+            "value": c3["fa2_node_updates_per_s"], "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": c3["ms_per_step"], "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "dtype": "f32", "data": "synthetic",
+            "config": {k: c3[k] for k in ("workload", "n_nodes", "kk_components", "fa2_components", "fa2_iters",
+                                          "kk_max_nodes", "kk_sweeps", "repulsion")},
+            "kk_only_ms": c3["kk_only_ms"], "layouts_per_s": c3["layouts_per_s"],
+            "gpu_launches": c3["gpu_launches_per_step"], "step_ms": c3["step_ms"]}), flush=True)
 
 
 def env_rank():
@@ -476,6 +503,7 @@ def main():
     ap.add_argument("--exact-iters", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="leave the batched-components object out of the line")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "serve", "precision"],
                     help="c2: the headline 200k-transaction graph; c3: 1e5 small + 2e3 mid-size components; "
                          "serve: k-hop layout requests on the 3M-transaction graph; "
@@ -689,6 +717,8 @@ def main():
                         for name, rep in (("fmm", bgl.REP_FMM), ("exact", bgl.REP_EXACT))}
 
     clocks = clk.summary()
+    # the batched-components workload (10^5 KK + 2,000 ForceAtlas2 components), two steps
+    c3 = c3_measure(bgl, local, 2, 3) if world == 1 and not args.no_c3 else None
     if rank != 0:
         if dist:
             dist.barrier()
@@ -722,6 +752,7 @@ def main():
         "force_error": {"reference": "GPU FP32 exact sum at the final layout (rms_rel); FP64 oracle on 2000 "
                                      "sampled nodes (vs_oracle)", **errs},
         "serving_vs_exact": serving_vs_exact,
+        "c3": c3,
         "exact_fa2": {"value": exact_rate, "unit": UNIT, "iters": args.exact_iters, "nodes": giant},
         "fmm_p16_step_ms": 1e3 * p16_s,
         "m2l_precision": m2l_prec,

@@ -89,7 +89,10 @@ typedef struct bgl_params {
     int32_t repulsion;      /* BGL_REP_EXACT, BGL_REP_FMM or BGL_REP_AUTO        default AUTO */
     int32_t fmm_p;          /* multipole expansion order, 1..24                 default 8 */
     int32_t leaf_size;      /* quadtree leaf capacity, 1..256                   default 64 */
-    int32_t fmm_min_nodes;  /* AUTO uses the FMM for components at least this big  default 8192 */
+    int32_t fmm_min_nodes;  /* AUTO uses the FMM for components at least this big  default 8192;
+                               -1: by measurement (below 2048 nodes exact, from 131072 FMM, in
+                               between the faster of the two, timed once per context and size
+                               octave; the choice may differ between processes) */
     int32_t swing_variant;  /* 0 as printed (Section 3.2), 1 ForceAtlas2 weights default 0 */
     int32_t kk_sweeps;      /* KK sweeps                                         default 200 */
     double kk_l;            /* KK edge length l                                  default 1 */

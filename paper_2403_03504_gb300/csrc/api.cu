@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <vector>
 
 #include "bgl_internal.cuh"
 #include "fmm.cuh"
@@ -101,7 +103,7 @@ void check_params(const bgl_params *p) {
     BGL_REQUIRE(p->repulsion >= BGL_REP_EXACT && p->repulsion <= BGL_REP_AUTO, "repulsion must be 0, 1 or 2");
     BGL_REQUIRE(p->fmm_p >= 1 && p->fmm_p <= 24, "fmm_p must be in [1, 24]");
     BGL_REQUIRE(p->leaf_size >= 1 && p->leaf_size <= 256, "leaf_size must be in [1, 256]");
-    BGL_REQUIRE(p->fmm_min_nodes >= 0, "fmm_min_nodes must be >= 0");
+    BGL_REQUIRE(p->fmm_min_nodes >= -1, "fmm_min_nodes must be >= -1");
     BGL_REQUIRE(p->swing_variant == 0 || p->swing_variant == 1, "swing_variant must be 0 or 1");
     BGL_REQUIRE(p->kk_sweeps >= 0, "kk_sweeps must be >= 0");
     BGL_REQUIRE(p->kk_l > 0, "kk_l must be > 0");
@@ -180,7 +182,11 @@ __global__ void gather_xy_kernel(const float2 *__restrict__ xy_nodes, const int3
 
 namespace bgl {
 
-// Full layout into a device array in node-id order.
+// Full layout into a device array in node-id order.  The Kamada-Kawai
+// components and the ForceAtlas2 components are independent (Section 4), so
+// the KK size classes run beside the ForceAtlas2 iterations: each class on
+// a stream of its own, captured into the same CUDA graph as the iteration
+// loop (one graph launch lays out every component).
 void layout_device(bgl_graph *g, const bgl_params *p, float *d_xy_out) {
     check_params(p);
     require_comp(g);
@@ -188,13 +194,53 @@ void layout_device(bgl_graph *g, const bgl_params *p, float *d_xy_out) {
     bgl_ctx *c = g->ctx;
     DevBuf<float2> xy(c->alloc, g->n);
     const int64_t q_fa2 = g->h_comp_off[g->n_fa2];
-    // small components: Kamada-Kawai (one warp per component)
-    kk_layout(g, p, xy.p, 0, g->n_fa2, g->n_comp, true);
-    // large components: ForceAtlas2
-    if (g->n_fa2 > 0) {
-        init_positions(g, p, xy.p, 0, q_fa2);
-        fa2_layout(g, p, xy.p, 0, 0, g->n_fa2, p->fa2_iters, nullptr);
+    std::unique_ptr<KkRun, void (*)(KkRun *)> kk(kk_prepare(g, g->n_fa2, g->n_comp), kk_destroy);
+    const int nk = kk_classes(kk.get());
+    std::vector<cudaStream_t> ks;
+    std::vector<cudaEvent_t> kev;
+    auto release = [&] {
+        for (auto e : kev) cudaEventDestroy(e);
+        for (auto st : ks) cudaStreamDestroy(st);
+        kev.clear();
+        ks.clear();
+    };
+    try {
+        for (int i = 0; i < nk; ++i) {
+            cudaStream_t st;
+            BGL_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            ks.push_back(st);
+        }
+        for (int i = 0; i < nk + 1; ++i) {
+            cudaEvent_t e;
+            BGL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            kev.push_back(e);
+        }
+        // small components: Kamada-Kawai, one stream per size class, forked
+        // from and joined back to stream s
+        SideWork kk_work = [&](cudaStream_t s) {
+            BGL_CUDA(cudaEventRecord(kev[nk], s));
+            for (int i = 0; i < nk; ++i) {
+                BGL_CUDA(cudaStreamWaitEvent(ks[i], kev[nk], 0));
+                kk_enqueue(kk.get(), i, p, xy.p, 0, true, p->kk_sweeps, nullptr, ks[i]);
+                BGL_CUDA(cudaEventRecord(kev[i], ks[i]));
+            }
+            for (int i = 0; i < nk; ++i) BGL_CUDA(cudaStreamWaitEvent(s, kev[i], 0));
+        };
+        if (g->n_fa2 > 0) {
+            // large components: ForceAtlas2, with the KK classes beside the iterations
+            init_positions(g, p, xy.p, 0, q_fa2);
+            fa2_layout(g, p, xy.p, 0, 0, g->n_fa2, p->fa2_iters, nullptr, nk ? kk_work : SideWork());
+        } else if (nk) {
+            kk_work(c->stream);
+        }
+        BGL_CUDA(cudaStreamSynchronize(c->stream));
+    } catch (...) {
+        // nothing may still write to the scratch when it goes back to the allocator
+        cudaDeviceSynchronize();
+        release();
+        throw;
     }
+    release();
     if (g->n > 0 && p->assemble) {
         assemble_device(g, p, xy.p, reinterpret_cast<float2 *>(d_xy_out), nullptr);
     } else if (g->n > 0) {

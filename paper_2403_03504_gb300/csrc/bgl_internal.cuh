@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <stdexcept>
@@ -130,6 +131,8 @@ struct bgl_ctx {
     // autotuner choices: exact-repulsion targets per thread by log2 of the pairs
     std::mutex tune_mu;
     std::map<int, int> tune_exact;
+    // measured exact/FMM choice by component size octave (fmm_min_nodes = -1)
+    std::map<int, bool> tune_fmm;
 };
 
 namespace bgl {
@@ -244,14 +247,26 @@ void init_positions(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t q0, i
 // sets SplitMix64 initial positions scaled by l * diam / 2; otherwise it
 // starts from xy.
 void kk_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init);
+// KK launches split in preparation (all scratch allocated) and launches that
+// allocate nothing, one per size class, on any stream
+struct KkRun;
+KkRun *kk_prepare(bgl_graph *g, int64_t c0, int64_t c1);
+void kk_destroy(KkRun *run);
+int kk_classes(const KkRun *run);
+void kk_enqueue(const KkRun *run, int i, const bgl_params *p, float2 *xy, int64_t qbase, bool init, int sweeps,
+                int32_t *d_out, cudaStream_t s);
 void kk_distances(bgl_graph *g, int64_t c, int32_t *d_out_dev);
 
 // ForceAtlas2 on components [c0, c1) (exact or FMM per component);
 // xy[q - qbase] holds the position of component-order position q;
 // `iters` iterations from F_{-1} = 0, s_G = 1.  d_stats (device, may be
 // null): swing, traction, s_G per iteration of component c0.
+// Work that runs beside the ForceAtlas2 iterations: enqueued on the given
+// stream (it may fork to streams of its own and must join back); with the
+// device-side loop it is captured and launched in the same graph.
+using SideWork = std::function<void(cudaStream_t)>;
 void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
-                double *d_stats);
+                double *d_stats, const SideWork &side = SideWork());
 // Assembly of the component layouts into one frame (assemble.cu, Section 4):
 // xy_comp[q] the per-component layout at component-order position q,
 // xy_out the assembled frame in node-id order; info (may be null) receives

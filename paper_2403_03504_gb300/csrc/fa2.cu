@@ -403,6 +403,76 @@ bool use_fmm(const bgl_params *p, int64_t n) {
     return n >= p->fmm_min_nodes;
 }
 
+// Measured exact/FMM crossover (repulsion AUTO with fmm_min_nodes = -1).
+// Components below TUNE_LO nodes take the exact sum, those of TUNE_HI or
+// more the FMM.  In between, the first component of each size octave that a
+// context meets is measured at its initial positions: one FMM evaluation
+// (its cost as it runs, one component after another on the stream), and
+// the exact sum's pair rate with the component's tiles repeated until they
+// fill every SM (the rate the exact tiles of a batch of components reach
+// together); the FMM is kept for that octave (and that p and leaf size) if
+// its evaluation takes less than n^2 pairs at that rate.
+constexpr int64_t TUNE_LO = 2048, TUNE_HI = 1 << 17;
+
+static bool use_fmm_for(bgl_graph *g, const bgl_params *p, int64_t c) {
+    const int64_t n = g->h_comp_off[c + 1] - g->h_comp_off[c];
+    if (p->repulsion != BGL_REP_AUTO || p->fmm_min_nodes >= 0) return use_fmm(p, n);
+    if (n < TUNE_LO) return false;
+    if (n >= TUNE_HI) return true;
+    bgl_ctx *ctx = g->ctx;
+    const int key = (int)std::log2((double)n) * 10000 + p->fmm_p * 300 + p->leaf_size;
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tune_fmm.find(key);
+        if (it != ctx->tune_fmm.end()) return it->second;
+    }
+    cudaStream_t s = ctx->stream;
+    const int64_t q0 = g->h_comp_off[c], q1 = g->h_comp_off[c + 1];
+    DevBuf<float2> xy(ctx->alloc, n), f(ctx->alloc, n);
+    init_positions(g, p, xy.p, q0, q1);
+    const std::vector<Tile> one = exact_tiles(g, c, std::vector<int64_t>{c}, 2);
+    // repeated until there are four tiles per SM (each copy writes the same forces)
+    const int reps = std::max<int>(1, (4 * ctx->num_sms + (int)one.size() - 1) / (int)one.size());
+    std::vector<Tile> ex;
+    for (int r = 0; r < reps; ++r) ex.insert(ex.end(), one.begin(), one.end());
+    DevBuf<Tile> tiles(ctx->alloc, ex.size());
+    BGL_CUDA(cudaMemcpyAsync(tiles.p, ex.data(), sizeof(Tile) * ex.size(), cudaMemcpyHostToDevice, s));
+    FmmPlan *pl = fmm_create(g, p, c);
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    float ms_fmm = 0.f, ms_exact = 0.f;
+    try {
+        for (auto &ev : e) BGL_CUDA(cudaEventCreate(&ev));
+        fmm_repulsion(pl, xy.p, q0, f.p, q0);
+        BGL_CUDA(cudaEventRecord(e[0], s));
+        fmm_repulsion(pl, xy.p, q0, f.p, q0);
+        BGL_CUDA(cudaEventRecord(e[1], s));
+        launch_exact(2, (int)ex.size(), tiles.p, g->comp_off.p, c, xy.p, g->mass.p, q0, (float)p->kr, nullptr, f.p, s);
+        BGL_CUDA(cudaEventRecord(e[2], s));
+        launch_exact(2, (int)ex.size(), tiles.p, g->comp_off.p, c, xy.p, g->mass.p, q0, (float)p->kr, nullptr, f.p, s);
+        BGL_CUDA(cudaEventRecord(e[3], s));
+        BGL_CUDA(cudaEventSynchronize(e[3]));
+        BGL_CUDA(cudaEventElapsedTime(&ms_fmm, e[0], e[1]));
+        BGL_CUDA(cudaEventElapsedTime(&ms_exact, e[2], e[3]));
+        const int err = fmm_error(pl);
+        if (err & 1) fail(BGL_ETIMEOUT, "fmm: a bounded device-side wait gave up");
+        if (err & 8) fail(BGL_ENUMERIC, "fmm: non-finite positions");
+        if (err) fail(BGL_ENOMEM, "fmm: tree or list capacity exceeded (error bits " + std::to_string(err) + ")");
+    } catch (...) {
+        for (auto ev : e)
+            if (ev) cudaEventDestroy(ev);
+        fmm_destroy(pl);
+        throw;
+    }
+    for (auto ev : e) cudaEventDestroy(ev);
+    fmm_destroy(pl);
+    // the exact sum of this component alone, at the batched pair rate
+    const double exact_ms = (double)ms_exact / reps;
+    const bool fmm = ms_fmm < exact_ms;
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    ctx->tune_fmm[key] = fmm;
+    return fmm;
+}
+
 // Everything one set of ForceAtlas2 components needs across iterations.
 struct Fa2Run {
     bgl_graph *g;
@@ -440,7 +510,7 @@ struct Fa2Run {
         std::vector<int64_t> roff(1, 0);
         for (int64_t c = c0; c < c1; ++c) {
             int64_t a = g->h_comp_off[c], b = g->h_comp_off[c + 1];
-            if (use_fmm(p, b - a)) {
+            if (use_fmm_for(g, p, c)) {
                 fmm.push_back(fmm_create(g, p, c));
                 fmm_comp.push_back(c);
             } else {
@@ -606,9 +676,27 @@ static bool host_loop() {
     return v && v[0] == '1';
 }
 
-static void run_iterations_host(Fa2Run &run, int iters, double *d_stats) {
+static void run_iterations_host(Fa2Run &run, int iters, double *d_stats, const SideWork &side) {
     bgl_ctx *ctx = run.g->ctx;
     cudaStream_t s = ctx->stream;
+    cudaEvent_t side_done = nullptr;
+    if (side) {
+        // the side work on its own stream beside the iterations, joined after them
+        BGL_CUDA(cudaEventCreateWithFlags(&side_done, cudaEventDisableTiming));
+        BGL_CUDA(cudaEventRecord(run.ev_fork, s));
+        BGL_CUDA(cudaStreamWaitEvent(run.side, run.ev_fork, 0));
+        try {
+            side(run.side);
+            BGL_CUDA(cudaEventRecord(side_done, run.side));
+        } catch (...) {
+            cudaEventDestroy(side_done);
+            throw;
+        }
+    }
+    struct EventGuard {
+        cudaEvent_t e;
+        ~EventGuard() { if (e) cudaEventDestroy(e); }
+    } side_guard{side_done};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const int64_t before = launch_count();
@@ -641,6 +729,7 @@ static void run_iterations_host(Fa2Run &run, int iters, double *d_stats) {
         throw;
     }
     count_launches(per_iter * iters);
+    if (side_done) BGL_CUDA(cudaStreamWaitEvent(s, side_done, 0));
     BGL_CUDA(cudaMemcpyAsync(ctx->h_flag + 1, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     BGL_CUDA(cudaStreamSynchronize(s));
     cudaGraphExecDestroy(exec);
@@ -653,15 +742,18 @@ static void run_iterations_host(Fa2Run &run, int iters, double *d_stats) {
 // one-thread kernel that counts the iterations and clears the condition
 // after the last, so the loop runs on the device without the host.
 // Nothing may allocate while the capture is open.
-static void run_iterations(Fa2Run &run, int iters, double *d_stats) {
-    if (iters <= 0) return;
+static void run_iterations(Fa2Run &run, int iters, double *d_stats, const SideWork &side = SideWork()) {
     bgl_ctx *ctx = run.g->ctx;
     cudaStream_t s = ctx->stream;
+    if (iters <= 0) {
+        if (side) side(s);
+        return;
+    }
     BGL_CUDA(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
     BGL_CUDA(cudaMemsetAsync(run.iter.p, 0, sizeof(int), s));
     BGL_CUDA(cudaMemsetAsync(run.loop.p, 0, sizeof(int), s));
     if (host_loop()) {
-        run_iterations_host(run, iters, d_stats);
+        run_iterations_host(run, iters, d_stats, side);
         return;
     }
     cudaGraph_t graph = nullptr;
@@ -706,6 +798,28 @@ static void run_iterations(Fa2Run &run, int iters, double *d_stats) {
             BGL_CUDA(cudaGraphNodeGetType(nd, &t));
             if (t == cudaGraphNodeTypeKernel) ++kernels;
         }
+        if (side) {
+            // the side work, captured on the run's side stream (it may fork
+            // to streams of its own), becomes a child graph beside the loop
+            cudaGraph_t child = nullptr;
+            BGL_CUDA(cudaStreamBeginCapture(run.side, cudaStreamCaptureModeThreadLocal));
+            ctx->alloc->forbid = true;
+            try {
+                side(run.side);
+            } catch (...) {
+                ctx->alloc->forbid = false;
+                cudaGraph_t tmp = nullptr;
+                cudaStreamEndCapture(run.side, &tmp);
+                if (tmp) cudaGraphDestroy(tmp);
+                throw;
+            }
+            ctx->alloc->forbid = false;
+            BGL_CUDA(cudaStreamEndCapture(run.side, &child));
+            cudaGraphNode_t cn;
+            const cudaError_t e = cudaGraphAddChildGraphNode(&cn, graph, nullptr, 0, child);
+            cudaGraphDestroy(child);
+            BGL_CUDA(e);
+        }
         BGL_CUDA(cudaGraphInstantiate(&exec, graph, 0));
     } catch (...) {
         cudaGraphDestroy(graph);
@@ -727,10 +841,13 @@ static void run_iterations(Fa2Run &run, int iters, double *d_stats) {
 }
 
 void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, int iters,
-                double *d_stats) {
-    if (c1 <= c0 || iters <= 0) return;
+                double *d_stats, const SideWork &side) {
+    if (c1 <= c0 || iters <= 0) {
+        if (side) side(g->ctx->stream);
+        return;
+    }
     Fa2Run run(g, p, xy, qbase, c0, c1);
-    run_iterations(run, iters, d_stats);
+    run_iterations(run, iters, d_stats, side);
 }
 
 // ---------------------------------------------------------------- resumable runs

@@ -20,6 +20,8 @@
 // Small components share a warp: lane groups of 4, 8, 16 or 32 lanes by
 // component size class, each group laying out its own component.
 #include <algorithm>
+#include <memory>
+#include <vector>
 
 #include "bgl_internal.cuh"
 #include "kk_common.cuh"
@@ -266,22 +268,42 @@ void init_positions(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t q0, i
     BGL_LAUNCH_CHECK();
 }
 
+// One size class of a KK launch: components [c0, c1) in groups of G lanes
+// with up to CPL nodes per lane; distances in global memory above 64 nodes.
+struct KkClass {
+    int G = 0, CPL = 0;
+    int64_t c0 = 0, c1 = 0;
+    int maxn = 1, gpb = 1;
+    size_t smem = 0;
+    DevBuf<uint8_t> gdist;
+    DevBuf<int64_t> gdist_off;
+};
+
+struct KkRun {
+    bgl_graph *g = nullptr;
+    std::vector<std::unique_ptr<KkClass>> cls;
+};
+
 template <int G, int CPL>
-static void kk_launch_group(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1,
-                            bool init, int sweeps, int32_t *d_out) {
+static void kk_prepare_class(KkRun &run, int64_t c0, int64_t c1) {
     if (c1 <= c0) return;
+    bgl_graph *g = run.g;
+    auto k = std::make_unique<KkClass>();
+    k->G = G;
+    k->CPL = CPL;
+    k->c0 = c0;
+    k->c1 = c1;
     int maxn = (int)(g->h_comp_off[c0 + 1] - g->h_comp_off[c0]);   // components sorted by size, descending
     BGL_REQUIRE(maxn <= G * CPL && maxn <= 255, "kk: component larger than its size class");
     if (maxn < 1) maxn = 1;
+    k->maxn = maxn;
     const bool glob = maxn > KK_SMEM_MAX_N;
     const size_t gb = kk_group_bytes(maxn, glob);
     const int max_groups = 256 / G;
-    const int gpb = (int)std::min<size_t>(max_groups, std::max<size_t>(1, (size_t)(200 * 1024) / gb));
-    const size_t smem = KK_TABLE_BYTES + gb * gpb;
-    // global distance matrices: n_c x stride(n_c) bytes per component
-    DevBuf<uint8_t> gdist;
-    DevBuf<int64_t> gdist_off;
+    k->gpb = (int)std::min<size_t>(max_groups, std::max<size_t>(1, (size_t)(200 * 1024) / gb));
+    k->smem = KK_TABLE_BYTES + gb * k->gpb;
     if (glob) {
+        // global distance matrices: n_c x stride(n_c) bytes per component
         std::vector<int64_t> off(c1 - c0);
         int64_t tot = 0;
         for (int64_t c = c0; c < c1; ++c) {
@@ -289,12 +311,20 @@ static void kk_launch_group(bgl_graph *g, const bgl_params *p, float2 *xy, int64
             off[c - c0] = tot;
             tot += nc * kk_row_stride((int)nc);
         }
-        gdist.reset(g->ctx->alloc, std::max<int64_t>(tot, 8));
-        gdist_off.reset(g->ctx->alloc, off.size());
-        BGL_CUDA(cudaMemcpyAsync(gdist_off.p, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice,
+        k->gdist.reset(g->ctx->alloc, std::max<int64_t>(tot, 8));
+        k->gdist_off.reset(g->ctx->alloc, off.size());
+        BGL_CUDA(cudaMemcpyAsync(k->gdist_off.p, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice,
                                  g->ctx->stream));
+        BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
     }
     BGL_CUDA(cudaFuncSetAttribute(kk_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    run.cls.push_back(std::move(k));
+}
+
+template <int G, int CPL>
+static void kk_enqueue_class(const KkRun &run, const KkClass &k, const bgl_params *p, float2 *xy, int64_t qbase,
+                             bool init, int sweeps, int32_t *d_out, cudaStream_t s) {
+    bgl_graph *g = run.g;
     KKArgs a;
     a.comp_off = g->comp_off.p;
     a.coff = g->coff.p;
@@ -302,23 +332,21 @@ static void kk_launch_group(bgl_graph *g, const bgl_params *p, float2 *xy, int64
     a.nodes = g->nodes.p;
     a.xy = xy;
     a.qbase = qbase;
-    a.c0 = c0;
-    a.nc = c1 - c0;
-    a.maxn = maxn;
-    a.gpb = gpb;
+    a.c0 = k.c0;
+    a.nc = k.c1 - k.c0;
+    a.maxn = k.maxn;
+    a.gpb = k.gpb;
     a.seed = p->seed;
     a.l = (float)p->kk_l;
     a.sweeps = sweeps;
     a.tol = (float)p->kk_tol;
     a.init = init ? 1 : 0;
     a.d_out = d_out;
-    a.gdist = glob ? gdist.p : nullptr;
-    a.gdist_off = glob ? gdist_off.p : nullptr;
-    const int64_t blocks = (a.nc + gpb - 1) / gpb;
-    kk_kernel<G, CPL><<<(unsigned)blocks, G * gpb, smem, g->ctx->stream>>>(a);
+    a.gdist = k.gdist.p;
+    a.gdist_off = k.gdist_off.p;
+    const int64_t blocks = (a.nc + k.gpb - 1) / k.gpb;
+    kk_kernel<G, CPL><<<(unsigned)blocks, G * k.gpb, k.smem, s>>>(a);
     BGL_LAUNCH_CHECK();
-    // the scratch goes back to the caching allocator only once the kernel is done
-    if (glob) BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
 }
 
 // first component index in [c0, c1) with at most `size` nodes (sizes descend)
@@ -335,19 +363,53 @@ static int64_t first_at_most(const bgl_graph *g, int64_t c0, int64_t c1, int64_t
 // Components in size classes: (128, 255] nodes 32 lanes x up to 8 nodes
 // each, (64, 128] 32 x 4, (32, 64] 32 x 2, (16, 32] 16 x 2, (8, 16] 8 x 2,
 // (4, 8] 4 x 2, <= 4 4 x 1; distances in global memory above 64 nodes.
+// Preparing allocates every class's scratch (held until the run is
+// destroyed) so that the launches need no allocation and no synchronisation.
+KkRun *kk_prepare(bgl_graph *g, int64_t c0, int64_t c1) {
+    auto run = std::make_unique<KkRun>();
+    run->g = g;
+    if (c1 > c0) {
+        const int64_t a128 = first_at_most(g, c0, c1, 128), a64 = first_at_most(g, c0, c1, 64),
+                      a32 = first_at_most(g, c0, c1, 32), a16 = first_at_most(g, c0, c1, 16),
+                      a8 = first_at_most(g, c0, c1, 8), a4 = first_at_most(g, c0, c1, 4);
+        kk_prepare_class<32, 8>(*run, c0, a128);
+        kk_prepare_class<32, 4>(*run, a128, a64);
+        kk_prepare_class<32, 2>(*run, a64, a32);
+        kk_prepare_class<16, 2>(*run, a32, a16);
+        kk_prepare_class<8, 2>(*run, a16, a8);
+        kk_prepare_class<4, 2>(*run, a8, a4);
+        kk_prepare_class<4, 1>(*run, a4, c1);
+    }
+    return run.release();
+}
+
+void kk_destroy(KkRun *run) { delete run; }
+
+int kk_classes(const KkRun *run) { return (int)run->cls.size(); }
+
+// launches size class i on stream s
+void kk_enqueue(const KkRun *run, int i, const bgl_params *p, float2 *xy, int64_t qbase, bool init, int sweeps,
+                int32_t *d_out, cudaStream_t s) {
+    const KkClass &k = *run->cls[i];
+    switch (k.G * 16 + k.CPL) {
+        case 32 * 16 + 8: kk_enqueue_class<32, 8>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 32 * 16 + 4: kk_enqueue_class<32, 4>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 32 * 16 + 2: kk_enqueue_class<32, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 16 * 16 + 2: kk_enqueue_class<16, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 8 * 16 + 2: kk_enqueue_class<8, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 4 * 16 + 2: kk_enqueue_class<4, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        default: kk_enqueue_class<4, 1>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+    }
+}
+
 static void kk_launch(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init,
                       int sweeps, int32_t *d_out) {
     if (c1 <= c0) return;
-    const int64_t a128 = first_at_most(g, c0, c1, 128), a64 = first_at_most(g, c0, c1, 64),
-                  a32 = first_at_most(g, c0, c1, 32), a16 = first_at_most(g, c0, c1, 16),
-                  a8 = first_at_most(g, c0, c1, 8), a4 = first_at_most(g, c0, c1, 4);
-    kk_launch_group<32, 8>(g, p, xy, qbase, c0, a128, init, sweeps, d_out);
-    kk_launch_group<32, 4>(g, p, xy, qbase, a128, a64, init, sweeps, d_out);
-    kk_launch_group<32, 2>(g, p, xy, qbase, a64, a32, init, sweeps, d_out);
-    kk_launch_group<16, 2>(g, p, xy, qbase, a32, a16, init, sweeps, d_out);
-    kk_launch_group<8, 2>(g, p, xy, qbase, a16, a8, init, sweeps, d_out);
-    kk_launch_group<4, 2>(g, p, xy, qbase, a8, a4, init, sweeps, d_out);
-    kk_launch_group<4, 1>(g, p, xy, qbase, a4, c1, init, sweeps, d_out);
+    std::unique_ptr<KkRun> run(kk_prepare(g, c0, c1));
+    for (int i = 0; i < kk_classes(run.get()); ++i)
+        kk_enqueue(run.get(), i, p, xy, qbase, init, sweeps, d_out, g->ctx->stream);
+    // the scratch goes back to the caching allocator only once the kernels are done
+    BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
 }
 
 void kk_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, int64_t c0, int64_t c1, bool init) {

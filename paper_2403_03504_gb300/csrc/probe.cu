@@ -33,15 +33,19 @@ __global__ void __launch_bounds__(PROBE_THREADS, 1) probe_kernel(int iters, floa
         a[k] = seed + 1e-3f * (float)(k + 1) + 1e-6f * (float)threadIdx.x;
         b[k] = seed - 1e-3f * (float)(k + 1);
     }
-    // the chains start after the first clock read and end before the second:
-    // volatile register barriers keep the compiler from moving the
-    // arithmetic across the clock reads
-#pragma unroll
-    for (int k = 0; k < PROBE_CHAINS; ++k) asm volatile("" : "+f"(a[k]), "+f"(b[k]));
+    // the chains start after the first clock read and end before the second
+    // by data dependence: their inputs take a term of the first clock value
+    // (zero in practice, unknown to the compiler), and their sum is stored to
+    // shared memory before the barrier that precedes the second read
+    __shared__ float red[32];
     __syncthreads();
     const long long t0 = clock64();
+    const float z = (float)(t0 >> 62);
 #pragma unroll
-    for (int k = 0; k < PROBE_CHAINS; ++k) asm volatile("" : "+f"(a[k]), "+f"(b[k]));
+    for (int k = 0; k < PROBE_CHAINS; ++k) {
+        a[k] += z;
+        b[k] += z;
+    }
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < PROBE_CHAINS; ++k) {
@@ -57,14 +61,17 @@ __global__ void __launch_bounds__(PROBE_THREADS, 1) probe_kernel(int iters, floa
             }
         }
     }
-#pragma unroll
-    for (int k = 0; k < PROBE_CHAINS; ++k) asm volatile("" : "+f"(a[k]), "+f"(b[k]));
-    const long long t1 = clock64();
-    __syncthreads();
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < PROBE_CHAINS; ++k) s += a[k] + b[k];
-    if (s == 1234.5f) sink[0] = s;   // keeps the chains live
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        float tot = 0.f;
+        for (int w = 0; w < PROBE_THREADS / 32; ++w) tot += red[w];
+        if (tot == 1234.5f) sink[0] = tot;   // keeps the chains live
+    }
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 

@@ -137,3 +137,46 @@ def test_batched_fa2_components_each_match_oracle(ctx):
         err = np.max(np.hypot(xy[vs, 0] - st.x, xy[vs, 1] - st.y))
         assert err <= 1e-3 * diag, (c, len(vs), err, diag)
     g.destroy()
+
+
+def test_measured_crossover_picks_exact_or_fmm_per_component(ctx):
+    """fmm_min_nodes = -1: components below 2,048 nodes take the exact sum,
+    those of 131,072 or more the FMM, the ones in between whichever was
+    faster when timed; each component equals, bitwise, its layout under the
+    kind it was given (components are independent)."""
+    bgl = _bgl()
+    small, _, _ = synth.forest(41, 3, 300.0, 300.0)
+    mid, _, _ = synth.forest(42, 1, 6000.0, 6000.0)
+    sizes = [140000, int(mid[0])] + [int(x) for x in small]
+    u, v, base = [], [], 0
+    for k, n in enumerate(sizes):
+        if k == 0:                                    # a long path
+            u.append(np.arange(base, base + n - 1))
+            v.append(np.arange(base + 1, base + n))
+        else:
+            s2, uu, vv = synth.forest(41 + k, 1, float(n), float(n))
+            assert int(s2[0]) == n
+            u.append(uu + base)
+            v.append(vv + base)
+        base += n
+    u = np.concatenate(u).astype(np.int32)
+    v = np.concatenate(v).astype(np.int32)
+    g = bgl.Graph.from_edges(ctx, base, u, v)
+    g.components(labels=False)
+    coff, _, nodes = g.component_nodes()
+    common = dict(seed=5, fa2_iters=3, kk_max_nodes=50, fmm_p=8, leaf_size=64)
+    tuned = g.layout(bgl.params(repulsion=bgl.REP_AUTO, fmm_min_nodes=-1, **common))
+    exact = g.layout(bgl.params(repulsion=bgl.REP_EXACT, **common))
+    fmm = g.layout(bgl.params(repulsion=bgl.REP_FMM, **common))
+    for c in range(len(coff) - 1):
+        vs = nodes[coff[c]:coff[c + 1]]
+        n = len(vs)
+        is_exact = np.array_equal(tuned[vs], exact[vs])
+        is_fmm = np.array_equal(tuned[vs], fmm[vs])
+        if n < 2048:
+            assert is_exact, (c, n)
+        elif n >= 131072:
+            assert is_fmm, (c, n)
+        else:
+            assert is_exact or is_fmm, (c, n)
+    g.destroy()

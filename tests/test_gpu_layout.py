@@ -334,3 +334,18 @@ def test_layout_c1_against_oracle(c1):
         gmax = max(np.hypot(*oracle.kk_grad_hess(xy[vs, 0], xy[vs, 1], d, 1.0, m)[:2]) for m in range(len(vs)))
         assert gmax <= 1e-3 * max(1.0, eo), (c, gmax)
         assert kk_sensitivity.energy_close(eg, eo), (int(c), len(vs), eg, eo)
+
+
+def test_layout_host_loop_equals_device_loop(c1, monkeypatch):
+    """A whole layout with KK and ForceAtlas2 components: the KK size
+    classes run beside the iterations (in the same graph with the device
+    loop, on a side stream with the host loop); both give the same bits."""
+    bgl = _bgl()
+    for p in (bgl.params(seed=2, fa2_iters=12, kk_sweeps=40, repulsion=bgl.REP_EXACT),
+              bgl.params(seed=2, fa2_iters=12, kk_sweeps=40, repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=32)):
+        monkeypatch.delenv("BGL_HOST_LOOP", raising=False)
+        a = c1.g.layout(p)
+        monkeypatch.setenv("BGL_HOST_LOOP", "1")
+        b = c1.g.layout(p)
+        monkeypatch.delenv("BGL_HOST_LOOP", raising=False)
+        assert np.array_equal(a, b)
