@@ -218,13 +218,25 @@ struct OsHist {
 // runs before its histogram kernel, and each block of the histogram kernel
 // (one per tile) zeroes its tile's status words (os_clear_status).
 OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n, bool clear = true);
+// The bounded waits of the scatter passes: err (null: the workspace's own
+// word) receives bit 1 when a wait gives up, and a pass started after that
+// does nothing; spin is the poll limit (0: the default, about half a second
+// of polling); stall_first = 1 makes the first tile of every pass withhold
+// its counts, so that the waits on it run out -- a test aid for the
+// failure path (BGL_ETIMEOUT), memory-safe because a tile that gives up
+// still writes inside [0, n).
+struct OsWait {
+    int *err = nullptr;
+    long long spin = 0;
+    int stall_first = 0;
+};
 // d_skip (device int, may be null = 0): the passes below *d_skip (0 or 2)
 // return at once, so the keys end up ordered by their top 32 - 8 * skip
 // bits only (stable: equal top bits keep the input order).  Read by each
 // pass when it starts.
 void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n,
                                const float2 *gxy = nullptr, const float *gmass = nullptr, float4 *gpts = nullptr,
-                               const int *d_skip = nullptr);
+                               const int *d_skip = nullptr, OsWait wait = OsWait());
 
 int bits_for(uint64_t max_value);   // number of bits needed to hold max_value
 

@@ -48,6 +48,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cstdlib>
+
 #include "fmm.cuh"
 #include "p2p.cuh"
 #include "sort_hist.cuh"
@@ -102,6 +104,13 @@ __host__ __device__ __forceinline__ int near_class(int points) {
 
 
 enum { ERR_SPIN = 1, ERR_LIST_OVERFLOW = 2, ERR_BOX_OVERFLOW = 4, ERR_BBOX = 8 };
+
+// After a bounded wait of the sort gave up, the points are not sorted and the
+// kernels that build on them return at once (the evaluation reports
+// BGL_ETIMEOUT; its forces are not written).  The error word does not change
+// while these kernels run (only the sort sets ERR_SPIN, earlier on the
+// stream), so every thread of a launch takes the same branch.
+__device__ __forceinline__ bool aborted(const int *err) { return (*err & ERR_SPIN) != 0; }
 
 // Root square and the per-level box geometry in FP32 (GB300's FP64 rate is
 // a small fraction of its FP32 rate, so nothing per point or per box uses it)
@@ -411,7 +420,9 @@ __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy
 __global__ void __launch_bounds__(TREE_THREADS) tree_count_kernel(const uint32_t *__restrict__ key, int n, int S,
                                                                  int8_t *__restrict__ cl, int8_t *__restrict__ lam,
                                                                  int *__restrict__ tcnt, int ntiles,
-                                                                 const int *__restrict__ sortskip, int *gmax) {
+                                                                 const int *__restrict__ sortskip, int *gmax,
+                                                                 const int *err) {
+    if (aborted(err)) return;
     // keys sorted on their top 16 bits only (two radix passes skipped):
     // boxes stop at level 8
     const int cap = *sortskip == 2 ? 8 : MAXLEV;
@@ -494,6 +505,7 @@ constexpr int SCAN_ITEMS = 8;
 // deep), the next sort orders the top 16 key bits only.
 __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int ntiles, int *levoff, int Bmax,
                                                                  int *err, const int *gmax, int *sortskip) {
+    if (aborted(err)) return;
     __shared__ int sv[SCAN_THREADS * SCAN_ITEMS];
     __shared__ int wsum[32];
     __shared__ int carry_s;
@@ -567,6 +579,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) tree_scan_kernel(int *tcnt, int 
 __global__ void __launch_bounds__(TREE_THREADS) tree_emit_kernel(Tree T, const int8_t *__restrict__ cl,
                                                                 const int8_t *__restrict__ lam,
                                                                 const int *__restrict__ tcnt, int ntiles, int Bmax) {
+    if (aborted(T.err)) return;
     constexpr int NW = TREE_THREADS / 32;
     constexpr int R = TREE_TILE / TREE_THREADS;        // rounds per warp
     constexpr int PW = TREE_TILE / NW;                 // points per warp
@@ -888,6 +901,7 @@ __device__ bool descend(const Tree &T, int cb, int L, int *front, int nf, int *s
 constexpr int LIST_WARPS = 8;
 
 __global__ void __launch_bounds__(LIST_WARPS * 32) nbr_lists_kernel(Tree T) {
+    if (aborted(T.err)) return;
     __shared__ int s_u[LIST_WARPS][LST_CAP], s_w[LIST_WARPS][LST_CAP];
     __shared__ int s_front[LIST_WARPS][2 * FRONT_CAP];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1088,6 +1102,7 @@ constexpr int VROWS = 32;             // rows of a translated expansion in vout
 // rows of vout for every box's V entries (the order of boxes in vout is
 // immaterial: each box reads back its own rows)
 __global__ void vbase_kernel(Tree T, int *vtot, int cap, int *vbase) {
+    if (aborted(T.err)) return;
     const int B = min(T.levoff[NLEV], T.Bmax);
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
         const int nv = T.lofs[5 * b + 2] - T.lofs[5 * b + 1];
@@ -1104,6 +1119,7 @@ __global__ void vbase_kernel(Tree T, int *vtot, int cap, int *vbase) {
 }
 
 __global__ void vclass_count_kernel(Tree T, int *count) {
+    if (aborted(T.err)) return;
     __shared__ int sc[VCLS];
     for (int i = threadIdx.x; i < VCLS; i += blockDim.x) sc[i] = 0;
     __syncthreads();
@@ -1118,6 +1134,7 @@ __global__ void vclass_count_kernel(Tree T, int *count) {
 // bucket starts (exclusive scan of the 49 counts, rounded up to tiles of 8);
 // the padding slots of every bucket hold {-1, -1}
 __global__ void vclass_scan_kernel(const int *count, int *start, int *cursor, int cap, int2 *pairs, int *err) {
+    if (aborted(err)) return;
     if (threadIdx.x != 0) return;
     int acc = 0;
     for (int c = 0; c < VCLS; ++c) {
@@ -1134,6 +1151,7 @@ __global__ void vclass_scan_kernel(const int *count, int *start, int *cursor, in
 // pairs[pos] = {V entry index in lidx, its row in vout}; slots are claimed
 // per block (shared counters, one global atomic per class and round)
 __global__ void vclass_scatter_kernel(Tree T, int *cursor, const int *vbase, int cap, int2 *pairs) {
+    if (aborted(T.err)) return;
     __shared__ int sc[VCLS], sb[VCLS];
     const int B = min(T.levoff[NLEV], T.Bmax);
     for (int r0 = blockIdx.x * blockDim.x; r0 < B; r0 += gridDim.x * blockDim.x) {
@@ -1167,6 +1185,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 __global__ void __launch_bounds__(256) m2l_bf16_kernel(Tree T, const float2 *__restrict__ M, int PT1, int p,
                                                        const int *__restrict__ start, const int2 *__restrict__ pairs,
                                                        const uint4 *__restrict__ tfrag, int cap, float *vout) {
+    if (aborted(T.err)) return;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -1253,6 +1272,7 @@ constexpr int P2M_MAX = 512;
 
 template <int PT>
 __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
+    if (aborted(a.T.err)) return;
     __shared__ float sbin[BN * BN];
     __shared__ float2 stage[8][4][PT + 1];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
@@ -1360,6 +1380,7 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
 // blocks per SM hide more of the latency of the list and expansion loads)
 template <int PT, bool TC>
 __global__ void __launch_bounds__(256, PT == 8 ? 4 : (PT == 12 ? 2 : 1)) m2l_kernel(ExpArgs a) {
+    if (aborted(a.T.err)) return;
     __shared__ float sbin[BN * BN];
     for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
     __syncthreads();
@@ -1592,6 +1613,7 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
 // tree (the emit kernel fills only the slots of children that exist; the
 // plan starts with all slots empty).
 __global__ void combine_kernel(LeafArgs la, int n) {
+    if (aborted(la.e.T.err)) return;
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     const Tree &T = la.e.T;
     for (int b = o, B = min(T.levoff[NLEV], T.Bmax); b < B; b += gridDim.x * blockDim.x)
@@ -1619,6 +1641,7 @@ __device__ __forceinline__ void near_dispatch(int r, const Tree &T, LeafArgs &la
 }
 
 __global__ void __launch_bounds__(NEAR_WARPS * 32) near_kernel(LeafArgs la) {
+    if (aborted(la.e.T.err)) return;
     const Tree &T = la.e.T;
     __shared__ __align__(16) float4 stage[NEAR_WARPS][2][NEAR_SRC];
     const int lane = threadIdx.x & 31;
@@ -1697,6 +1720,7 @@ __device__ __forceinline__ float2 m2p_term(const Tree &T, const Root *rt, const 
 
 template <int PT>
 __global__ void __launch_bounds__(FAR_WARPS * 32, 12) far_kernel(LeafArgs la) {
+    if (aborted(la.e.T.err)) return;
     __shared__ float sbin[(PT + 1) * (PT + 1)];   // C(l, m), l, m <= PT
     __shared__ float2 loc[FAR_WARPS][PT + 1];
     __shared__ float2 ancl[FAR_WARPS][MAXLEV - 1][PT + 1];
@@ -1836,6 +1860,7 @@ constexpr int HEAVY_WARPS = 16;
 
 template <int PT>
 __global__ void __launch_bounds__(HEAVY_WARPS * 32) far_heavy_kernel(LeafArgs la) {
+    if (aborted(la.e.T.err)) return;
     __shared__ float2 part[HEAVY_WARPS][32];
     const Tree &T = la.e.T;
     const Root *rt = T.root;
@@ -1942,6 +1967,7 @@ static std::vector<uint4> m2l_fragments(int p) {
 
 struct FmmPlan {
     bgl_graph *g = nullptr;
+    OsWait wait;           // bounded waits of the sort: error word, poll limit, test stall
     int64_t c = 0, q0 = 0;
     int n = 0, p = 8, PT = 8, S = 64, Bmax = 1, ntiles = 1, lcap = 1, grid_p = 1;
     float kr = 1.f;
@@ -2060,6 +2086,17 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         BGL_CUDA(cudaMemsetAsync(pl->epoch.p, 0, sizeof(unsigned), s));
         pl->tickets.reset(A, NTICKETS);
         pl->err.reset(A, 1);
+        pl->wait.err = pl->err.p;
+        {
+            // test aid for the failure path: BGL_TEST_SORT_STALL=1 makes the
+            // sort's first tile withhold its counts and the waits on it give
+            // up after 4,096 polls, so the evaluation reports BGL_ETIMEOUT
+            const char *v = std::getenv("BGL_TEST_SORT_STALL");
+            if (v && v[0] == '1') {
+                pl->wait.stall_first = 1;
+                pl->wait.spin = 1 << 12;
+            }
+        }
         pl->sortws.reserve(A, n, s);
         BGL_CUDA(cudaMemsetAsync(pl->counter.p, 0, sizeof(unsigned), s));
         BGL_CUDA(cudaMemsetAsync(pl->arrive.p, 0, sizeof(int) * bmax, s));
@@ -2163,7 +2200,8 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
         BGL_LAUNCH_CHECK();
         keys_kernel<<<nblk(n, 256 * KEY_ITEMS), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p, h);
         BGL_LAUNCH_CHECK();
-        radix_sort_u32_ws_scatter(ctx, pl->sortws, pl->key.p, pl->idx.p, n, xl, ml, pl->pts.p, pl->sortskip.p);
+        radix_sort_u32_ws_scatter(ctx, pl->sortws, pl->key.p, pl->idx.p, n, xl, ml, pl->pts.p, pl->sortskip.p,
+                                  pl->wait);
     } catch (...) {
         ctx->stream = keep;
         throw;
@@ -2174,7 +2212,7 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
 // tree: boxes in level order, ends, parents, children
 static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
     tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, pl->n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
-                                                          pl->ntiles, pl->sortskip.p, pl->tickets.p + 6);
+                                                          pl->ntiles, pl->sortskip.p, pl->tickets.p + 6, pl->err.p);
     BGL_LAUNCH_CHECK();
     tree_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(pl->tcnt.p, pl->ntiles, pl->levoff.p, pl->Bmax, pl->err.p,
                                                 pl->tickets.p + 6, pl->sortskip.p);
@@ -2309,6 +2347,7 @@ namespace {
 
 // interaction counts: P2P pairs, M2P and P2L point-box terms
 __global__ void count_kernel(Tree T, unsigned long long *out) {
+    if (aborted(T.err)) return;
     const int B = min(T.levoff[NLEV], T.Bmax);
     unsigned long long p2p = 0, m2p = 0, p2l = 0, leaves = 0, depth = 0, m2l = 0, heavy = 0;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {

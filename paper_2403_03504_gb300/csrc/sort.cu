@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(OS_THREADS, 2) os_scatter_kernel(OsBufs bf, in
                                                                  uint32_t *status, unsigned *ticket, int *err,
                                                                  const float2 *__restrict__ gxy,
                                                                  const float *__restrict__ gmass,
-                                                                 float4 *__restrict__ gpts) {
+                                                                 float4 *__restrict__ gpts, OsWait wait) {
     const int skip = d_skip ? *d_skip : 0;
     if (d < skip) return;
     const int shift = 8 * d;
@@ -317,10 +317,14 @@ __global__ void __launch_bounds__(OS_THREADS, 2) os_scatter_kernel(OsBufs bf, in
     __shared__ uint32_t skey[OS_TILE], sval[OS_TILE];
     __shared__ int tile_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) tile_s = (int)atomicAdd(ticket, 1u);
+    // after a wait gave up (in an earlier pass, or in this one before the
+    // block started) the keys are not sorted: blocks return before taking
+    // a tile, so no tile is left waiting for one that nobody holds
+    if (threadIdx.x == 0) tile_s = (*(volatile int *)err & 1) ? -1 : (int)atomicAdd(ticket, 1u);
     for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const int tile = tile_s;
+    if (tile < 0) return;
     const int64_t t0 = (int64_t)tile * OS_TILE;
     const int tcount = (int)(n - t0 < OS_TILE ? n - t0 : OS_TILE);
     const unsigned lt = (1u << lane) - 1u;
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(OS_THREADS, 2) os_scatter_kernel(OsBufs bf, in
         const uint32_t own = (uint32_t)s;
         uint32_t excl = 0;
         if (tile == 0) {
-            st[d] = OS_INC | own;
+            if (!wait.stall_first) st[d] = OS_INC | own;
         } else {
             st[(int64_t)tile * 256 + d] = OS_AGG | own;
             // look back OS_LB predecessors per step: their status words are
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(OS_THREADS, 2) os_scatter_kernel(OsBufs bf, in
                     if (done) break;
                     long long it = 0;
                     while ((v[w] & ~OS_MASK) == 0) {
-                        if (++it > OS_SPIN) {
+                        if (++it > wait.spin) {
                             atomicOr(err, 1);
                             v[w] = OS_INC;
                             break;
@@ -506,13 +510,14 @@ OsHist radix_sort_u32_ws_begin(bgl_ctx *c, SortWorkspace &ws, int64_t n, bool cl
 }
 
 void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, uint32_t *vals, int64_t n,
-                               const float2 *gxy, const float *gmass, float4 *gpts, const int *d_skip) {
+                               const float2 *gxy, const float *gmass, float4 *gpts, const int *d_skip, OsWait wait) {
     cudaStream_t s = c->stream;
     const int64_t nt = os_tiles(n);
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws.hist.p);
     uint32_t *base = hist + 4 * 256;
     unsigned *tickets = reinterpret_cast<unsigned *>(hist + 8 * 256);
-    int *err = reinterpret_cast<int *>(tickets + 5);
+    int *err = wait.err ? wait.err : reinterpret_cast<int *>(tickets + 5);
+    if (wait.spin <= 0) wait.spin = OS_SPIN;
     uint32_t *status = reinterpret_cast<uint32_t *>(ws.tiles.p);
     const OsBufs bf{keys, vals, ws.keys.p, ws.vals.p, ws.keys2.p, ws.vals2.p};
     for (int d = 0; d < 4; ++d) {
@@ -520,7 +525,7 @@ void radix_sort_u32_ws_scatter(bgl_ctx *c, SortWorkspace &ws, uint32_t *keys, ui
         os_scatter_kernel<<<(unsigned)nt, OS_THREADS, 0, s>>>(bf, d, d_skip, n, base + 256 * d,
                                                               status + (int64_t)d * 256 * nt, tickets + d, err,
                                                               g ? gxy : nullptr, g ? gmass : nullptr,
-                                                              g ? gpts : nullptr);
+                                                              g ? gpts : nullptr, wait);
         BGL_LAUNCH_CHECK();
     }
     // the sorted keys (and values unless gathered) are back in keys / vals

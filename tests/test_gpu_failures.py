@@ -6,7 +6,13 @@
 * BGL_ENOMEM: the context's allocator is told (bgl_debug_fail_alloc, a host
   hook) to refuse a device allocation partway through a graph build or a
   layout; the call returns BGL_ENOMEM, leaves its host output untouched, and
-  the next call on the same context gives the same layout as before."""
+  the next call on the same context gives the same layout as before.
+* BGL_ETIMEOUT: with BGL_TEST_SORT_STALL=1 in the environment when an FMM
+  plan is made, the first tile of each radix pass withholds its counts and
+  the bounded waits on it give up after 4,096 polls (no wait is endless and
+  every write stays inside the arrays); the evaluation's later kernels
+  return at once, the call reports BGL_ETIMEOUT, and the next call without
+  the switch gives the same result as a fresh context."""
 import numpy as np
 import pytest
 
@@ -81,4 +87,26 @@ def test_refused_allocation_reports_enomem_and_leaves_outputs(ctx):
     g2.components(labels=False)
     assert np.array_equal(g2.layout(p), want)
     g2.destroy()
+    g.destroy()
+
+
+def test_bounded_sort_wait_reports_etimeout(ctx, monkeypatch):
+    import paper_2403_03504_gb300 as bgl
+    n = 30000                                         # several radix tiles of 4,096 keys
+    g = bgl.Graph.from_edges(ctx, n, np.arange(n - 1), np.arange(1, n))
+    g.components(labels=False)
+    x, y = oracle.init_positions(3, np.arange(n))
+    xy = np.stack([x, y], 1).astype(np.float32)
+    p = bgl.params(repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=16)
+    want, wstats = g.fa2_step(0, p, 3, xy)
+    monkeypatch.setenv("BGL_TEST_SORT_STALL", "1")
+    with pytest.raises(bgl.BglError) as e:
+        g.fa2_repulsion(0, p, xy)
+    assert e.value.status == -4
+    with pytest.raises(bgl.BglError) as e:
+        g.fa2_step(0, p, 3, xy)
+    assert e.value.status == -4
+    monkeypatch.delenv("BGL_TEST_SORT_STALL")
+    got, stats = g.fa2_step(0, p, 3, xy)             # the context and the graph still work
+    assert np.array_equal(got, want) and np.array_equal(stats, wstats)
     g.destroy()
