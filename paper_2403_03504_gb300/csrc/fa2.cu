@@ -497,6 +497,31 @@ struct Fa2Run {
     std::vector<int64_t> fmm_comp;
     cudaStream_t side = nullptr;  // attraction + gravity, beside the repulsion
     cudaEvent_t ev_fork = nullptr, ev_fa = nullptr;
+    // A run whose only component is on the FMM path iterates fused: the FMM's
+    // combine pass sums swing and traction and sets s_G, and one kernel moves
+    // the points and makes the next evaluation's root square (no swing/traction
+    // kernel, no bounding-box kernel).  BGL_FUSED_ITERATION=0 turns it off.
+    bool fused = false;
+
+    void enable_fuse(double *d_stats) {
+        if (!fused) {
+            const char *v = std::getenv("BGL_FUSED_ITERATION");
+            if (v && v[0] == '0') return;
+            if (fmm.size() != 1 || n_ex_tiles != 0 || c1 - c0 != 1) return;
+        }
+        FmmFuse fz;
+        fz.fprev = fprev.p;
+        fz.variant = p->swing_variant;
+        fz.tau = p->tau;
+        fz.sg = sg.p;
+        fz.stats = d_stats;
+        fz.iter = iter.p;
+        fz.ks = (float)p->ks;
+        fz.ksmax = (float)p->ksmax;
+        fz.bad = g->ctx->d_flag + 1;
+        fmm_fuse(fmm[0], fz);
+        fused = true;
+    }
 
     Fa2Run(bgl_graph *g_, const bgl_params *p_, float2 *xy_, int64_t qbase_, int64_t c0_, int64_t c1_)
         : g(g_), p(p_), xy(xy_), qbase(qbase_), c0(c0_), c1(c1_) {
@@ -631,6 +656,12 @@ struct Fa2Run {
     // one full iteration (K1..K4)
     void iteration(double *d_stats) {
         cudaStream_t s = g->ctx->stream;
+        if (fused) {
+            // K3 in the FMM's combine pass, K4 with the next root square
+            forces(0);
+            fmm_update_root(fmm[0], xy, qbase, f.p, fprev.p, q0);
+            return;
+        }
         forces(0);
         RedArgs a;
         a.tiles = red_tiles.p;
@@ -723,6 +754,9 @@ static void run_iterations_host(Fa2Run &run, int iters, double *d_stats, const S
     }
     cudaGraphDestroy(graph);
     try {
+        // a fused iteration finds the root square made by the previous one;
+        // the first one's comes from the current positions
+        if (run.fused) fmm_root(run.fmm[0], run.xy, run.qbase);
         for (int k = 0; k < iters; ++k) BGL_CUDA(cudaGraphLaunch(exec, s));
     } catch (...) {
         cudaGraphExecDestroy(exec);
@@ -752,6 +786,7 @@ static void run_iterations(Fa2Run &run, int iters, double *d_stats, const SideWo
     BGL_CUDA(cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), s));
     BGL_CUDA(cudaMemsetAsync(run.iter.p, 0, sizeof(int), s));
     BGL_CUDA(cudaMemsetAsync(run.loop.p, 0, sizeof(int), s));
+    run.enable_fuse(d_stats);
     if (host_loop()) {
         run_iterations_host(run, iters, d_stats, side);
         return;
@@ -828,6 +863,7 @@ static void run_iterations(Fa2Run &run, int iters, double *d_stats, const SideWo
     cudaGraphDestroy(graph);
     count_launches(kernels * iters);
     try {
+        if (run.fused) fmm_root(run.fmm[0], run.xy, run.qbase);
         BGL_CUDA(cudaGraphLaunch(exec, s));
     } catch (...) {
         cudaGraphExecDestroy(exec);

@@ -50,6 +50,7 @@
 
 #include <cstdlib>
 
+#include "fa2_update.cuh"
 #include "fmm.cuh"
 #include "p2p.cuh"
 #include "sort_hist.cuh"
@@ -283,30 +284,23 @@ __device__ int cover(const Tree &T, unsigned epoch, int L, int cx, int cy) {
 
 // ---------------------------------------------------------------- bbox, keys, gather
 
-__global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__restrict__ part, unsigned *counter,
-                            Root *root, int *err, unsigned *epoch, int *tickets, OsHist h) {
+// This evaluation's work tickets, digit counts and sort pass tickets start
+// at zero (block 0 of the kernel that opens the evaluation).
+__device__ __forceinline__ void evaluation_clear(int *tickets, const OsHist &h) {
+    if (blockIdx.x != 0) return;
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) h.hist[i] = 0u;
+    if (threadIdx.x < NTICKETS) tickets[threadIdx.x] = 0;
+    if (threadIdx.x < 4) h.tickets[threadIdx.x] = 0u;
+}
+
+// The bounding box from each thread's (min x, max x, min y, max y): block
+// partials, and the last block to arrive makes the root square of the
+// quadtree (reading 15), resets the arrival counter and advances the epoch.
+// Every thread of the block calls it.
+__device__ void bbox_reduce_root(float mnx, float mxx, float mny, float mxy, float4 *__restrict__ part,
+                                 unsigned *counter, Root *root, int *err, unsigned *epoch) {
     __shared__ float4 wred[32];
     __shared__ bool last;
-    // this evaluation's work tickets, digit counts and sort pass tickets start at zero
-    if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) h.hist[i] = 0u;
-        if (threadIdx.x < NTICKETS) tickets[threadIdx.x] = 0;
-        if (threadIdx.x < 4) h.tickets[threadIdx.x] = 0u;
-    }
-    float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
-        float2 p[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) p[r] = i + r * stride < n ? xy[i + r * stride] : xy[i];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            mnx = fminf(mnx, p[r].x);
-            mxx = fmaxf(mxx, p[r].x);
-            mny = fminf(mny, p[r].y);
-            mxy = fmaxf(mxy, p[r].y);
-        }
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
@@ -379,8 +373,26 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
     *epoch = (*epoch % 0xFFFFFEu) + 1u;   // 1 .. 2^24 - 2; 0 never tags a live key
 }
 
-// Morton keys (KEY_ITEMS per thread) and, in the same pass, the digit
-// histograms of the radix sort that orders them
+__global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__restrict__ part, unsigned *counter,
+                            Root *root, int *err, unsigned *epoch, int *tickets, OsHist h) {
+    evaluation_clear(tickets, h);
+    float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+        float2 p[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) p[r] = i + r * stride < n ? xy[i + r * stride] : xy[i];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            mnx = fminf(mnx, p[r].x);
+            mxx = fmaxf(mxx, p[r].x);
+            mny = fminf(mny, p[r].y);
+            mxy = fmaxf(mxy, p[r].y);
+        }
+    }
+    bbox_reduce_root(mnx, mxx, mny, mxy, part, counter, root, err, epoch);
+}
+
 constexpr int KEY_ITEMS = 16;
 
 __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
@@ -1489,6 +1501,14 @@ struct LeafArgs {
     int *ticket;
     int *heavy, *nheavy;  // leaves whose W list the far_heavy kernel takes, and their count
     int heavy_cap;
+    // fused swing/traction (null fprev: not fused)
+    const float2 *fprev;  // fprev[q - fbase]
+    int variant;
+    double tau;
+    double *sg, *stats;
+    int *iter;
+    double2 *spart;       // per combine block
+    unsigned *scount;     // arrival count of the combine blocks
 };
 
 // Near field: the direct sum over the points of U for every target of a
@@ -1618,13 +1638,107 @@ __global__ void combine_kernel(LeafArgs la, int n) {
     const Tree &T = la.e.T;
     for (int b = o, B = min(T.levoff[NLEV], T.Bmax); b < B; b += gridDim.x * blockDim.x)
         T.bchild[b] = make_int4(-1, -1, -1, -1);
-    if (o >= n) return;
-    const int64_t q = la.q0 + o - la.fbase;
-    const float2 nr = la.f[q];
-    const float2 E = la.ef[o];
-    const float km = la.kr * la.mass[o];
-    const float2 a = la.fa ? la.fa[q] : make_float2(0.f, 0.f);
-    la.f[q] = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
+    float sw = 0.f, tr = 0.f;
+    if (o < n) {
+        const int64_t q = la.q0 + o - la.fbase;
+        const float2 nr = la.f[q];
+        const float2 E = la.ef[o];
+        const float km = la.kr * la.mass[o];
+        const float2 a = la.fa ? la.fa[q] : make_float2(0.f, 0.f);
+        const float2 F = make_float2(fmaf(km, nr.x + E.x, a.x), fmaf(km, nr.y - E.y, a.y));
+        la.f[q] = F;
+        if (la.fprev) fa2_swing_terms(F, la.fprev[q], la.mass[o], la.variant, sw, tr);
+    }
+    if (!la.fprev) return;
+    // swing/traction of the iteration (Section 3.2): FP32 within a warp, FP64
+    // across warps and blocks, blocks summed in order by the last to arrive
+    __shared__ double ws[32], wt[32];
+    __shared__ bool last;
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) {
+        sw += __shfl_xor_sync(0xffffffffu, sw, k);
+        tr += __shfl_xor_sync(0xffffffffu, tr, k);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        ws[warp] = (double)sw;
+        wt[warp] = (double)tr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, u = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s += ws[w];
+            u += wt[w];
+        }
+        la.spart[blockIdx.x] = make_double2(s, u);
+        __threadfence();
+        last = atomicAdd(la.scount, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the last block: thread t sums the partials t, t + blockDim, ... (fixed
+    // order), then the block's sums in warp order
+    double swg = 0.0, trc = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        const double2 v = __ldcg(&la.spart[k]);
+        swg += v.x;
+        trc += v.y;
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) {
+        swg += __shfl_xor_sync(0xffffffffu, swg, k);
+        trc += __shfl_xor_sync(0xffffffffu, trc, k);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        ws[warp] = swg;
+        wt[warp] = trc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        swg = 0.0;
+        trc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            swg += ws[w];
+            trc += wt[w];
+        }
+        const double s_new = fa2_global_speed(swg, trc, *la.sg, la.tau);
+        *la.sg = s_new;
+        if (la.stats) {
+            const int it = *la.iter;
+            la.stats[3 * it] = swg;
+            la.stats[3 * it + 1] = trc;
+            la.stats[3 * it + 2] = s_new;
+        }
+        *la.iter += 1;
+        *la.scount = 0u;
+    }
+}
+
+// Fused update: every point moves by s F (Section 3.2) and F_{t-1} <- F;
+// the new positions give the next evaluation's root square, and block 0
+// clears the next evaluation's tickets and counts (what bbox_kernel does).
+__global__ void update_root_kernel(float2 *xy, const float2 *__restrict__ f, float2 *fprev, int n, const double *sg,
+                                   float ks, float ksmax, int *bad, float4 *__restrict__ part, unsigned *counter,
+                                   Root *root, int *err, unsigned *epoch, int *tickets, OsHist h) {
+    evaluation_clear(tickets, h);
+    const float g = (float)*sg;
+    float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // one point per thread
+    if (i < n) {
+        const float2 F = f[i], P = fprev[i];
+        const float2 p = fa2_move(xy[i], F, P, g, ks, ksmax);
+        if (!isfinite(p.x) || !isfinite(p.y)) *bad = 1;
+        xy[i] = p;
+        fprev[i] = F;
+        mnx = fminf(mnx, p.x);
+        mxx = fmaxf(mxx, p.x);
+        mny = fminf(mny, p.y);
+        mxy = fmaxf(mxy, p.y);
+    }
+    bbox_reduce_root(mnx, mxx, mny, mxy, part, counter, root, err, epoch);
 }
 
 // the tile variant with R targets per lane
@@ -1968,6 +2082,10 @@ static std::vector<uint4> m2l_fragments(int p) {
 struct FmmPlan {
     bgl_graph *g = nullptr;
     OsWait wait;           // bounded waits of the sort: error word, poll limit, test stall
+    bool fused = false;    // fused ForceAtlas2 iteration (fmm_fuse): no bounding-box kernel, swing in combine
+    FmmFuse fz;
+    DevBuf<double2> spart; // swing/traction partial sums of the combine blocks
+    DevBuf<unsigned> scount;
     int64_t c = 0, q0 = 0;
     int n = 0, p = 8, PT = 8, S = 64, Bmax = 1, ntiles = 1, lcap = 1, grid_p = 1;
     float kr = 1.f;
@@ -2034,7 +2152,7 @@ FmmPlan *fmm_create(bgl_graph *g, const bgl_params *p, int64_t c) {
         // list entries: U <= 17 per leaf, V <= 27, W and X <= 8 per box
         pl->lcap = (int)std::min<int64_t>((int64_t)60 * bmax + 64, (int64_t)1 << 30);
         pl->root.reset(A, 1);
-        pl->part.reset(A, 1024);
+        pl->part.reset(A, std::max<int64_t>(1024, nblk(pl->n, 256)));   // bounding-box partials, one per block
         pl->counter.reset(A, 1);
         pl->key.reset(A, n);
         pl->idx.reset(A, n);
@@ -2182,7 +2300,19 @@ static LeafArgs leaf_args(FmmPlan *pl, const ExpArgs &a, float2 *f, int64_t fbas
     la.heavy = pl->heavy.p;
     la.nheavy = pl->tickets.p + 4;
     la.heavy_cap = pl->Bmax;
+    la.fprev = pl->fused ? pl->fz.fprev : nullptr;      // indexed like f
+    la.variant = pl->fz.variant;
+    la.tau = pl->fz.tau;
+    la.sg = pl->fz.sg;
+    la.stats = pl->fz.stats;
+    la.iter = pl->fz.iter;
+    la.spart = pl->spart.p;
+    la.scount = pl->scount.p;
     return la;
+}
+
+static unsigned bbox_blocks(const FmmPlan *pl) {
+    return (unsigned)std::min<int64_t>(2 * pl->g->ctx->num_sms, nblk(pl->n, 256));
 }
 
 // points: bounding box, keys, sort, gather (also clears the tickets and the list pool)
@@ -2193,11 +2323,15 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
     cudaStream_t keep = ctx->stream;
     ctx->stream = s;
     try {
-        // tickets, digit counts and look-back words are zeroed by bbox_kernel and keys_kernel
+        // tickets, digit counts and look-back words are zeroed by bbox_kernel
+        // (by update_root_kernel in a fused iteration, which also made the root)
+        // and keys_kernel
         const OsHist h = radix_sort_u32_ws_begin(ctx, pl->sortws, n, false);
-        bbox_kernel<<<std::min<int64_t>(2 * ctx->num_sms, nblk(n, 256)), 256, 0, s>>>(
-            xl, n, pl->part.p, pl->counter.p, pl->root.p, pl->err.p, pl->epoch.p, pl->tickets.p, h);
-        BGL_LAUNCH_CHECK();
+        if (!pl->fused) {
+            bbox_kernel<<<bbox_blocks(pl), 256, 0, s>>>(xl, n, pl->part.p, pl->counter.p, pl->root.p, pl->err.p,
+                                                       pl->epoch.p, pl->tickets.p, h);
+            BGL_LAUNCH_CHECK();
+        }
         keys_kernel<<<nblk(n, 256 * KEY_ITEMS), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p, h);
         BGL_LAUNCH_CHECK();
         radix_sort_u32_ws_scatter(ctx, pl->sortws, pl->key.p, pl->idx.p, n, xl, ml, pl->pts.p, pl->sortskip.p,
@@ -2456,6 +2590,34 @@ void fmm_profile(FmmPlan *pl, const float2 *xy, int64_t qbase, int reps, double 
     out[15] = fmax > 0.0 ? dmax / fmax : 0.0;
     out[16] = (double)skip_last;
     out[17] = (double)h[6];
+}
+
+void fmm_fuse(FmmPlan *pl, const FmmFuse &fz) {
+    bgl_ctx *ctx = pl->g->ctx;
+    pl->fz = fz;
+    if (!pl->spart.p) {
+        pl->spart.reset(ctx->alloc, nblk(pl->n, 256));
+        pl->scount.reset(ctx->alloc, 1);
+        BGL_CUDA(cudaMemsetAsync(pl->scount.p, 0, sizeof(unsigned), ctx->stream));
+    }
+    pl->fused = true;
+}
+
+void fmm_root(FmmPlan *pl, const float2 *xy, int64_t qbase) {
+    bgl_ctx *ctx = pl->g->ctx;
+    const OsHist h = radix_sort_u32_ws_begin(ctx, pl->sortws, pl->n, false);
+    bbox_kernel<<<bbox_blocks(pl), 256, 0, ctx->stream>>>(xy + (pl->q0 - qbase), pl->n, pl->part.p, pl->counter.p,
+                                                          pl->root.p, pl->err.p, pl->epoch.p, pl->tickets.p, h);
+    BGL_LAUNCH_CHECK();
+}
+
+void fmm_update_root(FmmPlan *pl, float2 *xy, int64_t qbase, const float2 *f, float2 *fprev, int64_t fbase) {
+    bgl_ctx *ctx = pl->g->ctx;
+    const OsHist h = radix_sort_u32_ws_begin(ctx, pl->sortws, pl->n, false);
+    update_root_kernel<<<nblk(pl->n, 256), 256, 0, ctx->stream>>>(
+        xy + (pl->q0 - qbase), f + (pl->q0 - fbase), fprev + (pl->q0 - fbase), pl->n, pl->fz.sg, pl->fz.ks,
+        pl->fz.ksmax, pl->fz.bad, pl->part.p, pl->counter.p, pl->root.p, pl->err.p, pl->epoch.p, pl->tickets.p, h);
+    BGL_LAUNCH_CHECK();
 }
 
 int fmm_sortskip(FmmPlan *pl) {

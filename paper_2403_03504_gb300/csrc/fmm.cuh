@@ -19,6 +19,28 @@ void fmm_destroy(FmmPlan *pl);
 void fmm_repulsion(FmmPlan *pl, const float2 *xy, int64_t qbase, float2 *f, int64_t fbase, const float2 *fa = nullptr,
                    cudaEvent_t fa_ready = nullptr);
 
+// Fused ForceAtlas2 iteration for a run whose only component is this plan's
+// (Section 3.2): the combine pass also sums swing and traction and its last
+// block sets s_G (and the statistics), and fmm_update_root moves the points
+// and makes the next evaluation's root square in the same pass, so the
+// evaluations skip their bounding-box kernel.  Arrays are indexed q - fbase
+// (positions q - qbase) as in fmm_repulsion.
+struct FmmFuse {
+    const float2 *fprev = nullptr;   // F_{t-1}, indexed like f
+    int variant = 0;
+    double tau = 1.0;
+    double *sg = nullptr;            // s_G of the component
+    double *stats = nullptr;         // optional: swing, traction, s_G per iteration
+    int *iter = nullptr;             // iteration counter of the statistics
+    float ks = 0.1f, ksmax = 10.f;
+    int *bad = nullptr;              // set when a position becomes non-finite
+};
+void fmm_fuse(FmmPlan *pl, const FmmFuse &fz);
+// the root square of positions xy (before the first fused evaluation)
+void fmm_root(FmmPlan *pl, const float2 *xy, int64_t qbase);
+// p += s F, F_{t-1} <- F for every point, and the next root square
+void fmm_update_root(FmmPlan *pl, float2 *xy, int64_t qbase, const float2 *f, float2 *fprev, int64_t fbase);
+
 // Counts and per-phase device times of `reps` evaluations (synchronises);
 // out[15]: boxes, leaves, depth, P2P pairs, M2L translations, M2P terms,
 // P2L terms, then milliseconds of: points (bbox, keys, sort, gather), tree,
