@@ -66,12 +66,30 @@ struct KKArgs {
 
 // Distance rows are padded to a multiple of 8 bytes (padding 255).
 __host__ __device__ __forceinline__ int kk_row_stride(int n) { return (n + 7) & ~7; }
-constexpr size_t KK_TABLE_BYTES = 2 * 256 * sizeof(float);
+constexpr size_t KK_TABLE_BYTES = 256 * sizeof(float2);
+
+// Shared memory of one lane group: its distance matrix (or, with the
+// matrices in global memory, one BFS row), then the positions of its
+// component's nodes (float2) and each node's sum of k_mi (float), each part
+// 16-byte aligned.
+struct KkGroupLayout {
+    size_t pos, ksum, bytes;
+};
+__host__ __device__ __forceinline__ KkGroupLayout kk_group_layout(int maxn, bool glob) {
+    const size_t a = 16;
+    const size_t d = glob ? (size_t)kk_row_stride(maxn) : (size_t)maxn * kk_row_stride(maxn);
+    KkGroupLayout L;
+    L.pos = (d + a - 1) / a * a;
+    L.ksum = L.pos + (8 * (size_t)maxn + a - 1) / a * a;
+    L.bytes = L.ksum + (4 * (size_t)maxn + a - 1) / a * a;
+    return L;
+}
 
 // One group of G lanes per component (G = 4, 8, 16 or 32); lane gl owns the
-// nodes gl + j G (j < CPL): their positions live in its registers, and their
-// distances to the current node m are read one step ahead (the next row's
-// loads are in flight during the current step).
+// nodes gl + j G (j < CPL): their distances to the current node m are read
+// one step ahead (the next row's loads are in flight during the current
+// step).  The positions live in the group's shared memory, so node m's is
+// one broadcast load and its move one store.
 template <int G, int CPL>
 __global__ void kk_kernel(KKArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -85,19 +103,19 @@ __global__ void kk_kernel(KKArgs a) {
     const int n = live ? (int)(a.comp_off[c + 1] - q0) : 0;
     const int ds = kk_row_stride(n);                 // row stride of the distance matrix
     const bool glob = a.gdist != nullptr;
-    const int dsm = kk_row_stride(a.maxn);
-    const size_t gbytes = glob ? (size_t)dsm : (size_t)a.maxn * dsm;
-    // per-block table: s_k[d] = d^-2, s_l[d] = l d (0 for d = 0 and d = 255)
-    float *s_k = reinterpret_cast<float *>(smem), *s_l = s_k + 256;
+    const KkGroupLayout gl_ = kk_group_layout(a.maxn, glob);
+    // per-block table: s_kl[d] = (d^-2, l d), zero for d = 0 and d = 255
+    float2 *s_kl = reinterpret_cast<float2 *>(smem);
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const bool ok = i != 0 && i != 255;
-        s_k[i] = ok ? 1.0f / (float)(i * i) : 0.f;
-        s_l[i] = ok ? a.l * (float)i : 0.f;
+        s_kl[i] = ok ? make_float2(1.0f / (float)(i * i), a.l * (float)i) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (c >= a.c0 + a.nc) return;
-    unsigned char *base = smem + KK_TABLE_BYTES + (size_t)grp * ((gbytes + 15) / 16 * 16);
+    unsigned char *base = smem + KK_TABLE_BYTES + (size_t)grp * gl_.bytes;
     uint8_t *dist = glob ? a.gdist + a.gdist_off[c - a.c0] : base;
+    float2 *pos = reinterpret_cast<float2 *>(base + gl_.pos);
+    float *ksum = reinterpret_cast<float *>(base + gl_.ksum);
 
     // 1. BFS from every node (Section 3.1: all-pairs shortest paths, unit weights)
     if (glob) {
@@ -162,29 +180,43 @@ __global__ void kk_kernel(KKArgs a) {
         }
     }
 
-    // 2. positions of the lane's nodes
+    // 2. positions of the component's nodes, and sum_i k_mi of every node m
+    // (constant over the sweeps: the Hessian's diagonal is that sum minus the
+    // position-dependent terms)
     const float scale = a.l * (float)diam * 0.5f;
-    float px[CPL], py[CPL];
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-        const int v = gl + j * G;
-        float2 p = make_float2(0.f, 0.f);
-        if (v < n) {
-            if (a.init) {
-                p = initial_position(a.seed, a.nodes[q0 + v]);
-                p.x *= scale;
-                p.y *= scale;
-            } else {
-                p = a.xy[q0 + v - a.qbase];
-            }
+    for (int v = gl; v < n; v += G) {
+        float2 p;
+        if (a.init) {
+            p = initial_position(a.seed, a.nodes[q0 + v]);
+            p.x *= scale;
+            p.y *= scale;
+        } else {
+            p = a.xy[q0 + v - a.qbase];
         }
-        px[j] = p.x;
-        py[j] = p.y;
+        pos[v] = p;
+        const uint8_t *row = dist + (size_t)(glob ? 0 : v) * ds;
+        float sk = 0.f;
+        if (!glob) {
+            for (int i = 0; i < n; ++i) sk += s_kl[row[i]].x;
+        }
+        ksum[v] = sk;
     }
+    if (glob) {
+        // one row at a time from global memory, the group's lanes over its entries
+        for (int v = 0; v < n; ++v) {
+            const uint8_t *row = dist + (size_t)v * ds;
+            float sk = 0.f;
+            for (int i = gl; i < n; i += G) sk += s_kl[row[i]].x;
+            sk = group_sum<G>(sk, gmask);
+            if (gl == 0) ksum[v] = sk;
+        }
+    }
+    __syncwarp(gmask);
 
     // 3. Gauss-Seidel Newton-Raphson sweeps.  k_mi = d^-2 and l_mi = l d come
     // from the block's table (0 for d = 0: the node itself; and for the 255
-    // padding of a row), so the pair terms need no branch.
+    // padding of a row), and r^2 carries a 1e-30 shift, so the pair terms
+    // need no branch (the node itself adds exactly 0).
     uint8_t dn[CPL];
 #pragma unroll
     for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? dist[gl + j * G] : 255;
@@ -198,62 +230,47 @@ __global__ void kk_kernel(KKArgs a) {
             const uint8_t *nrow = dist + (size_t)(m + 1 < n ? m + 1 : 0) * ds;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? nrow[gl + j * G] : 255;
-            // position of node m from its owner lane
-            const int owner = m % G, slot = m / G;
-            float ox = px[0], oy = py[0];
-#pragma unroll
-            for (int j = 1; j < CPL; ++j)
-                if (slot == j) {
-                    ox = px[j];
-                    oy = py[j];
-                }
-            const int src = (lane / G) * G + owner;
-            const float xm = __shfl_sync(gmask, ox, src), ym = __shfl_sync(gmask, oy, src);
+            const float2 pm = pos[m];
             float gx = 0.f, gy = 0.f, hxx = 0.f, hxy = 0.f, hyy = 0.f;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
                 if (j * G >= n) break;                   // the group's component has no node there
-                const float k = s_k[d[j]], lm = s_l[d[j]];
-                const float dx = xm - px[j], dy = ym - py[j];
-                const float r2 = fmaf(dx, dx, dy * dy);
-                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                const float t = lm * rinv;              // l_mi / r
+                const float2 kl = s_kl[d[j]];
+                const float2 pi = pos[gl + j * G < n ? gl + j * G : 0];
+                const float dx = pm.x - pi.x, dy = pm.y - pi.y;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
+                const float rinv = rsqrtf(r2);
+                const float t = kl.y * rinv;            // l_mi / r
                 const float u = t * rinv * rinv;        // l_mi / r^3
-                const float kdx = k * dx, kdy = k * dy;
-                gx = fmaf(kdx, 1.f - t, gx);
-                gy = fmaf(kdy, 1.f - t, gy);
-                hxx += k - u * kdy * dy;
-                hyy += k - u * kdx * dx;
-                hxy = fmaf(u * kdx, dy, hxy);
+                const float kdx = kl.x * dx, kdy = kl.x * dy;
+                const float omt = 1.f - t;
+                gx = fmaf(kdx, omt, gx);
+                gy = fmaf(kdy, omt, gy);
+                const float ukdx = u * kdx, ukdy = u * kdy;
+                hxx = fmaf(-ukdy, dy, hxx);
+                hyy = fmaf(-ukdx, dx, hyy);
+                hxy = fmaf(ukdx, dy, hxy);
             }
             gx = group_sum<G>(gx, gmask);
             gy = group_sum<G>(gy, gmask);
             hxx = group_sum<G>(hxx, gmask);
             hxy = group_sum<G>(hxy, gmask);
             hyy = group_sum<G>(hyy, gmask);
+            const float km = ksum[m];
             gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
             float dxm, dym;
-            // every lane holds the same sums, so every lane takes the same step
-            if (kk_step(gx, gy, hxx, hxy, hyy, a.l, &dxm, &dym) && gl == owner) {
-#pragma unroll
-                for (int j = 0; j < CPL; ++j)
-                    if (slot == j) {
-                        px[j] = xm + dxm;
-                        py[j] = ym + dym;
-                    }
-            }
+            // every lane holds the same sums and takes the same step; the
+            // node's owner stores the new position
+            if (kk_step(gx, gy, km + hxx, hxy, km + hyy, a.l, &dxm, &dym) && gl == m % G)
+                pos[m] = make_float2(pm.x + dxm, pm.y + dym);
+            __syncwarp(gmask);
         }
         if (a.tol > 0.f && gmax < a.tol) break;
     }
-#pragma unroll
-    for (int j = 0; j < CPL; ++j)
-        if (gl + j * G < n) a.xy[q0 + gl + j * G - a.qbase] = make_float2(px[j], py[j]);
+    for (int v = gl; v < n; v += G) a.xy[q0 + v - a.qbase] = pos[v];
 }
 
-size_t kk_group_bytes(int maxn, bool glob) {
-    const size_t d = glob ? (size_t)kk_row_stride(maxn) : (size_t)maxn * kk_row_stride(maxn);
-    return (d + 15) / 16 * 16;
-}
+size_t kk_group_bytes(int maxn, bool glob) { return kk_group_layout(maxn, glob).bytes; }
 
 // components above this size keep their distance matrix in global memory
 constexpr int KK_SMEM_MAX_N = 64;
