@@ -5,7 +5,9 @@
 // independent chains per thread, timed by clock64() inside the block, so
 // the rates come out per SM clock whatever the clock frequency was:
 //   0  FP32 pipe: fmaf chains                       -> FP32 lanes / clk / SM
-//   1  MUFU: rcp.approx.ftz.f32 chains              -> reciprocals / clk / SM
+//   1  MUFU: chains x <- rcp.approx(x) + 0.5 (the add keeps the chain from
+//      being an involution that the compiler may fold away; it runs on the
+//      FP32 pipe at 1/8 of that pipe's rate)  -> reciprocals / clk / SM
 //   2  the pair itself (p2p_pair: 7 FP32 operations and one reciprocal)
 //      on register-resident sources                 -> pairs / clk / SM
 // The pair rate is the ceiling of the near-field and exact kernels' inner
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(PROBE_THREADS, 1) probe_kernel(int iters, floa
             if (KIND == 0) {
                 a[k] = fmaf(a[k], 0.9999f, 1e-4f);
             } else if (KIND == 1) {
-                a[k] = rcp_approx(a[k]);
+                a[k] = rcp_approx(a[k]) + 0.5f;   // converges to (1 + sqrt(17)) / 4
             } else {
                 // the source follows the chain's own sums, so every pair
                 // depends on the previous one of its chain
