@@ -500,6 +500,7 @@ def main():
     ap.add_argument("--impl", default="bgl", choices=["bgl", "reference"])
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--leaf", type=int, default=64, help="FMM leaf size (points per leaf box at most)")
     ap.add_argument("--exact-iters", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -550,7 +551,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     ctx = bgl.Context(local)
     ctx.set_stream(stream)
-    p = bgl.params(seed=0, fa2_iters=args.iters, repulsion=bgl.REP_AUTO, fmm_p=args.p, leaf_size=64,
+    p = bgl.params(seed=0, fa2_iters=args.iters, repulsion=bgl.REP_AUTO, fmm_p=args.p, leaf_size=args.leaf,
                    kk_max_nodes=50, fmm_min_nodes=8192)
 
     # device-resident inputs
@@ -739,7 +740,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": CONFIG_NAME, "n_tx": tx.n_tx, "seed": 2, "n_nodes": n_nodes,
                    "fa2_nodes": fa2_nodes, "giant_nodes": giant, "kk_components": n_kk, "fa2_iters": args.iters,
-                   "repulsion": "fmm", "fmm_p": args.p, "leaf_size": 64, "kk_max_nodes": 50, "kk_sweeps": 200,
+                   "repulsion": "fmm", "fmm_p": args.p, "leaf_size": args.leaf, "kk_max_nodes": 50, "kk_sweeps": 200,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

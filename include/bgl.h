@@ -434,8 +434,10 @@ bgl_status bgl_fa2_iteration_noalloc(bgl_ctx *ctx, int64_t n, const int64_t *d_o
  * all-pairs repulsion of Section 3.2): out[0] FP32 FMA lanes, out[1] MUFU
  * reciprocals (rcp.approx) and out[2] repulsion pairs (7 FP32 operations and
  * one reciprocal, sources in registers), each per SM per clock from the
- * clock64() counts of one 1,024-thread block per SM; out[3] the SM count.
- * Synchronises the stream. */
+ * clock64() counts of one 1,024-thread block per SM; out[3] the SM count;
+ * out[4] repulsion pairs taken two at a time with packed FP32x2 arithmetic
+ * (7 packed operations and two reciprocals per two pairs).  out holds 5
+ * doubles.  Synchronises the stream. */
 bgl_status bgl_peak_probe(bgl_ctx *ctx, double *out);
 
 /* Number of kernels this process has launched through the library so far

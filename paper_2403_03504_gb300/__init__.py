@@ -251,10 +251,10 @@ class Context:
     def peak_probe(self) -> dict:
         """Measured FP32 lanes, MUFU reciprocals and repulsion pairs per SM
         clock (bgl_peak_probe), and the SM count."""
-        out = np.zeros(4)
+        out = np.zeros(5)
         self.check(self._lib.bgl_peak_probe(self.h, _hp(out)))
         return {"fp32_lanes_per_clk_sm": out[0], "mufu_rcp_per_clk_sm": out[1], "pairs_per_clk_sm": out[2],
-                "sms": int(out[3])}
+                "packed_pairs_per_clk_sm": out[4], "sms": int(out[3])}
 
     def debug_fail_alloc(self, after: int):
         """Test aid: the device allocation after `after` more successful ones

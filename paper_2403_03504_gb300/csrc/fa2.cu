@@ -30,6 +30,11 @@ namespace bgl {
 
 namespace {
 
+// pairs of a thread's targets summed with packed FP32x2 arithmetic in the
+// exact kernel (the rest scalar)
+#ifndef BGL_EXACT_PACKED
+#define BGL_EXACT_PACKED 2
+#endif
 constexpr int EX_THREADS = 256;                // a tile is EX_THREADS x R targets, R = 1, 2 or 4 (autotuned)
 constexpr int EX_STILE = 1024;                 // sources per shared-memory stage
 constexpr int HEAVY_DEG = 128;
@@ -71,11 +76,32 @@ __global__ void __launch_bounds__(EX_THREADS) exact_repulsion_kernel(
         float ax[EX_R], ay[EX_R];
 #pragma unroll
         for (int r = 0; r < EX_R; ++r) ax[r] = ay[r] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < cnt; ++j) {
-            const float4 q = src[j];
+        {
+            // targets 2k, 2k + 1 (k < R2) in packed FP32x2 (negated targets
+            // and sums, bitwise the scalar pair's result), the rest scalar
+            constexpr int R2 = EX_R / 2 < BGL_EXACT_PACKED ? EX_R / 2 : BGL_EXACT_PACKED;
+            float2 nzx[R2 > 0 ? R2 : 1], nzy[R2 > 0 ? R2 : 1], gx[R2 > 0 ? R2 : 1], gy[R2 > 0 ? R2 : 1];
 #pragma unroll
-            for (int r = 0; r < EX_R; ++r) p2p_pair(zx[r], zy[r], q, ax[r], ay[r]);
+            for (int k = 0; k < R2; ++k) {
+                nzx[k] = make_float2(-zx[2 * k], -zx[2 * k + 1]);
+                nzy[k] = make_float2(-zy[2 * k], -zy[2 * k + 1]);
+                gx[k] = gy[k] = make_float2(0.f, 0.f);
+            }
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q = src[j];
+#pragma unroll
+                for (int k = 0; k < R2; ++k) p2p_pair2(nzx[k], nzy[k], q, gx[k], gy[k]);
+#pragma unroll
+                for (int r = 2 * R2; r < EX_R; ++r) p2p_pair(zx[r], zy[r], q, ax[r], ay[r]);
+            }
+#pragma unroll
+            for (int k = 0; k < R2; ++k) {
+                ax[2 * k] = -gx[k].x;
+                ax[2 * k + 1] = -gx[k].y;
+                ay[2 * k] = -gy[k].x;
+                ay[2 * k + 1] = -gy[k].y;
+            }
         }
         // blocked accumulation: each stage's partial sum enters a
         // compensated (Kahan) running total

@@ -73,8 +73,11 @@ constexpr int NTICKETS = 24;
 constexpr int NEAR_BUCKET_COUNTS = 8;
 // Near-field tuning constants (compile-time): target lanes per warp,
 // sources per stage, unroll of the source loop, whether the staging code is
-// shared by the tile variants instead of inlined into each, and whether the
-// leaves are taken in buckets of equal tile shape (filled by the lists kernel).
+// shared by the tile variants instead of inlined into each, whether the
+// leaves are taken in buckets of equal tile shape (filled by the lists kernel),
+// and how many pairs of a lane's targets are summed with packed FP32x2
+// arithmetic (bitwise the same forces; the packed operations run on one of
+// the SM's two FMA pipes, so the rest stay scalar to use the other).
 #ifndef BGL_NEAR_LPS
 #define BGL_NEAR_LPS 8
 #endif
@@ -89,6 +92,9 @@ constexpr int NEAR_BUCKET_COUNTS = 8;
 #endif
 #ifndef BGL_NEAR_BUCKETS
 #define BGL_NEAR_BUCKETS 1
+#endif
+#ifndef BGL_NEAR_PACKED
+#define BGL_NEAR_PACKED 1
 #endif
 constexpr int NEAR_SRC = BGL_NEAR_SRC;
 constexpr int NEAR_WARPS = 1024 / NEAR_SRC;       // 32 KB of stage buffers per block
@@ -1587,6 +1593,18 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
         zy[r] = z.y;
         fx[r] = fy[r] = 0.f;
     }
+#if BGL_NEAR_PACKED
+    // targets 2k, 2k + 1 (k < R2) negated and packed, with their negated
+    // sums; targets from 2 R2 on stay scalar
+    constexpr int R2 = R / 2 < BGL_NEAR_PACKED ? R / 2 : BGL_NEAR_PACKED;
+    float2 nzx[R2 > 0 ? R2 : 1], nzy[R2 > 0 ? R2 : 1], gx[R2 > 0 ? R2 : 1], gy[R2 > 0 ? R2 : 1];
+#pragma unroll
+    for (int k = 0; k < R2; ++k) {
+        nzx[k] = make_float2(-zx[2 * k], -zx[2 * k + 1]);
+        nzy[k] = make_float2(-zy[2 * k], -zy[2 * k + 1]);
+        gx[k] = gy[k] = make_float2(0.f, 0.f);
+    }
+#endif
     int ui = us, off = 0, cur = 0;
     int cnt = stage_chunk(T, buf[0], ui, off, ue, lane);
     while (cnt > 0) {
@@ -1599,13 +1617,29 @@ __device__ __forceinline__ void near_tile(const Tree &T, LeafArgs &la, float4 (*
 #pragma unroll NEAR_UNROLL
         for (int j = 0; j < steps; ++j) {
             const float4 q = src[j * NEAR_SPLIT];
+#if BGL_NEAR_PACKED
+#pragma unroll
+            for (int k = 0; k < R2; ++k) p2p_pair2(nzx[k], nzy[k], q, gx[k], gy[k]);
+#pragma unroll
+            for (int r = 2 * R2; r < R; ++r) p2p_pair(zx[r], zy[r], q, fx[r], fy[r]);
+#else
 #pragma unroll
             for (int r = 0; r < R; ++r) p2p_pair(zx[r], zy[r], q, fx[r], fy[r]);
+#endif
         }
         __syncwarp();
         cur ^= 1;
         cnt = nxt;
     }
+#if BGL_NEAR_PACKED
+#pragma unroll
+    for (int k = 0; k < R2; ++k) {
+        fx[2 * k] = -gx[k].x;
+        fx[2 * k + 1] = -gx[k].y;
+        fy[2 * k] = -gy[k].x;
+        fy[2 * k + 1] = -gy[k].y;
+    }
+#endif
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         float sx = fx[r], sy = fy[r];

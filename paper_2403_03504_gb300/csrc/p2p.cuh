@@ -23,4 +23,20 @@ __device__ __forceinline__ void p2p_pair(float zx, float zy, const float4 &q, fl
     fy = fmaf(w, dy, fy);
 }
 
+// Two targets against one source with the packed FP32x2 instructions of
+// sm_100 and later (one issue slot for two lanes' worth of add, multiply or
+// FMA): 7 packed operations and two reciprocals for two pairs.  The targets
+// come negated (nzx = -zx) and the accumulators hold the negated sums,
+// g += m_j (z_j - z) / (|z_j - z|^2 + 1e-30): each operation is the sign
+// mirror of p2p_pair's (round-to-nearest is symmetric in sign), so -g equals,
+// bit for bit, what p2p_pair accumulates in the same order.
+__device__ __forceinline__ void p2p_pair2(float2 nzx, float2 nzy, const float4 &q, float2 &gx, float2 &gy) {
+    const float2 dx = __fadd2_rn(make_float2(q.x, q.x), nzx);
+    const float2 dy = __fadd2_rn(make_float2(q.y, q.y), nzy);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, make_float2(1e-30f, 1e-30f)));
+    const float2 w = __fmul2_rn(make_float2(q.z, q.z), make_float2(rcp_approx(r2.x), rcp_approx(r2.y)));
+    gx = __ffma2_rn(w, dx, gx);
+    gy = __ffma2_rn(w, dy, gy);
+}
+
 }  // namespace bgl
