@@ -64,6 +64,15 @@ constexpr int NLEV = MAXLEV + 1;
 constexpr int TREE_TILE = 1024;
 constexpr int TREE_THREADS = 256;
 constexpr int BN = 49;                 // binomial table dimension (n <= 48)
+
+// C(n, k) rounded to the nearest float (exact below 2^24), the value the
+// table holds; with compile-time n and k (fully unrolled loops) it folds to
+// an immediate operand
+__host__ __device__ constexpr float binom_f(int n, int k) {
+    unsigned long long v = 1;
+    for (int j = 0; j < k; ++j) v = v * (unsigned long long)(n - j) / (unsigned long long)(j + 1);
+    return (float)v;
+}
 constexpr int SRC_CAP = 2048;          // P2P sources staged per pass
 constexpr int LEAF_THREADS = 128;
 constexpr long long SPIN_LIMIT = 1ll << 24;
@@ -1048,6 +1057,11 @@ __device__ __forceinline__ float2 crcp(float2 a) {
     float d = 1.0f / (a.x * a.x + a.y * a.y);
     return make_float2(a.x * d, -a.y * d);
 }
+// 1 / a with the MUFU reciprocal (about one rounding of error more than crcp)
+__device__ __forceinline__ float2 crcp_fast(float2 a) {
+    const float d = rcp_approx(fmaf(a.x, a.x, a.y * a.y));
+    return make_float2(a.x * d, -a.y * d);
+}
 
 // Warp sum of the 2 (PT + 1) floats of a (real and imaginary parts
 // interleaved, float f = part f & 1 of coefficient f / 2), scattered: on
@@ -1399,9 +1413,6 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
 template <int PT, bool TC>
 __global__ void __launch_bounds__(256, PT == 8 ? 4 : (PT == 12 ? 2 : 1)) m2l_kernel(ExpArgs a) {
     if (aborted(a.T.err)) return;
-    __shared__ float sbin[BN * BN];
-    for (int i = threadIdx.x; i < BN * BN; i += blockDim.x) sbin[i] = a.binom[i];
-    __syncthreads();
     const Tree &T = a.T;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1429,7 +1440,7 @@ __global__ void __launch_bounds__(256, PT == 8 ? 4 : (PT == 12 ? 2 : 1)) m2l_ker
             const int ent = T.lidx[e];
             const int D = ent >> 6, cls = ent & 63;
             const float2 w = make_float2(2.0f * (float)(cls / 7 - 3), 2.0f * (float)(cls % 7 - 3));
-            const float2 iw = crcp(w);
+            const float2 iw = crcp_fast(w);
             const float2 *md = a.M + (size_t)D * (PT + 1);
             const float2 a0 = md[0];
             float2 ap[PT + 1];
@@ -1444,10 +1455,11 @@ __global__ void __launch_bounds__(256, PT == 8 ? 4 : (PT == 12 ? 2 : 1)) m2l_ker
             float2 pl = iw;
 #pragma unroll
             for (int l = 1; l <= PT; ++l) {
-                float2 s = make_float2(-a0.x / (float)l, -a0.y / (float)l);
+                const float nil = -1.0f / (float)l;          // l is a compile-time constant here
+                float2 s = make_float2(a0.x * nil, a0.y * nil);
 #pragma unroll
                 for (int k = 1; k <= PT; ++k) {
-                    const float cb = sbin[(l + k - 1) * BN + (k - 1)];
+                    const float cb = binom_f(l + k - 1, k - 1);
                     s.x = fmaf(cb, ap[k].x, s.x);
                     s.y = fmaf(cb, ap[k].y, s.y);
                 }
@@ -1463,11 +1475,11 @@ __global__ void __launch_bounds__(256, PT == 8 ? 4 : (PT == 12 ? 2 : 1)) m2l_ker
             const int C = T.lidx[e];
             for (int j = T.bstart[C] + lane; j < T.bend[C]; j += 32) {
                 const float4 s = T.pts[j];
-                const float2 t = cscale(crcp(make_float2(s.x - g.cx, s.y - g.cy)), g.r);
+                const float2 t = cscale(crcp_fast(make_float2(s.x - g.cx, s.y - g.cy)), g.r);
                 float2 pw = t;
 #pragma unroll
                 for (int l = 1; l <= PT; ++l) {
-                    const float c = -s.z / (float)l;
+                    const float c = s.z * (-1.0f / (float)l);
                     acc[l].x = fmaf(c, pw.x, acc[l].x);
                     acc[l].y = fmaf(c, pw.y, acc[l].y);
                     pw = cmul(pw, t);
