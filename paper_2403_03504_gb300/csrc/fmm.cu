@@ -408,7 +408,7 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
     bbox_reduce_root(mnx, mxx, mny, mxy, part, counter, root, err, epoch);
 }
 
-constexpr int KEY_ITEMS = 16;
+constexpr int KEY_ITEMS = OS_ITEMS;      // one key block per radix tile
 
 __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
                                                    uint32_t *__restrict__ key, uint32_t *__restrict__ idx, OsHist h) {
@@ -1321,6 +1321,9 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
         const int s = T.bstart[b], e = T.bend[b];
         const int2 mb = T.bmeta[b];
         if (e - s > P2M_MAX && !meta_leaf(mb)) continue;   // filled by M2M below
+        // whether the parent is filled by M2M (loaded ahead of the P2M sum)
+        const int pb0 = T.bparent[b];
+        const bool up0 = pb0 >= 0 && (T.bmeta[pb0].y & 255) >= 2 && T.bend[pb0] - T.bstart[pb0] > P2M_MAX;
         const BoxGeo g = box_geo_xy(rt, mb.x, mb.y & 255);
         const float ir = 1.0f / g.r;
         float2 acc[PT + 1];
@@ -1347,11 +1350,14 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
             if (k <= p) reinterpret_cast<float *>(a.M)[(size_t)b * (PT + 1) * 2 + f] =
                 k > 0 ? tot[c] * (-1.0f / (float)k) : tot[c];
         }
-        __threadfence();
+        // only a box whose parent is filled by M2M publishes its expansion (a
+        // fence, then the parent's arrival count)
         int child = b;
-        for (;;) {
+        for (bool up = up0;;) {
+            if (!up) break;
             const int pb = T.bparent[child];
-            if (pb < 0 || (T.bmeta[pb].y & 255) < 2 || T.bend[pb] - T.bstart[pb] <= P2M_MAX) break;
+            __threadfence();        // every lane's expansion writes, before lane 0's count
+            __syncwarp();
             int last = 0;
             const int4 ch = T.bchild[pb];
             const int cs[4] = {ch.x, ch.y, ch.z, ch.w};
@@ -1397,8 +1403,9 @@ __global__ void __launch_bounds__(256) up_kernel(ExpArgs a) {
                 a.M[(size_t)pb * (PT + 1) + l] = out;
             }
             __syncwarp();
-            __threadfence();
             child = pb;
+            const int gp = T.bparent[child];
+            up = gp >= 0 && (T.bmeta[gp].y & 255) >= 2 && T.bend[gp] - T.bstart[gp] > P2M_MAX;
         }
     }
 }

@@ -6,8 +6,12 @@ namespace bgl {
 
 // Radix tiles: OS_THREADS threads x OS_ITEMS keys.  A caller's histogram
 // kernel (os_block_hist, os_clear_status) runs one block per tile.
+#ifndef BGL_OS_ITEMS
+#define BGL_OS_ITEMS 16
+#endif
 constexpr int OS_THREADS = 256;
-constexpr int OS_ITEMS = 16;
+constexpr int OS_ITEMS = BGL_OS_ITEMS;
+static_assert(OS_ITEMS >= 1 && OS_ITEMS <= 32, "a thread's keys are tracked in a 32-bit mask");
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 
 // Adds the block's keys (key[r] for the bits r of `valid`) to the four 8-bit
