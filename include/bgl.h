@@ -299,6 +299,19 @@ bgl_status bgl_assemble(bgl_graph *g, const bgl_params *p, const float *xy_in, f
  * bgl_server_fetch: copies the result (node_ids[n] resident ids, xy[2n]) and
  *   forgets the request; NULL arrays only forget it.
  * bgl_server_stats: the largest estimated in-flight footprint so far.
+ * bgl_server_batching: from then on, a worker that takes a request also
+ *   takes the requests queued right behind it that have equal parameters
+ *   (field by field), while they number at most max_requests and their
+ *   neighbourhoods at most max_nodes nodes in all, and lays them out with one
+ *   layout: the disjoint union of their subgraphs, in which every node seeds
+ *   its initial position with its local id in its own request.  A k-hop
+ *   neighbourhood is connected, so every request is one component of the
+ *   union and its coordinates are bitwise those it gets alone.  Requests with
+ *   p->assemble = 1 are laid out alone.  max_requests = 1 (the default)
+ *   turns batching off; BGL_EINVAL for max_requests < 1 or max_nodes < 0.
+ * bgl_server_batch_stats: *batches layouts that served more than one
+ *   request so far, and *batched the requests they served (either may be
+ *   NULL).
  * bgl_server_destroy: finishes the queued requests and stops the workers.
  * A request's result does not depend on the other requests in flight.
  */
@@ -311,6 +324,8 @@ bgl_status bgl_server_submit(bgl_server *srv, int64_t seed, int32_t hops, int64_
 bgl_status bgl_server_wait(bgl_server *srv, int64_t id, int64_t *n_nodes, double *times, int64_t *bytes);
 bgl_status bgl_server_fetch(bgl_server *srv, int64_t id, int32_t *node_ids, float *xy);
 bgl_status bgl_server_stats(bgl_server *srv, int64_t *inflight_max_bytes);
+bgl_status bgl_server_batching(bgl_server *srv, int32_t max_requests, int64_t max_nodes);
+bgl_status bgl_server_batch_stats(bgl_server *srv, int64_t *batches, int64_t *batched);
 bgl_status bgl_server_destroy(bgl_server *srv);
 
 /* ------------------------------------------ resumable runs and checkpoints */

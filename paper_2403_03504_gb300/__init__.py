@@ -116,6 +116,8 @@ def _load():
         "bgl_server_wait": ([VP, I64, P64, VP, VP], I32),
         "bgl_server_fetch": ([VP, I64, VP, VP], I32),
         "bgl_server_stats": ([VP, P64], I32),
+        "bgl_server_batching": ([VP, I32, I64], I32),
+        "bgl_server_batch_stats": ([VP, P64, P64], I32),
         "bgl_server_destroy": ([VP], I32),
         "bgl_state_load": ([VP, VP, ctypes.c_size_t], I32),
         "bgl_fmm_stats": ([VP, I64, ctypes.POINTER(Params), VP, I32, VP], I32),
@@ -173,6 +175,19 @@ class Server:
         v = ctypes.c_int64()
         self._lib.bgl_server_stats(self.h, ctypes.byref(v))
         return v.value
+
+    def batching(self, max_requests: int, max_nodes: int):
+        """Queued requests with equal parameters share one layout, up to
+        max_requests of them and max_nodes nodes in all (1: off)."""
+        st = self._lib.bgl_server_batching(self.h, max_requests, max_nodes)
+        if st != 0:
+            raise BglError(st, "bgl_server_batching")
+
+    def batch_stats(self):
+        """(layouts that served several requests, requests they served)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._lib.bgl_server_batch_stats(self.h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
 
     def close(self):
         if self.h:

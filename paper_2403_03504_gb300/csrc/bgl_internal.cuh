@@ -167,6 +167,7 @@ struct bgl_graph {
     bgl::DevBuf<int64_t> coff;          // [n+1] CSR in component order (local = position)
     bgl::DevBuf<int32_t> cadj;          // [2 n_undir]
     bgl::DevBuf<float> mass;            // [n] degree + 1, component order
+    bgl::DevBuf<int32_t> seed_id;       // [n] id seeding each node's initial position (empty: the node id)
     std::vector<int64_t> h_comp_off;    // host copy of comp_off
     // split
     int32_t kk_max = -1;

@@ -23,6 +23,7 @@
 #include <cstring>
 
 #include "bgl_internal.cuh"
+#include "fa2_update.cuh"
 #include "fmm.cuh"
 #include "p2p.cuh"
 
@@ -39,7 +40,7 @@ constexpr int EX_THREADS = 256;                // a tile is EX_THREADS x R targe
 constexpr int EX_STILE = 1024;                 // sources per shared-memory stage
 constexpr int HEAVY_DEG = 128;
 constexpr int HEAVY_CHUNK = 2048;              // adjacency entries per block for high-degree nodes
-constexpr int RED_TILE = 1024;                 // nodes per swing/traction tile (4 per thread)
+constexpr int RED_TILE = 256;                  // nodes per swing/traction tile (one per thread)
 
 struct Tile {
     int32_t comp;      // component index relative to c0
@@ -242,25 +243,16 @@ __global__ void swing_traction_kernel(RedArgs a) {
     __shared__ double ws[32], wt[32];
     __shared__ bool last;
     const Tile t = a.tiles[blockIdx.x];
-    // FP32 within a warp (at most 128 terms: relative error below 1e-6),
-    // FP64 across warps, tiles and components (FP64 issue is scarce on this
-    // part, so it is kept off the per-node path)
+    // FP32 within a warp (32 terms), FP64 across warps, tiles and components
+    // (FP64 issue is scarce on this part, so it is kept off the per-node
+    // path).  The order is the fused FMM iteration's (combine_kernel): tiles
+    // of 256 consecutive nodes of a component, one node per thread, so a
+    // component gets the same s_G whether it is iterated alone or with others.
     float sw = 0.f, tr = 0.f;
-    const int len = (int)(t.t1 - t.t0);
-    const float2 *f = a.f + (t.t0 - a.qbase), *fp = a.fprev + (t.t0 - a.qbase);
-#pragma unroll 4
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        const float2 F = f[i], P = fp[i];
-        const float s = sqrtf((F.x - P.x) * (F.x - P.x) + (F.y - P.y) * (F.y - P.y));
-        const float u = sqrtf((F.x + P.x) * (F.x + P.x) + (F.y + P.y) * (F.y + P.y));
-        if (a.variant == 1) {
-            const float m = a.mass[t.t0 + i];
-            sw = fmaf(m, s, sw);
-            tr = fmaf(0.5f * m, u, tr);
-        } else {
-            sw += s;
-            tr += u;
-        }
+    const int i = threadIdx.x;
+    if (i < (int)(t.t1 - t.t0)) {
+        const int64_t q = t.t0 + i;
+        fa2_swing_terms(a.f[q - a.qbase], a.fprev[q - a.qbase], a.mass[q], a.variant, sw, tr);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -281,25 +273,32 @@ __global__ void swing_traction_kernel(RedArgs a) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the last block: one warp per component, lanes over its tiles, fixed
-    // butterfly order
+    // the last block: one warp per component.  It adds the component's tile
+    // sums in the fused iteration's order: "thread" t (0..255) of eight
+    // virtual warps sums the tiles t, t + 256, ... in order, each virtual
+    // warp's 32 sums go through the same butterfly, and the eight results are
+    // added in warp order (a butterfly leaves the same value in every lane)
     const int nwarps = (int)(blockDim.x >> 5);
     for (int c = warp; c < a.ncomp; c += nwarps) {
+        const int64_t k0 = a.tile_off[c], nk = a.tile_off[c + 1] - k0;
         double swg = 0.0, trc = 0.0;
-        for (int64_t k = a.tile_off[c] + lane; k < a.tile_off[c + 1]; k += 32) {
-            const double2 v = __ldcg(&a.partial[k]);   // written by other blocks: bypass L1
-            swg += v.x;
-            trc += v.y;
-        }
+        for (int w = 0; w < RED_TILE / 32; ++w) {
+            double s = 0.0, u = 0.0;
+            for (int64_t k = 32 * w + lane; k < nk; k += RED_TILE) {
+                const double2 v = __ldcg(&a.partial[k0 + k]);   // written by other blocks: bypass L1
+                s += v.x;
+                u += v.y;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            swg += __shfl_xor_sync(0xffffffffu, swg, o);
-            trc += __shfl_xor_sync(0xffffffffu, trc, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                u += __shfl_xor_sync(0xffffffffu, u, o);
+            }
+            swg += s;
+            trc += u;
         }
         if (lane == 0) {
-            double g = a.sg[c];
-            double s_new = swg > 0.0 ? a.tau * trc / swg : 1.5 * g;
-            if (s_new > 1.5 * g) s_new = 1.5 * g;
+            const double s_new = fa2_global_speed(swg, trc, a.sg[c], a.tau);
             a.sg[c] = s_new;
             if (c == 0 && a.stats) {
                 int it = *a.iter;
@@ -322,15 +321,8 @@ __global__ void update_kernel(const float2 *__restrict__ f, float2 *__restrict__
                               int64_t q1, int64_t qbase, int64_t c0, float ks, float ksmax, int *bad) {
     int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= q1) return;
-    float2 F = f[q - qbase], P = fprev[q - qbase];
-    float g = (float)sg[node_comp[q] - c0];
-    float sw = sqrtf((F.x - P.x) * (F.x - P.x) + (F.y - P.y) * (F.y - P.y));
-    float s = ks * g / (1.f + g * sqrtf(sw));
-    float fn = sqrtf(F.x * F.x + F.y * F.y);
-    if (fn > 0.f && s > ksmax / fn) s = ksmax / fn;
-    float2 p = xy[q - qbase];
-    p.x += s * F.x;
-    p.y += s * F.y;
+    const float2 F = f[q - qbase], P = fprev[q - qbase];
+    const float2 p = fa2_move(xy[q - qbase], F, P, (float)sg[node_comp[q] - c0], ks, ksmax);
     if (!isfinite(p.x) || !isfinite(p.y)) *bad = 1;
     xy[q - qbase] = p;
     fprev[q - qbase] = F;

@@ -30,11 +30,15 @@ namespace bgl {
 
 namespace {
 
-__global__ void init_positions_kernel(const int32_t *__restrict__ nodes, int64_t q0, int64_t q1, int64_t qbase,
-                                      uint64_t seed, float2 *__restrict__ xy) {
+// the id that seeds node v's initial position: v, or sid[v] for a graph that
+// carries its own (a union of subgraphs, each keeping its own ids)
+__device__ __forceinline__ int32_t seed_id_of(const int32_t *__restrict__ sid, int32_t v) { return sid ? sid[v] : v; }
+
+__global__ void init_positions_kernel(const int32_t *__restrict__ nodes, const int32_t *__restrict__ sid, int64_t q0,
+                                      int64_t q1, int64_t qbase, uint64_t seed, float2 *__restrict__ xy) {
     int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= q1) return;
-    xy[q - qbase] = initial_position(seed, nodes[q]);
+    xy[q - qbase] = initial_position(seed, seed_id_of(sid, nodes[q]));
 }
 
 template <int G>
@@ -49,6 +53,7 @@ struct KKArgs {
     const int64_t *coff;
     const int32_t *cadj;
     const int32_t *nodes;
+    const int32_t *sid;    // seed ids of the nodes (null: the node ids)
     float2 *xy;            // indexed by q - qbase
     int64_t qbase;
     int64_t c0, nc;        // components [c0, c0 + nc)
@@ -187,7 +192,7 @@ __global__ void kk_kernel(KKArgs a) {
     for (int v = gl; v < n; v += G) {
         float2 p;
         if (a.init) {
-            p = initial_position(a.seed, a.nodes[q0 + v]);
+            p = initial_position(a.seed, seed_id_of(a.sid, a.nodes[q0 + v]));
             p.x *= scale;
             p.y *= scale;
         } else {
@@ -280,8 +285,8 @@ constexpr int KK_SMEM_MAX_N = 64;
 void init_positions(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t q0, int64_t q1) {
     if (q1 <= q0) return;
     int64_t n = q1 - q0;
-    init_positions_kernel<<<(unsigned)((n + 255) / 256), 256, 0, g->ctx->stream>>>(g->nodes.p, q0, q1, q0, p->seed,
-                                                                                   xy);
+    init_positions_kernel<<<(unsigned)((n + 255) / 256), 256, 0, g->ctx->stream>>>(g->nodes.p, g->seed_id.p, q0, q1,
+                                                                                   q0, p->seed, xy);
     BGL_LAUNCH_CHECK();
 }
 
@@ -347,6 +352,7 @@ static void kk_enqueue_class(const KkRun &run, const KkClass &k, const bgl_param
     a.coff = g->coff.p;
     a.cadj = g->cadj.p;
     a.nodes = g->nodes.p;
+    a.sid = g->seed_id.p;
     a.xy = xy;
     a.qbase = qbase;
     a.c0 = k.c0;

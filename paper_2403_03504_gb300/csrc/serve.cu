@@ -26,6 +26,8 @@
 #include <memory>
 #include <thread>
 
+#include <atomic>
+
 #include "bgl_internal.cuh"
 
 namespace bgl {
@@ -35,6 +37,19 @@ namespace {
 constexpr int KH_TPB = 256;
 
 inline unsigned kh_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + KH_TPB - 1) / KH_TPB); }
+
+// dst[i] = src[i] + add, i < count (a request's edges in the batch's numbering)
+__global__ void kh_offset_copy_kernel(const int32_t *__restrict__ src, int32_t *__restrict__ dst, int64_t count,
+                                      int32_t add) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = src[i] + add;
+}
+
+// dst[i] = i, i < count (a request's local ids, seeding its initial positions)
+__global__ void kh_iota_kernel(int32_t *__restrict__ dst, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = (int32_t)i;
+}
 
 __global__ void kh_seed_kernel(int32_t *stamp, int32_t *vis, int32_t seed, int32_t epoch) {
     stamp[seed] = epoch;
@@ -214,11 +229,16 @@ struct ServeRequest {
 struct Server {
     bgl_graph *R = nullptr;
     int64_t budget = 0;
+    // batching: up to batch_max queued requests with equal parameters whose
+    // neighbourhoods total at most batch_nodes nodes share one layout
+    std::atomic<int> batch_max{1};
+    std::atomic<int64_t> batch_nodes{0};
     std::mutex mu;
     std::condition_variable cv_work, cv_mem, cv_done;
     std::deque<int64_t> queue;
     std::map<int64_t, std::unique_ptr<ServeRequest>> reqs;
     int64_t next_id = 1, inflight = 0, inflight_max = 0;
+    int64_t batches = 0, batched = 0;     // layouts of more than one request, and their requests
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<bgl_ctx *> ctxs;
@@ -229,11 +249,46 @@ static double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-static void serve_one(Server *S, bgl_ctx *ctx, KhopScratch &ws, ServeRequest *r) {
+static bool params_equal(const bgl_params &a, const bgl_params &b) {
+    return a.seed == b.seed && a.kk_max_nodes == b.kk_max_nodes && a.fa2_iters == b.fa2_iters && a.kr == b.kr &&
+           a.kg == b.kg && a.ks == b.ks && a.ksmax == b.ksmax && a.tau == b.tau && a.repulsion == b.repulsion &&
+           a.fmm_p == b.fmm_p && a.leaf_size == b.leaf_size && a.fmm_min_nodes == b.fmm_min_nodes &&
+           a.swing_variant == b.swing_variant && a.kk_sweeps == b.kk_sweeps && a.kk_l == b.kk_l &&
+           a.kk_tol == b.kk_tol && a.assemble == b.assemble && a.m2l_bf16 == b.m2l_bf16;
+}
+
+// A request's neighbourhood: node ids on the host (ascending), induced edges
+// in local ids on the device
+struct Extracted {
+    ServeRequest *r = nullptr;
+    int64_t n = 0, m = 0;
     DevBuf<int32_t> u, v;
-    int64_t m = 0;
-    const int64_t n = khop_extract(ctx, S->R, ws, r->seed, r->hops, r->cap, u, v, m);
-    if (n < 0) fail(BGL_EINVAL, "neighbourhood larger than max_nodes");
+};
+
+static void extract(Server *S, bgl_ctx *ctx, KhopScratch &ws, Extracted &x) {
+    ServeRequest *r = x.r;
+    x.n = khop_extract(ctx, S->R, ws, r->seed, r->hops, r->cap, x.u, x.v, x.m);
+    if (x.n < 0) fail(BGL_EINVAL, "neighbourhood larger than max_nodes");
+    r->nodes.resize(x.n);
+    // the visit list is the next extraction's scratch: copy it out now
+    BGL_CUDA(cudaMemcpyAsync(r->nodes.data(), ws.vis.p, sizeof(int32_t) * x.n, cudaMemcpyDeviceToHost, ctx->stream));
+    BGL_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+// Lays out one or several extracted neighbourhoods with one bgl_layout.
+// Several go in as one graph, the disjoint union of the requests' subgraphs
+// (request k's nodes numbered from the sum of the earlier sizes), whose
+// nodes keep their own local ids as the ids that seed their initial
+// positions.  A k-hop neighbourhood is connected, so each request is one
+// component of the union, and a component's layout depends only on its
+// seed ids, adjacency and the parameters: every request's coordinates are
+// bitwise those of its own layout.
+static void layout_group(Server *S, bgl_ctx *ctx, std::vector<Extracted> &grp) {
+    int64_t n = 0, m = 0;
+    for (auto &x : grp) {
+        n += x.n;
+        m += x.m;
+    }
     const int64_t fp = serve_footprint(n, m);
     {
         std::unique_lock<std::mutex> lk(S->mu);
@@ -241,25 +296,53 @@ static void serve_one(Server *S, bgl_ctx *ctx, KhopScratch &ws, ServeRequest *r)
         S->inflight += fp;
         S->inflight_max = std::max(S->inflight_max, S->inflight);
     }
-    r->footprint = fp;
-    r->t_admit = now_s();
+    const double t_admit = now_s();
+    for (auto &x : grp) {
+        x.r->footprint = fp;
+        x.r->t_admit = t_admit;
+    }
     ctx->alloc->reset_peak();
     const size_t live0 = ctx->alloc->live_bytes();
+    cudaStream_t s = ctx->stream;
     try {
         std::unique_ptr<bgl_graph> sub(new bgl_graph());
         sub->ctx = ctx;
-        graph_from_edges_device(sub.get(), n, m, u.p, v.p);
-        u.release();
-        v.release();
+        if (grp.size() == 1) {
+            graph_from_edges_device(sub.get(), n, m, grp[0].u.p, grp[0].v.p);
+        } else {
+            DevBuf<int32_t> u(ctx->alloc, std::max<int64_t>(m, 1)), v(ctx->alloc, std::max<int64_t>(m, 1));
+            sub->seed_id.reset(ctx->alloc, std::max<int64_t>(n, 1));
+            int64_t no = 0, mo = 0;
+            for (auto &x : grp) {
+                if (x.m > 0) {
+                    kh_offset_copy_kernel<<<kh_blocks(x.m), KH_TPB, 0, s>>>(x.u.p, u.p + mo, x.m, (int32_t)no);
+                    BGL_LAUNCH_CHECK();
+                    kh_offset_copy_kernel<<<kh_blocks(x.m), KH_TPB, 0, s>>>(x.v.p, v.p + mo, x.m, (int32_t)no);
+                    BGL_LAUNCH_CHECK();
+                }
+                kh_iota_kernel<<<kh_blocks(x.n), KH_TPB, 0, s>>>(sub->seed_id.p + no, x.n);
+                BGL_LAUNCH_CHECK();
+                no += x.n;
+                mo += x.m;
+            }
+            graph_from_edges_device(sub.get(), n, m, u.p, v.p);
+        }
+        for (auto &x : grp) {
+            x.u.release();
+            x.v.release();
+        }
         components_device(sub.get());
         DevBuf<float2> xy(ctx->alloc, std::max<int64_t>(n, 1));
-        layout_device(sub.get(), &r->p, reinterpret_cast<float *>(xy.p));
-        r->nodes.resize(n);
-        r->xy.resize(2 * n);
-        BGL_CUDA(cudaMemcpyAsync(r->nodes.data(), ws.vis.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
-        BGL_CUDA(cudaMemcpyAsync(r->xy.data(), xy.p, sizeof(float2) * n, cudaMemcpyDeviceToHost, ctx->stream));
-        BGL_CUDA(cudaStreamSynchronize(ctx->stream));
-        r->peak = (int64_t)(ctx->alloc->peak_bytes() - std::min(live0, ctx->alloc->peak_bytes()));
+        layout_device(sub.get(), &grp[0].r->p, reinterpret_cast<float *>(xy.p));
+        int64_t no = 0;
+        for (auto &x : grp) {
+            x.r->xy.resize(2 * x.n);
+            BGL_CUDA(cudaMemcpyAsync(x.r->xy.data(), xy.p + no, sizeof(float2) * x.n, cudaMemcpyDeviceToHost, s));
+            no += x.n;
+        }
+        BGL_CUDA(cudaStreamSynchronize(s));
+        const int64_t peak = (int64_t)(ctx->alloc->peak_bytes() - std::min(live0, ctx->alloc->peak_bytes()));
+        for (auto &x : grp) x.r->peak = peak;
     } catch (...) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->inflight -= fp;
@@ -268,39 +351,105 @@ static void serve_one(Server *S, bgl_ctx *ctx, KhopScratch &ws, ServeRequest *r)
     }
     std::lock_guard<std::mutex> lk(S->mu);
     S->inflight -= fp;
+    if (grp.size() > 1) {
+        ++S->batches;
+        S->batched += (int64_t)grp.size();
+    }
     S->cv_mem.notify_all();
+}
+
+static void finish(Server *S, ServeRequest *r, bgl_status st, const std::string &msg) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->status = st;
+    r->error = msg;
+    r->t_done = now_s();
+    r->done = true;
+    S->cv_done.notify_all();
+}
+
+// runs f, returning its failure as a status and message
+template <class F>
+static bgl_status guarded(F &&f, std::string &msg) {
+    try {
+        f();
+        return BGL_OK;
+    } catch (const Error &e) {
+        msg = e.what();
+        return e.status;
+    } catch (const std::exception &e) {
+        msg = e.what();
+        return BGL_ECUDA;
+    }
+}
+
+static void serve_group(Server *S, bgl_ctx *ctx, std::vector<Extracted> &grp) {
+    std::string msg;
+    const bgl_status st = guarded([&] { layout_group(S, ctx, grp); }, msg);
+    for (auto &x : grp) finish(S, x.r, st, msg);
+}
+
+// whether a request of n nodes may share a layout: its parameters lay out
+// every request alone (no assembly into one frame) and it is small
+static bool batchable(const Server *S, const ServeRequest *r, int64_t n) {
+    return S->batch_max > 1 && r->p.assemble == 0 && n <= S->batch_nodes;
 }
 
 static void worker_loop(Server *S, bgl_ctx *ctx) {
     cudaSetDevice(ctx->device);
     KhopScratch ws;
+    auto next = [&](const ServeRequest *like) -> ServeRequest * {
+        // the request at the head of the queue (any, or with like's parameters)
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (!like) S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+        if (S->queue.empty()) return nullptr;
+        ServeRequest *r = S->reqs[S->queue.front()].get();
+        if (like && !params_equal(r->p, like->p)) return nullptr;
+        S->queue.pop_front();
+        return r;
+    };
     for (;;) {
-        ServeRequest *r = nullptr;
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+        ServeRequest *r0 = next(nullptr);
+        if (!r0) {
+            std::lock_guard<std::mutex> lk(S->mu);
             if (S->stop && S->queue.empty()) return;
-            const int64_t id = S->queue.front();
-            S->queue.pop_front();
-            r = S->reqs[id].get();
+            continue;
         }
-        bgl_status st = BGL_OK;
+        std::vector<Extracted> grp(1);
+        grp[0].r = r0;
         std::string msg;
-        try {
-            serve_one(S, ctx, ws, r);
-        } catch (const Error &e) {
-            st = e.status;
-            msg = e.what();
-        } catch (const std::exception &e) {
-            st = BGL_ECUDA;
-            msg = e.what();
+        bgl_status st = guarded([&] { extract(S, ctx, ws, grp[0]); }, msg);
+        if (st != BGL_OK) {
+            finish(S, r0, st, msg);
+            continue;
         }
-        std::lock_guard<std::mutex> lk(S->mu);
-        r->status = st;
-        r->error = msg;
-        r->t_done = now_s();
-        r->done = true;
-        S->cv_done.notify_all();
+        // small requests queued behind it with the same parameters join it
+        std::vector<Extracted> rest;
+        if (batchable(S, r0, grp[0].n)) {
+            int64_t total = grp[0].n;
+            while ((int)grp.size() < S->batch_max) {
+                ServeRequest *r = next(r0);
+                if (!r) break;
+                Extracted x;
+                x.r = r;
+                st = guarded([&] { extract(S, ctx, ws, x); }, msg);
+                if (st != BGL_OK) {
+                    finish(S, r, st, msg);
+                    continue;
+                }
+                if (!batchable(S, r, x.n) || total + x.n > S->batch_nodes) {
+                    rest.push_back(std::move(x));       // laid out on its own, next
+                    break;
+                }
+                total += x.n;
+                grp.push_back(std::move(x));
+            }
+        }
+        serve_group(S, ctx, grp);
+        for (auto &x : rest) {
+            std::vector<Extracted> one;
+            one.push_back(std::move(x));
+            serve_group(S, ctx, one);
+        }
     }
 }
 
@@ -397,6 +546,21 @@ bgl_status bgl_server_fetch(bgl_server *srv, int64_t id, int32_t *node_ids, floa
     }
     srv->s.reqs.erase(it);
     return st;
+}
+
+bgl_status bgl_server_batching(bgl_server *srv, int32_t max_requests, int64_t max_nodes) {
+    if (!srv || max_requests < 1 || max_nodes < 0) return BGL_EINVAL;
+    srv->s.batch_nodes = max_nodes;
+    srv->s.batch_max = max_requests;
+    return BGL_OK;
+}
+
+bgl_status bgl_server_batch_stats(bgl_server *srv, int64_t *batches, int64_t *batched) {
+    if (!srv) return BGL_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->s.mu);
+    if (batches) *batches = srv->s.batches;
+    if (batched) *batched = srv->s.batched;
+    return BGL_OK;
 }
 
 bgl_status bgl_server_stats(bgl_server *srv, int64_t *inflight_max_bytes) {

@@ -180,3 +180,30 @@ def test_measured_crossover_picks_exact_or_fmm_per_component(ctx):
         else:
             assert is_exact or is_fmm, (c, n)
     g.destroy()
+
+
+def test_fused_iteration_is_bitwise_the_unfused_one(ctx, monkeypatch):
+    """A run whose only component is on the FMM iterates fused (swing and
+    traction sums and s_G in the combine pass, the next root square in the
+    update); the unfused iteration, taken when a run has several components,
+    sums in the same order, so a component's layout does not depend on what
+    shares its run (sharding and batched serving rely on it)."""
+    bgl = _bgl()
+    tx = synth.tx_lists(n_tx=3000, seed=11)
+    g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
+    g.components(labels=False)
+    coff, _, nodes = g.component_nodes()
+    vs = nodes[coff[0]:coff[1]]
+    x, y = oracle.init_positions(4, vs)
+    xy0 = np.stack([x, y], 1).astype(np.float32)
+    for variant in (0, 1):
+        p = bgl.params(seed=4, fa2_iters=60, repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=64, kk_max_nodes=50,
+                       swing_variant=variant)
+        fused = g.layout(p)
+        fxy, fstats = g.fa2_step(0, p, 40, xy0)
+        monkeypatch.setenv("BGL_FUSED_ITERATION", "0")
+        assert np.array_equal(fused, g.layout(p)), variant
+        uxy, ustats = g.fa2_step(0, p, 40, xy0)
+        assert np.array_equal(fxy, uxy) and np.array_equal(fstats, ustats), variant
+        monkeypatch.delenv("BGL_FUSED_ITERATION")
+    g.destroy()

@@ -121,3 +121,56 @@ def test_admission_by_footprint(ctx, c1):
     assert srv.wait(bad)[0] == EINVAL
     assert srv.wait(ok)[0] == 0
     srv.close()
+
+
+def _direct(ctx, g, seed, hops, p):
+    bgl = _bgl()
+    nodes, u, v = g.khop(seed, hops, 1 << 30)
+    sub = bgl.Graph.from_edges(ctx, len(nodes), u, v)
+    sub.components(labels=False)
+    xy = sub.layout(p)
+    sub.destroy()
+    return nodes, xy
+
+
+def test_batched_requests_are_bitwise_their_own_layouts(ctx, c1):
+    """With batching on and one slot, the requests queued behind the one in
+    progress with equal parameters share one layout (the disjoint union of
+    their neighbourhoods); each result equals the direct layout of its own
+    neighbourhood bit for bit: KK-sized, exact and FMM ForceAtlas2
+    neighbourhoods, two parameter sets in runs (only equal neighbours join),
+    an assembled request (laid out alone) and an oversize one (fails alone)."""
+    bgl = _bgl()
+    g, og = c1
+    deg = np.diff(og.off)
+    rng = np.random.default_rng(8)
+    seeds = [int(s) for s in rng.choice(og.n_nodes, 24, replace=False)]
+    p_ex = bgl.params(fa2_iters=30, kk_max_nodes=20, repulsion=bgl.REP_EXACT)
+    p_fmm = bgl.params(fa2_iters=30, kk_max_nodes=20, repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=16)
+    p_asm = bgl.params(fa2_iters=30, kk_max_nodes=20, assemble=1)
+    hub = int(np.argmax(deg))
+    reqs = [(hub, 3, p_ex)]                          # keeps the worker busy while the rest queue
+    for i, s in enumerate(seeds):
+        reqs.append((s, 1 + i % 3, p_ex if (i // 5) % 2 == 0 else p_fmm))
+    reqs.append((seeds[0], 2, p_asm))
+    srv = bgl.Server(g, slots=1, hbm_budget=8 << 30)
+    srv.batching(8, 1 << 20)
+    ids = [srv.submit(s, k, p) for s, k, p in reqs]
+    bad = srv.submit(hub, 3, p_ex, max_nodes=3)
+    sizes = []
+    for (s, k, p), rid in zip(reqs, ids):
+        st, n, t, b = srv.wait(rid)
+        assert st == 0, (s, k)
+        gids, gxy = srv.fetch(rid, n)
+        nodes, xy = _direct(ctx, g, s, k, p)
+        assert np.array_equal(gids, nodes) and np.array_equal(gxy, xy), (s, k, n)
+        sizes.append(n)
+    assert srv.wait(bad)[0] == EINVAL
+    batches, batched = srv.batch_stats()
+    assert batches >= 2 and batched >= 8, (batches, batched)
+    assert max(sizes) > 20 and min(sizes) <= 20          # both KK and ForceAtlas2 requests
+    srv.close()
+    srv = bgl.Server(g, slots=1)
+    with pytest.raises(bgl.BglError):
+        srv.batching(0, 10)
+    srv.close()
