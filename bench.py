@@ -51,6 +51,9 @@ CONFIG_NAME = "fmm-fa2-200k-tx"
 # The SM count is read from the device, the clock from nvidia-smi.
 PAIRS_PER_CLK = 16.0
 NEAR_PROFILE = os.path.join(ROOT, "profiles", "near_kernel_fmm_c2_giant.md")
+# serving: queued requests with equal parameters share a layout, up to 16 of
+# them and 262,144 nodes in all
+SERVE_BATCH = (16, 1 << 18)
 NEAR_SOURCES = ("fmm.cu", "fmm.cuh", "p2p.cuh")
 
 
@@ -96,12 +99,13 @@ def reduce_units_time(dist, units: float, seconds: float, device=None):
 
 
 def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, slots=4, budget=120 << 30,
-                  repulsion=None):
+                  repulsion=None, batch=None):
     """Poisson arrivals (rate per second) of k-hop layout requests (k uniform
     in 1..4, seeds uniform over the graph's address nodes, redrawn until the
-    neighbourhood has min_nodes..max_nodes nodes) served by a bgl Server;
-    returns latency percentiles (arrival -> coordinates on the host),
-    throughput and sizes."""
+    neighbourhood has min_nodes..max_nodes nodes) served by a bgl Server
+    (batch = (requests, nodes): queued requests share layouts up to those
+    totals; None: one request per layout); returns latency percentiles
+    (arrival -> coordinates on the host), throughput and sizes."""
     import ctypes
     lib = bgl._load()
     rng = np.random.default_rng(seed)
@@ -118,6 +122,8 @@ def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, s
     rep = bgl.REP_FMM if repulsion is None else repulsion
     p = bgl.params(seed=0, fa2_iters=iters, repulsion=rep, fmm_p=8, leaf_size=64, kk_max_nodes=50)
     srv = bgl.Server(g, slots=slots, hbm_budget=budget)
+    if batch:
+        srv.batching(*batch)
     t0 = time.perf_counter()
     arrive = t0 + np.cumsum(gaps)
     ids = []
@@ -138,6 +144,7 @@ def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, s
         fps.append(int(b[0]))
         peaks.append(int(b[1]))
     inflight = srv.inflight_max()
+    batches, batched = srv.batch_stats()
     srv.close()
     lat_ms = 1e3 * np.array(lat)
     wall = max(done) - min(sub)            # the server's steady clock
@@ -150,7 +157,9 @@ def serve_session(bgl, g, n_requests, rate, seed, iters, min_nodes, max_nodes, s
         "latency_ms_max": float(lat_ms.max()), "layouts_per_s": n_requests / wall,
         "node_updates_per_s": float(nodes.sum()) * iters / wall, "slots": slots, "hbm_budget_bytes": int(budget),
         "inflight_footprint_max_bytes": int(inflight), "peak_over_estimate_max": float(max(
-            pk / fp for pk, fp in zip(peaks, fps)))}
+            pk / fp for pk, fp in zip(peaks, fps))),
+        "batching": {"max_requests": batch[0], "max_nodes": batch[1], "shared_layouts": batches,
+                     "requests_in_shared_layouts": batched} if batch else None}
 
 
 def run_serve(args, rank, world, dist, local):
@@ -163,7 +172,8 @@ def run_serve(args, rank, world, dist, local):
     ctx = bgl.Context(local)
     g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
     n = args.requests or 100
-    out = serve_session(bgl, g, n, 50.0, 5, 300, 100, 2_000_000, slots=args.slots)
+    out = serve_session(bgl, g, n, 50.0, 5, 300, 100, 2_000_000, slots=args.slots,
+                        batch=SERVE_BATCH if args.batch else None)
     if rank == 0:
         print(json.dumps({"metric": "served k-hop layouts: latency (arrival -> coordinates on the host)",
                           "value": out["latency_ms_p99"], "unit": "ms (p99)", "higher_is_better": False,
@@ -511,6 +521,7 @@ def main():
                          "precision: FP32 against BF16 M2L on the 3M-transaction graph's giant component")
     ap.add_argument("--requests", type=int, default=0, help="serving requests (0: 40 in the c2 line, 100 for serve)")
     ap.add_argument("--slots", type=int, default=4, help="serving workers")
+    ap.add_argument("--batch", type=int, default=1, help="serving: 1 batches queued requests (SERVE_BATCH), 0 does not")
     ap.add_argument("--timed-only", action="store_true",
                     help="profiling case: warm-up and timed steps only (no end-to-end leg, no diagnostics); "
                          "prints the device-resident step times")
@@ -713,9 +724,12 @@ def main():
     # served layouts of k-hop neighbourhoods of this graph (latency)
     serving = serve_session(bgl, g0, args.requests or 40, 50.0, 2, 300, 100, 2_000_000, slots=4, budget=64 << 30)
     # the same requests, up to 60k nodes each, with FMM and with exact repulsion
+    # the same 40 requests served with FMM and with exact repulsion, with
+    # batching on (it takes the exact ones), and exact one request per layout
     serving_vs_exact = {name: serve_session(bgl, g0, args.requests or 40, 50.0, 3, 300, 100, 60_000, slots=4,
-                                            budget=64 << 30, repulsion=rep)
-                        for name, rep in (("fmm", bgl.REP_FMM), ("exact", bgl.REP_EXACT))}
+                                            budget=64 << 30, repulsion=rep, batch=bt)
+                        for name, rep, bt in (("fmm", bgl.REP_FMM, SERVE_BATCH), ("exact", bgl.REP_EXACT, SERVE_BATCH),
+                                              ("exact_unbatched", bgl.REP_EXACT, None))}
 
     clocks = clk.summary()
     # the batched-components workload (10^5 KK + 2,000 ForceAtlas2 components), two steps

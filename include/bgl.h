@@ -306,8 +306,12 @@ bgl_status bgl_assemble(bgl_graph *g, const bgl_params *p, const float *xy_in, f
  *   layout: the disjoint union of their subgraphs, in which every node seeds
  *   its initial position with its local id in its own request.  A k-hop
  *   neighbourhood is connected, so every request is one component of the
- *   union and its coordinates are bitwise those it gets alone.  Requests with
- *   p->assemble = 1 are laid out alone.  max_requests = 1 (the default)
+ *   union and its coordinates are bitwise those it gets alone.  Requests
+ *   with p->assemble = 1, and requests whose component takes ForceAtlas2
+ *   with FMM repulsion (its evaluations share no launches with the others,
+ *   so batching would only serialise them), are laid out alone.  The exact
+ *   sums of all components of one layout share their launches, which is
+ *   where batching gains.  max_requests = 1 (the default)
  *   turns batching off; BGL_EINVAL for max_requests < 1 or max_nodes < 0.
  * bgl_server_batch_stats: *batches layouts that served more than one
  *   request so far, and *batched the requests they served (either may be

@@ -388,10 +388,21 @@ static void serve_group(Server *S, bgl_ctx *ctx, std::vector<Extracted> &grp) {
     for (auto &x : grp) finish(S, x.r, st, msg);
 }
 
-// whether a request of n nodes may share a layout: its parameters lay out
-// every request alone (no assembly into one frame) and it is small
+// whether a request of n nodes (one component) avoids the FMM: KK, or
+// ForceAtlas2 with exact repulsion (AUTO below its threshold; below 2,048
+// nodes when the crossover is measured)
+static bool avoids_fmm(const bgl_params &p, int64_t n) {
+    if (n <= p.kk_max_nodes || p.repulsion == BGL_REP_EXACT) return true;
+    if (p.repulsion == BGL_REP_AUTO) return p.fmm_min_nodes >= 0 ? n < p.fmm_min_nodes : n < 2048;
+    return false;
+}
+
+// whether a request of n nodes may share a layout: it is small, lays out
+// without the FMM (the exact sums of all components of a run share their
+// launches, each FMM evaluation has its own, so batched FMM requests would
+// only run one after another) and without assembly into one frame
 static bool batchable(const Server *S, const ServeRequest *r, int64_t n) {
-    return S->batch_max > 1 && r->p.assemble == 0 && n <= S->batch_nodes;
+    return S->batch_max > 1 && r->p.assemble == 0 && n <= S->batch_nodes && avoids_fmm(r->p, n);
 }
 
 static void worker_loop(Server *S, bgl_ctx *ctx) {

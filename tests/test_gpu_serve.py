@@ -137,9 +137,10 @@ def test_batched_requests_are_bitwise_their_own_layouts(ctx, c1):
     """With batching on and one slot, the requests queued behind the one in
     progress with equal parameters share one layout (the disjoint union of
     their neighbourhoods); each result equals the direct layout of its own
-    neighbourhood bit for bit: KK-sized, exact and FMM ForceAtlas2
-    neighbourhoods, two parameter sets in runs (only equal neighbours join),
-    an assembled request (laid out alone) and an oversize one (fails alone)."""
+    neighbourhood bit for bit: KK-sized and exact ForceAtlas2 neighbourhoods
+    (batched), FMM ones (alone, or batched when KK-sized), two parameter
+    sets in runs (only equal neighbours join), an assembled request (alone)
+    and an oversize one (fails alone)."""
     bgl = _bgl()
     g, og = c1
     deg = np.diff(og.off)
