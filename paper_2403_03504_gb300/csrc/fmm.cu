@@ -411,8 +411,7 @@ __global__ void bbox_kernel(const float2 *__restrict__ xy, int n, float4 *__rest
 constexpr int KEY_ITEMS = OS_ITEMS;      // one key block per radix tile
 
 __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy, int n, const Root *__restrict__ root,
-                                                   uint32_t *__restrict__ key, uint32_t *__restrict__ idx, OsHist h,
-                                                   const int *__restrict__ sortskip) {
+                                                   uint32_t *__restrict__ key, uint32_t *__restrict__ idx, OsHist h) {
     const float ox = root->oxf, oy = root->oyf, sc = root->scale;
     const int i0 = blockIdx.x * 256 * KEY_ITEMS + threadIdx.x;
     uint32_t k[KEY_ITEMS];
@@ -437,9 +436,7 @@ __global__ void __launch_bounds__(256) keys_kernel(const float2 *__restrict__ xy
     }
     static_assert(256 * KEY_ITEMS == OS_TILE, "a key block is one radix tile");
     os_clear_status(h, blockIdx.x);
-    // the digits of the radix passes this sort runs (the low two are skipped
-    // after a tree of at most 8 levels)
-    os_block_hist<KEY_ITEMS>(k, valid, h, *sortskip);
+    os_block_hist<KEY_ITEMS>(k, valid, h);
 }
 
 
@@ -2388,8 +2385,7 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
                                                        pl->epoch.p, pl->tickets.p, h);
             BGL_LAUNCH_CHECK();
         }
-        keys_kernel<<<nblk(n, 256 * KEY_ITEMS), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p, h,
-                                                             pl->sortskip.p);
+        keys_kernel<<<nblk(n, 256 * KEY_ITEMS), 256, 0, s>>>(xl, n, pl->root.p, pl->key.p, pl->idx.p, h);
         BGL_LAUNCH_CHECK();
         radix_sort_u32_ws_scatter(ctx, pl->sortws, pl->key.p, pl->idx.p, n, xl, ml, pl->pts.p, pl->sortskip.p,
                                   pl->wait);

@@ -14,13 +14,12 @@ constexpr int OS_ITEMS = BGL_OS_ITEMS;
 static_assert(OS_ITEMS >= 1 && OS_ITEMS <= 32, "a thread's keys are tracked in a 32-bit mask");
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 
-// Adds the block's keys (key[r] for the bits r of `valid`) to the 8-bit digit
-// histograms d >= dlo of h (shared-memory counts, then one global atomic per
-// non-empty bin; the digits below dlo, whose passes the sort skips, stay
-// zero); the last block to arrive writes the exclusive digit bases and
-// resets the arrival count.  Every thread of a 256-thread block calls it.
+// Adds the block's keys (key[r] for the bits r of `valid`) to the four 8-bit
+// digit histograms of h (shared-memory counts, then one global atomic per
+// non-empty bin); the last block to arrive writes the exclusive digit bases
+// and resets the arrival count.  Every thread of a 256-thread block calls it.
 template <int ITEMS>
-__device__ void os_block_hist(const uint32_t (&key)[ITEMS], unsigned valid, OsHist h, int dlo = 0) {
+__device__ void os_block_hist(const uint32_t (&key)[ITEMS], unsigned valid, OsHist h) {
     __shared__ uint32_t sh[4][256];
     __shared__ uint32_t ws[8];
     __shared__ bool last;
@@ -30,8 +29,7 @@ __device__ void os_block_hist(const uint32_t (&key)[ITEMS], unsigned valid, OsHi
     for (int r = 0; r < ITEMS; ++r) {
         if (!((valid >> r) & 1u)) continue;
 #pragma unroll
-        for (int d = 0; d < 4; ++d)
-            if (d >= dlo) atomicAdd(&sh[d][(key[r] >> (8 * d)) & 0xFFu], 1u);
+        for (int d = 0; d < 4; ++d) atomicAdd(&sh[d][(key[r] >> (8 * d)) & 0xFFu], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
