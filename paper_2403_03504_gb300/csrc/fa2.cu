@@ -282,7 +282,9 @@ __global__ void swing_traction_kernel(RedArgs a) {
     for (int c = warp; c < a.ncomp; c += nwarps) {
         const int64_t k0 = a.tile_off[c], nk = a.tile_off[c + 1] - k0;
         double swg = 0.0, trc = 0.0;
-        for (int w = 0; w < RED_TILE / 32; ++w) {
+        // (a virtual warp past the component's tiles adds +0.0 to a sum of
+        // norms, which changes nothing: it is skipped)
+        for (int w = 0; w < RED_TILE / 32 && 32 * w < nk; ++w) {
             double s = 0.0, u = 0.0;
             for (int64_t k = 32 * w + lane; k < nk; k += RED_TILE) {
                 const double2 v = __ldcg(&a.partial[k0 + k]);   // written by other blocks: bypass L1

@@ -277,6 +277,12 @@ __global__ void kk_kernel(KKArgs a) {
 
 size_t kk_group_bytes(int maxn, bool glob) { return kk_group_layout(maxn, glob).bytes; }
 
+// lanes per component of the three largest size classes: 32 (0), 16 (1) or
+// 8 (2), with correspondingly more nodes per lane
+#ifndef BGL_KK_WIDE
+#define BGL_KK_WIDE 1
+#endif
+
 // components above this size keep their distance matrix in global memory
 constexpr int KK_SMEM_MAX_N = 64;
 
@@ -395,9 +401,19 @@ KkRun *kk_prepare(bgl_graph *g, int64_t c0, int64_t c1) {
         const int64_t a128 = first_at_most(g, c0, c1, 128), a64 = first_at_most(g, c0, c1, 64),
                       a32 = first_at_most(g, c0, c1, 32), a16 = first_at_most(g, c0, c1, 16),
                       a8 = first_at_most(g, c0, c1, 8), a4 = first_at_most(g, c0, c1, 4);
+#if BGL_KK_WIDE == 2
+        kk_prepare_class<8, 32>(*run, c0, a128);
+        kk_prepare_class<8, 16>(*run, a128, a64);
+        kk_prepare_class<8, 8>(*run, a64, a32);
+#elif BGL_KK_WIDE == 1
+        kk_prepare_class<16, 16>(*run, c0, a128);
+        kk_prepare_class<16, 8>(*run, a128, a64);
+        kk_prepare_class<16, 4>(*run, a64, a32);
+#else
         kk_prepare_class<32, 8>(*run, c0, a128);
         kk_prepare_class<32, 4>(*run, a128, a64);
         kk_prepare_class<32, 2>(*run, a64, a32);
+#endif
         kk_prepare_class<16, 2>(*run, a32, a16);
         kk_prepare_class<8, 2>(*run, a16, a8);
         kk_prepare_class<4, 2>(*run, a8, a4);
@@ -414,13 +430,23 @@ int kk_classes(const KkRun *run) { return (int)run->cls.size(); }
 void kk_enqueue(const KkRun *run, int i, const bgl_params *p, float2 *xy, int64_t qbase, bool init, int sweeps,
                 int32_t *d_out, cudaStream_t s) {
     const KkClass &k = *run->cls[i];
-    switch (k.G * 16 + k.CPL) {
-        case 32 * 16 + 8: kk_enqueue_class<32, 8>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
-        case 32 * 16 + 4: kk_enqueue_class<32, 4>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
-        case 32 * 16 + 2: kk_enqueue_class<32, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
-        case 16 * 16 + 2: kk_enqueue_class<16, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
-        case 8 * 16 + 2: kk_enqueue_class<8, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
-        case 4 * 16 + 2: kk_enqueue_class<4, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+    switch (k.G * 64 + k.CPL) {
+#if BGL_KK_WIDE == 2
+        case 8 * 64 + 32: kk_enqueue_class<8, 32>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 8 * 64 + 16: kk_enqueue_class<8, 16>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 8 * 64 + 8: kk_enqueue_class<8, 8>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+#elif BGL_KK_WIDE == 1
+        case 16 * 64 + 16: kk_enqueue_class<16, 16>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 16 * 64 + 8: kk_enqueue_class<16, 8>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 16 * 64 + 4: kk_enqueue_class<16, 4>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+#else
+        case 32 * 64 + 8: kk_enqueue_class<32, 8>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 32 * 64 + 4: kk_enqueue_class<32, 4>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 32 * 64 + 2: kk_enqueue_class<32, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+#endif
+        case 16 * 64 + 2: kk_enqueue_class<16, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 8 * 64 + 2: kk_enqueue_class<8, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 4 * 64 + 2: kk_enqueue_class<4, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
         default: kk_enqueue_class<4, 1>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
     }
 }
