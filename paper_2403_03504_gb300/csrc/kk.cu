@@ -109,11 +109,13 @@ __global__ void kk_kernel(KKArgs a) {
     const int ds = kk_row_stride(n);                 // row stride of the distance matrix
     const bool glob = a.gdist != nullptr;
     const KkGroupLayout gl_ = kk_group_layout(a.maxn, glob);
-    // per-block table: s_kl[d] = (d^-2, l d), zero for d = 0 and d = 255
+    // per-block table: s_kl[d] = (k, k l) with k = d^-2 and l = l_unit d,
+    // zero for d = 0 and d = 255
     float2 *s_kl = reinterpret_cast<float2 *>(smem);
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const bool ok = i != 0 && i != 255;
-        s_kl[i] = ok ? make_float2(1.0f / (float)(i * i), a.l * (float)i) : make_float2(0.f, 0.f);
+        const float k = 1.0f / (float)(i * i);
+        s_kl[i] = ok ? make_float2(k, k * (a.l * (float)i)) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (c >= a.c0 + a.nc) return;
@@ -218,10 +220,13 @@ __global__ void kk_kernel(KKArgs a) {
     }
     __syncwarp(gmask);
 
-    // 3. Gauss-Seidel Newton-Raphson sweeps.  k_mi = d^-2 and l_mi = l d come
+    // 3. Gauss-Seidel Newton-Raphson sweeps.  k_mi = d^-2 and k_mi l_mi come
     // from the block's table (0 for d = 0: the node itself; and for the 255
     // padding of a row), and r^2 carries a 1e-30 shift, so the pair terms
-    // need no branch (the node itself adds exactly 0).
+    // need no branch (the node itself adds exactly 0).  Per pair:
+    //   g += k (1 - l / r) (p_m - p_i),
+    //   H_xx -= k l dy^2 / r^3,  H_yy -= k l dx^2 / r^3,  H_xy += k l dx dy / r^3
+    // (the diagonal's sum_i k_mi is added once per node step).
     uint8_t dn[CPL];
 #pragma unroll
     for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? dist[gl + j * G] : 255;
@@ -245,16 +250,16 @@ __global__ void kk_kernel(KKArgs a) {
                 const float dx = pm.x - pi.x, dy = pm.y - pi.y;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
                 const float rinv = rsqrtf(r2);
-                const float t = kl.y * rinv;            // l_mi / r
-                const float u = t * rinv * rinv;        // l_mi / r^3
-                const float kdx = kl.x * dx, kdy = kl.x * dy;
-                const float omt = 1.f - t;
-                gx = fmaf(kdx, omt, gx);
-                gy = fmaf(kdy, omt, gy);
-                const float ukdx = u * kdx, ukdy = u * kdy;
-                hxx = fmaf(-ukdy, dy, hxx);
-                hyy = fmaf(-ukdx, dx, hyy);
-                hxy = fmaf(ukdx, dy, hxy);
+                // w = k l / r^3 (k l first: zero for the node itself, whose
+                // 1/r^3 would overflow), c = k - w r^2 = k (1 - l / r)
+                const float w = (kl.y * rinv) * (rinv * rinv);
+                const float c = fmaf(-w, r2, kl.x);
+                gx = fmaf(c, dx, gx);
+                gy = fmaf(c, dy, gy);
+                const float wdx = w * dx, wdy = w * dy;
+                hxx = fmaf(-wdy, dy, hxx);
+                hyy = fmaf(-wdx, dx, hyy);
+                hxy = fmaf(wdx, dy, hxy);
             }
             gx = group_sum<G>(gx, gmask);
             gy = group_sum<G>(gy, gmask);
@@ -281,6 +286,11 @@ size_t kk_group_bytes(int maxn, bool glob) { return kk_group_layout(maxn, glob).
 // 8 (2), with correspondingly more nodes per lane
 #ifndef BGL_KK_WIDE
 #define BGL_KK_WIDE 1
+#endif
+// lanes per component of the classes of 9-32 nodes: 16 and 8 (0), or 8 and
+// 4 with twice the nodes per lane (1)
+#ifndef BGL_KK_NARROW
+#define BGL_KK_NARROW 1
 #endif
 
 // components above this size keep their distance matrix in global memory
@@ -414,8 +424,13 @@ KkRun *kk_prepare(bgl_graph *g, int64_t c0, int64_t c1) {
         kk_prepare_class<32, 4>(*run, a128, a64);
         kk_prepare_class<32, 2>(*run, a64, a32);
 #endif
+#if BGL_KK_NARROW
+        kk_prepare_class<8, 4>(*run, a32, a16);
+        kk_prepare_class<4, 4>(*run, a16, a8);
+#else
         kk_prepare_class<16, 2>(*run, a32, a16);
         kk_prepare_class<8, 2>(*run, a16, a8);
+#endif
         kk_prepare_class<4, 2>(*run, a8, a4);
         kk_prepare_class<4, 1>(*run, a4, c1);
     }
@@ -444,8 +459,13 @@ void kk_enqueue(const KkRun *run, int i, const bgl_params *p, float2 *xy, int64_
         case 32 * 64 + 4: kk_enqueue_class<32, 4>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
         case 32 * 64 + 2: kk_enqueue_class<32, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
 #endif
+#if BGL_KK_NARROW
+        case 8 * 64 + 4: kk_enqueue_class<8, 4>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+        case 4 * 64 + 4: kk_enqueue_class<4, 4>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+#else
         case 16 * 64 + 2: kk_enqueue_class<16, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
         case 8 * 64 + 2: kk_enqueue_class<8, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
+#endif
         case 4 * 64 + 2: kk_enqueue_class<4, 2>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
         default: kk_enqueue_class<4, 1>(*run, k, p, xy, qbase, init, sweeps, d_out, s); break;
     }
