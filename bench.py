@@ -638,7 +638,10 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     if args.timed_only:
         if rank == 0:
-            print(json.dumps({"timed_only": True, "step_ms": step_ms, "gpu_launches": int(launches)}), flush=True)
+            # launches_before: the library's kernel launches before the timed
+            # region (a profiler's skip count, plus the framework's own kernels)
+            print(json.dumps({"timed_only": True, "step_ms": step_ms, "gpu_launches": int(launches),
+                              "launches_before": int(launches0)}), flush=True)
         if dist:
             dist.barrier()
             dist.destroy_process_group()
