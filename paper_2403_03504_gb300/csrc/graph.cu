@@ -233,14 +233,37 @@ __global__ void node_order_kernel(const uint32_t *__restrict__ ckey, const uint3
     mass[q] = (float)(d + 1);   // ForceAtlas2 mass: degree + 1
 }
 
+// the last q in [lo, hi] with coff[q] <= k (coff non-decreasing, coff[lo] <= k)
+__device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ coff, int64_t lo, int64_t hi, int64_t k) {
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (coff[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Component-order adjacency, one thread per entry k of the m2 entries (so a
+// hub's list is spread over many threads): its node q is the one whose range
+// [coff[q], coff[q + 1]) holds k, found by a binary search inside the nodes
+// of the block's entries; cadj[k] = pos[adj[off[v] + k - coff[q]]], v =
+// nodes[q].
 __global__ void comp_csr_kernel(const int32_t *__restrict__ nodes, const int32_t *__restrict__ pos,
                                 const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                                const int64_t *__restrict__ coff, int64_t n, int32_t *__restrict__ cadj) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    int32_t v = nodes[q];
-    int64_t a = off[v], e = off[v + 1], o = coff[q];
-    for (int64_t k = a; k < e; ++k) cadj[o + (k - a)] = pos[adj[k]];
+                                const int64_t *__restrict__ coff, int64_t n, int64_t m2, int32_t *__restrict__ cadj) {
+    __shared__ int64_t qrange[2];
+    const int64_t k0 = (int64_t)blockIdx.x * blockDim.x;
+    if (k0 >= m2) return;
+    if (threadIdx.x < 2) {
+        const int64_t kk = threadIdx.x == 0 ? k0 : min(m2, k0 + (int64_t)blockDim.x) - 1;
+        qrange[threadIdx.x] = owner_of(coff, 0, n - 1, kk);
+    }
+    __syncthreads();
+    const int64_t k = k0 + threadIdx.x;
+    if (k >= m2) return;
+    const int64_t q = owner_of(coff, qrange[0], qrange[1], k);
+    const int32_t v = nodes[q];
+    cadj[k] = pos[adj[off[v] + (k - coff[q])]];
 }
 
 }  // namespace
@@ -435,8 +458,11 @@ void components_device(bgl_graph *g) {
     BGL_LAUNCH_CHECK();
     scan_exclusive_i64(c, cdeg.p, g->coff.p, n, g->coff.p + n);
     g->cadj.reset(A, 2 * g->n_undir);
-    comp_csr_kernel<<<blocks_for(n), TPB, 0, s>>>(g->nodes.p, g->pos.p, g->off.p, g->adj.p, g->coff.p, n, g->cadj.p);
-    BGL_LAUNCH_CHECK();
+    if (g->n_undir > 0) {
+        comp_csr_kernel<<<blocks_for(2 * g->n_undir), TPB, 0, s>>>(g->nodes.p, g->pos.p, g->off.p, g->adj.p,
+                                                                   g->coff.p, n, 2 * g->n_undir, g->cadj.p);
+        BGL_LAUNCH_CHECK();
+    }
     g->h_comp_off.resize(nc + 1);
     BGL_CUDA(cudaMemcpyAsync(g->h_comp_off.data(), g->comp_off.p, sizeof(int64_t) * (nc + 1),
                              cudaMemcpyDeviceToHost, s));
