@@ -88,36 +88,61 @@ __global__ void kh_local_kernel(const int32_t *__restrict__ vis, int64_t n, int3
     if (r < n) local[vis[r]] = (int32_t)r;
 }
 
-// induced edges (r, local[w]) with local[w] > r: counts, then the lists
-__global__ void kh_edge_count_kernel(const int32_t *__restrict__ vis, int64_t n, const int64_t *__restrict__ off,
-                                     const int32_t *__restrict__ adj, const int32_t *__restrict__ stamp,
-                                     int32_t epoch, const int32_t *__restrict__ local, int64_t *__restrict__ cnt) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int32_t v = vis[r];
-    int64_t k = 0;
-    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
-        const int32_t w = adj[e];
-        if (stamp[w] == epoch && local[w] > r) ++k;
+// Induced edges (r, local[w]) with local[w] > r, one thread per adjacency
+// entry e of the neighbourhood's nodes (ds: their degree prefix sums), so a
+// hub's list is spread over many threads; entries in (node, adjacency)
+// order, so each node's edges keep its adjacency order.
+
+// the last r in [lo, hi] with ds[r] <= e (ds non-decreasing, ds[lo] <= e)
+__device__ __forceinline__ int64_t kh_owner(const int64_t *__restrict__ ds, int64_t lo, int64_t hi, int64_t e) {
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (ds[mid] <= e) lo = mid;
+        else hi = mid - 1;
     }
-    cnt[r] = k;
+    return lo;
 }
 
-__global__ void kh_edge_fill_kernel(const int32_t *__restrict__ vis, int64_t n, const int64_t *__restrict__ off,
-                                    const int32_t *__restrict__ adj, const int32_t *__restrict__ stamp, int32_t epoch,
-                                    const int32_t *__restrict__ local, const int64_t *__restrict__ start,
+// node r and neighbour w of entry e = blockIdx.x * blockDim.x + threadIdx.x
+// (false past E); the block's node range found once
+__device__ __forceinline__ bool kh_entry(const int32_t *__restrict__ vis, int64_t n, const int64_t *__restrict__ ds,
+                                         int64_t E, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                         int64_t &r, int32_t &w) {
+    __shared__ int64_t rr[2];
+    const int64_t k0 = (int64_t)blockIdx.x * blockDim.x;
+    if (threadIdx.x < 2) rr[threadIdx.x] = kh_owner(ds, 0, n - 1, threadIdx.x == 0 ? k0 : min(E, k0 + (int64_t)blockDim.x) - 1);
+    __syncthreads();
+    const int64_t e = k0 + threadIdx.x;
+    if (e >= E) return false;
+    r = kh_owner(ds, rr[0], rr[1], e);
+    w = adj[off[vis[r]] + (e - ds[r])];
+    return true;
+}
+
+__global__ void kh_edge_flag_kernel(const int32_t *__restrict__ vis, int64_t n, const int64_t *__restrict__ ds,
+                                    int64_t E, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                    const int32_t *__restrict__ stamp, int32_t epoch,
+                                    const int32_t *__restrict__ local, int32_t *__restrict__ keep) {
+    if ((int64_t)blockIdx.x * blockDim.x >= E) return;
+    int64_t r;
+    int32_t w;
+    if (!kh_entry(vis, n, ds, E, off, adj, r, w)) return;
+    keep[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = stamp[w] == epoch && local[w] > r ? 1 : 0;
+}
+
+__global__ void kh_edge_fill_kernel(const int32_t *__restrict__ vis, int64_t n, const int64_t *__restrict__ ds,
+                                    int64_t E, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                    const int32_t *__restrict__ stamp, int32_t epoch,
+                                    const int32_t *__restrict__ local, const int32_t *__restrict__ kpos,
                                     int32_t *__restrict__ u, int32_t *__restrict__ v) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int32_t g = vis[r];
-    int64_t k = start[r];
-    for (int64_t e = off[g]; e < off[g + 1]; ++e) {
-        const int32_t w = adj[e];
-        if (stamp[w] == epoch && local[w] > r) {
-            u[k] = (int32_t)r;
-            v[k] = local[w];
-            ++k;
-        }
+    if ((int64_t)blockIdx.x * blockDim.x >= E) return;
+    int64_t r;
+    int32_t w;
+    if (!kh_entry(vis, n, ds, E, off, adj, r, w)) return;
+    if (stamp[w] == epoch && local[w] > r) {
+        const int64_t k = kpos[(int64_t)blockIdx.x * blockDim.x + threadIdx.x];
+        u[k] = (int32_t)r;
+        v[k] = local[w];
     }
 }
 
@@ -192,19 +217,34 @@ static int64_t khop_extract(bgl_ctx *ctx, const bgl_graph *R, KhopScratch &ws, i
     BGL_CUDA(cudaMemcpyAsync(ws.vis.p, keys.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     kh_local_kernel<<<kh_blocks(n), KH_TPB, 0, s>>>(ws.vis.p, n, ws.local.p);
     BGL_LAUNCH_CHECK();
-    DevBuf<int64_t> ecnt(ctx->alloc, n), estart(ctx->alloc, n), etot(ctx->alloc, 1);
-    kh_edge_count_kernel<<<kh_blocks(n), KH_TPB, 0, s>>>(ws.vis.p, n, R->off.p, R->adj.p, ws.stamp.p, epoch,
-                                                         ws.local.p, ecnt.p);
+    // adjacency entries of the neighbourhood's nodes: degree prefix sums
+    kh_deg_kernel<<<kh_blocks(n), KH_TPB, 0, s>>>(ws.vis.p, n, R->off.p, ws.deg.p);
     BGL_LAUNCH_CHECK();
-    scan_exclusive_i64(ctx, ecnt.p, estart.p, n, etot.p);
-    m = 0;
-    BGL_CUDA(cudaMemcpyAsync(&m, etot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    scan_exclusive_i64(ctx, ws.deg.p, ws.dscan.p, n, ws.tot.p);
+    int64_t E = 0;
+    BGL_CUDA(cudaMemcpyAsync(&E, ws.tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BGL_CUDA(cudaStreamSynchronize(s));
+    BGL_REQUIRE(E < (int64_t(1) << 31), "khop: more than 2^31 adjacency entries in the neighbourhood");
+    m = 0;
+    DevBuf<int32_t> keep(ctx->alloc, std::max<int64_t>(E, 1)), kpos(ctx->alloc, std::max<int64_t>(E, 1));
+    DevBuf<int32_t> ktot(ctx->alloc, 1);
+    if (E > 0) {
+        kh_edge_flag_kernel<<<kh_blocks(E), KH_TPB, 0, s>>>(ws.vis.p, n, ws.dscan.p, E, R->off.p, R->adj.p,
+                                                            ws.stamp.p, epoch, ws.local.p, keep.p);
+        BGL_LAUNCH_CHECK();
+        scan_exclusive_i32(ctx, keep.p, kpos.p, E, ktot.p);
+        int32_t m32 = 0;
+        BGL_CUDA(cudaMemcpyAsync(&m32, ktot.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        BGL_CUDA(cudaStreamSynchronize(s));
+        m = m32;
+    }
     u.reset(ctx->alloc, std::max<int64_t>(m, 1));
     v.reset(ctx->alloc, std::max<int64_t>(m, 1));
-    kh_edge_fill_kernel<<<kh_blocks(n), KH_TPB, 0, s>>>(ws.vis.p, n, R->off.p, R->adj.p, ws.stamp.p, epoch,
-                                                        ws.local.p, estart.p, u.p, v.p);
-    BGL_LAUNCH_CHECK();
+    if (m > 0) {
+        kh_edge_fill_kernel<<<kh_blocks(E), KH_TPB, 0, s>>>(ws.vis.p, n, ws.dscan.p, E, R->off.p, R->adj.p,
+                                                            ws.stamp.p, epoch, ws.local.p, kpos.p, u.p, v.p);
+        BGL_LAUNCH_CHECK();
+    }
     return n;
 }
 
