@@ -231,7 +231,7 @@ __global__ void kk_kernel(KKArgs a) {
 #pragma unroll
     for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? dist[gl + j * G] : 255;
     for (int sw = 0; sw < a.sweeps; ++sw) {
-        float gmax = 0.f;
+        float gmax2 = 0.f;                           // largest squared gradient norm of the sweep
         for (int m = 0; m < n; ++m) {
             uint8_t d[CPL];
 #pragma unroll
@@ -267,7 +267,7 @@ __global__ void kk_kernel(KKArgs a) {
             hxy = group_sum<G>(hxy, gmask);
             hyy = group_sum<G>(hyy, gmask);
             const float km = ksum[m];
-            gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
+            gmax2 = fmaxf(gmax2, fmaf(gx, gx, gy * gy));
             float dxm, dym;
             // every lane holds the same sums and takes the same step; the
             // node's owner stores the new position
@@ -275,7 +275,7 @@ __global__ void kk_kernel(KKArgs a) {
                 pos[m] = make_float2(pm.x + dxm, pm.y + dym);
             __syncwarp(gmask);
         }
-        if (a.tol > 0.f && gmax < a.tol) break;
+        if (a.tol > 0.f && gmax2 < a.tol * a.tol) break;
     }
     for (int v = gl; v < n; v += G) a.xy[q0 + v - a.qbase] = pos[v];
 }

@@ -22,6 +22,16 @@ __device__ __forceinline__ float2 initial_position(uint64_t seed, int32_t id) {
     return make_float2(x, y);
 }
 
+// hardware reciprocal and square root (one MUFU operation each, about one
+// rounding of error): the step below is a safeguarded Newton move whose
+// rounding the sweeps do not amplify
+__device__ __forceinline__ float kk_rcp(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float kk_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 // Safeguarded Newton-Raphson step (Section 3.1) in FP32: with
 // H = l1 P1 + l2 P2 (l1 >= l2, P1 + P2 = I), delta = -(P1 g / e1 + P2 g / e2)
 // where e_i = l_i for positive curvature and max(|l_i|, 0.1 max|l|) otherwise;
@@ -29,7 +39,7 @@ __device__ __forceinline__ float2 initial_position(uint64_t seed, int32_t id) {
 __device__ __forceinline__ bool kk_step(float gx, float gy, float a, float b, float c, float l, float *dx,
                                         float *dy) {
     const float h = 0.5f * (a - c);
-    const float dd = sqrtf(h * h + b * b);
+    const float dd = kk_sqrt(fmaf(h, h, b * b));
     const float tr = 0.5f * (a + c);
     const float l1 = tr + dd, l2 = tr - dd;
     const float big = fmaxf(fabsf(l1), fabsf(l2));
@@ -38,15 +48,12 @@ __device__ __forceinline__ bool kk_step(float gx, float gy, float a, float b, fl
     const float e1 = l1 > 1e-12f * big ? l1 : fmaxf(fabsf(l1), fl);
     const float e2 = l2 > 1e-12f * big ? l2 : fmaxf(fabsf(l2), fl);
     float sx, sy;
-    // correctly rounded reciprocals (__frcp_rn) instead of divisions, and
-    // rsqrtf for the length cap: cheaper, and the step is a safeguarded
-    // Newton move whose rounding the sweeps do not amplify
-    const float ie1 = __frcp_rn(e1), ie2 = __frcp_rn(e2);
+    const float ie1 = kk_rcp(e1), ie2 = kk_rcp(e2);
     if (dd == 0.0f) {
         sx = -gx * ie1;
         sy = -gy * ie1;
     } else {
-        const float i2d = __frcp_rn(2.0f * dd);
+        const float i2d = kk_rcp(2.0f * dd);
         const float p1x = ((h + dd) * gx + b * gy) * i2d;
         const float p1y = (b * gx + (dd - h) * gy) * i2d;
         sx = -(p1x * ie1 + (gx - p1x) * ie2);
