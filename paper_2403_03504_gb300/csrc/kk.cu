@@ -90,12 +90,54 @@ __host__ __device__ __forceinline__ KkGroupLayout kk_group_layout(int maxn, bool
     return L;
 }
 
+// Lane gl's distances to its nodes gl, gl + G, ... in one row of the
+// distance matrix.  In shared memory (node order, row stride ds) byte by
+// byte; in global memory (GLOB: each lane's CPL bytes contiguous at gl CPL,
+// row stride G CPL, 255 past the component) as CPL / 4 words from one vector
+// load, a byte taken out only where it is used.
+template <int G, int CPL, bool GLOB>
+struct KkRow {
+    uint8_t b[CPL];
+    __device__ __forceinline__ void load(const uint8_t *row, int gl, int ds) {
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) b[j] = gl + j * G < ds ? row[gl + j * G] : 255;
+    }
+    __device__ __forceinline__ int get(int j) const { return b[j]; }
+};
+
+template <int G, int CPL>
+struct KkRow<G, CPL, true> {
+    static_assert(CPL % 4 == 0, "a lane's part of a global-memory row is whole words");
+    uint32_t w[CPL / 4];
+    __device__ __forceinline__ void load(const uint8_t *row, int gl, int) {
+        const uint8_t *src = row + gl * CPL;           // 4 CPL-byte aligned (row stride G CPL)
+        if constexpr (CPL == 4) {
+            w[0] = *reinterpret_cast<const uint32_t *>(src);
+        } else if constexpr (CPL == 8) {
+            const uint2 t = *reinterpret_cast<const uint2 *>(src);
+            w[0] = t.x;
+            w[1] = t.y;
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPL / 16; ++q) {
+                const uint4 t = reinterpret_cast<const uint4 *>(src)[q];
+                w[4 * q] = t.x;
+                w[4 * q + 1] = t.y;
+                w[4 * q + 2] = t.z;
+                w[4 * q + 3] = t.w;
+            }
+        }
+    }
+    __device__ __forceinline__ int get(int j) const { return (int)((w[j / 4] >> (8 * (j % 4))) & 255u); }
+};
+
 // One group of G lanes per component (G = 4, 8, 16 or 32); lane gl owns the
 // nodes gl + j G (j < CPL): their distances to the current node m are read
 // one step ahead (the next row's loads are in flight during the current
 // step).  The positions live in the group's shared memory, so node m's is
-// one broadcast load and its move one store.
-template <int G, int CPL>
+// one broadcast load and its move one store.  GLOB: the distance matrix is
+// in global memory (components of more than 64 nodes).
+template <int G, int CPL, bool GLOB>
 __global__ void kk_kernel(KKArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -106,8 +148,10 @@ __global__ void kk_kernel(KKArgs a) {
     const bool live = c < a.c0 + a.nc;
     const int64_t q0 = live ? a.comp_off[c] : 0;
     const int n = live ? (int)(a.comp_off[c + 1] - q0) : 0;
-    const int ds = kk_row_stride(n);                 // row stride of the distance matrix
-    const bool glob = a.gdist != nullptr;
+    constexpr bool glob = GLOB;
+    constexpr int GDS = G * CPL;                     // row stride in global memory
+    const int nds = kk_row_stride(n);                // node-order row stride (shared memory)
+    const int ds = glob ? GDS : nds;                 // row stride of the distance matrix
     const KkGroupLayout gl_ = kk_group_layout(a.maxn, glob);
     // per-block table: s_kl[d] = (k, k l) with k = d^-2 and l = l_unit d,
     // zero for d = 0 and d = 255
@@ -130,7 +174,7 @@ __global__ void kk_kernel(KKArgs a) {
         // level together in a shared row, which then goes to global memory
         uint8_t *row = base;
         for (int s = 0; s < n; ++s) {
-            for (int v = gl; v < ds; v += G) row[v] = v == s ? 0 : 255;
+            for (int v = gl; v < nds; v += G) row[v] = v == s ? 0 : 255;
             __syncwarp(gmask);
             for (int k = 0; k < 254; ++k) {
                 bool grew = false;
@@ -147,7 +191,11 @@ __global__ void kk_kernel(KKArgs a) {
                 __syncwarp(gmask);
                 if (!__any_sync(gmask, grew)) break;
             }
-            for (int v = gl; v < ds; v += G) dist[(size_t)s * ds + v] = row[v];
+            // lane gl's nodes gl, gl + G, ... at gl CPL .. gl CPL + CPL - 1
+            for (int j = 0; j < CPL; ++j) {
+                const int v = gl + j * G;
+                dist[(size_t)s * GDS + gl * CPL + j] = v < n ? row[v] : (uint8_t)255;
+            }
             __syncwarp(gmask);
         }
         __threadfence_block();
@@ -172,9 +220,11 @@ __global__ void kk_kernel(KKArgs a) {
         }
     }
     __syncwarp(gmask);
+    // slot of node v in a row
+    auto slot = [&](int v) { return glob ? (v % G) * CPL + v / G : v; };
     int diam = 0;
     for (int i = gl; i < n * n; i += G) {
-        int d = dist[(size_t)(i / n) * ds + i % n];
+        int d = dist[(size_t)(i / n) * ds + slot(i % n)];
         if (d != 255 && d > diam) diam = d;
     }
 #pragma unroll
@@ -182,7 +232,7 @@ __global__ void kk_kernel(KKArgs a) {
 
     if (a.d_out && c == a.c0) {
         for (int i = gl; i < n * n; i += G) {
-            const int d = dist[(size_t)(i / n) * ds + i % n];
+            const int d = dist[(size_t)(i / n) * ds + slot(i % n)];
             a.d_out[i] = d == 255 ? -1 : d;
         }
     }
@@ -213,7 +263,7 @@ __global__ void kk_kernel(KKArgs a) {
         for (int v = 0; v < n; ++v) {
             const uint8_t *row = dist + (size_t)v * ds;
             float sk = 0.f;
-            for (int i = gl; i < n; i += G) sk += s_kl[row[i]].x;
+            for (int j = 0; j < CPL && gl + j * G < n; ++j) sk += s_kl[row[gl * CPL + j]].x;
             sk = group_sum<G>(sk, gmask);
             if (gl == 0) ksum[v] = sk;
         }
@@ -227,25 +277,20 @@ __global__ void kk_kernel(KKArgs a) {
     //   g += k (1 - l / r) (p_m - p_i),
     //   H_xx -= k l dy^2 / r^3,  H_yy -= k l dx^2 / r^3,  H_xy += k l dx dy / r^3
     // (the diagonal's sum_i k_mi is added once per node step).
-    uint8_t dn[CPL];
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? dist[gl + j * G] : 255;
+    KkRow<G, CPL, GLOB> dn;
+    dn.load(dist, gl, ds);
     for (int sw = 0; sw < a.sweeps; ++sw) {
         float gmax2 = 0.f;                           // largest squared gradient norm of the sweep
         for (int m = 0; m < n; ++m) {
-            uint8_t d[CPL];
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) d[j] = dn[j];
+            const KkRow<G, CPL, GLOB> d = dn;
             // next row (m + 1, or row 0 for the next sweep) in flight
-            const uint8_t *nrow = dist + (size_t)(m + 1 < n ? m + 1 : 0) * ds;
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) dn[j] = gl + j * G < ds ? nrow[gl + j * G] : 255;
+            dn.load(dist + (size_t)(m + 1 < n ? m + 1 : 0) * ds, gl, ds);
             const float2 pm = pos[m];
             float gx = 0.f, gy = 0.f, hxx = 0.f, hxy = 0.f, hyy = 0.f;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
                 if (j * G >= n) break;                   // the group's component has no node there
-                const float2 kl = s_kl[d[j]];
+                const float2 kl = s_kl[d.get(j)];
                 const float2 pi = pos[gl + j * G < n ? gl + j * G : 0];
                 const float dx = pm.x - pi.x, dy = pm.y - pi.y;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
@@ -341,13 +386,15 @@ static void kk_prepare_class(KkRun &run, int64_t c0, int64_t c1) {
     k->gpb = (int)std::min<size_t>(max_groups, std::max<size_t>(1, (size_t)(200 * 1024) / gb));
     k->smem = KK_TABLE_BYTES + gb * k->gpb;
     if (glob) {
-        // global distance matrices: n_c x stride(n_c) bytes per component
+        // global distance matrices: n_c rows of G CPL bytes per component
+        // (a lane's part of a row contiguous and aligned for one vector load)
+        BGL_REQUIRE(CPL % 4 == 0, "kk: distances in global memory need a multiple of 4 nodes per lane");
         std::vector<int64_t> off(c1 - c0);
         int64_t tot = 0;
         for (int64_t c = c0; c < c1; ++c) {
             const int64_t nc = g->h_comp_off[c + 1] - g->h_comp_off[c];
             off[c - c0] = tot;
-            tot += nc * kk_row_stride((int)nc);
+            tot += nc * (int64_t)(G * CPL);
         }
         k->gdist.reset(g->ctx->alloc, std::max<int64_t>(tot, 8));
         k->gdist_off.reset(g->ctx->alloc, off.size());
@@ -355,7 +402,15 @@ static void kk_prepare_class(KkRun &run, int64_t c0, int64_t c1) {
                                  g->ctx->stream));
         BGL_CUDA(cudaStreamSynchronize(g->ctx->stream));
     }
-    BGL_CUDA(cudaFuncSetAttribute(kk_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    if constexpr (CPL % 4 == 0) {
+        if (glob) {
+            BGL_CUDA(cudaFuncSetAttribute(kk_kernel<G, CPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          220 * 1024));
+        }
+    }
+    if (!glob)
+        BGL_CUDA(cudaFuncSetAttribute(kk_kernel<G, CPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024));
     run.cls.push_back(std::move(k));
 }
 
@@ -384,7 +439,17 @@ static void kk_enqueue_class(const KkRun &run, const KkClass &k, const bgl_param
     a.gdist = k.gdist.p;
     a.gdist_off = k.gdist_off.p;
     const int64_t blocks = (a.nc + k.gpb - 1) / k.gpb;
-    kk_kernel<G, CPL><<<(unsigned)blocks, G * k.gpb, k.smem, s>>>(a);
+    bool launched = false;
+    if constexpr (CPL % 4 == 0) {
+        if (k.gdist.p) {
+            kk_kernel<G, CPL, true><<<(unsigned)blocks, G * k.gpb, k.smem, s>>>(a);
+            launched = true;
+        }
+    }
+    if (!launched) {
+        BGL_REQUIRE(!k.gdist.p, "kk: distances in global memory need a multiple of 4 nodes per lane");
+        kk_kernel<G, CPL, false><<<(unsigned)blocks, G * k.gpb, k.smem, s>>>(a);
+    }
     BGL_LAUNCH_CHECK();
 }
 
