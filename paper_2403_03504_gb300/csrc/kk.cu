@@ -73,16 +73,23 @@ struct KKArgs {
 __host__ __device__ __forceinline__ int kk_row_stride(int n) { return (n + 7) & ~7; }
 constexpr size_t KK_TABLE_BYTES = 256 * sizeof(float2);
 
-// Shared memory of one lane group: its distance matrix (or, with the
-// matrices in global memory, one BFS row), then the positions of its
-// component's nodes (float2) and each node's sum of k_mi (float), each part
-// 16-byte aligned.
+// Row stride of a shared-memory distance matrix: G CPL when the rows are
+// rewritten lane-major for the sweeps (CPL a multiple of 4), else node order
+// padded to 8 bytes.
+__host__ __device__ __forceinline__ int kk_smem_stride(int G, int CPL, int n) {
+    return CPL % 4 == 0 ? G * CPL : kk_row_stride(n);
+}
+
+// Shared memory of one lane group: its distance matrix (maxn rows of rs
+// bytes) or, with the matrices in global memory, one BFS row; then the
+// positions of its component's nodes (float2) and each node's sum of k_mi
+// (float), each part 16-byte aligned.
 struct KkGroupLayout {
     size_t pos, ksum, bytes;
 };
-__host__ __device__ __forceinline__ KkGroupLayout kk_group_layout(int maxn, bool glob) {
+__host__ __device__ __forceinline__ KkGroupLayout kk_group_layout(int maxn, bool glob, int rs) {
     const size_t a = 16;
-    const size_t d = glob ? (size_t)kk_row_stride(maxn) : (size_t)maxn * kk_row_stride(maxn);
+    const size_t d = glob ? (size_t)kk_row_stride(maxn) : (size_t)maxn * rs;
     KkGroupLayout L;
     L.pos = (d + a - 1) / a * a;
     L.ksum = L.pos + (8 * (size_t)maxn + a - 1) / a * a;
@@ -149,10 +156,13 @@ __global__ void kk_kernel(KKArgs a) {
     const int64_t q0 = live ? a.comp_off[c] : 0;
     const int n = live ? (int)(a.comp_off[c + 1] - q0) : 0;
     constexpr bool glob = GLOB;
-    constexpr int GDS = G * CPL;                     // row stride in global memory
-    const int nds = kk_row_stride(n);                // node-order row stride (shared memory)
-    const int ds = glob ? GDS : nds;                 // row stride of the distance matrix
-    const KkGroupLayout gl_ = kk_group_layout(a.maxn, glob);
+    // rows lane-major during the sweeps (one vector load per lane and row):
+    // in global memory always, in shared memory when CPL is a multiple of 4
+    constexpr bool PACKED = GLOB || CPL % 4 == 0;
+    constexpr int GDS = G * CPL;                     // row stride of a lane-major matrix
+    const int nds = kk_row_stride(n);                // node-order row (a BFS row in shared memory)
+    const int ds = PACKED ? GDS : nds;               // row stride of the distance matrix
+    const KkGroupLayout gl_ = kk_group_layout(a.maxn, glob, kk_smem_stride(G, CPL, a.maxn));
     // per-block table: s_kl[d] = (k, k l) with k = d^-2 and l = l_unit d,
     // zero for d = 0 and d = 255
     float2 *s_kl = reinterpret_cast<float2 *>(smem);
@@ -258,6 +268,21 @@ __global__ void kk_kernel(KKArgs a) {
         }
         ksum[v] = sk;
     }
+    if constexpr (!GLOB && PACKED) {
+        // the rows to the lane-major layout of the sweeps (lane gl's nodes gl,
+        // gl + G, ... at gl CPL ..), each lane rewriting its own rows once
+        // every lane has read the node-order ones (diameter, export)
+        __syncwarp(gmask);
+        for (int s = gl; s < n; s += G) {
+            uint8_t *row = dist + (size_t)s * GDS;
+            uint32_t w[GDS / 4];
+#pragma unroll
+            for (int q = 0; q < GDS / 4; ++q) w[q] = reinterpret_cast<const uint32_t *>(row)[q];
+#pragma unroll
+            for (int v = 0; v < GDS; ++v)
+                row[(v % G) * CPL + v / G] = (uint8_t)((w[v / 4] >> (8 * (v % 4))) & 255u);
+        }
+    }
     if (glob) {
         // one row at a time from global memory, the group's lanes over its entries
         for (int v = 0; v < n; ++v) {
@@ -277,12 +302,12 @@ __global__ void kk_kernel(KKArgs a) {
     //   g += k (1 - l / r) (p_m - p_i),
     //   H_xx -= k l dy^2 / r^3,  H_yy -= k l dx^2 / r^3,  H_xy += k l dx dy / r^3
     // (the diagonal's sum_i k_mi is added once per node step).
-    KkRow<G, CPL, GLOB> dn;
+    KkRow<G, CPL, PACKED> dn;
     dn.load(dist, gl, ds);
     for (int sw = 0; sw < a.sweeps; ++sw) {
         float gmax2 = 0.f;                           // largest squared gradient norm of the sweep
         for (int m = 0; m < n; ++m) {
-            const KkRow<G, CPL, GLOB> d = dn;
+            const KkRow<G, CPL, PACKED> d = dn;
             // next row (m + 1, or row 0 for the next sweep) in flight
             dn.load(dist + (size_t)(m + 1 < n ? m + 1 : 0) * ds, gl, ds);
             const float2 pm = pos[m];
@@ -325,7 +350,8 @@ __global__ void kk_kernel(KKArgs a) {
     for (int v = gl; v < n; v += G) a.xy[q0 + v - a.qbase] = pos[v];
 }
 
-size_t kk_group_bytes(int maxn, bool glob) { return kk_group_layout(maxn, glob).bytes; }
+size_t kk_group_bytes(int maxn, bool glob, int rs) { return kk_group_layout(maxn, glob, rs).bytes; }
+
 
 // lanes per component of the three largest size classes: 32 (0), 16 (1) or
 // 8 (2), with correspondingly more nodes per lane
@@ -381,7 +407,7 @@ static void kk_prepare_class(KkRun &run, int64_t c0, int64_t c1) {
     if (maxn < 1) maxn = 1;
     k->maxn = maxn;
     const bool glob = maxn > KK_SMEM_MAX_N;
-    const size_t gb = kk_group_bytes(maxn, glob);
+    const size_t gb = kk_group_bytes(maxn, glob, kk_smem_stride(G, CPL, maxn));
     const int max_groups = 256 / G;
     k->gpb = (int)std::min<size_t>(max_groups, std::max<size_t>(1, (size_t)(200 * 1024) / gb));
     k->smem = KK_TABLE_BYTES + gb * k->gpb;
