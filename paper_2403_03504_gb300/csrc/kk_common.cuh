@@ -38,6 +38,25 @@ __device__ __forceinline__ float kk_sqrt(float x) { return x > 0.f ? x * rsqrtf(
 // steps longer than l are shortened to l.  Returns false for H = 0.
 __device__ __forceinline__ bool kk_step(float gx, float gy, float a, float b, float c, float l, float *dx,
                                         float *dy) {
+    // positive definite with both eigenvalues above 1e-12 of the larger (tr
+    // > 0 and det > 4e-12 tr^2 imply it: l2 = det / l1 > 4e-12 tr^2 / (2 tr)
+    // >= 1e-12 l1 since l1 <= 2 tr): then e_i = l_i and the step is -H^-1 g
+    const float tr2 = a + c;
+    const float det = fmaf(a, c, -b * b);
+    if (tr2 > 0.f && det > 1e-12f * tr2 * tr2) {
+        const float id = kk_rcp(det);
+        float sx = -(c * gx - b * gy) * id;
+        float sy = -(a * gy - b * gx) * id;
+        const float len2 = fmaf(sx, sx, sy * sy);
+        if (len2 > l * l) {
+            const float sc = l * rsqrtf(len2);
+            sx *= sc;
+            sy *= sc;
+        }
+        *dx = sx;
+        *dy = sy;
+        return true;
+    }
     const float h = 0.5f * (a - c);
     const float dd = kk_sqrt(fmaf(h, h, b * b));
     const float tr = 0.5f * (a + c);
