@@ -48,6 +48,16 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask) {
     return v;
 }
 
+// two group sums at once, the adds packed (FP32x2; each component the same
+// add, in the same order, as group_sum)
+template <int G>
+__device__ __forceinline__ float2 group_sum2(float2 v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+        v = __fadd2_rn(v, make_float2(__shfl_xor_sync(mask, v.x, o), __shfl_xor_sync(mask, v.y, o)));
+    return v;
+}
+
 struct KKArgs {
     const int64_t *comp_off;
     const int64_t *coff;
@@ -82,17 +92,18 @@ __host__ __device__ __forceinline__ int kk_smem_stride(int G, int CPL, int n) {
 
 // Shared memory of one lane group: its distance matrix (maxn rows of rs
 // bytes) or, with the matrices in global memory, one BFS row; then the
-// positions of its component's nodes (float2) and each node's sum of k_mi
-// (float), each part 16-byte aligned.
+// positions (float2) of its component's nodes and of the lanes' padding
+// slots up to `slots` (G CPL), and each node's sum of k_mi (float), each
+// part 16-byte aligned.
 struct KkGroupLayout {
     size_t pos, ksum, bytes;
 };
-__host__ __device__ __forceinline__ KkGroupLayout kk_group_layout(int maxn, bool glob, int rs) {
+__host__ __device__ __forceinline__ KkGroupLayout kk_group_layout(int maxn, bool glob, int rs, int slots) {
     const size_t a = 16;
     const size_t d = glob ? (size_t)kk_row_stride(maxn) : (size_t)maxn * rs;
     KkGroupLayout L;
     L.pos = (d + a - 1) / a * a;
-    L.ksum = L.pos + (8 * (size_t)maxn + a - 1) / a * a;
+    L.ksum = L.pos + (8 * (size_t)(slots > maxn ? slots : maxn) + a - 1) / a * a;
     L.bytes = L.ksum + (4 * (size_t)maxn + a - 1) / a * a;
     return L;
 }
@@ -162,7 +173,7 @@ __global__ void kk_kernel(KKArgs a) {
     constexpr int GDS = G * CPL;                     // row stride of a lane-major matrix
     const int nds = kk_row_stride(n);                // node-order row (a BFS row in shared memory)
     const int ds = PACKED ? GDS : nds;               // row stride of the distance matrix
-    const KkGroupLayout gl_ = kk_group_layout(a.maxn, glob, kk_smem_stride(G, CPL, a.maxn));
+    const KkGroupLayout gl_ = kk_group_layout(a.maxn, glob, kk_smem_stride(G, CPL, a.maxn), GDS);
     // per-block table: s_kl[d] = (k, k l) with k = d^-2 and l = l_unit d,
     // zero for d = 0 and d = 255
     float2 *s_kl = reinterpret_cast<float2 *>(smem);
@@ -251,6 +262,9 @@ __global__ void kk_kernel(KKArgs a) {
     // (constant over the sweeps: the Hessian's diagonal is that sum minus the
     // position-dependent terms)
     const float scale = a.l * (float)diam * 0.5f;
+    // the lanes' slots past the component: a finite position (0, 0), whose
+    // pair terms are exactly zero (k = k l = 0 for the 255 distance)
+    for (int v = n + gl; v < GDS; v += G) pos[v] = make_float2(0.f, 0.f);
     for (int v = gl; v < n; v += G) {
         float2 p;
         if (a.init) {
@@ -316,7 +330,7 @@ __global__ void kk_kernel(KKArgs a) {
             for (int j = 0; j < CPL; ++j) {
                 if (j * G >= n) break;                   // the group's component has no node there
                 const float2 kl = s_kl[d.get(j)];
-                const float2 pi = pos[gl + j * G < n ? gl + j * G : 0];
+                const float2 pi = pos[gl + j * G];
                 const float dx = pm.x - pi.x, dy = pm.y - pi.y;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
                 const float rinv = rsqrtf(r2);
@@ -331,11 +345,13 @@ __global__ void kk_kernel(KKArgs a) {
                 hyy = fmaf(-wdx, dx, hyy);
                 hxy = fmaf(wdx, dy, hxy);
             }
-            gx = group_sum<G>(gx, gmask);
-            gy = group_sum<G>(gy, gmask);
-            hxx = group_sum<G>(hxx, gmask);
+            const float2 gs = group_sum2<G>(make_float2(gx, gy), gmask);
+            const float2 hs = group_sum2<G>(make_float2(hxx, hyy), gmask);
+            gx = gs.x;
+            gy = gs.y;
+            hxx = hs.x;
+            hyy = hs.y;
             hxy = group_sum<G>(hxy, gmask);
-            hyy = group_sum<G>(hyy, gmask);
             const float km = ksum[m];
             gmax2 = fmaxf(gmax2, fmaf(gx, gx, gy * gy));
             float dxm, dym;
@@ -350,7 +366,9 @@ __global__ void kk_kernel(KKArgs a) {
     for (int v = gl; v < n; v += G) a.xy[q0 + v - a.qbase] = pos[v];
 }
 
-size_t kk_group_bytes(int maxn, bool glob, int rs) { return kk_group_layout(maxn, glob, rs).bytes; }
+size_t kk_group_bytes(int maxn, bool glob, int rs, int slots) {
+    return kk_group_layout(maxn, glob, rs, slots).bytes;
+}
 
 
 // lanes per component of the three largest size classes: 32 (0), 16 (1) or
@@ -407,7 +425,7 @@ static void kk_prepare_class(KkRun &run, int64_t c0, int64_t c1) {
     if (maxn < 1) maxn = 1;
     k->maxn = maxn;
     const bool glob = maxn > KK_SMEM_MAX_N;
-    const size_t gb = kk_group_bytes(maxn, glob, kk_smem_stride(G, CPL, maxn));
+    const size_t gb = kk_group_bytes(maxn, glob, kk_smem_stride(G, CPL, maxn), G * CPL);
     const int max_groups = 256 / G;
     k->gpb = (int)std::min<size_t>(max_groups, std::max<size_t>(1, (size_t)(200 * 1024) / gb));
     k->smem = KK_TABLE_BYTES + gb * k->gpb;
