@@ -325,32 +325,31 @@ __global__ void kk_kernel(KKArgs a) {
             // next row (m + 1, or row 0 for the next sweep) in flight
             dn.load(dist + (size_t)(m + 1 < n ? m + 1 : 0) * ds, gl, ds);
             const float2 pm = pos[m];
-            float gx = 0.f, gy = 0.f, hxx = 0.f, hxy = 0.f, hyy = 0.f;
+            // (g_x, g_y) and (H_yy, H_xx) accumulate in FP32x2 pairs, each
+            // component the same operations as the scalar terms
+            float2 g2 = make_float2(0.f, 0.f), h2 = make_float2(0.f, 0.f);
+            float hxy = 0.f;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
                 if (j * G >= n) break;                   // the group's component has no node there
                 const float2 kl = s_kl[d.get(j)];
                 const float2 pi = pos[gl + j * G];
-                const float dx = pm.x - pi.x, dy = pm.y - pi.y;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
+                const float2 d = __ffma2_rn(pi, make_float2(-1.f, -1.f), pm);   // p_m - p_i, exact sign flip
+                const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, 1e-30f));
                 const float rinv = rsqrtf(r2);
                 // w = k l / r^3 (k l first: zero for the node itself, whose
                 // 1/r^3 would overflow), c = k - w r^2 = k (1 - l / r)
                 const float w = (kl.y * rinv) * (rinv * rinv);
                 const float c = fmaf(-w, r2, kl.x);
-                gx = fmaf(c, dx, gx);
-                gy = fmaf(c, dy, gy);
-                const float wdx = w * dx, wdy = w * dy;
-                hxx = fmaf(-wdy, dy, hxx);
-                hyy = fmaf(-wdx, dx, hyy);
-                hxy = fmaf(wdx, dy, hxy);
+                g2 = __ffma2_rn(make_float2(c, c), d, g2);
+                const float2 nwd = __fmul2_rn(make_float2(-w, -w), d);         // (-w dx, -w dy)
+                h2 = __ffma2_rn(nwd, make_float2(d.x, d.y), h2);                 // H_yy -= w dx^2, H_xx -= w dy^2
+                hxy = fmaf(-nwd.x, d.y, hxy);
             }
-            const float2 gs = group_sum2<G>(make_float2(gx, gy), gmask);
-            const float2 hs = group_sum2<G>(make_float2(hxx, hyy), gmask);
-            gx = gs.x;
-            gy = gs.y;
-            hxx = hs.x;
-            hyy = hs.y;
+            // h2 holds (H_yy, H_xx)
+            const float2 gs = group_sum2<G>(g2, gmask);
+            const float2 hs = group_sum2<G>(make_float2(h2.y, h2.x), gmask);
+            const float gx = gs.x, gy = gs.y, hxx = hs.x, hyy = hs.y;
             hxy = group_sum<G>(hxy, gmask);
             const float km = ksum[m];
             gmax2 = fmaxf(gmax2, fmaf(gx, gx, gy * gy));
