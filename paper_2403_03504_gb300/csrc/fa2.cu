@@ -225,7 +225,6 @@ struct RedArgs {
     const Tile *tiles;        // node tiles, each inside one component
     const int64_t *tile_off;  // per component: first tile, [ncomp+1]
     int ncomp;
-    int ntiles;
     const float2 *f, *fprev;
     const float *mass;
     int64_t qbase;
@@ -233,7 +232,7 @@ struct RedArgs {
     double tau;
     double2 *partial;         // [ntiles]
     double *sg;               // [ncomp]
-    unsigned *counter;        // zero between launches
+    unsigned *counter;        // [ncomp] tiles of each component done, zero between launches
     double *stats;            // optional, component 0
     int *iter;                // iteration counter for stats
 };
@@ -267,53 +266,54 @@ __global__ void swing_traction_kernel(RedArgs a) {
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s += ws[w]; u += wt[w]; }
         a.partial[blockIdx.x] = make_double2(s, u);
         __threadfence();
-        unsigned done = atomicAdd(a.counter, 1u);
-        last = done == (unsigned)(a.ntiles - 1);
+        const unsigned ntc = (unsigned)(a.tile_off[t.comp + 1] - a.tile_off[t.comp]);
+        last = atomicAdd(&a.counter[t.comp], 1u) == ntc - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the last block: one warp per component.  It adds the component's tile
-    // sums in the fused iteration's order: "thread" t (0..255) of eight
-    // virtual warps sums the tiles t, t + 256, ... in order, each virtual
-    // warp's 32 sums go through the same butterfly, and the eight results are
-    // added in warp order (a butterfly leaves the same value in every lane)
-    const int nwarps = (int)(blockDim.x >> 5);
-    for (int c = warp; c < a.ncomp; c += nwarps) {
-        const int64_t k0 = a.tile_off[c], nk = a.tile_off[c + 1] - k0;
-        double swg = 0.0, trc = 0.0;
-        // (a virtual warp past the component's tiles adds +0.0 to a sum of
-        // norms, which changes nothing: it is skipped)
-        for (int w = 0; w < RED_TILE / 32 && 32 * w < nk; ++w) {
-            double s = 0.0, u = 0.0;
-            for (int64_t k = 32 * w + lane; k < nk; k += RED_TILE) {
-                const double2 v = __ldcg(&a.partial[k0 + k]);   // written by other blocks: bypass L1
-                s += v.x;
-                u += v.y;
-            }
+    // the component's last tile to finish adds its tile sums in the fused
+    // iteration's order (combine_kernel's last block, also 256 threads):
+    // thread t sums the tiles t, t + 256, ... in order, a butterfly in each
+    // warp, then the warps' results in warp order
+    const int c = t.comp;
+    const int64_t k0 = a.tile_off[c], nk = a.tile_off[c + 1] - k0;
+    double swg = 0.0, trc = 0.0;
+    for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) {
+        const double2 v = __ldcg(&a.partial[k0 + k]);   // written by other blocks: bypass L1
+        swg += v.x;
+        trc += v.y;
+    }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s += __shfl_xor_sync(0xffffffffu, s, o);
-                u += __shfl_xor_sync(0xffffffffu, u, o);
-            }
-            swg += s;
-            trc += u;
+    for (int o = 16; o > 0; o >>= 1) {
+        swg += __shfl_xor_sync(0xffffffffu, swg, o);
+        trc += __shfl_xor_sync(0xffffffffu, trc, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        ws[warp] = swg;
+        wt[warp] = trc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        swg = 0.0;
+        trc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            swg += ws[w];
+            trc += wt[w];
         }
-        if (lane == 0) {
-            const double s_new = fa2_global_speed(swg, trc, a.sg[c], a.tau);
-            a.sg[c] = s_new;
-            if (c == 0 && a.stats) {
-                int it = *a.iter;
+        const double s_new = fa2_global_speed(swg, trc, a.sg[c], a.tau);
+        a.sg[c] = s_new;
+        if (c == 0) {
+            if (a.stats) {
+                const int it = *a.iter;
                 a.stats[3 * it] = swg;
                 a.stats[3 * it + 1] = trc;
                 a.stats[3 * it + 2] = s_new;
             }
+            *a.iter += 1;
         }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *a.counter = 0u;
-        *a.iter += 1;
+        a.counter[c] = 0u;
     }
 }
 
@@ -583,8 +583,8 @@ struct Fa2Run {
         std::vector<double> ones(c1 - c0, 1.0);
         sg.reset(A, c1 - c0);
         BGL_CUDA(cudaMemcpyAsync(sg.p, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, s));
-        counter.reset(A, 1);
-        BGL_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned), s));
+        counter.reset(A, std::max<int64_t>(c1 - c0, 1));
+        BGL_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned) * std::max<int64_t>(c1 - c0, 1), s));
         iter.reset(A, 1);
         BGL_CUDA(cudaMemsetAsync(iter.p, 0, sizeof(int), s));
         loop.reset(A, 1);
@@ -687,7 +687,6 @@ struct Fa2Run {
         a.tiles = red_tiles.p;
         a.tile_off = red_tile_off.p;
         a.ncomp = (int)(c1 - c0);
-        a.ntiles = n_red_tiles;
         a.f = f.p - (q0 - qbase);
         a.fprev = fprev.p - (q0 - qbase);
         a.mass = g->mass.p;
