@@ -1,23 +1,26 @@
 // Kamada-Kawai layout of small components (Section 3.1) and the initial
 // positions shared by every component.
 //
-// A group of lanes lays out one component of at most 255 nodes:
-//  1. all-pairs hop distances by a BFS from every node (lane s runs the BFS
-//     of sources s, s+32, ...) into a uint8 matrix -- in shared memory for
-//     components of up to 64 nodes, in global memory (one BFS row per lane
-//     staged in shared memory) for larger ones, so that a few large
-//     components do not take all of an SM's shared memory; with unit edge
-//     weights this equals the Floyd-Warshall result the paper names, at
-//     O(n (n + E)) instead of O(n^3) work;
-//  2. optional initial positions (SplitMix64 per node id) scaled by
-//     l * diameter / 2;
+// A group of G lanes lays out one component of at most 255 nodes; lane gl
+// owns the nodes gl, gl + G, ... (CPL of them at most):
+//  1. all-pairs hop distances by a BFS from every node into a uint8 matrix:
+//     for components of up to 64 nodes in shared memory (lane s runs the
+//     BFS of sources s, s + G, ...), for larger ones in global memory (the
+//     group expands one source at a time in a shared row), so that a few
+//     large components do not take all of an SM's shared memory; with unit
+//     edge weights this equals the Floyd-Warshall result the paper names, at
+//     O(n (n + E)) instead of O(n^3) work.  For the sweeps each row holds a
+//     lane's distances contiguously (rewritten after the BFS in shared
+//     memory), so a lane reads its part of a row with one vector load;
+//  2. optional initial positions (SplitMix64 per node id, or per the seed
+//     id a graph carries) scaled by l * diameter / 2, in shared memory;
 //  3. Gauss-Seidel sweeps: for m = 0..n-1 the lanes sum the gradient and
 //     Hessian of the KK energy over all i != m (each lane over its own
-//     consecutive nodes, positions in registers; xor-butterfly reduction so
-//     every lane holds identical sums), take a safeguarded 2x2
-//     Newton-Raphson step (kk_step, FP32; the FP64 rate of GB300 is a small
-//     fraction of its FP32 rate) and the owner lane moves p_m.
-// Small components share a warp: lane groups of 4, 8, 16 or 32 lanes by
+//     nodes; xor-butterfly sums so every lane holds identical totals), take
+//     a safeguarded 2x2 Newton-Raphson step (kk_step, FP32; the FP64 rate of
+//     GB300 is a small fraction of its FP32 rate) and the owner lane moves
+//     p_m.
+// Small components share a warp: lane groups of 4, 8 or 16 lanes by
 // component size class, each group laying out its own component.
 #include <algorithm>
 #include <memory>
