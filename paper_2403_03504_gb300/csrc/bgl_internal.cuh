@@ -139,8 +139,8 @@ namespace bgl {
 // device address of the allocation-free iteration's scratch array on the
 // current device (cudaGetSymbolAddress; allocates nothing)
 void *noalloc_scratch_address();
-// ALU throughput probes (probe.cu): out[4] = FP32 lanes, MUFU reciprocals and
-// pairs per SM clock, and the SM count
+// ALU throughput probes (probe.cu): out[5] = FP32 lanes, MUFU reciprocals and
+// pairs per SM clock, the SM count, and packed FP32x2 pairs per SM clock
 void peak_probe(bgl_ctx *c, double *out);
 struct Fa2Session;
 void fa2_session_destroy(Fa2Session *s);

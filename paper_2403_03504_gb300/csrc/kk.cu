@@ -510,9 +510,10 @@ static int64_t first_at_most(const bgl_graph *g, int64_t c0, int64_t c1, int64_t
     return lo;
 }
 
-// Components in size classes: (128, 255] nodes 32 lanes x up to 8 nodes
-// each, (64, 128] 32 x 4, (32, 64] 32 x 2, (16, 32] 16 x 2, (8, 16] 8 x 2,
-// (4, 8] 4 x 2, <= 4 4 x 1; distances in global memory above 64 nodes.
+// Components in size classes (lanes x nodes per lane, BGL_KK_WIDE = 1 and
+// BGL_KK_NARROW = 1): (128, 255] nodes 16 x 16, (64, 128] 16 x 8, (32, 64]
+// 16 x 4, (16, 32] 8 x 4, (8, 16] 4 x 4, (4, 8] 4 x 2, <= 4 4 x 1; distances
+// in global memory above 64 nodes.
 // Preparing allocates every class's scratch (held until the run is
 // destroyed) so that the launches need no allocation and no synchronisation.
 KkRun *kk_prepare(bgl_graph *g, int64_t c0, int64_t c1) {
