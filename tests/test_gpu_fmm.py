@@ -120,6 +120,25 @@ def test_fmm_sort_passes_follow_tree_depth(path30k):
     assert deep["sortmode_rel_diff"] == 0.0
 
 
+def test_fmm_device_loop_equals_host_loop_across_tree_depths(path30k, monkeypatch):
+    """In the device-side loop the sort's two low radix passes sit under a
+    graph IF node whose condition the keys kernel sets from the sort-pass
+    skip; the host loop launches them and they return at once.  From a
+    clustered start (trees deeper than 8 levels: the full sort) and a uniform
+    one (shallow trees: two passes skipped after the first evaluation) the
+    positions and statistics of both loops are bitwise the same."""
+    bgl = _bgl()
+    p = bgl.params(repulsion=bgl.REP_FMM, fmm_p=8)
+    for xy in (synth.points(5, path30k.n, "clustered", scale=20.0), synth.points(7, path30k.n, "uniform", scale=50.0)):
+        monkeypatch.delenv("BGL_HOST_LOOP", raising=False)
+        a, sa = path30k.g.fa2_step(0, p, 6, xy)
+        monkeypatch.setenv("BGL_HOST_LOOP", "1")
+        b, sb = path30k.g.fa2_step(0, p, 6, xy)
+        monkeypatch.delenv("BGL_HOST_LOOP", raising=False)
+        assert np.all(np.isfinite(a))
+        assert np.array_equal(a, b) and np.array_equal(sa, sb)
+
+
 def test_fmm_small_leaf_sizes(path30k):
     bgl = _bgl()
     xy = synth.points(5, path30k.n, "clustered", scale=20.0)
