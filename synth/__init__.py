@@ -16,6 +16,7 @@ Section 4 / Figs. 4-5):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -113,6 +114,23 @@ def forest(seed: int, n_comp: int, lo: float, hi: float):
     u = np.zeros(ne.value, np.int32)
     v = np.zeros(ne.value, np.int32)
     lib.synth_forest_edges(seed, n_comp, _p(sizes), _p(u), _p(v))
+    return sizes, u, v
+
+
+def forest_of_sizes(seed: int, sizes):
+    """The recipe of `forest` (random recursive trees, round(0.1 (n - 1))
+    extra edges each where they fit) with the given component sizes.
+
+    Returns (sizes[int64], u[int32 m], v[int32 m])."""
+    lib = _load()
+    sizes = np.ascontiguousarray(sizes, np.int64)
+    ne = 0
+    for n in sizes.tolist():
+        extra = int(math.floor(0.1 * (n - 1) + 0.5))
+        ne += (n - 1) + min(extra, n * (n - 1) // 2 - (n - 1))
+    u = np.zeros(ne, np.int32)
+    v = np.zeros(ne, np.int32)
+    lib.synth_forest_edges(seed, len(sizes), _p(sizes), _p(u), _p(v))
     return sizes, u, v
 
 

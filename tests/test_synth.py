@@ -75,3 +75,15 @@ def test_forest_recipe():
     assert nc == len(sizes)                                  # every component connected, none merged
     starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
     assert np.array_equal(lab[starts], np.arange(len(sizes)))  # consecutive ids per component
+
+
+def test_forest_of_given_sizes_follows_the_same_recipe():
+    sizes, u, v = synth.forest(17, 300, 3.0, 200.0)
+    s2, u2, v2 = synth.forest_of_sizes(17, sizes)
+    assert np.array_equal(s2, sizes) and np.array_equal(u2, u) and np.array_equal(v2, v)
+    want = [1, 2, 3, 4, 5, 8, 9, 16, 17, 32, 33, 255]
+    s3, u3, v3 = synth.forest_of_sizes(23, want)
+    n = int(s3.sum())
+    g = sp.coo_matrix((np.ones(len(u3)), (u3, v3)), shape=(n, n)).tocsr()
+    nc, lab = connected_components(g, directed=False)
+    assert nc == len(want) and np.array_equal(np.bincount(lab), want)
