@@ -240,6 +240,41 @@ def run_precision(args, rank, world, dist, local):
     ctx.close()
 
 
+def c3_edges():
+    """The batched-components graph: 1e5 forest components of 3-200 nodes,
+    then 2e3 of 200-5,000 (node ids consecutive per component)."""
+    import synth
+    ss, us, vs = synth.forest(**synth.C3_SMALL)
+    sm, um, vm = synth.forest(**synth.C3_MID)
+    n_small = int(ss.sum())
+    n = n_small + int(sm.sum())
+    u = np.concatenate([us, um + n_small]).astype(np.int32)
+    v = np.concatenate([vs, vm + n_small]).astype(np.int32)
+    return n, u, v
+
+
+def c3_kk_kernels(bgl, local):
+    """Profiling case: the Kamada-Kawai size classes of the batched layout
+    alone (no ForceAtlas2 iterations), twice, launched from the host."""
+    import torch
+    n, u, v = c3_edges()
+    ctx = bgl.Context(local)
+    g = bgl.Graph.from_edges(ctx, n, u, v)
+    g.components(labels=False)
+    p_kk = bgl.params(seed=0, fa2_iters=0, repulsion=bgl.REP_AUTO, kk_max_nodes=200)
+    d_xy = torch.empty((n, 2), dtype=torch.float32, device=torch.device("cuda", local))
+    ms = []
+    for _ in range(2):
+        t = time.perf_counter()
+        g.layout_dev(p_kk, d_xy)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t) * 1e3)
+    print(json.dumps({"kernels_only": True, "workload": "c3-kk", "kk_components": int(g.split(200)[0]),
+                      "layout_ms": ms}))
+    g.destroy()
+    ctx.close()
+
+
 def c3_measure(bgl, local, steps, warmup, iters=50, rank=0, world=1, dist=None):
     """Batched components: 100,000 forest components of 3-200 nodes (KK, at
     most 200 nodes) and 2,000 of 200-5,000 nodes (ForceAtlas2, exact or FMM
@@ -249,15 +284,9 @@ def c3_measure(bgl, local, steps, warmup, iters=50, rank=0, world=1, dist=None):
     (longest-processing-time packing).  Returns the step times, the KK-only
     times and the ForceAtlas2 node-updates/s."""
     import torch
-    import synth
     from paper_2403_03504_gb300 import shard
 
-    ss, us, vs = synth.forest(**synth.C3_SMALL)
-    sm, um, vm = synth.forest(**synth.C3_MID)
-    n_small = int(ss.sum())
-    n = n_small + int(sm.sum())
-    u = np.concatenate([us, um + n_small]).astype(np.int32)
-    v = np.concatenate([vs, vm + n_small]).astype(np.int32)
+    n, u, v = c3_edges()
     ctx = bgl.Context(local)
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     ctx.set_stream(stream)
@@ -320,6 +349,10 @@ def c3_measure(bgl, local, steps, warmup, iters=50, rank=0, world=1, dist=None):
 def run_c3(args, rank, world, dist, local):
     """The batched-components workload as its own bench line."""
     import paper_2403_03504_gb300 as bgl
+    if args.kernels_only:
+        if rank == 0:
+            c3_kk_kernels(bgl, local)
+        return
     c3 = c3_measure(bgl, local, args.steps, args.warmup, args.iters, rank, world, dist)
     if rank == 0:
         print(json.dumps({
@@ -526,7 +559,8 @@ def main():
                     help="profiling case: warm-up and timed steps only (no end-to-end leg, no diagnostics); "
                          "prints the device-resident step times")
     ap.add_argument("--kernels-only", action="store_true",
-                    help="profiling case: FMM and exact repulsion on the giant component only")
+                    help="profiling case: FMM and exact repulsion on the giant component only "
+                         "(with --workload c3: the Kamada-Kawai classes of the batched layout only)")
     ap.add_argument("--positions", default="",
                     help="with --kernels-only: giant-component positions from this .npy file "
                          "(written by --save-positions) instead of N(0, 300^2) points")
