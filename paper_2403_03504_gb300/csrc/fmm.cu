@@ -2442,17 +2442,29 @@ static void launch_down(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
         m2l_kernel<PT, false><<<pl->grid_p, 256, 0, s>>>(a);
     BGL_LAUNCH_CHECK();
 }
-// persistent near-field grid: every resident block of every SM
-static int near_blocks_per_sm() {
-    static const int bps = [] {
+// Persistent near-field grid: every resident block of every SM when the
+// near field runs alone, one block per SM fewer when the far-field kernels
+// run beside it on the side stream.  Four near blocks take nearly all of an
+// SM's registers, so the latency-bound far-field kernels beside them found
+// no room until near blocks retired (bench step 149.3 ms with four near
+// blocks per SM, 147.7 with three, 154.3 with two).  BGL_NEAR_BLOCKS_PER_SM
+// (read once per process) sets the count for both cases, up to the
+// resident maximum.
+static int near_blocks_per_sm(bool beside) {
+    static const int full = [] {
         int b = 0;
         BGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, near_kernel, NEAR_WARPS * 32, 0));
         return b > 0 ? b : 1;
     }();
-    return bps;
+    static const int forced = [] {
+        const char *v = std::getenv("BGL_NEAR_BLOCKS_PER_SM");
+        return v ? std::atoi(v) : 0;
+    }();
+    if (forced > 0) return std::min(forced, full);
+    return beside && full > 1 ? full - 1 : full;
 }
-static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
-    near_kernel<<<pl->g->ctx->num_sms * near_blocks_per_sm(), NEAR_WARPS * 32, 0, s>>>(la);
+static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s, bool beside) {
+    near_kernel<<<pl->g->ctx->num_sms * near_blocks_per_sm(beside), NEAR_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
 }
 template <int PT>
@@ -2492,7 +2504,7 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
         if (ev) BGL_CUDA(cudaEventRecord(ev[4], s));
         launch_down<PT>(pl, a, s);
         if (ev) BGL_CUDA(cudaEventRecord(ev[5], s));
-        launch_near(pl, la, s);
+        launch_near(pl, la, s, false);
         if (ev) BGL_CUDA(cudaEventRecord(ev[6], s));
         launch_far<PT>(pl, la, s);
         if (fa_ready) BGL_CUDA(cudaStreamWaitEvent(s, fa_ready, 0));
@@ -2506,7 +2518,7 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
     launch_up<PT>(pl, a, t);
     phase_lists(pl, T, s);
     BGL_CUDA(cudaEventRecord(pl->ev[1], s));           // lists built
-    launch_near(pl, la, s);
+    launch_near(pl, la, s, true);
     BGL_CUDA(cudaStreamWaitEvent(t, pl->ev[1], 0));
     launch_down<PT>(pl, a, t);
     launch_far<PT>(pl, la, t);
