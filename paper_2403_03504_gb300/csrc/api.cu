@@ -118,8 +118,11 @@ using namespace bgl;
 
 namespace {
 
+// Runs one C-ABI call: device made current, exceptions turned into statuses,
+// and the call's NVTX range named after the calling entry point.
 template <class F>
-bgl_status guarded(bgl_ctx *c, F &&fn) {
+bgl_status guarded(bgl_ctx *c, F &&fn, const char *name = __builtin_FUNCTION()) {
+    BGL_RANGE(name);
     try {
         if (c) BGL_CUDA(cudaSetDevice(c->device));
         fn();

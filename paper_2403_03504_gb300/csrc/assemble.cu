@@ -292,6 +292,7 @@ __global__ void compose_kernel(int64_t n, const float2 *__restrict__ xy, const i
 
 void assemble_device(bgl_graph *g, const bgl_params *p, const float2 *xy_comp, float2 *xy_out_nodes,
                      AssemblyOut *info) {
+    BGL_RANGE("assembly into one frame (Section 4)");
     bgl_ctx *ctx = g->ctx;
     cudaStream_t s = ctx->stream;
     Allocator *A = ctx->alloc;

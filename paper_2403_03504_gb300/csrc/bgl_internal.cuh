@@ -39,6 +39,32 @@ int64_t launch_count();
         if (!(cond)) ::bgl::fail(BGL_EINVAL, msg); \
     } while (0)
 
+// ------------------------------------------------------------- tracing
+
+// NVTX range over a host-side phase: every C-ABI call, and inside a layout
+// the graph build, components, size split, Kamada-Kawai and ForceAtlas2
+// phases and the FMM evaluation's phases.  A trace tool that is attached
+// (NVTX injection) shows them on its timeline and maps them onto the
+// kernels launched inside; without one a range costs a few nanoseconds.
+// Ranges are host markers: work captured into a CUDA graph is marked where
+// it was captured (once per layout), not where the graph replays it.
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+#else
+struct Range {
+    explicit Range(const char *) {}
+};
+#endif
+#define BGL_RANGE_CAT2(a, b) a##b
+#define BGL_RANGE_CAT(a, b) BGL_RANGE_CAT2(a, b)
+#define BGL_RANGE(name) ::bgl::Range BGL_RANGE_CAT(bgl_range_, __LINE__)(name)
+
 // ------------------------------------------------------------- allocator
 
 // Caching device allocator: freed blocks are kept per context and reused

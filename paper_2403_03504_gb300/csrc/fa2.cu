@@ -675,6 +675,7 @@ struct Fa2Run {
 
     // one full iteration (K1..K4)
     void iteration(double *d_stats) {
+        BGL_RANGE("ForceAtlas2 iteration: forces, swing/traction, update (Section 3.2)");
         cudaStream_t s = g->ctx->stream;
         if (fused) {
             // K3 in the FMM's combine pass, K4 with the next root square
@@ -901,6 +902,7 @@ void fa2_layout(bgl_graph *g, const bgl_params *p, float2 *xy, int64_t qbase, in
         if (side) side(g->ctx->stream);
         return;
     }
+    BGL_RANGE("ForceAtlas2 iterations (Section 3.2)");
     Fa2Run run(g, p, xy, qbase, c0, c1);
     run_iterations(run, iters, d_stats, side);
 }

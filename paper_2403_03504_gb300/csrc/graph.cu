@@ -329,6 +329,7 @@ static void finish_edges(bgl_graph *g, uint64_t *ekey, int64_t m, int b) {
 
 void graph_build_device(bgl_graph *g, int64_t T, int64_t n_in, int64_t n_out, const int64_t *d_in_off,
                         const uint64_t *d_in_addr, const int64_t *d_out_off, const uint64_t *d_out_addr) {
+    BGL_RANGE("graph build (Section 2)");
     bgl_ctx *c = g->ctx;
     Allocator *A = c->alloc;
     cudaStream_t s = c->stream;
@@ -384,6 +385,7 @@ void graph_build_device(bgl_graph *g, int64_t T, int64_t n_in, int64_t n_out, co
 }
 
 void graph_from_edges_device(bgl_graph *g, int64_t n, int64_t m, const int32_t *d_u, const int32_t *d_v) {
+    BGL_RANGE("graph from edges");
     bgl_ctx *c = g->ctx;
     g->n_tx = 0;
     g->n_addr = 0;
@@ -398,6 +400,7 @@ void graph_from_edges_device(bgl_graph *g, int64_t n, int64_t m, const int32_t *
 }
 
 void components_device(bgl_graph *g) {
+    BGL_RANGE("components (Section 4)");
     bgl_ctx *c = g->ctx;
     Allocator *A = c->alloc;
     cudaStream_t s = c->stream;
@@ -472,6 +475,7 @@ void components_device(bgl_graph *g) {
 }
 
 void split_device(bgl_graph *g, int32_t kk_max) {
+    BGL_RANGE("size split (Section 4)");
     if (!g->has_comp) fail(BGL_ESTATE, "split: run bgl_components first");
     BGL_REQUIRE(kk_max >= 0, "split: kk_max_nodes must be >= 0");
     // components are sorted by size descending: FA2 ones come first

@@ -517,6 +517,7 @@ static int64_t first_at_most(const bgl_graph *g, int64_t c0, int64_t c1, int64_t
 // Preparing allocates every class's scratch (held until the run is
 // destroyed) so that the launches need no allocation and no synchronisation.
 KkRun *kk_prepare(bgl_graph *g, int64_t c0, int64_t c1) {
+    BGL_RANGE("Kamada-Kawai: size classes, scratch, BFS distances (Section 3.1)");
     auto run = std::make_unique<KkRun>();
     run->g = g;
     if (c1 > c0) {
@@ -556,6 +557,7 @@ int kk_classes(const KkRun *run) { return (int)run->cls.size(); }
 // launches size class i on stream s
 void kk_enqueue(const KkRun *run, int i, const bgl_params *p, float2 *xy, int64_t qbase, bool init, int sweeps,
                 int32_t *d_out, cudaStream_t s) {
+    BGL_RANGE("Kamada-Kawai: Newton sweeps of one size class (Section 3.1)");
     const KkClass &k = *run->cls[i];
     switch (k.G * 64 + k.CPL) {
 #if BGL_KK_WIDE == 2

@@ -306,6 +306,7 @@ struct Extracted {
 };
 
 static void extract(Server *S, bgl_ctx *ctx, KhopScratch &ws, Extracted &x) {
+    BGL_RANGE("serving: k-hop extraction");
     ServeRequest *r = x.r;
     x.n = khop_extract(ctx, S->R, ws, r->seed, r->hops, r->cap, x.u, x.v, x.m);
     if (x.n < 0) fail(BGL_EINVAL, "neighbourhood larger than max_nodes");
@@ -324,6 +325,7 @@ static void extract(Server *S, bgl_ctx *ctx, KhopScratch &ws, Extracted &x) {
 // seed ids, adjacency and the parameters: every request's coordinates are
 // bitwise those of its own layout.
 static void layout_group(Server *S, bgl_ctx *ctx, std::vector<Extracted> &grp) {
+    BGL_RANGE("serving: layout of a request group");
     int64_t n = 0, m = 0;
     for (auto &x : grp) {
         n += x.n;
