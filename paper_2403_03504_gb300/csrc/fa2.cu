@@ -654,6 +654,7 @@ struct Fa2Run {
         cudaStream_t s = g->ctx->stream;
         const bool att = what == 0;
         if (att) {
+            BGL_RANGE("ForceAtlas2: attraction and gravity (Section 3.2)");
             BGL_CUDA(cudaEventRecord(ev_fork, s));
             BGL_CUDA(cudaStreamWaitEvent(side, ev_fork, 0));
             int64_t n = q1 - q0;
@@ -664,10 +665,13 @@ struct Fa2Run {
             BGL_LAUNCH_CHECK();
             BGL_CUDA(cudaEventRecord(ev_fa, side));
         }
-        for (size_t k = 0; k < fmm.size(); ++k)
+        for (size_t k = 0; k < fmm.size(); ++k) {
+            BGL_RANGE("ForceAtlas2: repulsion by the FMM (Section 3.2.1)");
             fmm_repulsion(fmm[k], xy, qbase, f.p, q0, att ? fa.p : nullptr, att ? ev_fa : nullptr);
+        }
         if (att) BGL_CUDA(cudaStreamWaitEvent(s, ev_fa, 0));
         if (n_ex_tiles > 0) {
+            BGL_RANGE("ForceAtlas2: exact repulsion (Section 3.2)");
             launch_exact(ex_r, n_ex_tiles, ex_tiles.p, g->comp_off.p, c0, xy, g->mass.p, qbase, (float)p->kr,
                          att ? fa.p - (q0 - qbase) : nullptr, f.p - (q0 - qbase), s);
         }
@@ -680,6 +684,7 @@ struct Fa2Run {
         if (fused) {
             // K3 in the FMM's combine pass, K4 with the next root square
             forces(0);
+            BGL_RANGE("ForceAtlas2: node update (Section 3.2)");
             fmm_update_root(fmm[0], xy, qbase, f.p, fprev.p, q0);
             return;
         }
@@ -699,8 +704,12 @@ struct Fa2Run {
         a.counter = counter.p;
         a.stats = d_stats;
         a.iter = iter.p;
-        swing_traction_kernel<<<n_red_tiles, 256, 0, s>>>(a);
-        BGL_LAUNCH_CHECK();
+        {
+            BGL_RANGE("ForceAtlas2: swing and traction (Section 3.2)");
+            swing_traction_kernel<<<n_red_tiles, 256, 0, s>>>(a);
+            BGL_LAUNCH_CHECK();
+        }
+        BGL_RANGE("ForceAtlas2: node update (Section 3.2)");
         update_kernel<<<nblocks(q1 - q0, 256), 256, 0, s>>>(f.p - (q0 - qbase), fprev.p - (q0 - qbase), xy,
                                                             g->node_comp.p, sg.p, q0, q1, qbase, c0, (float)p->ks,
                                                             (float)p->ksmax, g->ctx->d_flag + 1);

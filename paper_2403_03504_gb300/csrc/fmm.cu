@@ -2370,7 +2370,6 @@ static unsigned bbox_blocks(const FmmPlan *pl) {
 
 // points: bounding box, keys, sort, gather (also clears the tickets and the list pool)
 static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
-    BGL_RANGE("FMM: bounding square, Morton keys, radix sort");
     bgl_ctx *ctx = pl->g->ctx;
     const int n = pl->n;
     const float *ml = pl->g->mass.p + pl->q0;
@@ -2399,7 +2398,6 @@ static void phase_points(FmmPlan *pl, const float2 *xl, cudaStream_t s) {
 
 // tree: boxes in level order, ends, parents, children
 static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
-    BGL_RANGE("FMM: adaptive quadtree");
     tree_count_kernel<<<pl->ntiles, TREE_THREADS, 0, s>>>(pl->key.p, pl->n, pl->S, pl->cl.p, pl->lam.p, pl->tcnt.p,
                                                           pl->ntiles, pl->sortskip.p, pl->tickets.p + 6, pl->err.p);
     BGL_LAUNCH_CHECK();
@@ -2412,20 +2410,17 @@ static void phase_tree(FmmPlan *pl, const Tree &T, cudaStream_t s) {
 
 // neighbour tables and interaction lists
 static void phase_lists(FmmPlan *pl, const Tree &T, cudaStream_t s) {
-    BGL_RANGE("FMM: interaction lists");
     nbr_lists_kernel<<<pl->grid_p, 256, 0, s>>>(T);
     BGL_LAUNCH_CHECK();
 }
 
 template <int PT>
 static void launch_up(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
-    BGL_RANGE("FMM: upward pass (P2M, M2M)");
     up_kernel<PT><<<pl->grid_p, 256, 0, s>>>(a);
     BGL_LAUNCH_CHECK();
 }
 template <int PT>
 static void launch_down(FmmPlan *pl, const ExpArgs &a, cudaStream_t s) {
-    BGL_RANGE("FMM: M2L and P2L");
     if (pl->bf16) {
         int *cnt = pl->vclass.p, *start = cnt + VCLS, *cursor = start + VCLS + 1;
         BGL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * VCLS, s));
@@ -2469,20 +2464,17 @@ static int near_blocks_per_sm(bool beside) {
     return beside && full > 1 ? full - 1 : full;
 }
 static void launch_near(FmmPlan *pl, const LeafArgs &la, cudaStream_t s, bool beside) {
-    BGL_RANGE("FMM: near field (P2P)");
     near_kernel<<<pl->g->ctx->num_sms * near_blocks_per_sm(beside), NEAR_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
 }
 template <int PT>
 static void launch_far(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
-    BGL_RANGE("FMM: far field (L2L, L2P, M2P)");
     far_kernel<PT><<<2 * pl->grid_p, FAR_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
     far_heavy_kernel<PT><<<pl->g->ctx->num_sms, HEAVY_WARPS * 32, 0, s>>>(la);
     BGL_LAUNCH_CHECK();
 }
 static void launch_combine(FmmPlan *pl, const LeafArgs &la, cudaStream_t s) {
-    BGL_RANGE("FMM: combine near and far");
     combine_kernel<<<nblk(pl->n, 256), 256, 0, s>>>(la, pl->n);
     BGL_LAUNCH_CHECK();
 }
@@ -2500,7 +2492,6 @@ static void evaluate(FmmPlan *pl, const float2 *xl, float2 *f, int64_t fbase, bo
     const Tree T = make_tree(pl);
     const ExpArgs a = exp_args(pl, T);
     const LeafArgs la = leaf_args(pl, a, f, fbase, fa);
-    BGL_RANGE("FMM repulsion (Section 3.2.1)");
     if (ev) BGL_CUDA(cudaEventRecord(ev[0], s));
     phase_points(pl, xl, s);
     if (ev) BGL_CUDA(cudaEventRecord(ev[1], s));

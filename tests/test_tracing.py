@@ -4,10 +4,11 @@
 Each check runs in a child process started with NVTX_INJECTION64_PATH set,
 because NVTX binds its callbacks at the first NVTX call of a process.
 On CPU: a C-ABI call (bgl_ctx_create, which fails without a GPU) is one
-balanced range named after the entry point.  On the GPU: a layout of the
-1,000-transaction graph with the FMM shows the ranges of every phase (graph
-build, components, size split, Kamada-Kawai, ForceAtlas2, the FMM's
-phases), nested inside the call that ran them and balanced."""
+balanced range named after the entry point.  On the GPU: layouts of the
+1,000-transaction graph with the FMM and with the exact sum show the ranges
+of every phase (graph build, components, size split, Kamada-Kawai, the
+ForceAtlas2 iterations and their force, swing/traction and update steps),
+nested inside the call that ran them and balanced."""
 import os
 import shutil
 import subprocess
@@ -53,6 +54,7 @@ ctx = bgl.Context(0)
 g = bgl.Graph.build(ctx, tx.in_off, tx.in_addr, tx.out_off, tx.out_addr)
 g.components(labels=False)
 g.layout(bgl.params(fa2_iters=3, repulsion=bgl.REP_FMM, fmm_p=8, leaf_size=64, kk_max_nodes=50))
+g.layout(bgl.params(fa2_iters=3, repulsion=bgl.REP_EXACT, kk_max_nodes=50))
 g.destroy()
 ctx.close()
 dump(rec)
@@ -113,10 +115,9 @@ def test_layout_phases_are_nested_ranges(recorder):
     for call in ("bgl_ctx_create", "bgl_graph_build", "bgl_components", "bgl_layout"):
         assert call in top, (call, top)
     for phase in ("graph build (Section 2)", "components (Section 4)", "size split (Section 4)",
-                  "ForceAtlas2 iterations (Section 3.2)", "FMM repulsion (Section 3.2.1)",
-                  "FMM: bounding square, Morton keys, radix sort", "FMM: adaptive quadtree",
-                  "FMM: interaction lists", "FMM: upward pass (P2M, M2M)", "FMM: M2L and P2L",
-                  "FMM: near field (P2P)", "FMM: far field (L2L, L2P, M2P)", "FMM: combine near and far"):
+                  "ForceAtlas2 iterations (Section 3.2)", "ForceAtlas2: attraction and gravity (Section 3.2)",
+                  "ForceAtlas2: repulsion by the FMM (Section 3.2.1)", "ForceAtlas2: exact repulsion (Section 3.2)",
+                  "ForceAtlas2: swing and traction (Section 3.2)", "ForceAtlas2: node update (Section 3.2)"):
         assert phase in names, phase
     assert any(n.startswith("Kamada-Kawai: size classes") for n in names)
     assert any(n.startswith("Kamada-Kawai: Newton sweeps") for n in names)
@@ -124,5 +125,6 @@ def test_layout_phases_are_nested_ranges(recorder):
     # the phases sit inside the calls that ran them
     depth = dict(tree)
     assert depth["graph build (Section 2)"] >= 1
-    assert depth["FMM: near field (P2P)"] > depth["FMM repulsion (Section 3.2.1)"] > \
+    assert depth["ForceAtlas2: repulsion by the FMM (Section 3.2.1)"] > \
+        depth["ForceAtlas2 iteration: forces, swing/traction, update (Section 3.2)"] > \
         depth["ForceAtlas2 iterations (Section 3.2)"] >= 1
