@@ -207,6 +207,19 @@ def test_bfs_unreachable_marked():
     assert d[0, 1] == 1 and d[0, 2] == -1 and d[2, 3] == -1 and d[3, 3] == 0
 
 
+def test_floyd_warshall_marks_unreachable_pairs_as_bfs_does():
+    """Two paths 0-1-2 and 3-4 plus the isolated node 5: distances inside a
+    part are path lengths, every pair across parts is -1 (both methods)."""
+    g = oracle.graph_from_edges(6, [0, 1, 3], [1, 2, 4])
+    want = np.full((6, 6), -1, np.int32)
+    for part in ([0, 1, 2], [3, 4], [5]):
+        for a in part:
+            for b in part:
+                want[a, b] = abs(a - b)
+    assert np.array_equal(oracle.floyd_warshall(g.off, g.adj), want)
+    assert np.array_equal(oracle.bfs_apsp(g.off, g.adj), want)
+
+
 # ------------------------------------------------------------- Section 3.2 forces
 
 def _two_node():
@@ -374,6 +387,19 @@ def test_kk_gradient_hessian_finite_differences():
         assert np.allclose(o[2:], [hxx, hxy, hyy], rtol=1e-4, atol=1e-5)
 
 
+def test_kk_coincident_pair_contributes_nothing():
+    """A node at the same place as p_m adds no term to p_m's gradient and
+    Hessian (r = 0 has no direction); the other terms are the textbook sums:
+    with p_m = (0, 0), a coincident node and a node at (2, 0) at graph
+    distance 1 (k = 1, l_mi = l = 1): g = (dx - l dx / r, 0) = (-1, 0),
+    H_xx = 1 - l dy^2 / r^3 = 1, H_yy = 1 - l dx^2 / r^3 = 1 / 2, H_xy = 0."""
+    g = oracle.graph_from_edges(3, [0, 0], [1, 2])
+    d = oracle.bfs_apsp(g.off, g.adj)
+    o = oracle.kk_grad_hess(np.array([0.0, 0.0, 2.0]), np.array([0.0, 0.0, 0.0]), d, 1.0, 0)
+    assert np.allclose(o, [-1.0, 0.0, 1.0, 0.0, 0.5], rtol=1e-15, atol=0)
+    assert np.isfinite(oracle.kk_energy(np.array([0.0, 0.0, 2.0]), np.zeros(3), d, 1.0))
+
+
 @pytest.mark.parametrize("case", range(len(_golden("kk_newton_step.json")["cases"])))
 def test_kk_newton_step_golden(case):
     """The safeguarded 2x2 Newton step against hand-worked cases: the plain
@@ -392,6 +418,36 @@ def test_kk_two_nodes_reach_distance_l():
     for l in (1.0, 2.5):
         x, y, e, _, _ = oracle.kk_run([0.3, -0.1], [0.2, 0.4], d, l, 50)
         assert math.hypot(x[0] - x[1], y[0] - y[1]) == pytest.approx(l, rel=1e-12)
+
+
+def test_kk_run_energy_trace_skips_and_tolerance_stop():
+    """The run's outputs by their definitions: energy[s] is the energy after
+    sweep s + 1 (a run of s + 1 sweeps from the same start ends there); a
+    node whose Hessian is zero is skipped and counted, once per sweep; with
+    tol > 0 the run ends after the first sweep in which no node saw a
+    gradient of length tol or more."""
+    rng = np.random.default_rng(8)
+    g = _random_connected(rng, 7, 3)
+    d = oracle.bfs_apsp(g.off, g.adj)
+    x0, y0 = rng.normal(size=7), rng.normal(size=7)
+    _, _, e, skipped, done = oracle.kk_run(x0, y0, d, 1.0, 6)
+    assert done == 6 and skipped == 0 and len(e) == 6
+    for s in range(6):
+        xs, ys, _, _, _ = oracle.kk_run(x0, y0, d, 1.0, s + 1)
+        assert e[s] == oracle.kk_energy(xs, ys, d, 1.0)
+    # two coincident nodes: r = 0 leaves both Hessians zero, both skipped
+    g2 = oracle.graph_from_edges(2, [0], [1])
+    d2 = oracle.bfs_apsp(g2.off, g2.adj)
+    x, y, e2, skipped, done = oracle.kk_run([0.5, 0.5], [1.0, 1.0], d2, 1.0, 3)
+    assert (skipped, done) == (6, 3) and list(x) == [0.5, 0.5] and list(y) == [1.0, 1.0]
+    # already at the minimum: the first sweep sees g = 0 and ends the run
+    x, y, _, _, done = oracle.kk_run([0.0, 1.0], [0.0, 0.0], d2, 1.0, 50, tol=1e-9)
+    assert done == 1
+    # from 3 l apart the first sweep sees |g| > tol, so at least two sweeps
+    # run, and the run ends well before 50 once the distance is l
+    x, y, _, _, done = oracle.kk_run([0.0, 3.0], [0.0, 0.0], d2, 1.0, 50, tol=1e-9)
+    assert 2 <= done < 50
+    assert math.hypot(x[0] - x[1], y[0] - y[1]) == pytest.approx(1.0, abs=1e-9)
 
 
 @pytest.mark.parametrize("n", [3, 4, 5, 6])
@@ -579,6 +635,7 @@ def test_kkw_weighted_path_is_realised_exactly():
     x, y = oracle.init_positions(4, np.arange(4))
     x, y, e = oracle.kkw_run(x * 3, y * 3, d, length[1:].mean(), 300)
     assert e[-1] <= 1e-18 + 1e-12 * e[0]
+    assert e[-1] == oracle.kkw_energy(x, y, d)             # the trace is the energy after each sweep
     r = np.hypot(x[:, None] - x[None], y[:, None] - y[None])
     assert np.allclose(r, d, rtol=1e-6, atol=1e-8)
 
