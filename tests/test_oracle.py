@@ -238,6 +238,12 @@ def test_fa2_two_node_closed_form():
             assert np.allclose(f["fgrav"][0], [0, 0], atol=0)
             assert np.allclose(f["frep"][1], [4 * kr / d, 0], rtol=1e-15)
             assert np.allclose(f["fgrav"][1], [-2 * kg * d, 0], rtol=1e-15)
+            # error scales: repulsion terms kr m_i m_j / d; all terms adds |p_i - p_j| and |kg m_i p_i|
+            assert np.allclose(f["srep"], [4 * kr / d, 4 * kr / d], rtol=1e-15, atol=0)
+            assert np.allclose(f["sabs"], [4 * kr / d + d, 4 * kr / d + d + 2 * kg * d], rtol=1e-15, atol=0)
+            # E = |p0 - p1|^2 / 2 - kr m0 m1 ln|p0 - p1| + kg (m0 |p0|^2 + m1 |p1|^2) / 2
+            e = oracle.fa2_energy([0.0, d], [0.0, 0.0], [2.0, 2.0], off, adj, kr, kg)
+            assert e == pytest.approx(d * d / 2 - 4 * kr * math.log(d) + kg * d * d, rel=1e-14, abs=1e-15)
 
 
 def _comp_c1(kind="largest"):
@@ -299,6 +305,10 @@ def test_fa2_coincident_pair_contributes_nothing():
     adj = np.zeros(0, np.int32)
     f = oracle.fa2_forces([1.0, 1.0, 2.0], [0.0, 0.0, 0.0], [1.0, 1.0, 1.0], off, adj, 1.0, 0.0)
     assert np.allclose(f["frep"][0], [-1.0, 0.0]) and np.all(np.isfinite(f["frep"]))
+    assert f["srep"][0] == 1.0 and f["srep"][2] == 2.0
+    # the energy omits the coincident pair: -ln 2 - ln 2 from the pairs with node 2 at distance 2
+    e = oracle.fa2_energy([1.0, 1.0, 3.0], [0.0, 0.0, 0.0], [1.0, 1.0, 1.0], off, adj, 1.0, 0.0)
+    assert e == pytest.approx(-2 * math.log(2.0), rel=1e-15)
 
 
 def test_fa2_two_node_iterations_golden():
@@ -337,6 +347,28 @@ def test_fa2_swing_variants_golden(variant):
     assert np.allclose(st.x, ev["x"], rtol=1e-14, atol=0)
     assert np.allclose(st.fpx, e["F_x"], rtol=1e-14, atol=0)
     assert np.all(st.y == 0) and np.all(st.fpy == 0)
+
+
+@pytest.mark.parametrize("case", range(len(_golden("fa2_iteration_2d.json")["cases"])))
+def test_fa2_iteration_2d_golden(case):
+    """One iteration of one edge off the axes, worked by hand: tau != 1,
+    s_G != 1 with the 1.5 s_G cap binding and not, the ksmax cap binding for
+    one node only and for forces shorter than 1/2, variant 1, a small swing
+    with a large s_G, and F_t = F_{t-1} (swg = 0)."""
+    gd = _golden("fa2_iteration_2d.json")
+    cm, c = gd["common"], gd["cases"][case]
+    g = oracle.graph_from_edges(2, [0], [1])
+    assert np.array_equal(np.diff(g.off) + 1.0, cm["mass"])
+    st = oracle.FA2State(np.array(c.get("x0", cm["x"])), np.array(c.get("y0", cm["y"])), np.array(c["fprev_x"]),
+                         np.array(c["fprev_y"]), c["sg"])
+    st, stats = oracle.fa2_run(None, None, cm["mass"], g.off, g.adj, 1, c["kr"], c["kg"], cm["ks"], c["ksmax"],
+                               c["tau"], variant=c["variant"], state=st)
+    assert np.allclose(stats[0], c["stats"], rtol=1e-14, atol=1e-15), c["name"]
+    assert np.allclose(st.x, c["x"], rtol=1e-14, atol=1e-15), c["name"]
+    assert np.allclose(st.y, c["y"], rtol=1e-14, atol=1e-15), c["name"]
+    assert np.allclose(st.fpx, c["F_x"], rtol=1e-14, atol=1e-15) and np.allclose(st.fpy, c["F_y"], rtol=1e-14,
+                                                                                 atol=1e-15)
+    assert st.sg == pytest.approx(c["stats"][2], rel=1e-14)
 
 
 def test_fa2_speed_cap_limits_displacement():
