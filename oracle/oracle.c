@@ -44,9 +44,14 @@
  *     random starts where H is indefinite).
  * "parity unpinned": none.  Every function has a pin in tests/test_oracle.py;
  * the safeguarded KK step (orc_kk_step) by hand-worked 2x2 cases
- * (tests/golden/kk_newton_step.json: plain, shortened, indefinite, floored,
- * zero), both swing/traction variants by a hand-worked iteration of a
- * three-node path with unequal masses (tests/golden/fa2_swing_variants.json).
+ * (tests/golden/kk_newton_step.json: plain, shortened, isotropic,
+ * indefinite, floored, a small positive eigenvalue kept, zero), both
+ * swing/traction variants by a hand-worked iteration of a three-node path
+ * with unequal masses (tests/golden/fa2_swing_variants.json), the iteration
+ * off the axes with tau != 1, s_G != 1 and both caps by six hand-worked cases
+ * (tests/golden/fa2_iteration_2d.json).  Every single-operator, constant or
+ * statement mutation of this file that changes a result on valid input
+ * fails one of the pins.
  */
 #include <math.h>
 #include <stdint.h>
