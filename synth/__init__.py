@@ -60,6 +60,10 @@ def _load():
             lib.synth_forest_sizes.restype = None
             lib.synth_forest_edges.argtypes = [ctypes.c_uint64, ctypes.c_int64] + [ctypes.c_void_p] * 3
             lib.synth_forest_edges.restype = None
+            lib.synth_splitmix64_stream.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
+            lib.synth_splitmix64_stream.restype = None
+            lib.synth_zipf_sample.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+            lib.synth_zipf_sample.restype = None
             _lib = lib
     return _lib
 
@@ -154,3 +158,17 @@ def points(seed: int, n: int, kind: str = "uniform", scale: float = 1.0):
     else:
         raise ValueError(kind)
     return np.ascontiguousarray(xy.astype(np.float32))
+
+
+def splitmix64_stream(seed: int, n: int) -> np.ndarray:
+    """The generator's SplitMix64: first n outputs from state `seed` (test hook)."""
+    out = np.zeros(n, np.uint64)
+    _load().synth_splitmix64_stream(seed, n, _p(out))
+    return out
+
+
+def zipf_sample(seed: int, N: int, n: int) -> np.ndarray:
+    """n draws of the generator's Zipf(1.2) sampler on {1..N} (test hook)."""
+    out = np.zeros(n, np.int64)
+    _load().synth_zipf_sample(seed, N, n, _p(out))
+    return out

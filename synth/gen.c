@@ -224,3 +224,18 @@ void synth_forest_edges(uint64_t seed, int64_t n_comp, const int64_t *sizes, int
         base += n;
     }
 }
+
+/* Test hooks of the two samplers above (the generator's own streams are
+ * unchanged by them): the first n outputs of SplitMix64 from state `seed`,
+ * and n Zipf(1.2) draws on {1..N} from the stream with state `seed`. */
+void synth_splitmix64_stream(uint64_t seed, int64_t n, uint64_t *out)
+{
+    sm64 g = { seed };
+    for (int64_t i = 0; i < n; ++i) out[i] = sm64_next(&g);
+}
+
+void synth_zipf_sample(uint64_t seed, int64_t N, int64_t n, int64_t *out)
+{
+    sm64 g = { seed };
+    for (int64_t i = 0; i < n; ++i) out[i] = zipf_draw(&g, N);
+}

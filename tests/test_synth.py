@@ -75,6 +75,15 @@ def test_forest_recipe():
     assert nc == len(sizes)                                  # every component connected, none merged
     starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
     assert np.array_equal(lab[starts], np.arange(len(sizes)))  # consecutive ids per component
+    # no edge twice (as an unordered pair): the extra edges join nodes not already adjacent
+    lo, hi = np.minimum(u, v).astype(np.int64), np.maximum(u, v).astype(np.int64)
+    assert len(np.unique(lo << 32 | hi)) == len(u)
+    # each component starts with its random recursive tree: node k attaches to some j < k
+    e0 = np.concatenate([[0], np.cumsum(sizes - 1 + extra)[:-1]]).astype(np.int64)
+    for c in range(0, len(sizes), 997):
+        k = np.arange(1, sizes[c])
+        assert np.array_equal(v[e0[c] + k - 1], starts[c] + k)
+        assert np.all(u[e0[c] + k - 1] >= starts[c]) and np.all(u[e0[c] + k - 1] < starts[c] + k)
 
 
 def test_forest_of_given_sizes_follows_the_same_recipe():
@@ -87,3 +96,43 @@ def test_forest_of_given_sizes_follows_the_same_recipe():
     g = sp.coo_matrix((np.ones(len(u3)), (u3, v3)), shape=(n, n)).tocsr()
     nc, lab = connected_components(g, directed=False)
     assert nc == len(want) and np.array_equal(np.bincount(lab), want)
+
+
+def test_generator_splitmix64_matches_published_vectors():
+    """The generator's SplitMix64 against the same published vectors as the
+    oracle's (tests/golden/splitmix64.json)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "splitmix64.json")))
+    for v in g["vectors"]:
+        got = synth.splitmix64_stream(v["seed"], 3)
+        if "outputs_hex" in v:
+            assert [f"{int(x):016x}" for x in got] == v["outputs_hex"]
+        else:
+            assert [str(int(x)) for x in got] == v["outputs_dec"]
+
+
+@pytest.mark.parametrize("N", [1, 2, 12, 1000])
+def test_zipf_sampler_follows_the_exact_law(N):
+    """Rejection-inversion Zipf(1.2) on {1..N} against P(k) = k^-1.2 / H:
+    a chi-square test over the first 30 values and the tail beyond (fixed
+    seed, 400,000 draws, rejected at p < 1e-6), and the law's mean."""
+    stats = pytest.importorskip("scipy.stats")
+    n = 400_000
+    x = synth.zipf_sample(77 + N, N, n)
+    assert x.min() >= 1 and x.max() <= N
+    k = np.arange(1, N + 1, dtype=np.float64)
+    p = k ** -1.2
+    p /= p.sum()
+    if N == 1:
+        assert np.all(x == 1)
+        return
+    m = min(N, 30)
+    obs = np.bincount(x, minlength=N + 1)[1:]
+    o = np.append(obs[:m], obs[m:].sum()) if N > m else obs
+    e = np.append(p[:m], p[m:].sum()) * n if N > m else p * n
+    chi2 = float(((o - e) ** 2 / e).sum())
+    assert stats.chi2.sf(chi2, len(o) - 1) > 1e-6, chi2
+    mean = float((k * p).sum())
+    sd = float(np.sqrt((k * k * p).sum() - mean * mean))
+    assert abs(x.mean() - mean) < 6 * sd / np.sqrt(n)
