@@ -98,6 +98,28 @@ def test_cost_model_follows_the_split():
     assert c[3] == 51 ** 2 * 10 and c[4] == shard.FMM_PAIRS_PER_NODE * 9000 * 10
 
 
+def test_cost_model_mirrors_the_library():
+    """The planner's repulsion codes, its default crossover and its exact/FMM
+    rule are the library's (header enum, bgl_params_default, and AUTO using
+    the FMM from fmm_min_nodes nodes on)."""
+    import re
+    import paper_2403_03504_gb300 as bgl
+    from paper_2403_03504_gb300 import shard
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bgl.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"BGL_REP_(EXACT|FMM|AUTO) = (\d+)", hdr))
+    assert (shard.REP_EXACT, shard.REP_FMM, shard.REP_AUTO) == (enum["EXACT"], enum["FMM"], enum["AUTO"])
+    assert (bgl.REP_EXACT, bgl.REP_FMM, bgl.REP_AUTO) == (enum["EXACT"], enum["FMM"], enum["AUTO"])
+    p = bgl.params()
+    import inspect
+    defaults = inspect.signature(shard.component_costs).parameters
+    assert defaults["fmm_min_nodes"].default == p.fmm_min_nodes
+    for name in ("repulsion", "kk_max_nodes", "fa2_iters", "kk_sweeps"):
+        assert defaults[name].default == getattr(p, name), name
+    m = p.fmm_min_nodes
+    c = shard.component_costs([m - 1, m], kk_max_nodes=50, fa2_iters=1, repulsion=shard.REP_AUTO, fmm_min_nodes=m)
+    assert c[0] == (m - 1) ** 2 and c[1] == shard.FMM_PAIRS_PER_NODE * m
+
+
 def _shard_rank(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
