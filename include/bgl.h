@@ -104,6 +104,8 @@ typedef struct bgl_params {
 } bgl_params;
 
 /* ---------------------------------------------------------------- context */
+/* The context calls are the library's own plumbing (device, stream, memory
+ * pool, error text, defaults); the paper has no counterpart for them. */
 
 /* Create a context on CUDA device `device`, with its own non-blocking
  * stream and device memory pool.  *out receives the handle. */
@@ -140,7 +142,7 @@ void bgl_params_default(bgl_params *p);
 bgl_status bgl_graph_build(bgl_ctx *ctx, int64_t n_tx, const int64_t *in_off, const uint64_t *in_addr,
                            const int64_t *out_off, const uint64_t *out_addr, bgl_graph **out);
 
-/* As bgl_graph_build, from device arrays; n_in = in_off[n_tx] and
+/* As bgl_graph_build (Section 2), from device arrays; n_in = in_off[n_tx] and
  * n_out = out_off[n_tx] are passed by the caller.  Offsets are validated on
  * the device (BGL_EINVAL if inconsistent).  Synchronises the stream once. */
 bgl_status bgl_graph_build_dev(bgl_ctx *ctx, int64_t n_tx, int64_t n_in, int64_t n_out,
@@ -154,24 +156,28 @@ bgl_status bgl_graph_build_dev(bgl_ctx *ctx, int64_t n_tx, int64_t n_in, int64_t
 bgl_status bgl_graph_from_edges(bgl_ctx *ctx, int64_t n, int64_t m, const int32_t *u, const int32_t *v,
                                 bgl_graph **out);
 
-/* Sizes of a built graph (any pointer may be NULL). */
+/* Sizes of a built graph of Section 2 (any pointer may be NULL). */
 bgl_status bgl_graph_sizes(const bgl_graph *g, int64_t *n_nodes, int64_t *n_addr, int64_t *n_dir_edges,
                            int64_t *n_undir_edges);
 
-/* Address keys in id order: key_out[k] is the key of node n_tx + k (n_addr entries). */
+/* Address keys in id order (the address nodes of Section 2): key_out[k] is
+ * the key of node n_tx + k (n_addr entries). */
 bgl_status bgl_graph_addresses(const bgl_graph *g, uint64_t *key_out);
 
-/* Directed edges sorted by (src, dst): n_dir_edges entries each. */
+/* Directed edges of Section 2 sorted by (src, dst): n_dir_edges entries each. */
 bgl_status bgl_graph_edges(const bgl_graph *g, int32_t *src, int32_t *dst);
 
-/* Undirected adjacency in CSR form: off[n_nodes+1], adj[2 n_undir_edges],
+/* Undirected adjacency in CSR form (the graph of Section 2 with directions
+ * ignored, as Sections 3 and 4 use it): off[n_nodes+1], adj[2 n_undir_edges],
  * neighbours of each node in ascending id. */
 bgl_status bgl_graph_csr(const bgl_graph *g, int64_t *off, int32_t *adj);
 
-/* deg_out[n_nodes]: number of distinct undirected neighbours. */
+/* deg_out[n_nodes]: number of distinct undirected neighbours (the degree
+ * that sets ForceAtlas2's mass, Section 3.2). */
 bgl_status bgl_degrees(const bgl_graph *g, int32_t *deg_out);
 
-/* Release a graph and its device memory.  NULL is ignored. */
+/* Release a graph and its device memory (plumbing, no counterpart in the
+ * paper).  NULL is ignored. */
 bgl_status bgl_graph_destroy(bgl_graph *g);
 
 /* ------------------------------------------------- components (Section 4) */
@@ -181,7 +187,8 @@ bgl_status bgl_graph_destroy(bgl_graph *g);
  * node's component; *n_comp the number of components. */
 bgl_status bgl_components(bgl_graph *g, int32_t *label_out, int64_t *n_comp);
 
-/* Component order (needs bgl_components): comp_off[n_comp+1] node offsets,
+/* Component order of Section 4's split (needs bgl_components; BGL_ESTATE
+ * otherwise): comp_off[n_comp+1] node offsets,
  * comp_label[n_comp], nodes[n_nodes] node ids grouped by component.  Any
  * pointer may be NULL. */
 bgl_status bgl_component_nodes(const bgl_graph *g, int64_t *comp_off, int32_t *comp_label, int32_t *nodes);
@@ -194,8 +201,9 @@ bgl_status bgl_split(bgl_graph *g, int32_t kk_max_nodes, int64_t *n_kk, int64_t 
 /* ------------------------------------------------------ layout (Section 4) */
 
 /*
- * Lay out every component (needs bgl_components; runs the split with
- * p->kk_max_nodes).  Initial positions: node id v starts at
+ * Lay out every component (Section 4: Kamada-Kawai, Section 3.1, for the
+ * small ones, ForceAtlas2, Section 3.2, for the rest; needs bgl_components,
+ * BGL_ESTATE otherwise; runs the split with p->kk_max_nodes).  Initial positions: node id v starts at
  * (x, y) = ((h1 >> 40) 2^-24 * 2 - 1, (h2 >> 40) 2^-24 * 2 - 1), where h1, h2
  * are the first two outputs of SplitMix64 seeded with
  * p->seed XOR (v * 0x9E3779B97F4A7C15); Kamada-Kawai components scale these
@@ -205,7 +213,7 @@ bgl_status bgl_split(bgl_graph *g, int32_t kk_max_nodes, int64_t *n_kk, int64_t 
  */
 bgl_status bgl_layout(bgl_graph *g, const bgl_params *p, float *xy_out);
 
-/* As bgl_layout, writing the device array d_xy_out[2 n_nodes]; does not
+/* As bgl_layout (Section 4), writing the device array d_xy_out[2 n_nodes]; does not
  * synchronise the stream after the last kernel. */
 bgl_status bgl_layout_dev(bgl_graph *g, const bgl_params *p, float *d_xy_out);
 
@@ -215,20 +223,22 @@ bgl_status bgl_layout_dev(bgl_graph *g, const bgl_params *p, float *d_xy_out);
  * local order.  Components of up to 255 nodes. */
 bgl_status bgl_kk_distances(bgl_graph *g, int64_t c, int32_t *d_out);
 
-/* Kamada-Kawai on component c (at most 255 nodes) from the caller's local
+/* Kamada-Kawai (Section 3.1) on component c (at most 255 nodes, BGL_EINVAL
+ * above) from the caller's local
  * positions xy_inout[2 n_c] (x, y interleaved), p->kk_sweeps sweeps. */
 bgl_status bgl_kk_run(bgl_graph *g, int64_t c, const bgl_params *p, float *xy_inout);
 
-/* One ForceAtlas2 force evaluation on component c at local positions
+/* One ForceAtlas2 force evaluation (Section 3.2; repulsion by Section
+ * 3.2.1's FMM when chosen) on component c at local positions
  * xy_in[2 n_c]: f_out[2 n_c] receives the total force (repulsion + attraction
  * + gravity).  p->repulsion selects the exact sum or the FMM (AUTO follows
  * p->fmm_min_nodes). */
 bgl_status bgl_fa2_forces(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, float *f_out);
 
-/* As bgl_fa2_forces, repulsion only. */
+/* As bgl_fa2_forces, repulsion only (Section 3.2, or 3.2.1 with the FMM). */
 bgl_status bgl_fa2_repulsion(bgl_graph *g, int64_t c, const bgl_params *p, const float *xy_in, float *f_out);
 
-/* `iters` ForceAtlas2 iterations on component c from local positions
+/* `iters` ForceAtlas2 iterations (Section 3.2) on component c from local positions
  * xy_inout[2 n_c], starting from F_{-1} = 0 and s_G = 1.  stats_out
  * (3 * iters doubles, may be NULL) receives swing, traction and s_G of every
  * iteration. */
@@ -460,7 +470,8 @@ bgl_status bgl_fa2_iteration_noalloc(bgl_ctx *ctx, int64_t n, const int64_t *d_o
 bgl_status bgl_peak_probe(bgl_ctx *ctx, double *out);
 
 /* Number of kernels this process has launched through the library so far
- * (direct launches plus the kernel nodes of every CUDA graph replay). */
+ * (direct launches plus the kernel nodes of every CUDA graph replay); a
+ * measurement aid with no counterpart in the paper. */
 int64_t bgl_launch_count(void);
 
 /* Test aid for the failure paths (the paper has no counterpart): after
