@@ -366,7 +366,9 @@ bgl_status bgl_fa2_session_advance(bgl_graph *g, int32_t iters, double *stats_ou
 bgl_status bgl_fa2_session_positions(bgl_graph *g, float *xy_out, int64_t *iters_done);
 
 /*
- * Checkpoint of the graph's session: everything the iteration needs to
+ * Checkpoint of the graph's session (recovery of a long layout; the paper
+ * has no counterpart, what it saves is the state of Section 3.2's
+ * iteration): everything the iteration needs to
  * continue -- positions, F_{t-1}, s_G, the iteration count, the parameters
  * and the FMM's choice of radix passes for its next sort -- in a host
  * buffer owned by the caller, plus the identity of

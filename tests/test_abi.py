@@ -76,3 +76,22 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     lib.bgl_last_error.restype = ctypes.c_char_p
     lib.bgl_last_error.argtypes = [ctypes.c_void_p]
     assert lib.bgl_last_error(None) == b"context is NULL"
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration of bgl.h is documented by a comment -- its own, or the
+    note of its group since the last section divider -- that names the
+    paper's section it implements, or says that the paper has no
+    counterpart (library plumbing and measurement aids)."""
+    src = open(HEADER).read()
+    comments = [(m.start(), m.end(), m.group(0)) for m in re.finditer(r"/\*.*?\*/", src, flags=re.S)]
+    missing = []
+    for m in re.finditer(r"\n(?:bgl_status|void|int64_t|const char \*)\s*(bgl_[a-z0-9_]+)\s*\(", src):
+        group = []
+        for c in reversed([c for c in comments if c[1] <= m.start()]):
+            group.append(c[2])
+            if c[2].startswith("/* ----"):
+                break
+        if not any(re.search(r"Section|counterpart", c) for c in group):
+            missing.append(m.group(1))
+    assert not missing, missing
