@@ -23,7 +23,8 @@ class _FakeGraph:
         self.n, self.done, self.calls = n, 0, []
 
     def component_nodes(self):
-        return np.array([0, self.n], np.int64), None, None
+        # a 3-node component 0 before the session's component 1
+        return np.array([0, 3, 3 + self.n], np.int64), None, None
 
     def session_begin(self, c, p, xy):
         assert len(xy) == self.n
@@ -68,15 +69,20 @@ def test_lines_chunks_and_numbering():
 def test_resume_numbers_on_and_zero_iterations(tmp_path):
     g = _FakeGraph(4)
     path = str(tmp_path / "m.jsonl")
-    metrics.run_logged(g, 0, None, 5, np.zeros((4, 2)), path, chunk=2)
-    metrics.run_logged(g, 0, None, 4, None, str(tmp_path / "m2.jsonl"), chunk=3, resume=True)
+    metrics.run_logged(g, 1, None, 5, np.zeros((4, 2)), path, chunk=1)
+    assert g.calls == [1] * 5
+    xy = metrics.run_logged(g, 1, None, 4, None, str(tmp_path / "m2.jsonl"), chunk=3, resume=True)
+    assert xy.shape == (4, 2)                      # n of component 1, from the component offsets
     assert [r["iter"] for r in metrics.read(path)] == [1, 2, 3, 4, 5]
-    assert [r["iter"] for r in metrics.read(str(tmp_path / "m2.jsonl"))] == [6, 7, 8, 9]
-    assert metrics.run_logged(g, 0, None, 0, np.zeros((4, 2)), None).shape == (4, 2)
+    recs = metrics.read(str(tmp_path / "m2.jsonl"))
+    assert [r["iter"] for r in recs] == [6, 7, 8, 9] and all(r["n"] == 4 and r["component"] == 1 for r in recs)
+    assert metrics.run_logged(g, 1, None, 0, np.zeros((4, 2)), None).shape == (4, 2)
     with pytest.raises(ValueError):
-        metrics.run_logged(g, 0, None, 3, np.zeros((4, 2)), None, chunk=0)
+        metrics.run_logged(g, 1, None, 3, np.zeros((4, 2)), None, chunk=0)
     with pytest.raises(ValueError):
-        metrics.run_logged(g, 0, None, 3, None, None)
+        metrics.run_logged(g, 1, None, -1, np.zeros((4, 2)), None)
+    with pytest.raises(ValueError):
+        metrics.run_logged(g, 1, None, 3, None, None)
 
 
 @pytest.mark.gpu
