@@ -4,14 +4,17 @@ With N GPUs every rank lays out its own replica of the workload (the
 components are independent, nothing is exchanged), and the reported value is
 the units all ranks processed divided by the slowest rank's time.  The GPU
 part needs GPUs; its over-ranks arithmetic and the reference arm's
-single-printer rule do not, and are checked here."""
+single-printer rule do not, and are checked here.  So is the sharding of one
+graph's components over ranks (Section 4: components are independent):
+longest-processing-time packing within Graham's bound, the cost model's
+agreement with the library, and two gloo ranks whose merged layout (the
+oracle's, on the host) equals the one-rank layout bit for bit."""
 import json
 import os
 import socket
 import subprocess
 import sys
 
-import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
